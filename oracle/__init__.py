@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the windowed FDiRW hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import this
+package.  The product path (``paper_2408_11376_gb300``) never imports it and shares no code with it.
+
+The arithmetic lives in ``fdirw_oracle.c`` (plain C, FP64, no FMA contraction); this module compiles it
+with gcc on first use and marshals numpy arrays.  Section/equation citations refer to the paper
+(Mao, Hu, Li, "A GPU accelerated mixed-precision FDiRW solver"):
+
+* ``face_conductance``  -- Eq. 1 discretised by finite differences (harmonic-mean face rule: a reading;
+  the paper does not state the face rule).
+* ``stable_dt_sub``     -- largest substep keeping every explicit coefficient non-negative.
+* ``source_kernel`` / ``kernels`` -- Sec. 3.1: column s of p is an explicit FD march from a unit point
+  source at s; here on the window of radius R, zero flux at window and domain faces, renormalised to
+  unit mass in FP64.
+* ``superpose``         -- Eq. 8 / Eq. 14: c' = p c.
+* ``full_march``        -- the fine-mesh FD solver of Sec. 4.1 over the whole domain (linearity pin).
+* ``mass``              -- Eq. 7: total mass.
+
+Parity status: every function above is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``
+(closed forms, invariants, brute force).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fdirw_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (OpenMP, -ffp-contract=off). Returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.fo_face_conductance.argtypes = [ctypes.c_int] * 3 + [_D] * 4
+            lib.fo_face_conductance.restype = None
+            lib.fo_max_face_sum.argtypes = [ctypes.c_int] * 3 + [_D] * 3
+            lib.fo_max_face_sum.restype = ctypes.c_double
+            lib.fo_source_kernel.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                                            ctypes.c_int, ctypes.c_int64, _D, _D]
+            lib.fo_source_kernel.restype = ctypes.c_int
+            lib.fo_kernels.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                                      _I64, ctypes.c_int64, _D, _D]
+            lib.fo_kernels.restype = ctypes.c_int
+            lib.fo_superpose.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                                        _D, _D]
+            lib.fo_superpose.restype = ctypes.c_int
+            lib.fo_full_march.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, ctypes.c_int, _D, _D]
+            lib.fo_full_march.restype = ctypes.c_int
+            lib.fo_mass.argtypes = [_D, ctypes.c_int64]
+            lib.fo_mass.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Conductance:
+    """Face conductances of a grid (gx, gy, gz: +x/+y/+z face of each cell)."""
+
+    def __init__(self, shape, D):
+        self.shape = tuple(int(v) for v in shape)
+        nx, ny, nz = self.shape
+        self.D = _f64(D).reshape(-1)
+        if self.D.size != nx * ny * nz:
+            raise ValueError("D has the wrong size")
+        self.gx = np.empty_like(self.D)
+        self.gy = np.empty_like(self.D)
+        self.gz = np.empty_like(self.D)
+        _load().fo_face_conductance(nx, ny, nz, _p(self.D), _p(self.gx), _p(self.gy), _p(self.gz))
+
+    @property
+    def args(self):
+        nx, ny, nz = self.shape
+        return (nx, ny, nz, _p(self.gx), _p(self.gy), _p(self.gz))
+
+
+def face_conductance(shape, D):
+    """(gx, gy, gz) float64 arrays: harmonic-mean conductance of each cell's +x/+y/+z face."""
+    g = Conductance(shape, D)
+    return g.gx, g.gy, g.gz
+
+
+def max_face_sum(shape, D) -> float:
+    g = Conductance(shape, D)
+    return float(_load().fo_max_face_sum(*g.args))
+
+
+def stable_dt_sub(shape, D, h: float = 1.0) -> float:
+    """Largest dt_sub with dt_sub * max_cell(sum of face conductances) / h^2 <= 1."""
+    m = max_face_sum(shape, D)
+    return float("inf") if m == 0.0 else h * h / m
+
+
+def lam_of(dt_macro: float, n_sub: int, h: float = 1.0) -> float:
+    """lam = dt_sub / h^2 with dt_sub = dt_macro / n_sub."""
+    return 0.0 if n_sub == 0 else (dt_macro / n_sub) / (h * h)
+
+
+def source_kernel(shape, D, lam: float, R: int, n_sub: int, s: int, cond: Conductance | None = None):
+    """(kernel, mass_before): kernel is a (2R+1,2R+1,2R+1) array indexed [oz+R, oy+R, ox+R]."""
+    g = cond or Conductance(shape, D)
+    W1 = 2 * R + 1
+    out = np.empty(W1 ** 3, dtype=np.float64)
+    m = ctypes.c_double(0.0)
+    rc = _load().fo_source_kernel(*g.args, float(lam), int(R), int(n_sub), int(s), _p(out), ctypes.byref(m))
+    if rc != 0:
+        raise ValueError("fo_source_kernel rejected its arguments")
+    return out.reshape(W1, W1, W1), m.value
+
+
+def kernels(shape, D, lam: float, R: int, n_sub: int, sources, cond: Conductance | None = None):
+    """(kernels [n, 2R+1, 2R+1, 2R+1], masses_before [n]) for a list of sources (OpenMP over sources)."""
+    g = cond or Conductance(shape, D)
+    src = np.ascontiguousarray(sources, dtype=np.int64).reshape(-1)
+    W1 = 2 * R + 1
+    out = np.empty((src.size, W1, W1, W1), dtype=np.float64)
+    masses = np.empty(src.size, dtype=np.float64)
+    rc = _load().fo_kernels(*g.args, float(lam), int(R), int(n_sub), src.ctypes.data_as(_I64), src.size,
+                            _p(out), _p(masses))
+    if rc != 0:
+        raise ValueError("fo_kernels rejected its arguments")
+    return out, masses
+
+
+def superpose(shape, D, lam: float, R: int, n_sub: int, c, cond: Conductance | None = None) -> np.ndarray:
+    """One macro step c' = p c (Eq. 8) with windowed kernels."""
+    g = cond or Conductance(shape, D)
+    c = _f64(c).reshape(-1)
+    out = np.empty_like(c)
+    if _load().fo_superpose(*g.args, float(lam), int(R), int(n_sub), _p(c), _p(out)) != 0:
+        raise ValueError("fo_superpose failed")
+    return out
+
+
+def full_march(shape, D, lam: float, n_sub: int, c, cond: Conductance | None = None) -> np.ndarray:
+    """Brute-force explicit FD march of the whole field over the full domain."""
+    g = cond or Conductance(shape, D)
+    c = _f64(c).reshape(-1)
+    out = np.empty_like(c)
+    if _load().fo_full_march(*g.args, float(lam), int(n_sub), _p(c), _p(out)) != 0:
+        raise ValueError("fo_full_march failed")
+    return out
+
+
+def mass(c) -> float:
+    """Total mass sum(c) (Eq. 7)."""
+    c = _f64(c).reshape(-1)
+    return float(_load().fo_mass(_p(c), c.size))
+
+
+def set_threads(n: int) -> None:
+    """Sets the OpenMP thread count used by ``kernels`` (via omp_set_num_threads from libgomp)."""
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_set_num_threads(int(n))
+    except OSError:
+        os.environ["OMP_NUM_THREADS"] = str(int(n))
