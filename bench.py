@@ -1,0 +1,332 @@
+"""FDiRW hot-path benchmark on GB300.
+
+One benchmark step is one pass of the whole hot path over one synthetic workload:
+  fdirw_create   -- face conductances and stability check
+  fdirw_kernels  -- per-source windowed FD march + FP64 renormalisation (kernel cache)
+  fdirw_step     -- `macro_steps` superposition steps and the FP64 mass budget
+Metric: macro-steps/s of that job (the kernel build is amortised over the workload's macro steps),
+timed with CUDA events on the stream the library launches on, inputs resident in HBM.  Extra keys give
+source-kernels/s (march kernel alone) and the steady-state macro-steps/s (gather + scale per step).
+
+  python bench.py [--steps K] [--warmup W] [--workload fdirw-192c-r8] [--prec fp32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, bounded samples
+  torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas (one per GPU), weak scaling
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FDiRW macro-steps/sec at 192³ and source-kernels/sec vs plain FP64 GPU at ≤1e-5 rel L2"
+UNIT = "macro-steps/s"
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
+FLOP_PER_CELL_SUBSTEP = 13       # coefficient form of the 7-point update: 1 MUL + 6 FMA
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+
+def oracle_sample(w, D, n_sources: int, seed: int = 7):
+    """Times the FP64 CPU oracle's kernel marches on a seeded sample of sources (all host threads).
+    The oracle recomputes every source's kernel for each superposition step, so one of its macro steps
+    costs N kernel marches; the sample gives seconds per source."""
+    import oracle
+    shape = (w.n,) * 3
+    lam = oracle.stable_dt_sub(shape, D)
+    cond = oracle.Conductance(shape, D)
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, w.n ** 3, n_sources)
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.kernels(shape, D, lam, w.R, w.n_sub, src, cond)
+    dt = time.perf_counter() - t0
+    return dt / n_sources, threads, dt
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    _, D, _ = w.make()
+    N = w.n ** 3
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        t_src, threads, _ = oracle_sample(w, D, args.ref_sample, seed=100 + i)
+        if i >= args.warmup:
+            per_step.append(t_src)
+    t_src = statistics.mean(per_step)
+    value = 1.0 / (N * t_src)
+    sample = (f"{args.ref_sample} seeded random sources of {w.name} per step (FP64 windowed marches); "
+              f"macro-steps/s = 1/(N * seconds per source), the oracle recomputing every kernel each step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * N * t_src, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": f"{w.n}^3", "R": w.R, "n_sub": w.n_sub,
+                       "macro_steps": w.steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- CUDA path
+
+def run_ours(args, w):
+    import torch
+    from paper_2408_11376_gb300 import build as libbuild
+    from paper_2408_11376_gb300 import fdirw
+
+    ws, rank, local = _dist()
+    libbuild.build()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    _, D_host, c_host = w.make()
+    shape = (w.n,) * 3
+    N = w.n ** 3
+    D = torch.from_numpy(D_host).to(dev)
+    c0 = torch.from_numpy(c_host).to(dev)
+    c1 = torch.empty_like(c0)
+    stream = torch.cuda.Stream(device=dev)
+    dt_sub = fdirw.fdirw_stable_dt(shape, D, device=local)
+    dt_macro = w.n_sub * dt_sub
+    prec = args.prec
+
+    def one_pass(times=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream)
+            ev[1].record(stream)
+            fdirw.fdirw_kernels(ctx)
+            ev[2].record(stream)
+            mass = fdirw.fdirw_step(ctx, c0, c1, w.steps, want_mass=True)
+            ev[3].record(stream)
+            info = fdirw.fdirw_get_info(ctx)
+            fdirw.fdirw_destroy(ctx)
+        if times is not None:
+            stream.synchronize()
+            times.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                          ev[0].elapsed_time(ev[3]), info["kernels_ms"], info["last_gather_ms"], mass, info))
+        return mass
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    times = []
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            one_pass(times)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    total_ms = start.elapsed_time(end)
+    if pg:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    info = times[-1][7]
+    mass0 = float(np.sum(c_host))
+    march_ms = statistics.mean(t[4] for t in times)
+    gather_ms = statistics.mean(t[5] for t in times)
+    steps_ms = statistics.mean(t[2] for t in times)
+
+    # e2e through the C ABI with pinned host buffers: H2D of D and c, D2H of c' inside the timed region.
+    e2e = None
+    if not args.no_e2e:
+        Dp = torch.from_numpy(D_host).pin_memory()
+        cp = torch.from_numpy(c_host).pin_memory()
+        op = torch.empty_like(cp).pin_memory()
+
+        def e2e_pass():
+            with torch.cuda.stream(stream):
+                ctx = fdirw.fdirw_create(shape, Dp, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream)
+                fdirw.fdirw_step(ctx, cp, op, w.steps, want_mass=True)
+                fdirw.fdirw_destroy(ctx)
+
+        e2e_pass()
+        torch.cuda.synchronize(dev)
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_pass()
+        ee.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = es.elapsed_time(ee) / args.e2e_steps
+        if pg:
+            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": ws * w.steps * 1000.0 / e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+               "d2h_bytes_per_step": 8 * N + 8}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak_tflops = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = FLOP_PER_CELL_SUBSTEP * w.n_sub * info["window_cells"]
+    achieved = flops / (march_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    roofline = {"bound": "alu", "kernel": "march_f32_kernel<R>" if prec != "fp64" else "march_f64_kernel<R>",
+                "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": args.traffic,
+                "peak_source": f"FP32 pipe: {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz, {peak_src})",
+                "algorithmic": f"{FLOP_PER_CELL_SUBSTEP} flop per cell-substep x n_sub x sum of clipped window cells "
+                               f"({info['window_cells']:.4g})"}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (num_sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        t_src, threads, dt = oracle_sample(w, D_host, args.ref_sample)
+        cpu = {"value": 1.0 / (N * t_src), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.ref_sample} seeded random sources of {w.name} ({dt:.1f} s of FP64 windowed marches "
+                         f"on {threads} host threads); macro-steps/s = 1/(N * seconds per source), the oracle "
+                         "recomputing every kernel each step"}
+
+    n_launch = 4 + 1 + 2 + 2 * w.steps + 2      # conductance + 3 coef, march, mass(in), scale+gather per step, mass(out)
+    value = ws * w.steps * args.steps * 1000.0 / total_ms
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": w.name, "grid": f"{w.n}^3", "R": w.R, "n_sub": w.n_sub, "macro_steps": w.steps,
+                   "prec": prec, "porosity": w.porosity, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 (kernel cache {info['cache_bytes'] / 1e9:.1f} GB, read every step)"},
+        "source_kernels_per_s": N / (march_ms * 1e-3),
+        "steady_macro_steps_per_s": 1000.0 * w.steps / steps_ms,
+        "phase_ms": {"create": statistics.mean(t[0] for t in times), "kernels": statistics.mean(t[1] for t in times),
+                     "march_kernel": march_ms, "steps": steps_ms, "gather_kernel": gather_ms},
+        "mass_rel_err": abs(times[-1][6] - mass0) / mass0,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": n_launch * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="fdirw-192c-r8")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per march launch from an ncu capture of the current kernel")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    from paper_2408_11376_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

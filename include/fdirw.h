@@ -1,0 +1,161 @@
+/*
+ * fdirw.h -- C ABI of the GB300 FDiRW hot path (libfdirw.so).
+ *
+ * FDiRW (Finite Difference informed Random Walker; Mao, Hu & Li, Sec. 3.1) advances a fast diffusion
+ * process over a long macro step dt by superposing precomputed mass proportions:
+ *
+ *     c(t + dt) = p(dt) c(t)                                            (Eq. 8, without the p_BC term)
+ *
+ * where column s of p is obtained by an explicit finite-difference march of the diffusion equation
+ * (Eq. 1, pure-diffusion part) from a unit point source at cell s (Sec. 3.1, text after Eq. 9).
+ * This library computes every column at full grid resolution on a local window: the cube of cells
+ * within L-infinity distance R of the source, clipped to the domain, with zero flux through the window
+ * faces and the domain faces.  The stored columns form a banded operator (the "kernel cache");
+ * one macro step is then a deterministic gather  c'(x) = sum_o K_o(x) * sigma(x-o) * c(x-o).
+ *
+ * Discretisation (readings of points the paper leaves open):
+ *   - grid nx*ny*nz of cubic cells of side h; cell index i = x + nx*(y + ny*z) (x fastest);
+ *   - face conductance between neighbouring cells a, b: harmonic mean 2 D_a D_b / (D_a + D_b)
+ *     (0 if D_a + D_b == 0);
+ *   - substep dt_sub = dt_macro / n_sub, lam = dt_sub / h^2; one substep
+ *     u_i <- u_i + lam * sum_{faces f of i inside window and domain} g_f (u_nb - u_i);
+ *   - explicit stability (all coefficients >= 0): lam * max_i(sum of the face conductances of i) <= 1;
+ *   - each stored column is renormalised to unit total mass in FP64 (sigma, below).
+ *
+ * Conventions of this API:
+ *   - Pointers to fields (D_map, c_in, c_out) may be host or device memory (detected with
+ *     cudaPointerGetAttributes); device pointers must live on the context's device.  Arrays are
+ *     float64, N = nx*ny*nz elements, x fastest, and are owned by the caller.
+ *   - Work is issued on the stream given at creation (NULL = legacy default stream).  A call that
+ *     returns data in host memory (mass_out, a host c_out, fdirw_read_kernels, fdirw_stable_dt)
+ *     synchronises that stream before returning; otherwise calls return as soon as the work is queued.
+ *   - Every int-returning call returns FDIRW_OK (0) or a negative FDIRW_ERR_* code, and then
+ *     fdirw_last_error() describes the failure.  No call aborts the process.
+ *   - A context is not thread-safe: use one context per host thread or serialise calls.
+ */
+#ifndef FDIRW_H
+#define FDIRW_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FDIRW_API __attribute__((visibility("default")))
+#else
+#define FDIRW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDIRW_OK            0
+#define FDIRW_ERR_ARG      -1   /* invalid argument (bad size, NaN/Inf/negative D, bad pointer, ...) */
+#define FDIRW_ERR_UNSTABLE -2   /* lam * max face-conductance sum > 1 (explicit march would not be stable) */
+#define FDIRW_ERR_NOMEM    -3   /* device allocation failed or would exceed opts.mem_limit */
+#define FDIRW_ERR_CUDA     -4   /* a CUDA runtime call failed (message has the CUDA error string) */
+#define FDIRW_ERR_TIMEOUT  -5   /* a bounded device-side wait gave up (reserved; no current kernel waits) */
+#define FDIRW_ERR_STATE    -6   /* call not valid in the context's current state */
+
+/* Arithmetic of the path (Sec. 3.3: lower precision for the stored proportions, higher precision for
+ * accumulation; Table 2 lists the paper's FP64 / FP32 / FP32-FP16 variants). */
+typedef enum {
+    FDIRW_FP64            = 0,  /* FP64 march, FP64 storage, FP64 gather: the plain FP64 path           */
+    FDIRW_FP32            = 1,  /* FP32 march, FP32 storage, FP64 renormalisation, extended accumulation */
+    FDIRW_FP32_STORE_FP16 = 2,  /* FP32 march, FP16 storage of the kernel cache, same renorm/accumulation */
+    FDIRW_FP32_STORE_BF16 = 3   /* FP32 march, BF16 storage of the kernel cache, same renorm/accumulation */
+} fdirw_prec;
+
+typedef struct {
+    int32_t nx, ny, nz;   /* cells per axis, each >= 1 */
+    double  h;            /* cell size, > 0 */
+} fdirw_grid;
+
+typedef struct {
+    int32_t  prec;        /* fdirw_prec */
+    int32_t  device;      /* CUDA device ordinal; -1 = the calling thread's current device */
+    void*    stream;      /* cudaStream_t for all work; NULL = legacy default stream */
+    uint64_t mem_limit;   /* cap on the device bytes this context allocates; 0 = no cap */
+} fdirw_opts;
+
+typedef struct {
+    int64_t  n_cells;        /* N */
+    int32_t  window_R;       /* R */
+    int32_t  n_sub;          /* substeps per macro step */
+    int32_t  prec;           /* fdirw_prec in use */
+    int32_t  kernels_ready;  /* 1 once the kernel cache holds the current kernels */
+    double   dt_sub;         /* dt_macro / n_sub */
+    double   lam;            /* dt_sub / h^2 */
+    double   max_face_sum;   /* max over cells of the sum of its face conductances */
+    uint64_t cache_bytes;    /* bytes of the kernel cache (N * (2R+1)^3 * storage size) */
+    uint64_t device_bytes;   /* all device bytes held by the context */
+    double   window_cells;   /* sum over sources of their clipped window sizes */
+    float    kernels_ms;     /* device time of the last kernel-cache build (march kernel only) */
+    float    last_gather_ms; /* device time of the last gather launch */
+    double   last_mass_in;   /* FP64 total of c_in at the last fdirw_step */
+    double   last_mass_out;  /* FP64 total of c_out after the last fdirw_step (if it was computed) */
+} fdirw_info;
+
+typedef struct fdirw_ctx fdirw_ctx;
+
+/* Largest stable substep for a diffusivity map: h^2 / max_i(sum of face conductances of cell i),
+ * +inf (HUGE_VAL) when every conductance is 0.  D_map: N float64 values (host or device), finite, >= 0.
+ * Synchronises.  Errors: FDIRW_ERR_ARG (bad grid, NULL pointer, NaN/Inf/negative D), FDIRW_ERR_CUDA,
+ * FDIRW_ERR_NOMEM. */
+FDIRW_API int fdirw_stable_dt(const fdirw_grid* grid, const double* D_map, int32_t device, double* dt_sub_max);
+
+/* Create a context for one diffusivity map (Sec. 3.1: p is fixed while the domain is fixed, Sec. 5).
+ *   grid       : grid dimensions and cell size
+ *   D_map      : N cell diffusivities (host or device), finite and >= 0; copied, not retained
+ *   dt_macro   : macro step (>= 0, finite); dt_sub = dt_macro / n_sub
+ *   window_R   : window radius, 0 <= R <= 8 (R = 0 gives the identity operator)
+ *   n_sub      : explicit substeps per macro step, >= 0 (0 gives the identity operator)
+ *   opts       : NULL for defaults (FDIRW_FP32, current device, default stream, no cap)
+ *   out        : receives the context (set to NULL on failure)
+ * Computes the face conductances on the device and checks stability; the kernel cache is built
+ * lazily (fdirw_kernels or the first fdirw_step).  Errors: FDIRW_ERR_ARG, FDIRW_ERR_UNSTABLE,
+ * FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, int32_t window_R,
+                 int32_t n_sub, const fdirw_opts* opts, fdirw_ctx** out);
+
+/* Build (or rebuild) the kernel cache: for every source cell s, march a unit mass over its window for
+ * n_sub substeps (Sec. 3.1), store the result in the storage precision and sigma_s = 1 / (FP64 sum of
+ * the stored values).  Idempotent; asynchronous on the context stream.
+ * Errors: FDIRW_ERR_ARG (NULL ctx), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_kernels(fdirw_ctx* ctx);
+
+/* Advance a field n_steps macro steps with the superposition c' = p c (Eq. 8, Eq. 14):
+ *   c_in, c_out : N float64 values each (host or device); c_in == c_out is allowed (in place)
+ *   n_steps     : >= 0 (0 copies c_in to c_out)
+ *   mass_out    : host pointer or NULL; receives the FP64 total of c_out (Eq. 7), computed on the
+ *                 device with a fixed reduction order
+ * Builds the kernel cache first if needed.  Results are bitwise reproducible for a given context
+ * configuration (no atomics in the gather).  Errors: FDIRW_ERR_ARG, FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_step(fdirw_ctx* ctx, const double* c_in, double* c_out, int32_t n_steps, double* mass_out);
+
+/* FP64 total of a field (host or device, N values) with the library's fixed reduction order.
+ * Synchronises.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_mass(fdirw_ctx* ctx, const double* c, double* mass_out);
+
+/* Copy renormalised kernels out of the cache: for each of n source indices, (2R+1)^3 float64 values on
+ * the offset layout o = x - s (o_x fastest, index (ox+R) + (2R+1)*((oy+R) + (2R+1)*(oz+R))), equal to
+ * stored value * sigma_s, and 0 where x is outside the domain.  sources: host int64 array; out: host
+ * float64 array of n*(2R+1)^3.  Synchronises.  Errors: FDIRW_ERR_ARG (index out of range),
+ * FDIRW_ERR_STATE (cache not built), FDIRW_ERR_CUDA, FDIRW_ERR_NOMEM. */
+FDIRW_API int fdirw_read_kernels(fdirw_ctx* ctx, const int64_t* sources, int64_t n, double* out);
+
+/* Snapshot of the context's configuration and last timings.  Synchronises on the timing events. */
+FDIRW_API int fdirw_get_info(fdirw_ctx* ctx, fdirw_info* out);
+
+/* Release all device memory held by the context.  NULL-safe. */
+FDIRW_API void fdirw_destroy(fdirw_ctx* ctx);
+
+/* Message of the last failed call on ctx, or of the last failed call on this host thread when ctx is
+ * NULL (for failures of fdirw_create / fdirw_stable_dt).  Never NULL; the string stays valid until the
+ * next call on the same context / thread. */
+FDIRW_API const char* fdirw_last_error(const fdirw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDIRW_H */

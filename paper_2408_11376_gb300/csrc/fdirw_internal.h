@@ -1,0 +1,71 @@
+// Internal declarations shared by the CUDA translation units of libfdirw (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fdirw {
+
+// Largest window radius the register-resident march supports (window (2R+1)^3 = 4913 cells at R = 8).
+constexpr int kMaxR = 8;
+
+enum class Store : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+
+inline int store_bytes(Store s) { return s == Store::F64 ? 8 : s == Store::F32 ? 4 : 2; }
+
+struct Grid {
+    int nx, ny, nz;
+    int64_t n;     // nx*ny*nz
+};
+
+// ---------------------------------------------------------------- setup.cu
+// Checks D (finite, >= 0), computes FP64 harmonic-mean face conductances gx/gy/gz (+x/+y/+z face of each
+// cell, 0 across the domain edge), the maximum per-cell face sum (as the bit pattern of a non-negative
+// double, for atomicMax) and the number of invalid D values.  *max_bits and *bad must be zeroed first.
+cudaError_t launch_conductance(const double* D, Grid g, double* gx, double* gy, double* gz,
+                               unsigned long long* max_bits, unsigned long long* bad, cudaStream_t st);
+// coef = lam * g (FP32, one rounding from FP64).
+cudaError_t launch_coef_f32(const double* g, double lam, int64_t n, float* coef, cudaStream_t st);
+// coef = lam * g in place (FP64).
+cudaError_t launch_coef_f64(double* g, double lam, int64_t n, cudaStream_t st);
+
+// ---------------------------------------------------------------- march.cu
+struct MarchArgs {
+    Grid g;
+    int R;
+    int n_sub;
+    const float* ax; const float* ay; const float* az;     // FP32 path: lam*g
+    const double* dx; const double* dy; const double* dz;  // FP64 path: lam*g
+    void* Q;              // kernel cache, (2R+1)^3 planes of N values, destination-indexed
+    Store store;
+    double* sigma;        // N: 1 / FP64 sum of the stored values of each source
+    int64_t src_begin, src_end;
+};
+cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);
+
+// ---------------------------------------------------------------- superpose.cu
+// Padded layout of the scaled field chat = sigma * c: (nx+2R) x (ny+2R) x (nz+2R), zero halo.
+struct Pad {
+    int px, py, pz;
+    int64_t n;
+};
+inline Pad make_pad(const Grid& g, int R) {
+    Pad p{g.nx + 2 * R, g.ny + 2 * R, g.nz + 2 * R, 0};
+    p.n = (int64_t)p.px * p.py * p.pz;
+    return p;
+}
+// chat = sigma * c into the interior of the padded buffer; FP64 (split == false) or as a float2 (hi, lo)
+// pair with hi = fp32(v), lo = fp32(v - hi) (split == true).
+cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, bool split,
+                         cudaStream_t st);
+// c_out(x) = sum_o Q[o][x] * chat(x - o).
+cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
+                          cudaStream_t st);
+// Deterministic FP64 total: partials[kMassBlocks] then one block.  partials must hold kMassBlocks doubles.
+constexpr int kMassBlocks = 1024;
+cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* out, cudaStream_t st);
+// Renormalised kernels of listed sources on the (2R+1)^3 offset layout.
+cudaError_t launch_read_kernels(const void* Q, Store store, const double* sigma, Grid g, int R,
+                                const int64_t* sources, int64_t n_src, double* out, cudaStream_t st);
+
+}  // namespace fdirw

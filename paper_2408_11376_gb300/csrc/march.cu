@@ -1,0 +1,335 @@
+// Per-source windowed explicit FD march (Sec. 3.1: column s of p is the explicit-FD solution from a
+// unit point source at s) and FP64 renormalisation of the stored kernel.
+//
+// Work decomposition (persistent grid, batches of SPB sources per CTA):
+//   - one thread per z-column (ci, cj) of a source's (2R+1)^3 window; the column's 2R+1 cells live in
+//     registers for the whole march;
+//   - the FP32 path also keeps the 6 face coefficients of each cell in registers (they are constant over
+//     the march), so a substep costs 1 MUL + 6 FMA + 1 ADD per cell; the z neighbours are in the same thread and
+//     the x/y neighbours are read from a double-buffered shared-memory copy of every column (one
+//     __syncthreads per substep);
+//   - the FP64 path (the plain FP64 baseline) keeps u and the diagonal in registers and the face
+//     coefficients in shared memory (FP64 registers would not fit), same exchange scheme;
+//   - after the march each thread rounds its cells to the storage type, writes them into the
+//     destination-indexed cache Q[o][s + o] and sums the stored values in FP64; a fixed-order block
+//     reduction gives sigma_s = 1 / sum.
+// Window cells outside the domain carry no coefficients, so they stay 0; faces leaving the window or
+// the domain have coefficient 0 (zero flux).  Bound: FP32 pipe + shared-memory bandwidth (FP32 path),
+// FP64 pipe (FP64 path).  HBM traffic is only the coefficient loads (L2-resident) and the cache writes.
+#include "fdirw_internal.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace fdirw {
+
+namespace {
+
+template <int R>
+struct Shape {
+    static constexpr int W1 = 2 * R + 1;
+    static constexpr int COLS = W1 * W1;
+    static constexpr int W = W1 * W1 * W1;
+    static constexpr int SPB = (512 / COLS) > 0 ? (512 / COLS) : 1;      // sources per CTA (FP32 path)
+    static constexpr int THREADS = ((SPB * COLS + 31) / 32) * 32;
+    // FP64 path: 2 exchange buffers + 3 face arrays of SPB*W doubles must fit in ~200 KB.
+    static constexpr int SPB64_CAP = 200000 / (5 * W * 8);
+    static constexpr int SPB64 = SPB64_CAP < 1 ? 1 : (SPB64_CAP < SPB ? SPB64_CAP : SPB);
+    static constexpr int THREADS64 = ((SPB64 * COLS + 31) / 32) * 32;
+};
+
+// Rounds v to the storage type, writes it to Q[idx] and returns the stored value widened to double.
+__device__ __forceinline__ double put(void* Q, Store st, int64_t idx, float v) {
+    if (st == Store::F32) {
+        reinterpret_cast<float*>(Q)[idx] = v;
+        return (double)v;
+    } else if (st == Store::F16) {
+        const __half h = __float2half_rn(v);
+        reinterpret_cast<__half*>(Q)[idx] = h;
+        return (double)__half2float(h);
+    } else {
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        reinterpret_cast<__nv_bfloat16*>(Q)[idx] = b;
+        return (double)__bfloat162float(b);
+    }
+}
+
+// sigma_s = 1 / (sum of the per-column FP64 partials of slot) for every slot of the batch, fixed order:
+// warp w takes slots w, w + nwarps, ...; lane l sums columns l, l + 32, ...; then a xor-butterfly.
+template <int COLS, int SPB>
+__device__ __forceinline__ void finish_sigma(const double* red, int64_t batch_first, int64_t src_end,
+                                             double* sigma) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int slot = warp; slot < SPB; slot += nwarps) {
+        double acc = 0.0;
+        for (int c = lane; c < COLS; c += 32) acc += red[slot * COLS + c];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        const int64_t s = batch_first + slot;
+        if (lane == 0 && s < src_end) sigma[s] = acc > 0.0 ? 1.0 / acc : 0.0;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(Shape<R>::THREADS, 1) march_f32_kernel(MarchArgs a) {
+    using S = Shape<R>;
+    constexpr int W1 = S::W1, COLS = S::COLS, SPB = S::SPB;
+    constexpr int BUF = SPB * COLS * W1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* xbuf = reinterpret_cast<float*>(smem_raw);                                  // [2][SPB*COLS][W1]
+    double* red = reinterpret_cast<double*>(smem_raw + ((2 * BUF * 4 + 15) / 16) * 16);  // [SPB*COLS]
+
+    const int t = threadIdx.x;
+    const bool active = t < SPB * COLS;
+    const int slot = active ? t / COLS : 0;
+    const int col = active ? t - slot * COLS : 0;
+    const int ci = col % W1, cj = col / W1;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
+
+    const int base = (slot * COLS + col) * W1;
+    const int xm = ci > 0 ? base - W1 : base;
+    const int xp = ci < 2 * R ? base + W1 : base;
+    const int ym = cj > 0 ? base - W1 * W1 : base;
+    const int yp = cj < 2 * R ? base + W1 * W1 : base;
+
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        const int64_t first = a.src_begin + b * SPB;
+        const int64_t s = first + slot;
+        const bool src_ok = active && s < a.src_end;
+        int sx = 0, sy = 0, sz = 0;
+        if (src_ok) {
+            sx = (int)(s % nx);
+            const int64_t r = s / nx;
+            sy = (int)(r % ny);
+            sz = (int)(r / ny);
+        }
+        const int x = sx - R + ci, y = sy - R + cj;
+        const bool col_ok = src_ok && x >= 0 && x < nx && y >= 0 && y < ny;
+
+        // am = -(sum of the cell's face coefficients): the update is u += am*u + sum c*u_nb, i.e. the
+        // increment is formed at full FP32 relative precision before it is added (1 - sum c rounded
+        // once would bias near-delta kernels by half an ulp of 1 every substep).
+        float u[W1], am[W1], cxm[W1], cxp[W1], cym[W1], cyp[W1], cz[W1];
+#pragma unroll
+        for (int k = 0; k < W1; k++) {
+            const int z = sz - R + k;
+            const bool ok = col_ok && z >= 0 && z < nz;
+            float vxm = 0.f, vxp = 0.f, vym = 0.f, vyp = 0.f, vz = 0.f;
+            if (ok) {
+                const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                if (ci > 0 && x > 0) vxm = __ldg(a.ax + i - 1);
+                if (ci < 2 * R && x + 1 < nx) vxp = __ldg(a.ax + i);
+                if (cj > 0 && y > 0) vym = __ldg(a.ay + i - nx);
+                if (cj < 2 * R && y + 1 < ny) vyp = __ldg(a.ay + i);
+                if (k < 2 * R && z + 1 < nz) vz = __ldg(a.az + i);
+            }
+            cxm[k] = vxm; cxp[k] = vxp; cym[k] = vym; cyp[k] = vyp; cz[k] = vz;
+            u[k] = (src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < W1; k++) {
+            const float zm = k > 0 ? cz[k - 1] : 0.f;
+            am[k] = -(((cxm[k] + cxp[k]) + (cym[k] + cyp[k])) + (zm + cz[k]));
+        }
+
+        for (int it = 0; it < a.n_sub; it++) {
+            float* buf = xbuf + (it & 1) * BUF;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < W1; k++) buf[base + k] = u[k];
+            }
+            __syncthreads();
+            float prev = 0.f;
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                const float cur = u[k];
+                float v = am[k] * cur;
+                v = fmaf(cxm[k], buf[xm + k], v);
+                v = fmaf(cxp[k], buf[xp + k], v);
+                v = fmaf(cym[k], buf[ym + k], v);
+                v = fmaf(cyp[k], buf[yp + k], v);
+                if (k > 0) v = fmaf(cz[k - 1], prev, v);
+                if (k + 1 < W1) v = fmaf(cz[k], u[k + 1], v);
+                prev = cur;
+                u[k] = __fadd_rn(cur, v);
+            }
+        }
+
+        // Epilogue: round to storage, write Q[o][x] (x = s + o, the cell itself), FP64 column sum.
+        double colsum = 0.0;
+        if (col_ok) {
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                const int z = sz - R + k;
+                if (z >= 0 && z < nz) {
+                    const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                    const int64_t o = ci + W1 * (cj + W1 * k);
+                    colsum += put(a.Q, a.store, o * a.g.n + i, u[k]);
+                }
+            }
+        }
+        if (active) red[t] = colsum;
+        __syncthreads();
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
+        __syncthreads();   // red and xbuf are reused by the next batch
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(MarchArgs a) {
+    using S = Shape<R>;
+    constexpr int W1 = S::W1, COLS = S::COLS, SPB = S::SPB64;
+    constexpr int BUF = SPB * COLS * W1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* xbuf = reinterpret_cast<double*>(smem_raw);   // [2][BUF]
+    double* fx = xbuf + 2 * BUF;                           // +x face coefficient of each window cell
+    double* fy = fx + BUF;                                 // +y
+    double* fz = fy + BUF;                                 // +z
+    double* red = fz + BUF;                                // [SPB*COLS]
+
+    const int t = threadIdx.x;
+    const bool active = t < SPB * COLS;
+    const int slot = active ? t / COLS : 0;
+    const int col = active ? t - slot * COLS : 0;
+    const int ci = col % W1, cj = col / W1;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
+
+    const int base = (slot * COLS + col) * W1;
+    const int xm = ci > 0 ? base - W1 : base;
+    const int xp = ci < 2 * R ? base + W1 : base;
+    const int ym = cj > 0 ? base - W1 * W1 : base;
+    const int yp = cj < 2 * R ? base + W1 * W1 : base;
+
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        const int64_t first = a.src_begin + b * SPB;
+        const int64_t s = first + slot;
+        const bool src_ok = active && s < a.src_end;
+        int sx = 0, sy = 0, sz = 0;
+        if (src_ok) {
+            sx = (int)(s % nx);
+            const int64_t r = s / nx;
+            sy = (int)(r % ny);
+            sz = (int)(r / ny);
+        }
+        const int x = sx - R + ci, y = sy - R + cj;
+        const bool col_ok = src_ok && x >= 0 && x < nx && y >= 0 && y < ny;
+
+        double u[W1];
+#pragma unroll
+        for (int k = 0; k < W1; k++) {
+            const int z = sz - R + k;
+            const bool ok = col_ok && z >= 0 && z < nz;
+            double vxp = 0.0, vyp = 0.0, vz = 0.0;
+            if (ok) {
+                const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                if (ci < 2 * R && x + 1 < nx) vxp = __ldg(a.dx + i);
+                if (cj < 2 * R && y + 1 < ny) vyp = __ldg(a.dy + i);
+                if (k < 2 * R && z + 1 < nz) vz = __ldg(a.dz + i);
+            }
+            if (active) { fx[base + k] = vxp; fy[base + k] = vyp; fz[base + k] = vz; }
+            u[k] = (src_ok && ci == R && cj == R && k == R) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        double a0[W1];
+#pragma unroll
+        for (int k = 0; k < W1; k++) {
+            const double vxm = ci > 0 ? fx[xm + k] : 0.0;
+            const double vym = cj > 0 ? fy[ym + k] : 0.0;
+            const double vzm = k > 0 ? fz[base + k - 1] : 0.0;
+            a0[k] = 1.0 - (((vxm + fx[base + k]) + (vym + fy[base + k])) + (vzm + fz[base + k]));
+        }
+
+        for (int it = 0; it < a.n_sub; it++) {
+            double* buf = xbuf + (it & 1) * BUF;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < W1; k++) buf[base + k] = u[k];
+            }
+            __syncthreads();
+            double prev = 0.0;
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                const double cur = u[k];
+                double v = a0[k] * cur;
+                if (ci > 0) v = fma(fx[xm + k], buf[xm + k], v);
+                v = fma(fx[base + k], buf[xp + k], v);
+                if (cj > 0) v = fma(fy[ym + k], buf[ym + k], v);
+                v = fma(fy[base + k], buf[yp + k], v);
+                if (k > 0) v = fma(fz[base + k - 1], prev, v);
+                if (k + 1 < W1) v = fma(fz[base + k], u[k + 1], v);
+                prev = cur;
+                u[k] = v;
+            }
+        }
+
+        double colsum = 0.0;
+        if (col_ok) {
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                const int z = sz - R + k;
+                if (z >= 0 && z < nz) {
+                    const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                    const int64_t o = ci + W1 * (cj + W1 * k);
+                    reinterpret_cast<double*>(a.Q)[o * a.g.n + i] = u[k];
+                    colsum += u[k];
+                }
+            }
+        }
+        if (active) red[t] = colsum;
+        __syncthreads();
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
+        __syncthreads();
+    }
+}
+
+template <int R>
+cudaError_t launch_r(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    using S = Shape<R>;
+    const int64_t nsrc = a.src_end - a.src_begin;
+    if (nsrc <= 0) return cudaSuccess;
+    if (a.store == Store::F64) {
+        const size_t smem = (size_t)(5 * S::SPB64 * S::W + S::SPB64 * S::COLS) * 8;
+        cudaError_t e = cudaFuncSetAttribute(march_f64_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_f64_kernel<R>, S::THREADS64, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const int64_t nbatch = (nsrc + S::SPB64 - 1) / S::SPB64;
+        const int64_t grid = nbatch < (int64_t)num_sms * per_sm ? nbatch : (int64_t)num_sms * per_sm;
+        march_f64_kernel<R><<<(unsigned)grid, S::THREADS64, smem, st>>>(a);
+    } else {
+        const size_t smem = (size_t)((2 * S::SPB * S::W * 4 + 15) / 16) * 16 + (size_t)S::SPB * S::COLS * 8;
+        cudaError_t e = cudaFuncSetAttribute(march_f32_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_f32_kernel<R>, S::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const int64_t nbatch = (nsrc + S::SPB - 1) / S::SPB;
+        const int64_t grid = nbatch < (int64_t)num_sms * per_sm ? nbatch : (int64_t)num_sms * per_sm;
+        march_f32_kernel<R><<<(unsigned)grid, S::THREADS, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    switch (a.R) {
+        case 1: return launch_r<1>(a, num_sms, st);
+        case 2: return launch_r<2>(a, num_sms, st);
+        case 3: return launch_r<3>(a, num_sms, st);
+        case 4: return launch_r<4>(a, num_sms, st);
+        case 5: return launch_r<5>(a, num_sms, st);
+        case 6: return launch_r<6>(a, num_sms, st);
+        case 7: return launch_r<7>(a, num_sms, st);
+        case 8: return launch_r<8>(a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fdirw

@@ -1,0 +1,393 @@
+// One FDiRW macro step as a deterministic gather (Eq. 8 / Eq. 14 with a banded p):
+//
+//     chat(s)  = sigma_s * c(s)                                   (FP64 renormalisation, Sec. 3.3)
+//     c'(x)    = sum_o Q[o][x] * chat(x - o),  o in [-R, R]^3 in a fixed order
+//
+// Q is destination-indexed (Q[o][x] = stored kernel of source x - o at offset o), so a thread that owns
+// VX consecutive destinations reads VX consecutive values of each plane: 16-byte aligned vector loads,
+// coalesced across the warp, every cache value read exactly once per step.  chat is stored with a zero
+// halo of R cells on every side, so x - o never leaves the buffer and no bounds test is needed.
+//
+// Accumulation (Sec. 3.3: multiply in the storage precision, accumulate in higher precision):
+//   - FP64 storage: FP64 FMA.
+//   - FP32/FP16/BF16 storage: GB300 issues FP64 FMAs at 1/73 of the FP32 rate (measured), so the sum is
+//     kept as an unevaluated pair of FP32 values (s, c) -- error-free product (FMA residual) and
+//     error-free addition (Knuth TwoSum) -- with chat split into hi = fp32(v), lo = fp32(v - hi).  The pair
+//     carries ~48 significant bits; it is converted to FP64 once per destination.
+// The work per step is HBM-bound in the cache read (N * (2R+1)^3 * storage bytes).
+#include "fdirw_internal.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace fdirw {
+
+namespace {
+
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// s + c += q * (hi + lo), all error-free except the q*lo product and the final c update (both ~2^-48
+// relative to the running total).  Written with _rn intrinsics so that no step is contracted into an FMA.
+__device__ __forceinline__ void ff_madd(float& s, float& c, float q, float2 ch) {
+    const float p = __fmul_rn(q, ch.x);
+    const float e = __fmaf_rn(q, ch.y, __fmaf_rn(q, ch.x, -p));   // residual of p, plus q*lo
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+template <typename T, int VX>
+struct Vec;
+template <> struct Vec<double, 2> { using type = double2; };
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<__half, 8> { using type = uint4; };
+template <> struct Vec<__nv_bfloat16, 8> { using type = uint4; };
+
+// Loads VX consecutive stored values (16 bytes) and widens them to float.
+template <typename ST, int VX>
+__device__ __forceinline__ void load_q(const ST* p, float (&q)[VX]) {
+    using V = typename Vec<ST, VX>::type;
+    const V v = __ldcs(reinterpret_cast<const V*>(p));     // streamed: read once per step
+    const ST* e = reinterpret_cast<const ST*>(&v);
+#pragma unroll
+    for (int j = 0; j < VX; j++) q[j] = widen(e[j]);
+}
+
+// Mixed path: ST in {float, half, bf16}, VX = 16 / sizeof(ST), chat as float2 (hi, lo).
+template <typename ST, int R>
+__global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q, const float2* __restrict__ chat,
+                                                        Grid g, Pad p, double* __restrict__ out) {
+    constexpr int VX = 16 / sizeof(ST);
+    constexpr int W1 = 2 * R + 1;
+    constexpr int NC = VX + 2 * R;
+    const int nxv = g.nx / VX;
+    const int64_t nthreads = (int64_t)nxv * g.ny * g.nz;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= nthreads) return;
+    const int xv = (int)(tid % nxv);
+    const int64_t r = tid / nxv;
+    const int y = (int)(r % g.ny);
+    const int z = (int)(r / g.ny);
+    const int x0 = xv * VX;
+    const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
+
+    float s[VX], c[VX];
+#pragma unroll
+    for (int j = 0; j < VX; j++) { s[j] = 0.f; c[j] = 0.f; }
+
+    for (int oz = -R; oz <= R; oz++) {
+        for (int oy = -R; oy <= R; oy++) {
+            // chat row of the sources x - o for ox in [-R, R]: padded x in [x0, x0 + VX + 2R).
+            const float2* row = chat + ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + x0;
+            float2 ch[NC];
+#pragma unroll
+            for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
+            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+#pragma unroll
+            for (int ox = -R; ox <= R; ox++) {
+                float q[VX];
+                load_q<ST, VX>(qrow + (int64_t)(ox + R) * g.n, q);
+#pragma unroll
+                for (int j = 0; j < VX; j++) ff_madd(s[j], c[j], q[j], ch[j - ox + R]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < VX; j++) out[i0 + j] = (double)s[j] + (double)c[j];
+}
+
+// FP64 path: FP64 storage, FP64 chat, FP64 FMA accumulation, VX = 2.
+template <int R>
+__global__ void __launch_bounds__(256) gather_f64_kernel(const double* __restrict__ Q, const double* __restrict__ chat,
+                                                         Grid g, Pad p, double* __restrict__ out) {
+    constexpr int VX = 2;
+    constexpr int W1 = 2 * R + 1;
+    constexpr int NC = VX + 2 * R;
+    const int nxv = g.nx / VX;
+    const int64_t nthreads = (int64_t)nxv * g.ny * g.nz;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= nthreads) return;
+    const int xv = (int)(tid % nxv);
+    const int64_t r = tid / nxv;
+    const int y = (int)(r % g.ny);
+    const int z = (int)(r / g.ny);
+    const int x0 = xv * VX;
+    const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int oz = -R; oz <= R; oz++) {
+        for (int oy = -R; oy <= R; oy++) {
+            const double* row = chat + ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + x0;
+            double ch[NC];
+#pragma unroll
+            for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
+            const double* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+#pragma unroll
+            for (int ox = -R; ox <= R; ox++) {
+                const double2 q = __ldcs(reinterpret_cast<const double2*>(qrow + (int64_t)(ox + R) * g.n));
+                acc0 = fma(q.x, ch[0 - ox + R], acc0);
+                acc1 = fma(q.y, ch[1 - ox + R], acc1);
+            }
+        }
+    }
+    out[i0] = acc0;
+    out[i0 + 1] = acc1;
+}
+
+// Any nx (no vector alignment): one destination per thread, runtime R, same arithmetic as above.
+template <typename ST, bool FF>
+__global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict__ Q, const void* __restrict__ chat,
+                                                            Grid g, Pad p, int R, double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int x = (int)(i % g.nx);
+    const int64_t r = i / g.nx;
+    const int y = (int)(r % g.ny);
+    const int z = (int)(r / g.ny);
+    const int W1 = 2 * R + 1;
+    float s = 0.f, c = 0.f;
+    double acc = 0.0;
+    int o = 0;
+    for (int oz = -R; oz <= R; oz++)
+        for (int oy = -R; oy <= R; oy++)
+            for (int ox = -R; ox <= R; ox++, o++) {
+                const int64_t pi = ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + (x - ox + R);
+                const ST qv = Q[(int64_t)o * g.n + i];
+                if constexpr (FF) {
+                    ff_madd(s, c, widen(qv), reinterpret_cast<const float2*>(chat)[pi]);
+                } else {
+                    acc = fma((double)qv, reinterpret_cast<const double*>(chat)[pi], acc);
+                }
+            }
+    (void)W1;
+    out[i] = FF ? (double)s + (double)c : acc;
+}
+
+__global__ void scale_kernel(const double* __restrict__ c, const double* __restrict__ sigma, Grid g, int R, Pad p,
+                             void* __restrict__ chat, bool split) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx);
+        const int64_t r = i / g.nx;
+        const int y = (int)(r % g.ny);
+        const int z = (int)(r / g.ny);
+        const int64_t pi = ((int64_t)(z + R) * p.py + (y + R)) * p.px + (x + R);
+        const double v = sigma[i] * c[i];
+        if (split) {
+            const float hi = (float)v;
+            const float lo = (float)(v - (double)hi);
+            reinterpret_cast<float2*>(chat)[pi] = make_float2(hi, lo);
+        } else {
+            reinterpret_cast<double*>(chat)[pi] = v;
+        }
+    }
+}
+
+// Fixed-order FP64 reduction, pass 1: block b sums the contiguous chunk b (thread-strided, then a tree).
+__global__ void __launch_bounds__(256) mass_partial_kernel(const double* __restrict__ c, int64_t n,
+                                                           double* __restrict__ partials) {
+    __shared__ double sh[8];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = lo + chunk < n ? lo + chunk : n;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += c[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+// Pass 2: one block of kMassBlocks threads sums the partials.
+__global__ void __launch_bounds__(kMassBlocks) mass_final_kernel(const double* __restrict__ partials,
+                                                                 double* __restrict__ out) {
+    __shared__ double sh[kMassBlocks / 32];
+    double v = partials[threadIdx.x];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = sh[threadIdx.x];
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0) *out = w;
+    }
+}
+
+template <typename ST>
+__global__ void read_kernels_kernel(const ST* __restrict__ Q, const double* __restrict__ sigma, Grid g, int R,
+                                    const int64_t* __restrict__ sources, int64_t n_src, double* __restrict__ out) {
+    const int W1 = 2 * R + 1;
+    const int64_t W = (int64_t)W1 * W1 * W1;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_src * W; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / W;
+        const int o = (int)(t % W);
+        const int64_t s = sources[q];
+        const int ox = o % W1 - R, oy = (o / W1) % W1 - R, oz = o / (W1 * W1) - R;
+        const int sx = (int)(s % g.nx);
+        const int64_t r = s / g.nx;
+        const int sy = (int)(r % g.ny), sz = (int)(r / g.ny);
+        const int x = sx + ox, y = sy + oy, z = sz + oz;
+        double v = 0.0;
+        if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+            const int64_t i = (int64_t)x + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
+            v = (double)widen(Q[(int64_t)o * g.n + i]) * sigma[s];
+        }
+        out[t] = v;
+    }
+}
+template <>
+__global__ void read_kernels_kernel<double>(const double* __restrict__ Q, const double* __restrict__ sigma, Grid g,
+                                            int R, const int64_t* __restrict__ sources, int64_t n_src,
+                                            double* __restrict__ out) {
+    const int W1 = 2 * R + 1;
+    const int64_t W = (int64_t)W1 * W1 * W1;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_src * W; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / W;
+        const int o = (int)(t % W);
+        const int64_t s = sources[q];
+        const int ox = o % W1 - R, oy = (o / W1) % W1 - R, oz = o / (W1 * W1) - R;
+        const int sx = (int)(s % g.nx);
+        const int64_t r = s / g.nx;
+        const int sy = (int)(r % g.ny), sz = (int)(r / g.ny);
+        const int x = sx + ox, y = sy + oy, z = sz + oz;
+        double v = 0.0;
+        if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+            const int64_t i = (int64_t)x + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
+            v = Q[(int64_t)o * g.n + i] * sigma[s];
+        }
+        out[t] = v;
+    }
+}
+
+int blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename ST, int R>
+cudaError_t gather_ff_r(const void* Q, const void* chat, Grid g, Pad p, double* out, cudaStream_t st) {
+    constexpr int VX = 16 / sizeof(ST);
+    const int64_t nt = (int64_t)(g.nx / VX) * g.ny * g.nz;
+    gather_ff_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q),
+                                                                   reinterpret_cast<const float2*>(chat), g, p, out);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t gather_ff(const void* Q, const void* chat, Grid g, int R, Pad p, double* out, cudaStream_t st) {
+    switch (R) {
+        case 1: return gather_ff_r<ST, 1>(Q, chat, g, p, out, st);
+        case 2: return gather_ff_r<ST, 2>(Q, chat, g, p, out, st);
+        case 3: return gather_ff_r<ST, 3>(Q, chat, g, p, out, st);
+        case 4: return gather_ff_r<ST, 4>(Q, chat, g, p, out, st);
+        case 5: return gather_ff_r<ST, 5>(Q, chat, g, p, out, st);
+        case 6: return gather_ff_r<ST, 6>(Q, chat, g, p, out, st);
+        case 7: return gather_ff_r<ST, 7>(Q, chat, g, p, out, st);
+        case 8: return gather_ff_r<ST, 8>(Q, chat, g, p, out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+cudaError_t gather_f64_r(const void* Q, const void* chat, Grid g, Pad p, double* out, cudaStream_t st) {
+    const int64_t nt = (int64_t)(g.nx / 2) * g.ny * g.nz;
+    gather_f64_kernel<R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const double*>(Q),
+                                                               reinterpret_cast<const double*>(chat), g, p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_f64(const void* Q, const void* chat, Grid g, int R, Pad p, double* out, cudaStream_t st) {
+    switch (R) {
+        case 1: return gather_f64_r<1>(Q, chat, g, p, out, st);
+        case 2: return gather_f64_r<2>(Q, chat, g, p, out, st);
+        case 3: return gather_f64_r<3>(Q, chat, g, p, out, st);
+        case 4: return gather_f64_r<4>(Q, chat, g, p, out, st);
+        case 5: return gather_f64_r<5>(Q, chat, g, p, out, st);
+        case 6: return gather_f64_r<6>(Q, chat, g, p, out, st);
+        case 7: return gather_f64_r<7>(Q, chat, g, p, out, st);
+        case 8: return gather_f64_r<8>(Q, chat, g, p, out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, bool split,
+                         cudaStream_t st) {
+    const Pad p = make_pad(g, R);
+    int b = blocks_for(g.n, 256);
+    if (b > 152 * 16) b = 152 * 16;
+    scale_kernel<<<b, 256, 0, st>>>(c, sigma, g, R, p, chat, split);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
+                          cudaStream_t st) {
+    const Pad p = make_pad(g, R);
+    const int vx = 16 / store_bytes(store);
+    if (R >= 1 && R <= kMaxR && g.nx % vx == 0) {
+        switch (store) {
+            case Store::F64: return gather_f64(Q, chat, g, R, p, c_out, st);
+            case Store::F32: return gather_ff<float>(Q, chat, g, R, p, c_out, st);
+            case Store::F16: return gather_ff<__half>(Q, chat, g, R, p, c_out, st);
+            case Store::BF16: return gather_ff<__nv_bfloat16>(Q, chat, g, R, p, c_out, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+    const int b = blocks_for(g.n, 256);
+    switch (store) {
+        case Store::F64:
+            gather_scalar_kernel<double, false><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), chat, g, p, R, c_out);
+            break;
+        case Store::F32:
+            gather_scalar_kernel<float, true><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), chat, g, p, R, c_out);
+            break;
+        case Store::F16:
+            gather_scalar_kernel<__half, true><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), chat, g, p, R, c_out);
+            break;
+        case Store::BF16:
+            gather_scalar_kernel<__nv_bfloat16, true><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), chat,
+                                                                        g, p, R, c_out);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* out, cudaStream_t st) {
+    mass_partial_kernel<<<kMassBlocks, 256, 0, st>>>(c, n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mass_final_kernel<<<1, kMassBlocks, 0, st>>>(partials, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_kernels(const void* Q, Store store, const double* sigma, Grid g, int R,
+                                const int64_t* sources, int64_t n_src, double* out, cudaStream_t st) {
+    const int64_t W = (int64_t)(2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+    int b = blocks_for(n_src * W, 256);
+    if (b > 152 * 16) b = 152 * 16;
+    switch (store) {
+        case Store::F64:
+            read_kernels_kernel<double><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), sigma, g, R, sources, n_src, out);
+            break;
+        case Store::F32:
+            read_kernels_kernel<float><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), sigma, g, R, sources, n_src, out);
+            break;
+        case Store::F16:
+            read_kernels_kernel<__half><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), sigma, g, R, sources, n_src, out);
+            break;
+        case Store::BF16:
+            read_kernels_kernel<__nv_bfloat16><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), sigma, g, R,
+                                                                   sources, n_src, out);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fdirw

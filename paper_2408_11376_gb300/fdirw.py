@@ -1,0 +1,249 @@
+"""ctypes binding of libfdirw (the C ABI declared in include/fdirw.h): argument marshalling only.
+
+Every step of the FDiRW hot path runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing or cannot be loaded, importing this module's functions raises.
+
+Fields may be numpy arrays (host memory) or torch tensors (host or CUDA); both are passed to the library
+as raw pointers and must be contiguous float64 with N = nx*ny*nz elements, x fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+FDIRW_OK = 0
+FDIRW_ERR_ARG = -1
+FDIRW_ERR_UNSTABLE = -2
+FDIRW_ERR_NOMEM = -3
+FDIRW_ERR_CUDA = -4
+FDIRW_ERR_TIMEOUT = -5
+FDIRW_ERR_STATE = -6
+
+FDIRW_FP64 = 0
+FDIRW_FP32 = 1
+FDIRW_FP32_STORE_FP16 = 2
+FDIRW_FP32_STORE_BF16 = 3
+PRECISIONS = {"fp64": FDIRW_FP64, "fp32": FDIRW_FP32, "fp16": FDIRW_FP32_STORE_FP16, "bf16": FDIRW_FP32_STORE_BF16}
+
+EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "fdirw_mass", "fdirw_read_kernels",
+            "fdirw_get_info", "fdirw_destroy", "fdirw_last_error")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfdirw.so")
+
+
+class FdirwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fdirw error {code}: {msg}")
+        self.code = code
+
+
+class fdirw_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("h", ctypes.c_double)]
+
+
+class fdirw_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("mem_limit", ctypes.c_uint64)]
+
+
+class fdirw_info(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("window_R", ctypes.c_int32), ("n_sub", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("kernels_ready", ctypes.c_int32), ("dt_sub", ctypes.c_double),
+                ("lam", ctypes.c_double), ("max_face_sum", ctypes.c_double), ("cache_bytes", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("window_cells", ctypes.c_double),
+                ("kernels_ms", ctypes.c_float), ("last_gather_ms", ctypes.c_float),
+                ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Loads libfdirw.so (built by ``paper_2408_11376_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"libfdirw.so not found at {p}: run paper_2408_11376_gb300.build.build() "
+                              "(the CUDA path has no fallback)")
+        lib = ctypes.CDLL(p)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.fdirw_stable_dt.argtypes = [ctypes.POINTER(fdirw_grid), vp, i32, dp]
+        lib.fdirw_create.argtypes = [ctypes.POINTER(fdirw_grid), vp, ctypes.c_double, i32, i32,
+                                     ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
+        lib.fdirw_kernels.argtypes = [vp]
+        lib.fdirw_step.argtypes = [vp, vp, vp, i32, dp]
+        lib.fdirw_mass.argtypes = [vp, vp, dp]
+        lib.fdirw_read_kernels.argtypes = [vp, vp, i64, vp]
+        lib.fdirw_get_info.argtypes = [vp, ctypes.POINTER(fdirw_info)]
+        lib.fdirw_destroy.argtypes = [vp]
+        lib.fdirw_destroy.restype = None
+        lib.fdirw_last_error.argtypes = [vp]
+        lib.fdirw_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("fdirw_destroy", "fdirw_last_error"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != FDIRW_OK:
+        msg = load().fdirw_last_error(ctx)
+        raise FdirwError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a) -> int:
+    """Raw data pointer of a contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)!r}")
+
+
+def _check_f64(a, n: int):
+    dt = getattr(a, "dtype", None)
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == np.float64
+    else:
+        ok = str(dt) == "torch.float64"
+    if not ok:
+        raise TypeError("fields must be float64")
+    size = a.size if isinstance(a, np.ndarray) else a.numel()
+    if size != n:
+        raise ValueError(f"field has {size} elements, expected {n}")
+
+
+# --------------------------------------------------------------------------- C-ABI mirrors
+
+def fdirw_stable_dt(shape, D, h: float = 1.0, device: int = -1) -> float:
+    lib = load()
+    nx, ny, nz = (int(v) for v in shape)
+    _check_f64(D, nx * ny * nz)
+    g = fdirw_grid(nx, ny, nz, float(h))
+    out = ctypes.c_double(0.0)
+    _check(lib.fdirw_stable_dt(ctypes.byref(g), ctypes.c_void_p(_ptr(D)), int(device), ctypes.byref(out)))
+    return out.value
+
+
+def fdirw_create(shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp32", h: float = 1.0,
+                 device: int = -1, stream=None, mem_limit: int = 0) -> int:
+    """Returns the context handle (an integer address); release it with fdirw_destroy."""
+    lib = load()
+    nx, ny, nz = (int(v) for v in shape)
+    _check_f64(D, nx * ny * nz)
+    g = fdirw_grid(nx, ny, nz, float(h))
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit))
+    ctx = ctypes.c_void_p(0)
+    _check(lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(_ptr(D)), float(dt_macro), int(window_R), int(n_sub),
+                            ctypes.byref(o), ctypes.byref(ctx)))
+    return ctx.value
+
+
+def fdirw_kernels(ctx: int) -> None:
+    _check(load().fdirw_kernels(ctypes.c_void_p(ctx)), ctypes.c_void_p(ctx))
+
+
+def fdirw_step(ctx: int, c_in, c_out, n_steps: int = 1, want_mass: bool = False):
+    """Advances c_in by n_steps macro steps into c_out; returns the FP64 total of c_out if want_mass."""
+    m = ctypes.c_double(0.0)
+    _check(load().fdirw_step(ctypes.c_void_p(ctx), ctypes.c_void_p(_ptr(c_in)), ctypes.c_void_p(_ptr(c_out)),
+                             int(n_steps), ctypes.byref(m) if want_mass else None), ctypes.c_void_p(ctx))
+    return m.value if want_mass else None
+
+
+def fdirw_mass(ctx: int, c) -> float:
+    m = ctypes.c_double(0.0)
+    _check(load().fdirw_mass(ctypes.c_void_p(ctx), ctypes.c_void_p(_ptr(c)), ctypes.byref(m)), ctypes.c_void_p(ctx))
+    return m.value
+
+
+def fdirw_read_kernels(ctx: int, sources, R: int) -> np.ndarray:
+    """Renormalised kernels of the given sources, shape [n, 2R+1, 2R+1, 2R+1] indexed [oz+R, oy+R, ox+R]."""
+    src = np.ascontiguousarray(sources, dtype=np.int64).reshape(-1)
+    W1 = 2 * int(R) + 1
+    out = np.empty((src.size, W1, W1, W1), dtype=np.float64)
+    _check(load().fdirw_read_kernels(ctypes.c_void_p(ctx), ctypes.c_void_p(src.ctypes.data), src.size,
+                                     ctypes.c_void_p(out.ctypes.data)), ctypes.c_void_p(ctx))
+    return out
+
+
+def fdirw_get_info(ctx: int) -> dict:
+    info = fdirw_info()
+    _check(load().fdirw_get_info(ctypes.c_void_p(ctx), ctypes.byref(info)), ctypes.c_void_p(ctx))
+    return info.as_dict()
+
+
+def fdirw_destroy(ctx: int) -> None:
+    if ctx:
+        load().fdirw_destroy(ctypes.c_void_p(ctx))
+
+
+def fdirw_last_error(ctx: int | None = None) -> str:
+    m = load().fdirw_last_error(ctypes.c_void_p(ctx) if ctx else None)
+    return m.decode() if m else ""
+
+
+# --------------------------------------------------------------------------- convenience owner
+
+class FDiRW:
+    """Owns one context: ``FDiRW(shape, D, dt_macro, R, n_sub, prec)``; ``step(c_in, c_out, n)``; ``close()``."""
+
+    def __init__(self, shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp32", h: float = 1.0,
+                 device: int = -1, stream=None, mem_limit: int = 0):
+        self.shape = tuple(int(v) for v in shape)
+        self.R = int(window_R)
+        self.n = self.shape[0] * self.shape[1] * self.shape[2]
+        self.ctx = fdirw_create(self.shape, D, dt_macro, window_R, n_sub, prec, h, device, stream, mem_limit)
+
+    def kernels(self):
+        fdirw_kernels(self.ctx)
+
+    def step(self, c_in, c_out, n_steps: int = 1, want_mass: bool = False):
+        _check_f64(c_in, self.n)
+        _check_f64(c_out, self.n)
+        return fdirw_step(self.ctx, c_in, c_out, n_steps, want_mass)
+
+    def mass(self, c) -> float:
+        _check_f64(c, self.n)
+        return fdirw_mass(self.ctx, c)
+
+    def read_kernels(self, sources) -> np.ndarray:
+        return fdirw_read_kernels(self.ctx, sources, self.R)
+
+    def info(self) -> dict:
+        return fdirw_get_info(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            fdirw_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,77 @@
+"""C-ABI library checks that need no GPU: it loads, exports every declared symbol, validates arguments on
+the host, and the product path has no route to the oracle or a CPU fallback."""
+import ast
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2408_11376_gb300 import build as libbuild
+from paper_2408_11376_gb300 import fdirw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fdirw.h")).read()
+    return re.findall(r"FDIRW_API\s+[\w\s\*]+?\b(fdirw_\w+)\s*\(", src)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return fdirw.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) == len(set(names)) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(fdirw.EXPORTED)
+
+
+def test_host_side_argument_checks(lib):
+    D = np.ones(64)
+    bad = [((0, 4, 4), 1.0, 2, 3, 1.0), ((4, 4, 4), float("nan"), 2, 3, 1.0), ((4, 4, 4), 1.0, 9, 3, 1.0),
+           ((4, 4, 4), 1.0, -1, 3, 1.0), ((4, 4, 4), 1.0, 2, -3, 1.0), ((4, 4, 4), -1.0, 2, 3, 1.0),
+           ((4, 4, 4), 1.0, 2, 3, 0.0)]
+    for shape, dt, R, n_sub, h in bad:
+        g = fdirw.fdirw_grid(*shape, h)
+        ctx = ctypes.c_void_p(1234)
+        rc = lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), dt, R, n_sub, None, ctypes.byref(ctx))
+        assert rc == fdirw.FDIRW_ERR_ARG, (shape, dt, R, n_sub, h)
+        assert ctx.value is None
+        assert fdirw.fdirw_last_error()
+    g = fdirw.fdirw_grid(4, 4, 4, 1.0)
+    assert lib.fdirw_create(ctypes.byref(g), None, 1.0, 2, 3, None, ctypes.byref(ctypes.c_void_p())) == fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_kernels(None) == fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_step(None, None, None, 1, None) == fdirw.FDIRW_ERR_ARG
+    lib.fdirw_destroy(None)   # NULL-safe
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    saved = fdirw._lib
+    try:
+        fdirw._lib = None
+        with pytest.raises(ImportError):
+            fdirw.load(str(tmp_path / "missing.so"))
+    finally:
+        fdirw._lib = saved
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2408_11376_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(".py"):
+                tree = ast.parse(open(os.path.join(dirpath, f)).read())
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        assert not any(a.name.split(".")[0] == "oracle" for a in node.names), f
+                    if isinstance(node, ast.ImportFrom):
+                        assert (node.module or "").split(".")[0] != "oracle", f
+            if f.endswith((".cu", ".h", ".cpp", ".c")):
+                assert "fdirw_oracle" not in open(os.path.join(dirpath, f)).read(), f

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle (element by element where the
+oracle finishes in seconds; sampled kernels and sampled destinations at the full 96^3 and 192^3 sizes).
+
+Tolerances (relative L2 of the field after the stated steps, and per-kernel relative L2):
+FP64 path <= 1e-12, FP32 <= 1e-5, FP16/BF16 storage <= 1e-3 with the total mass exact to 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_11376_gb300 import FDiRW, FdirwError, fdirw, synth
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-3}
+KERNEL_TOL = {"fp64": 1e-13, "fp32": 3e-6, "fp16": 2e-3, "bf16": 8e-3}
+DEV = "cuda:0"
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(shape, seed, kind="two_phase", porosity=0.4, d_solid=1e-5):
+    if kind == "rough":
+        return synth.random_diffusivity(shape, seed, 6.0)
+    p = synth.sphere_packing(shape, porosity, seed, r_range=(1.5, 3.5))
+    return synth.diffusivity_two_phase(p, 1.0, d_solid) if kind == "two_phase" else synth.diffusivity_per_sphere(p)
+
+
+def _gpu_run(shape, D, dt_sub, R, n_sub, c0, steps, prec, sources=None):
+    Dd = torch.from_numpy(D).to(DEV)
+    cin = torch.from_numpy(np.ascontiguousarray(c0)).to(DEV)
+    cout = torch.empty_like(cin)
+    with FDiRW(shape, Dd, n_sub * dt_sub, R, n_sub, prec) as f:
+        m = f.step(cin, cout, steps, want_mass=True)
+        ks = f.read_kernels(sources) if sources is not None else None
+        info = f.info()
+    return cout.cpu().numpy(), m, ks, info
+
+
+def _oracle_steps(shape, D, lam, R, n_sub, c0, steps):
+    c = c0.copy()
+    for _ in range(steps):
+        c = oracle.superpose(shape, D, lam, R, n_sub, c)
+    return c
+
+
+def _oracle_at(shape, D, lam, R, n_sub, c, dests):
+    """c'(x) for listed destinations: sum over the sources within L-inf distance R of x of c(s) k_s(x)."""
+    nx, ny, nz = shape
+    cond = oracle.Conductance(shape, D)
+    out = []
+    for x in dests:
+        xx, xy, xz = x % nx, (x // nx) % ny, x // (nx * ny)
+        src, offs = [], []
+        for sz in range(max(xz - R, 0), min(xz + R, nz - 1) + 1):
+            for sy in range(max(xy - R, 0), min(xy + R, ny - 1) + 1):
+                for sx in range(max(xx - R, 0), min(xx + R, nx - 1) + 1):
+                    src.append(sx + nx * (sy + ny * sz))
+                    offs.append((xz - sz + R, xy - sy + R, xx - sx + R))
+        ks, _ = oracle.kernels(shape, D, lam, R, n_sub, src, cond)
+        out.append(sum(c[s] * ks[q][o] for q, (s, o) in enumerate(zip(src, offs))))
+    return np.array(out)
+
+
+# ------------------------------------------------------------------------- kernels, element by element
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("shape,R,n_sub", [((20, 18, 16), 3, 50), ((21, 19, 18), 8, 60)])
+def test_kernels_match_oracle(prec, shape, R, n_sub):
+    D = _case(shape, 11)
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    src = np.arange(N)
+    _, _, ks, _ = _gpu_run(shape, D, lam, R, n_sub, np.zeros(N), 0, prec, src)
+    ref, _ = oracle.kernels(shape, D, lam, R, n_sub, src)
+    ks = ks.reshape(N, -1)
+    ref = ref.reshape(N, -1)
+    err = np.linalg.norm(ks - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= KERNEL_TOL[prec], (prec, err.max())
+    # FP64 renormalisation: every stored kernel times sigma sums to 1.
+    assert np.max(np.abs(ks.sum(axis=1) - 1.0)) <= 1e-12
+    assert ks.min() >= 0.0
+
+
+# ------------------------------------------------------------------------- steps, element by element
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("shape,R,n_sub,kind", [
+    ((24, 16, 12), 3, 40, "two_phase"),   # aligned x: vectorised gather, several CTAs and batches
+    ((13, 11, 9), 2, 25, "rough"),        # ragged x: scalar gather path
+    ((16, 9, 7), 5, 30, "per_sphere"),    # windows larger than most of the domain
+])
+def test_steps_match_oracle(prec, shape, R, n_sub, kind):
+    D = _case(shape, 21, kind)
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    c0 = synth.random_field(N, 22, 0.0, 2.0)
+    got, m, _, _ = _gpu_run(shape, D, lam, R, n_sub, c0, 2, prec)
+    ref = _oracle_steps(shape, D, lam, R, n_sub, c0, 2)
+    assert _rel(got, ref) <= FIELD_TOL[prec], (prec, _rel(got, ref))
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload_32_full(prec):
+    """32^3, porosity 0.4, D 1/1e-5, R=3, n_sub=50 at the stability limit, 2 macro steps, c=1 in solid."""
+    w = synth.WORKLOADS["fdirw-32c-r3"]
+    p, D, c0 = w.make()
+    shape = (w.n,) * 3
+    lam = oracle.stable_dt_sub(shape, D)
+    got, m, _, _ = _gpu_run(shape, D, lam, w.R, w.n_sub, c0, w.steps, prec)
+    ref = _oracle_steps(shape, D, lam, w.R, w.n_sub, c0, w.steps)
+    assert _rel(got, ref) <= FIELD_TOL[prec]
+    assert abs(m - oracle.mass(c0)) <= 1e-12 * oracle.mass(c0)
+
+
+# ------------------------------------------------------------------------- degenerate and edge cases
+
+def test_window_covers_domain_equals_full_march():
+    shape = (5, 4, 3)
+    D = _case(shape, 31, "rough")
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(60, 32)
+    for prec in ("fp64", "fp32"):
+        got, _, _, _ = _gpu_run(shape, D, lam, 8, 17, c0, 1, prec)
+        ref = oracle.full_march(shape, D, lam, 17, c0)
+        assert _rel(got, ref) <= FIELD_TOL[prec]
+
+
+@pytest.mark.parametrize("shape,R,n_sub,D_zero", [
+    ((6, 5, 4), 2, 0, False),    # n_sub = 0
+    ((6, 5, 4), 0, 9, False),    # R = 0
+    ((6, 5, 4), 3, 9, True),     # D = 0 everywhere
+    ((1, 1, 1), 4, 9, False),    # one cell
+])
+def test_identity_cases(shape, R, n_sub, D_zero):
+    N = int(np.prod(shape))
+    D = np.zeros(N) if D_zero else _case(shape, 41, "rough")
+    c0 = synth.random_field(N, 42)
+    for prec in ("fp64", "fp32", "bf16"):
+        got, m, _, _ = _gpu_run(shape, D, 0.1 if D_zero else oracle.stable_dt_sub(shape, D), R, n_sub, c0, 3, prec)
+        assert np.allclose(got, c0, rtol=0, atol=1e-15 * np.abs(c0).max()), prec
+
+
+def test_one_dimensional_chain():
+    shape = (64, 1, 1)
+    D = _case(shape, 43, "rough")
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(64, 44)
+    got, _, _, _ = _gpu_run(shape, D, lam, 6, 33, c0, 3, "fp64")
+    assert _rel(got, _oracle_steps(shape, D, lam, 6, 33, c0, 3)) <= 1e-12
+
+
+def test_deterministic_bitwise():
+    shape = (24, 16, 12)
+    D = _case(shape, 51)
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(24 * 16 * 12, 52)
+    for prec in ("fp64", "bf16"):
+        a, ma, _, _ = _gpu_run(shape, D, lam, 4, 30, c0, 3, prec)
+        b, mb, _, _ = _gpu_run(shape, D, lam, 4, 30, c0, 3, prec)
+        assert np.array_equal(a, b) and ma == mb
+
+
+def test_host_pointers_and_in_place():
+    shape = (16, 12, 10)
+    D = _case(shape, 61)
+    lam = oracle.stable_dt_sub(shape, D)
+    N = 1920
+    c0 = synth.random_field(N, 62)
+    dev, _, _, _ = _gpu_run(shape, D, lam, 3, 20, c0, 2, "fp32")
+    with FDiRW(shape, D, 20 * lam, 3, 20, "fp32") as f:          # host D
+        host_out = np.empty(N)
+        m = f.step(c0, host_out, 2, want_mass=True)             # host in, host out
+        assert np.array_equal(host_out, dev)
+        assert m == f.mass(host_out)
+        t = torch.from_numpy(c0.copy()).to(DEV)
+        f.step(t, t, 2)                                         # in place on the device
+        assert np.array_equal(t.cpu().numpy(), dev)
+        t0 = torch.from_numpy(c0).to(DEV)
+        f.step(t0, host_out, 2)                                 # device in, host out
+        assert np.array_equal(host_out, dev)
+
+
+def test_errors_are_reported():
+    shape = (8, 8, 8)
+    D = _case(shape, 71)
+    lam = oracle.stable_dt_sub(shape, D)
+    with pytest.raises(FdirwError) as e:
+        FDiRW(shape, D, 10 * lam * 1.01, 2, 10)
+    assert e.value.code == fdirw.FDIRW_ERR_UNSTABLE
+    bad = D.copy()
+    bad[5] = np.nan
+    with pytest.raises(FdirwError) as e:
+        FDiRW(shape, bad, 10 * lam, 2, 10)
+    assert e.value.code == fdirw.FDIRW_ERR_ARG
+    bad[5] = -1.0
+    with pytest.raises(FdirwError) as e:
+        FDiRW(shape, torch.from_numpy(bad).to(DEV), 10 * lam, 2, 10)
+    assert e.value.code == fdirw.FDIRW_ERR_ARG
+    with FDiRW(shape, D, 10 * lam, 2, 10, mem_limit=600_000) as f:
+        with pytest.raises(FdirwError) as e:
+            f.kernels()
+        assert e.value.code == fdirw.FDIRW_ERR_NOMEM
+    with FDiRW(shape, D, 10 * lam, 2, 10) as f:
+        with pytest.raises(FdirwError) as e:
+            f.read_kernels([0])
+        assert e.value.code == fdirw.FDIRW_ERR_STATE
+        f.kernels()
+        with pytest.raises(FdirwError) as e:
+            f.read_kernels([512])
+        assert e.value.code == fdirw.FDIRW_ERR_ARG
+    assert abs(fdirw.fdirw_stable_dt(shape, D) - lam) <= 1e-15 * lam
+
+
+# ------------------------------------------------------------------------- full-size workloads, sampled
+
+def _sample_sources(shape, n_random, seed):
+    nx, ny, nz = shape
+    corners = [x + nx * (y + ny * z) for x in (0, nx - 1) for y in (0, ny - 1) for z in (0, nz - 1)]
+    edges = [nx // 2, nx * (ny // 2), nx * ny * (nz // 2) + nx - 1, (nx * ny * nz) // 2 + nx // 3]
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([corners, edges, rng.integers(0, nx * ny * nz, n_random)]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload_96_sampled(prec):
+    """96^3, porosity 0.35, per-sphere log10 D ratio U[3,8], R=6, n_sub=120, Gaussian blob."""
+    w = synth.WORKLOADS["fdirw-96c-r6"]
+    _, D, c0 = w.make()
+    shape = (w.n,) * 3
+    lam = oracle.stable_dt_sub(shape, D)
+    src = _sample_sources(shape, 40, 96)
+    got, m, ks, _ = _gpu_run(shape, D, lam, w.R, w.n_sub, c0, 1, prec, src)
+    ref, _ = oracle.kernels(shape, D, lam, w.R, w.n_sub, src)
+    err = np.linalg.norm((ks - ref).reshape(len(src), -1), axis=1) / np.linalg.norm(ref.reshape(len(src), -1), axis=1)
+    assert err.max() <= KERNEL_TOL[prec]
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+    N = w.n ** 3
+    centre = (w.n // 2) * (1 + w.n + w.n * w.n)
+    dests = np.array([0, N - 1, centre, centre + 7, centre - 5 * w.n])
+    ref_at = _oracle_at(shape, D, lam, w.R, w.n_sub, c0, dests)
+    assert np.max(np.abs(got[dests] - ref_at)) <= FIELD_TOL[prec] * np.abs(ref_at).max()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_workload_192_sampled(prec):
+    """192^3, porosity 0.4, D 1/1e-6, R=8, n_sub=200, c=1 in solid: the benchmark's launch configuration."""
+    w = synth.WORKLOADS["fdirw-192c-r8"]
+    _, D, c0 = w.make()
+    shape = (w.n,) * 3
+    lam = oracle.stable_dt_sub(shape, D)
+    src = _sample_sources(shape, 24, 192)
+    got, m, ks, info = _gpu_run(shape, D, lam, w.R, w.n_sub, c0, 1, prec, src)
+    assert info["kernels_ms"] > 0
+    ref, _ = oracle.kernels(shape, D, lam, w.R, w.n_sub, src)
+    err = np.linalg.norm((ks - ref).reshape(len(src), -1), axis=1) / np.linalg.norm(ref.reshape(len(src), -1), axis=1)
+    assert err.max() <= KERNEL_TOL[prec]
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+    N = w.n ** 3
+    dests = np.array([0, N - 1, (w.n // 2) * (1 + w.n + w.n * w.n)])
+    ref_at = _oracle_at(shape, D, lam, w.R, w.n_sub, c0, dests)
+    assert np.max(np.abs(got[dests] - ref_at)) <= FIELD_TOL[prec] * np.abs(ref_at).max()
