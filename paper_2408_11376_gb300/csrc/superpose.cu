@@ -10,10 +10,11 @@
 //
 // Accumulation (Sec. 3.3: multiply in the storage precision, accumulate in higher precision):
 //   - FP64 storage: FP64 FMA.
-//   - FP32/FP16/BF16 storage: GB300 issues FP64 FMAs at 1/73 of the FP32 rate (measured), so the sum is
-//     kept as an unevaluated pair of FP32 values (s, c) -- error-free product (FMA residual) and
-//     error-free addition (Knuth TwoSum) -- with chat split into hi = fp32(v), lo = fp32(v - hi).  The pair
-//     carries ~48 significant bits; it is converted to FP64 once per destination.
+//   - FP32/FP16/BF16 storage: GB300 issues FP64 FMAs at 1/73 of the FP32 rate (measured), so each row of
+//     2R+1 terms is summed as an unevaluated pair of FP32 values (s, c) -- error-free product (FMA
+//     residual) and error-free addition (Knuth TwoSum), with chat split into hi = fp32(v),
+//     lo = fp32(v - hi) -- and the row result is added to an FP64 accumulator (2 FP64 adds per row
+//     instead of 2R+1 FP64 FMAs).
 // The work per step is HBM-bound in the cache read (N * (2R+1)^3 * storage bytes).
 #include "fdirw_internal.h"
 
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
     const int x0 = xv * VX;
     const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
 
-    float s[VX], c[VX];
+    double acc[VX];
 #pragma unroll
-    for (int j = 0; j < VX; j++) { s[j] = 0.f; c[j] = 0.f; }
+    for (int j = 0; j < VX; j++) acc[j] = 0.0;
 
     for (int oz = -R; oz <= R; oz++) {
         for (int oy = -R; oy <= R; oy++) {
@@ -87,6 +88,11 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
 #pragma unroll
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
             const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+            // The FP32 pair restarts at zero on every row of 2R+1 terms, so its compensation term stays
+            // within a few ulps of the row sum; the row is then added to the FP64 accumulator.
+            float s[VX], c[VX];
+#pragma unroll
+            for (int j = 0; j < VX; j++) { s[j] = 0.f; c[j] = 0.f; }
 #pragma unroll
             for (int ox = -R; ox <= R; ox++) {
                 float q[VX];
@@ -94,10 +100,12 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
 #pragma unroll
                 for (int j = 0; j < VX; j++) ff_madd(s[j], c[j], q[j], ch[j - ox + R]);
             }
+#pragma unroll
+            for (int j = 0; j < VX; j++) acc[j] += (double)s[j] + (double)c[j];
         }
     }
 #pragma unroll
-    for (int j = 0; j < VX; j++) out[i0 + j] = (double)s[j] + (double)c[j];
+    for (int j = 0; j < VX; j++) out[i0 + j] = acc[j];
 }
 
 // FP64 path: FP64 storage, FP64 chat, FP64 FMA accumulation, VX = 2.
@@ -147,12 +155,11 @@ __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict
     const int64_t r = i / g.nx;
     const int y = (int)(r % g.ny);
     const int z = (int)(r / g.ny);
-    const int W1 = 2 * R + 1;
-    float s = 0.f, c = 0.f;
     double acc = 0.0;
     int o = 0;
     for (int oz = -R; oz <= R; oz++)
-        for (int oy = -R; oy <= R; oy++)
+        for (int oy = -R; oy <= R; oy++) {
+            float s = 0.f, c = 0.f;
             for (int ox = -R; ox <= R; ox++, o++) {
                 const int64_t pi = ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + (x - ox + R);
                 const ST qv = Q[(int64_t)o * g.n + i];
@@ -162,8 +169,9 @@ __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict
                     acc = fma((double)qv, reinterpret_cast<const double*>(chat)[pi], acc);
                 }
             }
-    (void)W1;
-    out[i] = FF ? (double)s + (double)c : acc;
+            if constexpr (FF) acc += (double)s + (double)c;
+        }
+    out[i] = acc;
 }
 
 __global__ void scale_kernel(const double* __restrict__ c, const double* __restrict__ sigma, Grid g, int R, Pad p,

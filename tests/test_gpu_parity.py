@@ -141,8 +141,12 @@ def test_identity_cases(shape, R, n_sub, D_zero):
     D = np.zeros(N) if D_zero else _case(shape, 41, "rough")
     c0 = synth.random_field(N, 42)
     for prec in ("fp64", "fp32", "bf16"):
-        got, m, _, _ = _gpu_run(shape, D, 0.1 if D_zero else oracle.stable_dt_sub(shape, D), R, n_sub, c0, 3, prec)
-        assert np.allclose(got, c0, rtol=0, atol=1e-15 * np.abs(c0).max()), prec
+        dt = oracle.stable_dt_sub(shape, D)
+        dt = 0.1 if not np.isfinite(dt) else dt        # no faces at all: any substep is stable
+        got, m, _, _ = _gpu_run(shape, D, dt, R, n_sub, c0, 3, prec)
+        # FP64: exact; mixed path: the chat split keeps ~48 bits per step
+        tol = 0.0 if prec == "fp64" else 1e-13
+        assert np.allclose(got, c0, rtol=0, atol=tol * np.abs(c0).max()), prec
 
 
 def test_one_dimensional_chain():
@@ -201,7 +205,7 @@ def test_errors_are_reported():
     with pytest.raises(FdirwError) as e:
         FDiRW(shape, torch.from_numpy(bad).to(DEV), 10 * lam, 2, 10)
     assert e.value.code == fdirw.FDIRW_ERR_ARG
-    with FDiRW(shape, D, 10 * lam, 2, 10, mem_limit=600_000) as f:
+    with FDiRW(shape, D, 10 * lam, 2, 10, mem_limit=100_000) as f:     # create needs ~40 KB, the cache 256 KB
         with pytest.raises(FdirwError) as e:
             f.kernels()
         assert e.value.code == fdirw.FDIRW_ERR_NOMEM
