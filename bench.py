@@ -289,6 +289,7 @@ def run_ours(args, w):
         "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": w.name, "grid": f"{w.n}^3", "R": w.R, "n_sub": w.n_sub, "macro_steps": w.steps,
                    "prec": prec, "porosity": w.porosity, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "march_threads_per_column": info["march_parts"],
                    "l2": f"inputs larger than L2 (kernel cache {info['cache_bytes'] / 1e9:.1f} GB, read every step)"},
         "source_kernels_per_s": N / (march_ms * 1e-3),
         "steady_macro_steps_per_s": 1000.0 * w.steps / steps_ms,

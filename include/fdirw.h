@@ -75,6 +75,10 @@ typedef struct {
     int32_t  device;      /* CUDA device ordinal; -1 = the calling thread's current device */
     void*    stream;      /* cudaStream_t for all work; NULL = legacy default stream */
     uint64_t mem_limit;   /* cap on the device bytes this context allocates; 0 = no cap */
+    int32_t  march_parts; /* FP32 march thread mapping: threads per window column, 1..3; 0 = autotune
+                             (each candidate timed once on the first build for a device, R and storage
+                             type, result cached for the process; that build synchronises the stream) */
+    int32_t  reserved;    /* must be 0 */
 } fdirw_opts;
 
 typedef struct {
@@ -93,6 +97,8 @@ typedef struct {
     float    last_gather_ms; /* device time of the last gather launch */
     double   last_mass_in;   /* FP64 total of c_in at the last fdirw_step */
     double   last_mass_out;  /* FP64 total of c_out after the last fdirw_step (if it was computed) */
+    int32_t  march_parts;    /* thread mapping of the last kernel-cache build (threads per column) */
+    int32_t  reserved;
 } fdirw_info;
 
 typedef struct fdirw_ctx fdirw_ctx;
@@ -109,7 +115,7 @@ FDIRW_API int fdirw_stable_dt(const fdirw_grid* grid, const double* D_map, int32
  *   dt_macro   : macro step (>= 0, finite); dt_sub = dt_macro / n_sub
  *   window_R   : window radius, 0 <= R <= 8 (R = 0 gives the identity operator)
  *   n_sub      : explicit substeps per macro step, >= 0 (0 gives the identity operator)
- *   opts       : NULL for defaults (FDIRW_FP32, current device, default stream, no cap)
+ *   opts       : NULL for defaults (FDIRW_FP32, current device, default stream, no cap, autotune)
  *   out        : receives the context (set to NULL on failure)
  * Computes the face conductances on the device and checks stability; the kernel cache is built
  * lazily (fdirw_kernels or the first fdirw_step).  Errors: FDIRW_ERR_ARG, FDIRW_ERR_UNSTABLE,

@@ -22,6 +22,7 @@ struct fdirw_ctx {
     int prec = FDIRW_FP32;
     Store store = Store::F32;
     int num_sms = 0;
+    int parts_req = 0, parts_used = 0;
     uint64_t mem_limit = 0, allocated = 0;
     void* coef[3] = {nullptr, nullptr, nullptr};   // lam * g: float (mixed) or double (FP64)
     void* Q = nullptr;
@@ -203,9 +204,10 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     if (window_R < 0 || window_R > fdirw::kMaxR)
         return fail(nullptr, FDIRW_ERR_ARG, "window_R must be in [0, " + std::to_string(fdirw::kMaxR) + "]");
     if (n_sub < 0) return fail(nullptr, FDIRW_ERR_ARG, "n_sub must be >= 0");
-    fdirw_opts o{FDIRW_FP32, -1, nullptr, 0};
+    fdirw_opts o{FDIRW_FP32, -1, nullptr, 0, 0, 0};
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP64 || o.prec > FDIRW_FP32_STORE_BF16) return fail(nullptr, FDIRW_ERR_ARG, "unknown prec");
+    if (o.march_parts < 0 || o.march_parts > 3) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 3]");
 
     DeviceGuard dg(o.device);
     if (!dg.ok) return fail(nullptr, FDIRW_ERR_CUDA, "cannot select CUDA device " + std::to_string(o.device));
@@ -213,6 +215,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     cudaGetDevice(&c->device);
     c->stream = reinterpret_cast<cudaStream_t>(o.stream);
     c->mem_limit = o.mem_limit;
+    c->parts_req = o.march_parts;
     c->g = Grid{grid->nx, grid->ny, grid->nz, (int64_t)grid->nx * grid->ny * grid->nz};
     c->h = grid->h;
     c->dt_macro = dt_macro;
@@ -311,7 +314,7 @@ int fdirw_kernels(fdirw_ctx* c) {
     a.src_begin = 0;
     a.src_end = c->g.n;
     FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
-    FDIRW_CUDA(c, fdirw::launch_march(a, c->num_sms, c->stream));
+    FDIRW_CUDA(c, fdirw::launch_march(a, c->num_sms, c->parts_req, c->stream, &c->parts_used));
     FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
     c->kernels_timed = true;
     c->kernels_ready = true;
@@ -437,6 +440,7 @@ int fdirw_get_info(fdirw_ctx* c, fdirw_info* out) {
     out->window_cells = c->window_cells;
     out->last_mass_in = c->mass_in;
     out->last_mass_out = c->mass_out;
+    out->march_parts = c->parts_used;
     float ms = 0.f;
     if (c->kernels_timed) {
         FDIRW_CUDA(c, cudaEventSynchronize(c->ev[1]));

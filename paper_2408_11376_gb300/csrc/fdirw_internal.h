@@ -41,7 +41,9 @@ struct MarchArgs {
     double* sigma;        // N: 1 / FP64 sum of the stored values of each source
     int64_t src_begin, src_end;
 };
-cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);
+// parts_req: threads per window column for the FP32 march (1..3), or 0 to autotune (timed once per
+// device, R and storage, then cached); parts_used receives the mapping launched.
+cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used);
 
 // ---------------------------------------------------------------- superpose.cu
 // Padded layout of the scaled field chat = sigma * c: (nx+2R) x (ny+2R) x (nz+2R), zero halo.

@@ -21,6 +21,11 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace fdirw {
 
 namespace {
@@ -30,27 +35,43 @@ struct Shape {
     static constexpr int W1 = 2 * R + 1;
     static constexpr int COLS = W1 * W1;
     static constexpr int W = W1 * W1 * W1;
-    static constexpr int SPB = (512 / COLS) > 0 ? (512 / COLS) : 1;      // sources per CTA (FP32 path)
-    static constexpr int THREADS = ((SPB * COLS + 31) / 32) * 32;
+    static constexpr int SPB = (512 / COLS) > 0 ? (512 / COLS) : 1;
     // FP64 path: 2 exchange buffers + 3 face arrays of SPB*W doubles must fit in ~200 KB.
     static constexpr int SPB64_CAP = 200000 / (5 * W * 8);
     static constexpr int SPB64 = SPB64_CAP < 1 ? 1 : (SPB64_CAP < SPB ? SPB64_CAP : SPB);
     static constexpr int THREADS64 = ((SPB64 * COLS + 31) / 32) * 32;
 };
 
-// Rounds v to the storage type, writes it to Q[idx] and returns the stored value widened to double.
-__device__ __forceinline__ double put(void* Q, Store st, int64_t idx, float v) {
+// FP32 path thread mapping: P threads per window z-column, each owning KS consecutive cells.
+template <int R, int P>
+struct Map32 {
+    static constexpr int W1 = 2 * R + 1;
+    static constexpr int COLS = W1 * W1;
+    static constexpr int KS = (W1 + P - 1) / P;
+    static constexpr int TPS = P * COLS;                       // threads per source
+    static constexpr int SPB = (512 / TPS) > 0 ? (512 / TPS) : 1;    // sources per CTA
+    static constexpr int THREADS = ((SPB * TPS + 31) / 32) * 32;
+    // Split mappings aim at ~1024 resident threads per SM; the single-column mapping needs the
+    // registers of a whole SM for one CTA (6 coefficients + state per cell, 2R+1 cells per thread).
+    static constexpr int MIN_BLOCKS = P == 1 ? 1 : ((1024 / THREADS) > 0 ? 1024 / THREADS : 1);
+    static constexpr int BUF = SPB * COLS * W1;                // floats per exchange buffer
+    static constexpr size_t SMEM = (size_t)((2 * BUF * 4 + 15) / 16) * 16 + (size_t)SPB * COLS * 8;
+};
+
+// Rounds v to the storage type, writes it to Q[idx] and returns the stored value widened to float
+// (exact for every storage type).
+__device__ __forceinline__ float put(void* Q, Store st, int64_t idx, float v) {
     if (st == Store::F32) {
         reinterpret_cast<float*>(Q)[idx] = v;
-        return (double)v;
+        return v;
     } else if (st == Store::F16) {
         const __half h = __float2half_rn(v);
         reinterpret_cast<__half*>(Q)[idx] = h;
-        return (double)__half2float(h);
+        return __half2float(h);
     } else {
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
         reinterpret_cast<__nv_bfloat16*>(Q)[idx] = b;
-        return (double)__bfloat162float(b);
+        return __bfloat162float(b);
     }
 }
 
@@ -69,20 +90,23 @@ __device__ __forceinline__ void finish_sigma(const double* red, int64_t batch_fi
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(Shape<R>::THREADS, 1) march_f32_kernel(MarchArgs a) {
-    using S = Shape<R>;
-    constexpr int W1 = S::W1, COLS = S::COLS, SPB = S::SPB;
-    constexpr int BUF = SPB * COLS * W1;
+template <int R, int P>
+__global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS) march_f32_kernel(MarchArgs a) {
+    using M = Map32<R, P>;
+    constexpr int W1 = M::W1, COLS = M::COLS, KS = M::KS, TPS = M::TPS, SPB = M::SPB, BUF = M::BUF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* xbuf = reinterpret_cast<float*>(smem_raw);                                  // [2][SPB*COLS][W1]
     double* red = reinterpret_cast<double*>(smem_raw + ((2 * BUF * 4 + 15) / 16) * 16);  // [SPB*COLS]
 
     const int t = threadIdx.x;
-    const bool active = t < SPB * COLS;
-    const int slot = active ? t / COLS : 0;
-    const int col = active ? t - slot * COLS : 0;
+    const bool active = t < SPB * TPS;
+    const int slot = active ? t / TPS : 0;
+    const int rr = active ? t - slot * TPS : 0;
+    const int part = rr / COLS;
+    const int col = rr - part * COLS;
     const int ci = col % W1, cj = col / W1;
+    const int k0 = part * KS;                                  // first own cell of the column
+    const int kn = (W1 - k0) < KS ? (W1 - k0) : KS;            // number of own cells
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const int64_t nxy = (int64_t)nx * ny;
     const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
@@ -92,6 +116,8 @@ __global__ void __launch_bounds__(Shape<R>::THREADS, 1) march_f32_kernel(MarchAr
     const int xp = ci < 2 * R ? base + W1 : base;
     const int ym = cj > 0 ? base - W1 * W1 : base;
     const int yp = cj < 2 * R ? base + W1 * W1 : base;
+    const int kbelow = k0 > 0 ? k0 - 1 : k0;                   // cell read for the -z face of cell k0
+    const int kabove = k0 + kn < W1 ? k0 + kn : k0;            // cell read for the +z face of the last cell
 
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
         const int64_t first = a.src_begin + b * SPB;
@@ -110,11 +136,14 @@ __global__ void __launch_bounds__(Shape<R>::THREADS, 1) march_f32_kernel(MarchAr
         // am = -(sum of the cell's face coefficients): the update is u += am*u + sum c*u_nb, i.e. the
         // increment is formed at full FP32 relative precision before it is added (1 - sum c rounded
         // once would bias near-delta kernels by half an ulp of 1 every substep).
-        float u[W1], am[W1], cxm[W1], cxp[W1], cym[W1], cyp[W1], cz[W1];
+        // cz[j] is the +z face of own cell j; czb is the -z face of own cell 0.
+        float u[KS], am[KS], cxm[KS], cxp[KS], cym[KS], cyp[KS], cz[KS];
+        float czb = 0.f;
 #pragma unroll
-        for (int k = 0; k < W1; k++) {
+        for (int j = 0; j < KS; j++) {
+            const int k = k0 + j;
             const int z = sz - R + k;
-            const bool ok = col_ok && z >= 0 && z < nz;
+            const bool ok = col_ok && j < kn && z >= 0 && z < nz;
             float vxm = 0.f, vxp = 0.f, vym = 0.f, vyp = 0.f, vz = 0.f;
             if (ok) {
                 const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
@@ -123,53 +152,72 @@ __global__ void __launch_bounds__(Shape<R>::THREADS, 1) march_f32_kernel(MarchAr
                 if (cj > 0 && y > 0) vym = __ldg(a.ay + i - nx);
                 if (cj < 2 * R && y + 1 < ny) vyp = __ldg(a.ay + i);
                 if (k < 2 * R && z + 1 < nz) vz = __ldg(a.az + i);
+                if (j == 0 && k > 0 && z > 0) czb = __ldg(a.az + i - nxy);
             }
-            cxm[k] = vxm; cxp[k] = vxp; cym[k] = vym; cyp[k] = vyp; cz[k] = vz;
-            u[k] = (src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
+            cxm[j] = vxm; cxp[j] = vxp; cym[j] = vym; cyp[j] = vyp; cz[j] = vz;
+            u[j] = (src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
         }
 #pragma unroll
-        for (int k = 0; k < W1; k++) {
-            const float zm = k > 0 ? cz[k - 1] : 0.f;
-            am[k] = -(((cxm[k] + cxp[k]) + (cym[k] + cyp[k])) + (zm + cz[k]));
+        for (int j = 0; j < KS; j++) {
+            const float zm = j > 0 ? cz[j - 1] : czb;
+            am[j] = -(((cxm[j] + cxp[j]) + (cym[j] + cyp[j])) + (zm + cz[j]));
         }
 
         for (int it = 0; it < a.n_sub; it++) {
             float* buf = xbuf + (it & 1) * BUF;
             if (active) {
 #pragma unroll
-                for (int k = 0; k < W1; k++) buf[base + k] = u[k];
+                for (int j = 0; j < KS; j++)
+                    if (j < kn) buf[base + k0 + j] = u[j];
             }
             __syncthreads();
-            float prev = 0.f;
+            float prev = buf[base + kbelow];        // z-neighbour below own cell 0 (coefficient 0 if none)
+            const float next_last = buf[base + kabove];
 #pragma unroll
-            for (int k = 0; k < W1; k++) {
-                const float cur = u[k];
-                float v = am[k] * cur;
-                v = fmaf(cxm[k], buf[xm + k], v);
-                v = fmaf(cxp[k], buf[xp + k], v);
-                v = fmaf(cym[k], buf[ym + k], v);
-                v = fmaf(cyp[k], buf[yp + k], v);
-                if (k > 0) v = fmaf(cz[k - 1], prev, v);
-                if (k + 1 < W1) v = fmaf(cz[k], u[k + 1], v);
-                prev = cur;
-                u[k] = __fadd_rn(cur, v);
-            }
-        }
-
-        // Epilogue: round to storage, write Q[o][x] (x = s + o, the cell itself), FP64 column sum.
-        double colsum = 0.0;
-        if (col_ok) {
-#pragma unroll
-            for (int k = 0; k < W1; k++) {
-                const int z = sz - R + k;
-                if (z >= 0 && z < nz) {
-                    const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                    const int64_t o = ci + W1 * (cj + W1 * k);
-                    colsum += put(a.Q, a.store, o * a.g.n + i, u[k]);
+            for (int j = 0; j < KS; j++) {
+                if (j < kn) {                      // the last part of a column may own fewer cells
+                    const float cur = u[j];
+                    const int k = k0 + j;
+                    float v = am[j] * cur;
+                    v = fmaf(cxm[j], buf[xm + k], v);
+                    v = fmaf(cxp[j], buf[xp + k], v);
+                    v = fmaf(cym[j], buf[ym + k], v);
+                    v = fmaf(cyp[j], buf[yp + k], v);
+                    v = fmaf(j > 0 ? cz[j - 1] : czb, prev, v);
+                    v = fmaf(cz[j], (j + 1 < KS) ? (j + 1 < kn ? u[j + 1] : next_last) : next_last, v);
+                    prev = cur;
+                    u[j] = __fadd_rn(cur, v);
                 }
             }
         }
-        if (active) red[t] = colsum;
+
+        // Epilogue: round to storage and write Q[o][x] (x = s + o, the cell itself); the stored values
+        // (exact in FP32) go back to shared memory so that each column is summed in k order by one
+        // thread, whatever P is.
+        float* sbuf = xbuf + (a.n_sub & 1) * BUF;   // not the buffer the last substep read
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < KS; j++) {
+                if (j < kn) {
+                    const int k = k0 + j;
+                    const int z = sz - R + k;
+                    float st = 0.f;
+                    if (col_ok && z >= 0 && z < nz) {
+                        const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                        const int64_t o = ci + W1 * (cj + W1 * k);
+                        st = put(a.Q, a.store, o * a.g.n + i, u[j]);
+                    }
+                    sbuf[base + k] = st;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < SPB * COLS; c += blockDim.x) {
+            double colsum = 0.0;
+#pragma unroll
+            for (int k = 0; k < W1; k++) colsum += (double)sbuf[c * W1 + k];
+            red[c] = colsum;
+        }
         __syncthreads();
         finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
         __syncthreads();   // red and xbuf are reused by the next batch
@@ -285,51 +333,142 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
     }
 }
 
+template <int R, int P>
+cudaError_t launch_f32(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    using M = Map32<R, P>;
+    const int64_t nsrc = a.src_end - a.src_begin;
+    if (nsrc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(march_f32_kernel<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_f32_kernel<R, P>, M::THREADS, M::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t nbatch = (nsrc + M::SPB - 1) / M::SPB;
+    const int64_t grid = nbatch < (int64_t)num_sms * per_sm ? nbatch : (int64_t)num_sms * per_sm;
+    march_f32_kernel<R, P><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int R>
-cudaError_t launch_r(const MarchArgs& a, int num_sms, cudaStream_t st) {
+cudaError_t launch_f32_p(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
+    switch (P) {
+        case 1: return launch_f32<R, 1>(a, num_sms, st);
+        case 2: return launch_f32<R, 2>(a, num_sms, st);
+        case 3: return launch_f32<R, 3>(a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+cudaError_t launch_f64(const MarchArgs& a, int num_sms, cudaStream_t st) {
     using S = Shape<R>;
     const int64_t nsrc = a.src_end - a.src_begin;
     if (nsrc <= 0) return cudaSuccess;
-    if (a.store == Store::F64) {
-        const size_t smem = (size_t)(5 * S::SPB64 * S::W + S::SPB64 * S::COLS) * 8;
-        cudaError_t e = cudaFuncSetAttribute(march_f64_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_f64_kernel<R>, S::THREADS64, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const int64_t nbatch = (nsrc + S::SPB64 - 1) / S::SPB64;
-        const int64_t grid = nbatch < (int64_t)num_sms * per_sm ? nbatch : (int64_t)num_sms * per_sm;
-        march_f64_kernel<R><<<(unsigned)grid, S::THREADS64, smem, st>>>(a);
-    } else {
-        const size_t smem = (size_t)((2 * S::SPB * S::W * 4 + 15) / 16) * 16 + (size_t)S::SPB * S::COLS * 8;
-        cudaError_t e = cudaFuncSetAttribute(march_f32_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_f32_kernel<R>, S::THREADS, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const int64_t nbatch = (nsrc + S::SPB - 1) / S::SPB;
-        const int64_t grid = nbatch < (int64_t)num_sms * per_sm ? nbatch : (int64_t)num_sms * per_sm;
-        march_f32_kernel<R><<<(unsigned)grid, S::THREADS, smem, st>>>(a);
-    }
+    const size_t smem = (size_t)(5 * S::SPB64 * S::W + S::SPB64 * S::COLS) * 8;
+    cudaError_t e = cudaFuncSetAttribute(march_f64_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_f64_kernel<R>, S::THREADS64, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t nbatch = (nsrc + S::SPB64 - 1) / S::SPB64;
+    const int64_t grid = nbatch < (int64_t)num_sms * per_sm ? nbatch : (int64_t)num_sms * per_sm;
+    march_f64_kernel<R><<<(unsigned)grid, S::THREADS64, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t dispatch(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
+    if (a.store == Store::F64) {
+        switch (a.R) {
+            case 1: return launch_f64<1>(a, num_sms, st);
+            case 2: return launch_f64<2>(a, num_sms, st);
+            case 3: return launch_f64<3>(a, num_sms, st);
+            case 4: return launch_f64<4>(a, num_sms, st);
+            case 5: return launch_f64<5>(a, num_sms, st);
+            case 6: return launch_f64<6>(a, num_sms, st);
+            case 7: return launch_f64<7>(a, num_sms, st);
+            case 8: return launch_f64<8>(a, num_sms, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (a.R) {
+        case 1: return launch_f32_p<1>(a, P, num_sms, st);
+        case 2: return launch_f32_p<2>(a, P, num_sms, st);
+        case 3: return launch_f32_p<3>(a, P, num_sms, st);
+        case 4: return launch_f32_p<4>(a, P, num_sms, st);
+        case 5: return launch_f32_p<5>(a, P, num_sms, st);
+        case 6: return launch_f32_p<6>(a, P, num_sms, st);
+        case 7: return launch_f32_p<7>(a, P, num_sms, st);
+        case 8: return launch_f32_p<8>(a, P, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Thread-mapping autotuner (P = threads per window column).  Each candidate is timed once on the
+// context stream over a sample of the real sources (the sample's results are identical whatever P is,
+// and the full launch overwrites them); the fastest is cached per (device, R, storage) for the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+int default_parts(int R) { return R >= 4 ? 2 : 1; }
+
+cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* best) {
+    const int W1 = 2 * a.R + 1, cols = W1 * W1;
+    const int64_t per_wave = (int64_t)num_sms * ((512 / cols) > 0 ? 512 / cols : 1);
+    MarchArgs s = a;
+    s.src_end = a.src_begin + std::min<int64_t>(a.src_end - a.src_begin, 16 * per_wave);
+    MarchArgs warm = a;
+    warm.src_end = a.src_begin + std::min<int64_t>(a.src_end - a.src_begin, per_wave);
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    float best_ms = 1e30f;
+    *best = default_parts(a.R);
+    for (int P = 1; P <= 3 && e == cudaSuccess; P++) {
+        if (P > W1) break;
+        e = dispatch(warm, P, num_sms, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = dispatch(s, P, num_sms, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) { best_ms = ms; *best = P; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
 }
 
 }  // namespace
 
-cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st) {
-    switch (a.R) {
-        case 1: return launch_r<1>(a, num_sms, st);
-        case 2: return launch_r<2>(a, num_sms, st);
-        case 3: return launch_r<3>(a, num_sms, st);
-        case 4: return launch_r<4>(a, num_sms, st);
-        case 5: return launch_r<5>(a, num_sms, st);
-        case 6: return launch_r<6>(a, num_sms, st);
-        case 7: return launch_r<7>(a, num_sms, st);
-        case 8: return launch_r<8>(a, num_sms, st);
-        default: return cudaErrorInvalidValue;
+cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
+    int P = 1;
+    if (a.store != Store::F64) {
+        if (parts_req >= 1 && parts_req <= 3) {
+            P = parts_req;
+        } else {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            const auto key = std::make_tuple(dev, a.R, (int)a.store);
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune.find(key);
+                if (it != g_tune.end()) P = it->second; else P = 0;
+            }
+            if (P == 0) {
+                cudaError_t e = tune_parts(a, num_sms, st, &P);
+                if (e != cudaSuccess) return e;
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune[key] = P;
+            }
+        }
     }
+    if (parts_used) *parts_used = P;
+    return dispatch(a, P, num_sms, st);
 }
 
 }  // namespace fdirw

@@ -47,7 +47,7 @@ class fdirw_grid(ctypes.Structure):
 
 class fdirw_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("mem_limit", ctypes.c_uint64)]
+                ("mem_limit", ctypes.c_uint64), ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fdirw_info(ctypes.Structure):
@@ -56,7 +56,8 @@ class fdirw_info(ctypes.Structure):
                 ("lam", ctypes.c_double), ("max_face_sum", ctypes.c_double), ("cache_bytes", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("window_cells", ctypes.c_double),
                 ("kernels_ms", ctypes.c_float), ("last_gather_ms", ctypes.c_float),
-                ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double)]
+                ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double),
+                ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -142,7 +143,7 @@ def fdirw_stable_dt(shape, D, h: float = 1.0, device: int = -1) -> float:
 
 
 def fdirw_create(shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp32", h: float = 1.0,
-                 device: int = -1, stream=None, mem_limit: int = 0) -> int:
+                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0) -> int:
     """Returns the context handle (an integer address); release it with fdirw_destroy."""
     lib = load()
     nx, ny, nz = (int(v) for v in shape)
@@ -150,7 +151,7 @@ def fdirw_create(shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp3
     g = fdirw_grid(nx, ny, nz, float(h))
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
-    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit))
+    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), int(march_parts), 0)
     ctx = ctypes.c_void_p(0)
     _check(lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(_ptr(D)), float(dt_macro), int(window_R), int(n_sub),
                             ctypes.byref(o), ctypes.byref(ctx)))
@@ -207,11 +208,12 @@ class FDiRW:
     """Owns one context: ``FDiRW(shape, D, dt_macro, R, n_sub, prec)``; ``step(c_in, c_out, n)``; ``close()``."""
 
     def __init__(self, shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp32", h: float = 1.0,
-                 device: int = -1, stream=None, mem_limit: int = 0):
+                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0):
         self.shape = tuple(int(v) for v in shape)
         self.R = int(window_R)
         self.n = self.shape[0] * self.shape[1] * self.shape[2]
-        self.ctx = fdirw_create(self.shape, D, dt_macro, window_R, n_sub, prec, h, device, stream, mem_limit)
+        self.ctx = fdirw_create(self.shape, D, dt_macro, window_R, n_sub, prec, h, device, stream, mem_limit,
+                                march_parts)
 
     def kernels(self):
         fdirw_kernels(self.ctx)
