@@ -75,9 +75,11 @@ typedef struct {
     int32_t  device;      /* CUDA device ordinal; -1 = the calling thread's current device */
     void*    stream;      /* cudaStream_t for all work; NULL = legacy default stream */
     uint64_t mem_limit;   /* cap on the device bytes this context allocates; 0 = no cap */
-    int32_t  march_parts; /* FP32 march thread mapping: threads per window column, 1..3; 0 = autotune
-                             (each candidate timed once on the first build for a device, R and storage
-                             type, result cached for the process; that build synchronises the stream) */
+    int32_t  march_parts; /* FP32 march thread mapping: 1..3 = threads per window column; 4 = one thread
+                             per 2x2 block of window columns with the face coefficients in Tensor Memory;
+                             0 = autotune (each candidate timed once on the first build for a device, R
+                             and storage type, result cached for the process; that build synchronises the
+                             stream) */
     int32_t  reserved;    /* must be 0 */
 } fdirw_opts;
 
@@ -97,7 +99,7 @@ typedef struct {
     float    last_gather_ms; /* device time of the last gather launch */
     double   last_mass_in;   /* FP64 total of c_in at the last fdirw_step */
     double   last_mass_out;  /* FP64 total of c_out after the last fdirw_step (if it was computed) */
-    int32_t  march_parts;    /* thread mapping of the last kernel-cache build (threads per column) */
+    int32_t  march_parts;    /* thread mapping of the last kernel-cache build (see fdirw_opts) */
     int32_t  reserved;
 } fdirw_info;
 

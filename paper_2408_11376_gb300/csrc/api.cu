@@ -207,7 +207,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     fdirw_opts o{FDIRW_FP32, -1, nullptr, 0, 0, 0};
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP64 || o.prec > FDIRW_FP32_STORE_BF16) return fail(nullptr, FDIRW_ERR_ARG, "unknown prec");
-    if (o.march_parts < 0 || o.march_parts > 3) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 3]");
+    if (o.march_parts < 0 || o.march_parts > 4) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 4]");
 
     DeviceGuard dg(o.device);
     if (!dg.ok) return fail(nullptr, FDIRW_ERR_CUDA, "cannot select CUDA device " + std::to_string(o.device));

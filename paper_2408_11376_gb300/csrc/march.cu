@@ -333,6 +333,320 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
     }
 }
 
+// ---------------------------------------------------------------------------------------------------
+// 2x2-block mapping with TMEM-resident coefficients (mapping id 4).
+//
+// Each thread owns a 2x2 block of window columns (4*(2R+1) cells, u in registers), so the halo it
+// exchanges through shared memory per substep drops from 5 to 3 words per cell.  The 12 x/y face
+// coefficients of a block level (and the 4 diagonals, while they fit) no longer fit in registers; they
+// live in Tensor Memory, one TMEM lane per thread, and are streamed back level by level with
+// tcgen05.ld while the previous level computes (TMEM is read at ~2.5x the shared-memory rate on GB300).
+// The z faces and the remaining diagonals stay in registers.  The FP32 operations per cell and their
+// order are the same as in march_f32_kernel, so the results are bitwise identical.
+//
+// One CTA of 256 threads per SM (two threads per TMEM lane, 256 columns each; the CTA allocates all 512
+// columns once and frees them before it exits, and its shared-memory request keeps a second CTA off the
+// SM so an allocation never waits).
+template <int R>
+struct MapTm {
+    static constexpr int W1 = 2 * R + 1;
+    static constexpr int COLS = W1 * W1;
+    static constexpr int NB = R + 1;                      // blocks per window axis (last one half padding)
+    static constexpr int TPS = NB * NB;                   // threads per source
+    static constexpr int THREADS = 256;
+    static constexpr int SPB = THREADS / TPS;
+    static constexpr int LEVEL = 4 * THREADS;             // floats per level: [sub-column][thread]
+    static constexpr int BUF = W1 * LEVEL;                // floats per exchange buffer
+    static constexpr int LA0 = (256 - 12 * W1) / 4;
+    static constexpr int LA = LA0 < W1 ? LA0 : W1;        // levels whose diagonals live in TMEM
+    static constexpr int NR = W1 - LA;                    // levels whose diagonals live in registers
+    static constexpr size_t SMEM_USED = (size_t)2 * BUF * 4 + (size_t)SPB * COLS * 8;
+    static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+};
+
+__device__ __forceinline__ void tm_st16(uint32_t a, const uint32_t (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                    "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
+}
+__device__ __forceinline__ void tm_st8(uint32_t a, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]) : "memory");
+}
+__device__ __forceinline__ void tm_st4(uint32_t a, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+                 :: "r"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+}
+__device__ __forceinline__ void tm_ld16(uint32_t a, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(a));
+}
+__device__ __forceinline__ void tm_ld12(uint32_t a8, uint32_t a4, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(a8));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]) : "r"(a4));
+}
+// Waits for every outstanding tcgen05.ld of the thread; the registers are in-out operands so that no
+// use of them is scheduled before the wait.
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
+}
+
+// TMEM word offsets of a block level: levels < LA hold 16 words [12 faces, 4 diagonals] at 16k; the
+// remaining levels hold their 12 faces as 8 words in region A and 4 words in region B (every access is
+// aligned to its width).
+template <int R>
+__device__ __forceinline__ void tm_level_offsets(int k, uint32_t& o16, uint32_t& o8, uint32_t& o4) {
+    using M = MapTm<R>;
+    o16 = (uint32_t)(16 * k);
+    o8 = (uint32_t)(16 * M::LA + 8 * (k - M::LA));
+    o4 = (uint32_t)(16 * M::LA + 8 * M::NR + 4 * (k - M::LA));
+}
+
+template <int R>
+__device__ __forceinline__ void tm_load_level(uint32_t tbase, int k, uint32_t (&r)[16]) {
+    uint32_t o16, o8, o4;
+    tm_level_offsets<R>(k, o16, o8, o4);
+    if (k < MapTm<R>::LA) tm_ld16(tbase + o16, r);
+    else tm_ld12(tbase + o8, tbase + o4, r);
+}
+
+template <int R>
+__global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
+    using M = MapTm<R>;
+    constexpr int W1 = M::W1, COLS = M::COLS, NB = M::NB, TPS = M::TPS, SPB = M::SPB;
+    constexpr int LEVEL = M::LEVEL, PLANE = M::THREADS, BUF = M::BUF, LA = M::LA, NR = M::NR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* xbuf = reinterpret_cast<float*>(smem_raw);                         // [2][W1][4][256]
+    double* red = reinterpret_cast<double*>(smem_raw + (size_t)2 * BUF * 4);  // [SPB*COLS]
+    __shared__ uint32_t s_taddr;
+
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(dst) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const uint32_t tbase = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * (warp >> 2));
+
+    const bool active = t < SPB * TPS;
+    const int slot = active ? t / TPS : 0;
+    const int b = active ? t - slot * TPS : 0;
+    const int bi = b % NB, bj = b / NB;
+    // Neighbour blocks; the own index at the window edge (the matching faces are 0) and for idle threads.
+    const int tl = (active && bi > 0) ? t - 1 : t;
+    const int tr = (active && bi < NB - 1) ? t + 1 : t;
+    const int tb = (active && bj > 0) ? t - NB : t;
+    const int tt = (active && bj < NB - 1) ? t + NB : t;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
+
+    for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+        const int64_t first = a.src_begin + bt * SPB;
+        const int64_t s = first + slot;
+        const bool src_ok = active && s < a.src_end;
+        int sx = 0, sy = 0, sz = 0;
+        if (src_ok) {
+            sx = (int)(s % nx);
+            const int64_t r = s / nx;
+            sy = (int)(r % ny);
+            sz = (int)(r / ny);
+        }
+        // Window cell (x, y, k) -> global cell; validity; face coefficients (0 outside window/domain).
+        auto cell_ok = [&](int x, int y, int k) -> bool {
+            const int gx = sx - R + x, gy = sy - R + y, gz = sz - R + k;
+            return src_ok && x >= 0 && x < W1 && y >= 0 && y < W1 && k >= 0 && k < W1 &&
+                   gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+        };
+        auto gidx = [&](int x, int y, int k) -> int64_t {
+            return (int64_t)(sx - R + x) + (int64_t)nx * (sy - R + y) + nxy * (sz - R + k);
+        };
+        auto xface = [&](int x, int y, int k) -> float {   // face between window x and x+1
+            return (x + 1 < W1 && cell_ok(x, y, k) && sx - R + x + 1 < nx) ? __ldg(a.ax + gidx(x, y, k)) : 0.f;
+        };
+        auto yface = [&](int x, int y, int k) -> float {
+            return (y + 1 < W1 && cell_ok(x, y, k) && sy - R + y + 1 < ny) ? __ldg(a.ay + gidx(x, y, k)) : 0.f;
+        };
+        auto zface = [&](int x, int y, int k) -> float {
+            return (k + 1 < W1 && cell_ok(x, y, k) && sz - R + k + 1 < nz) ? __ldg(a.az + gidx(x, y, k)) : 0.f;
+        };
+
+        // Registers: state u[sub][k], z faces cz[sub][k] (+z face of the cell), diagonals of the levels
+        // whose TMEM slot has no room for them.  Sub-column sc = sxb + 2*syb at window (2bi+sxb, 2bj+syb).
+        float u[4][W1], cz[4][W1], amr[NR > 0 ? NR : 1][4];
+#pragma unroll
+        for (int sc = 0; sc < 4; sc++) {
+            const int x = 2 * bi + (sc & 1), y = 2 * bj + (sc >> 1);
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                cz[sc][k] = zface(x, y, k);
+                u[sc][k] = (src_ok && x == R && y == R && k == R) ? 1.f : 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < W1; k++) {
+            // faces of the level: rows (syb) for x, columns (sxb) for y
+            float f[16];
+            const int x0 = 2 * bi, y0 = 2 * bj;
+            f[0] = bi > 0 ? xface(x0 - 1, y0, k) : 0.f;       // L0
+            f[1] = xface(x0, y0, k);                           // I0
+            f[2] = xface(x0 + 1, y0, k);                       // R0
+            f[3] = bi > 0 ? xface(x0 - 1, y0 + 1, k) : 0.f;   // L1
+            f[4] = xface(x0, y0 + 1, k);                       // I1
+            f[5] = xface(x0 + 1, y0 + 1, k);                   // R1
+            f[6] = bj > 0 ? yface(x0, y0 - 1, k) : 0.f;       // B0
+            f[7] = yface(x0, y0, k);                           // J0
+            f[8] = yface(x0, y0 + 1, k);                       // T0
+            f[9] = bj > 0 ? yface(x0 + 1, y0 - 1, k) : 0.f;   // B1
+            f[10] = yface(x0 + 1, y0, k);                      // J1
+            f[11] = yface(x0 + 1, y0 + 1, k);                  // T1
+            // diagonals, same association as march_f32_kernel: -(((cxm+cxp)+(cym+cyp))+(czm+czp))
+            const float cxm[4] = {f[0], f[1], f[3], f[4]}, cxp[4] = {f[1], f[2], f[4], f[5]};
+            const float cym[4] = {f[6], f[9], f[7], f[10]}, cyp[4] = {f[7], f[10], f[8], f[11]};
+#pragma unroll
+            for (int sc = 0; sc < 4; sc++) {
+                const float zm = k > 0 ? cz[sc][k - 1] : 0.f;
+                f[12 + sc] = -(((cxm[sc] + cxp[sc]) + (cym[sc] + cyp[sc])) + (zm + cz[sc][k]));
+            }
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) w[q] = __float_as_uint(f[q]);
+            uint32_t o16, o8, o4;
+            tm_level_offsets<R>(k, o16, o8, o4);
+            if (k < LA) {
+                tm_st16(tbase + o16, w);
+            } else {
+                tm_st8(tbase + o8, w);
+                tm_st4(tbase + o4, w + 8);
+#pragma unroll
+                for (int sc = 0; sc < 4; sc++) amr[(k - LA) < NR ? k - LA : 0][sc] = f[12 + sc];
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+        for (int it = 0; it < a.n_sub; it++) {
+            float* buf = xbuf + (it & 1) * BUF;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < W1; k++)
+#pragma unroll
+                    for (int sc = 0; sc < 4; sc++) buf[k * LEVEL + sc * PLANE + t] = u[sc][k];
+            }
+            __syncthreads();
+            // cc: coefficients of level k (ready); cn: level k+1, loaded while level k computes.
+            uint32_t cc[16], cn[16];
+            tm_load_level<R>(tbase, 0, cc);
+            tm_wait_ld(cc);
+            float prev[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                if (k + 1 < W1) tm_load_level<R>(tbase, k + 1, cn);
+                const float* lv = buf + k * LEVEL;
+                const float l0 = lv[1 * PLANE + tl], l1 = lv[3 * PLANE + tl];
+                const float r0 = lv[0 * PLANE + tr], r1 = lv[2 * PLANE + tr];
+                const float b0 = lv[2 * PLANE + tb], b1 = lv[3 * PLANE + tb];
+                const float t0 = lv[0 * PLANE + tt], t1 = lv[1 * PLANE + tt];
+                float c[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) c[q] = __uint_as_float(cc[q]);
+                const float cxm[4] = {c[0], c[1], c[3], c[4]}, cxp[4] = {c[1], c[2], c[4], c[5]};
+                const float cym[4] = {c[6], c[9], c[7], c[10]}, cyp[4] = {c[7], c[10], c[8], c[11]};
+                const float uxm[4] = {l0, u[0][k], l1, u[2][k]}, uxp[4] = {u[1][k], r0, u[3][k], r1};
+                const float uym[4] = {b0, b1, u[0][k], u[1][k]}, uyp[4] = {u[2][k], u[3][k], t0, t1};
+                float nu[4];
+#pragma unroll
+                for (int sc = 0; sc < 4; sc++) {
+                    const float cur = u[sc][k];
+                    const float am = k < LA ? c[12 + sc] : amr[(k - LA) >= 0 ? k - LA : 0][sc];
+                    float v = am * cur;
+                    v = fmaf(cxm[sc], uxm[sc], v);
+                    v = fmaf(cxp[sc], uxp[sc], v);
+                    v = fmaf(cym[sc], uym[sc], v);
+                    v = fmaf(cyp[sc], uyp[sc], v);
+                    v = fmaf(k > 0 ? cz[sc][k > 0 ? k - 1 : 0] : 0.f, prev[sc], v);
+                    v = fmaf(cz[sc][k], k + 1 < W1 ? u[sc][k + 1 < W1 ? k + 1 : k] : 0.f, v);
+                    nu[sc] = __fadd_rn(cur, v);
+                }
+#pragma unroll
+                for (int sc = 0; sc < 4; sc++) { prev[sc] = u[sc][k]; u[sc][k] = nu[sc]; }
+                if (k + 1 < W1) {
+                    tm_wait_ld(cn);
+#pragma unroll
+                    for (int q = 0; q < 16; q++) cc[q] = cn[q];
+                }
+            }
+        }
+
+        // Epilogue: store, then per-column FP64 sums in k order (same order as march_f32_kernel).
+        float* sbuf = xbuf + (a.n_sub & 1) * BUF;
+        if (active) {
+#pragma unroll
+            for (int sc = 0; sc < 4; sc++) {
+                const int x = 2 * bi + (sc & 1), y = 2 * bj + (sc >> 1);
+#pragma unroll
+                for (int k = 0; k < W1; k++) {
+                    float stv = 0.f;
+                    if (cell_ok(x, y, k)) {
+                        const int64_t o = x + W1 * (y + W1 * k);
+                        stv = put(a.Q, a.store, o * a.g.n + gidx(x, y, k), u[sc][k]);
+                    }
+                    sbuf[k * LEVEL + sc * PLANE + t] = stv;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < SPB * COLS; c += blockDim.x) {
+            const int sl = c / COLS, cc = c - sl * COLS;
+            const int x = cc % W1, y = cc / W1;
+            const int tt2 = sl * TPS + (x >> 1) + NB * (y >> 1);
+            const int sc = (x & 1) + 2 * (y & 1);
+            double colsum = 0.0;
+#pragma unroll
+            for (int k = 0; k < W1; k++) colsum += (double)sbuf[k * LEVEL + sc * PLANE + tt2];
+            red[c] = colsum;
+        }
+        __syncthreads();
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
+        __syncthreads();
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr) : "memory");
+}
+
+template <int R>
+cudaError_t launch_tm(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    using M = MapTm<R>;
+    static_assert(M::SPB >= 1, "a source must fit one CTA");
+    const int64_t nsrc = a.src_end - a.src_begin;
+    if (nsrc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(march_tm_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tm_kernel<R>, M::THREADS, M::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm != 1) return cudaErrorInvalidConfiguration;   // TMEM allocation assumes one CTA per SM
+    const int64_t nbatch = (nsrc + M::SPB - 1) / M::SPB;
+    const int64_t grid = nbatch < (int64_t)num_sms ? nbatch : (int64_t)num_sms;
+    march_tm_kernel<R><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int R, int P>
 cudaError_t launch_f32(const MarchArgs& a, int num_sms, cudaStream_t st) {
     using M = Map32<R, P>;
@@ -356,6 +670,7 @@ cudaError_t launch_f32_p(const MarchArgs& a, int P, int num_sms, cudaStream_t st
         case 1: return launch_f32<R, 1>(a, num_sms, st);
         case 2: return launch_f32<R, 2>(a, num_sms, st);
         case 3: return launch_f32<R, 3>(a, num_sms, st);
+        case 4: return launch_tm<R>(a, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -427,8 +742,8 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     float best_ms = 1e30f;
     *best = default_parts(a.R);
-    for (int P = 1; P <= 3 && e == cudaSuccess; P++) {
-        if (P > W1) break;
+    for (int P = 1; P <= 4 && e == cudaSuccess; P++) {
+        if (P <= 3 && P > W1) continue;
         e = dispatch(warm, P, num_sms, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         if (e == cudaSuccess) e = dispatch(s, P, num_sms, st);
@@ -448,7 +763,7 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
     int P = 1;
     if (a.store != Store::F64) {
-        if (parts_req >= 1 && parts_req <= 3) {
+        if (parts_req >= 1 && parts_req <= 4) {
             P = parts_req;
         } else {
             int dev = 0;

@@ -47,7 +47,7 @@ def test_host_side_argument_checks(lib):
         assert fdirw.fdirw_last_error()
     g = fdirw.fdirw_grid(4, 4, 4, 1.0)
     assert lib.fdirw_create(ctypes.byref(g), None, 1.0, 2, 3, None, ctypes.byref(ctypes.c_void_p())) == fdirw.FDIRW_ERR_ARG
-    for bad_opts in (fdirw.fdirw_opts(7, -1, None, 0, 0, 0), fdirw.fdirw_opts(1, -1, None, 0, 4, 0)):
+    for bad_opts in (fdirw.fdirw_opts(7, -1, None, 0, 0, 0), fdirw.fdirw_opts(1, -1, None, 0, 5, 0)):
         rc = lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), 1.0, 2, 3, ctypes.byref(bad_opts),
                               ctypes.byref(ctypes.c_void_p()))
         assert rc == fdirw.FDIRW_ERR_ARG
