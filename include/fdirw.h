@@ -158,9 +158,29 @@ FDIRW_API int fdirw_get_info(fdirw_ctx* ctx, fdirw_info* out);
 FDIRW_API void fdirw_destroy(fdirw_ctx* ctx);
 
 /* Message of the last failed call on ctx, or of the last failed call on this host thread when ctx is
- * NULL (for failures of fdirw_create / fdirw_stable_dt).  Never NULL; the string stays valid until the
- * next call on the same context / thread. */
+ * NULL (for failures of fdirw_create / fdirw_stable_dt / fdirw_mass_noalloc).  Never NULL; the string
+ * stays valid until the next call on the same context / thread. */
 FDIRW_API const char* fdirw_last_error(const fdirw_ctx* ctx);
+
+/* FP64 total of a device field without allocating any memory.  The paper has no counterpart: this is a
+ * library service for callers that may not call cudaMalloc when they need the mass budget -- a host
+ * framework that owns and pre-partitions all device memory, a real-time loop in which an allocation (and
+ * the synchronisation it can imply) is not allowed, or a caller that holds no fdirw context (creating one
+ * allocates).  The reduction scratch is a fixed array compiled into the library: 2^14 FP64 partial sums
+ * (128 KiB per GPU, held from the library's load until the process exits), one per chunk of 2^16 cells.
+ *   c        : n float64 values in device memory of the current device (x fastest; any layout works)
+ *   n        : 0 <= n <= 2^30 (larger fields are rejected with FDIRW_ERR_ARG: they need more partials
+ *              than the fixed scratch holds)
+ *   mass_out : one float64 in device memory of the current device; receives the total
+ *   stream   : cudaStream_t to launch on (NULL = legacy default stream); the call is asynchronous
+ * The first call on a device looks the scratch address up (cudaGetSymbolAddress) and caches it: make that
+ * first call before any stream capture.  All calls share the scratch, so calls whose kernels may overlap
+ * on the GPU (unordered streams or host threads) race and can return wrong totals; order them.  Nothing in
+ * the scratch needs clearing (each call writes every partial it reads).  The reduction order is fixed,
+ * so the result is reproducible; it can differ from fdirw_mass in the last bits (different chunking).
+ * Errors: FDIRW_ERR_ARG (n out of range, NULL, misaligned or non-device pointers), FDIRW_ERR_CUDA; the
+ * message is available from fdirw_last_error(NULL). */
+FDIRW_API int fdirw_mass_noalloc(const double* c, int64_t n, double* mass_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -171,6 +171,11 @@ void release(fdirw_ctx* c) {
 
 }  // namespace
 
+int fdirw::set_thread_error(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
 extern "C" {
 
 const char* fdirw_last_error(const fdirw_ctx* ctx) {

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace fdirw {
@@ -17,6 +19,9 @@ struct Grid {
     int nx, ny, nz;
     int64_t n;     // nx*ny*nz
 };
+
+// Records msg as this host thread's last error (what fdirw_last_error(NULL) returns); returns code.
+int set_thread_error(int code, const std::string& msg);
 
 // ---------------------------------------------------------------- setup.cu
 // Checks D (finite, >= 0), computes FP64 harmonic-mean face conductances gx/gy/gz (+x/+y/+z face of each

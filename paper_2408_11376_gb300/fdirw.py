@@ -29,7 +29,7 @@ FDIRW_FP32_STORE_BF16 = 3
 PRECISIONS = {"fp64": FDIRW_FP64, "fp32": FDIRW_FP32, "fp16": FDIRW_FP32_STORE_FP16, "bf16": FDIRW_FP32_STORE_BF16}
 
 EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "fdirw_mass", "fdirw_read_kernels",
-            "fdirw_get_info", "fdirw_destroy", "fdirw_last_error")
+            "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfdirw.so")
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         lib.fdirw_destroy.restype = None
         lib.fdirw_last_error.argtypes = [vp]
         lib.fdirw_last_error.restype = ctypes.c_char_p
+        lib.fdirw_mass_noalloc.argtypes = [vp, i64, vp, vp]
         for name in EXPORTED:
             if name not in ("fdirw_destroy", "fdirw_last_error"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -195,6 +196,15 @@ def fdirw_get_info(ctx: int) -> dict:
 def fdirw_destroy(ctx: int) -> None:
     if ctx:
         load().fdirw_destroy(ctypes.c_void_p(ctx))
+
+
+def fdirw_mass_noalloc(c, mass_out, stream=None) -> None:
+    """FP64 total of the device field c written into the one-element device tensor mass_out, with no
+    allocation inside the library (fixed scratch; fields of up to 2^30 cells).  Asynchronous on stream."""
+    n = c.numel() if hasattr(c, "numel") else int(np.asarray(c).size)
+    st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    _check(load().fdirw_mass_noalloc(ctypes.c_void_p(_ptr(c)), int(n), ctypes.c_void_p(_ptr(mass_out)),
+                                     ctypes.c_void_p(st)))
 
 
 def fdirw_last_error(ctx: int | None = None) -> str:

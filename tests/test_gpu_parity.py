@@ -13,6 +13,12 @@ from paper_2408_11376_gb300 import FDiRW, FdirwError, fdirw, synth
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_2408_11376_gb300 import build
+    build.build()                      # no-op when libfdirw.so is up to date
+
 FIELD_TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-3}
 KERNEL_TOL = {"fp64": 1e-13, "fp32": 1e-5, "fp16": 2e-3, "bf16": 8e-3}
 DEV = "cuda:0"
