@@ -8,7 +8,7 @@ Metric: macro-steps/s of that job (the kernel build is amortised over the worklo
 timed with CUDA events on the stream the library launches on, inputs resident in HBM.  Extra keys give
 source-kernels/s (march kernel alone) and the steady-state macro-steps/s (gather + scale per step).
 
-  python bench.py [--steps K] [--warmup W] [--workload fdirw-192c-r8] [--prec fp32]
+  python bench.py [--steps K] [--warmup W] [--workload fdirw-192c-r8] [--prec bf16]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, bounded samples
   torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas (one per GPU), weak scaling
 """
@@ -91,6 +91,21 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The largest of every rank's time (all ranks get it); identity without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world_size: int, units_per_rank: float, max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    return world_size * units_per_rank * 1000.0 / max_ms
 
 
 def _dist():
@@ -211,11 +226,7 @@ def run_ours(args, w):
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
-    total_ms = start.elapsed_time(end)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(start.elapsed_time(end), pg, dev)
     info = times[-1][7]
     mass0 = float(np.sum(c_host))
     march_ms = statistics.mean(t[4] for t in times)
@@ -243,18 +254,18 @@ def run_ours(args, w):
             e2e_pass()
         ee.record(stream)
         torch.cuda.synchronize(dev)
-        e_ms = es.elapsed_time(ee) / args.e2e_steps
-        if pg:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": ws * w.steps * 1000.0 / e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+        e_ms = max_over_ranks(es.elapsed_time(ee) / args.e2e_steps, pg, dev)
+        e2e = {"value": job_rate(ws, w.steps, e_ms), "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                "d2h_bytes_per_step": 8 * N + 8}
 
     if rank != 0:
         if pg:
             pg.destroy_process_group()
         return 0
+
+    fp64 = None
+    if not args.no_fp64 and ws == 1:
+        fp64 = fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec=prec)
 
     peaks, peak_src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -263,7 +274,9 @@ def run_ours(args, w):
     flops = FLOP_PER_CELL_SUBSTEP * w.n_sub * info["window_cells"]
     achieved = flops / (march_ms * 1e-3) / 1e12
     clocks = clk.summary()
-    roofline = {"bound": "alu", "kernel": "march_f32_kernel<R>" if prec != "fp64" else "march_f64_kernel<R>",
+    kname = ("march_f64_kernel<R>" if prec == "fp64" else
+             "march_tm_kernel<R>" if info["march_parts"] == 4 else f"march_f32_kernel<R,{info['march_parts']}>")
+    roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                 "traffic": args.traffic,
                 "peak_source": f"FP32 pipe: {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz "
@@ -282,7 +295,7 @@ def run_ours(args, w):
                          "recomputing every kernel each step"}
 
     n_launch = 4 + 1 + 2 + 2 * w.steps + 2      # conductance + 3 coef, march, mass(in), scale+gather per step, mass(out)
-    value = ws * w.steps * args.steps * 1000.0 / total_ms
+    value = job_rate(ws, w.steps * args.steps, total_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -296,13 +309,60 @@ def run_ours(args, w):
         "phase_ms": {"create": statistics.mean(t[0] for t in times), "kernels": statistics.mean(t[1] for t in times),
                      "march_kernel": march_ms, "steps": steps_ms, "gather_kernel": gather_ms},
         "mass_rel_err": abs(times[-1][6] - mass0) / mass0,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu_baseline": fp64,
         "gpu_launches": n_launch * args.steps, "clocks": clocks,
     }
+    if fp64:
+        line["speedup_vs_fp64_gpu"] = value / fp64["macro_steps_per_s"]
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
+    """The plain FP64 GPU FDiRW (FP64 march, FP64 cache, FP64 gather) run once over the workload, timed
+    with CUDA events, keeping its field after every macro step; then every reduced-precision mode is run
+    step by step and compared with it (relative L2 per step, and the mass budget)."""
+    N = c0.numel()
+    ref = torch.empty((w.steps, N), dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, "fp64", stream=stream)
+        ev[1].record(stream)
+        fdirw.fdirw_kernels(ctx)
+        ev[2].record(stream)
+        cur = c0
+        for t in range(w.steps):
+            fdirw.fdirw_step(ctx, cur, ref[t], 1)
+            cur = ref[t]
+        ev[3].record(stream)
+        info = fdirw.fdirw_get_info(ctx)
+        fdirw.fdirw_destroy(ctx)
+    stream.synchronize()
+    job_ms = ev[0].elapsed_time(ev[3])
+    out = {"macro_steps_per_s": 1000.0 * w.steps / job_ms, "job_ms": job_ms,
+           "source_kernels_per_s": N / (info["kernels_ms"] * 1e-3), "march_kernel_ms": info["kernels_ms"],
+           "steps_ms": ev[2].elapsed_time(ev[3]), "cache_gb": info["cache_bytes"] / 1e9, "rel_l2_vs_fp64": {}}
+    mass0 = float(c0.sum().item())
+    out["mass_rel_err"] = abs(float(ref[-1].sum().item()) - mass0) / mass0
+    for p in ("fp32", "fp16", "bf16"):
+        with torch.cuda.stream(stream):
+            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, p, stream=stream)
+            a = torch.empty_like(c0)
+            errs = []
+            cur = c0
+            for t in range(w.steps):
+                fdirw.fdirw_step(ctx, cur, a, 1)
+                errs.append(float((torch.linalg.vector_norm(a - ref[t]) / torch.linalg.vector_norm(ref[t])).item()))
+                cur = a.clone()
+            m = fdirw.fdirw_mass(ctx, a)
+            fdirw.fdirw_destroy(ctx)
+        out["rel_l2_vs_fp64"][p] = {"max_over_steps": max(errs), "last": errs[-1], "mass_rel_err": abs(m - mass0) / mass0}
+    del ref
+    torch.cuda.empty_cache()
+    return out
 
 
 def main(argv=None):
@@ -312,10 +372,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fdirw-192c-r8")
-    ap.add_argument("--prec", choices=["fp64", "fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "fp16", "bf16"], default="bf16",
+                    help="kernel-cache storage (BF16 meets 1e-5 rel L2 vs FP64 on fdirw-192c-r8, see the fp64 leg)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU baseline and accuracy leg")
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per march launch from an ncu capture of the current kernel")
