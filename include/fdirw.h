@@ -162,6 +162,48 @@ FDIRW_API void fdirw_destroy(fdirw_ctx* ctx);
  * stays valid until the next call on the same context / thread. */
 FDIRW_API const char* fdirw_last_error(const fdirw_ctx* ctx);
 
+/* ---------------------------------------------------------------------------------------------------
+ * Learned surrogate of the spreading kernel (no counterpart in the paper: it predicts the column of p of
+ * Sec. 3.1 that the FD march computes, and the march stays its fallback).
+ *
+ * Network: features of source s on the 17^3 patch centred on s -- clamp(log10 D / 8 + 1, -0.5, 1.5) and a
+ * domain mask in the domain (0 outside), and a source marker at the centre -- then 4 convolutions (3^3
+ * taps, 16 -> 16 channels, zero padding, bias) with ReLU after the first three, BF16 weights and
+ * activations, FP32 accumulation on the tensor cores; head y = exp(z[channel 0]) on in-domain cells.
+ * Gate: a prediction is accepted when |sum y - 1| <= 1e-3 (FP64 sum).
+ * Parameters (host float arrays of FDIRW_NET_NPARAM values): weights [4][27][16 co][16 ci] (tap index
+ * (dx+1) + 3(dy+1) + 9(dz+1)), then biases [4][16].  Only output channel 0 of layer 4 is used (its
+ * other weights and biases must be 0 and are kept at 0 by training).
+ * Sources are host int64 arrays of cell indices of the context's grid; per call at most 1024 sources.
+ * Kernel arrays are n * 17^3 float64 values, offset o = (i-8, j-8, k-8) at index i + 17 (j + 17 k), host or
+ * device memory.  The calls run on the context's stream and synchronise it before returning. */
+#define FDIRW_NET_NPARAM (4 * 27 * 16 * 16 + 4 * 16)
+typedef struct fdirw_net fdirw_net;
+
+/* Creates a network from host parameters on `device` (-1 = current).  Errors: FDIRW_ERR_ARG, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_net_create(const float* params, int32_t device, fdirw_net** out);
+/* Copies the current FP32 parameters to host memory. */
+FDIRW_API int fdirw_net_params(fdirw_net* net, float* params_out);
+FDIRW_API void fdirw_net_destroy(fdirw_net* net);
+/* Predicted kernels (unnormalised head output y, nullable), their FP64 masses (host, nullable) and gate
+ * decisions (host int32, nullable) for n sources of ctx's domain. */
+FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                                double* kernels_out, double* mass_out, int32_t* accept_out);
+/* Gradients of the training loss sum_i sum_v (k_iv + 1e-7)(z_iv - ln(k_iv + 1e-7))^2 (k = targets, z = the
+ * head's pre-exponential output, in-domain cells only) with respect to the parameters (host,
+ * FDIRW_NET_NPARAM floats, nullable) and the mean loss over the batch (host, nullable). */
+FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                                  const double* targets, float* grads_out, double* loss_out);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean of those gradients; loss_out as above. */
+FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                                   const double* targets, float lr, double* loss_out);
+/* Builds the kernel cache with the network: every source is predicted, accepted predictions are stored
+ * (rounded to the storage type, sigma = 1 / FP64 sum of the stored values), and the rejected sources are
+ * marched with the FD march.  Needs window_R = 8 and an FP32-march precision.  accepted_out (host,
+ * nullable) receives the number of accepted sources.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_NOMEM,
+ * FDIRW_ERR_CUDA, FDIRW_ERR_TIMEOUT (a convolution's bounded wait on its MMAs gave up). */
+FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* ctx, fdirw_net* net, int64_t* accepted_out);
+
 /* FP64 total of a device field without allocating any memory.  The paper has no counterpart: this is a
  * library service for callers that may not call cudaMalloc when they need the mass budget -- a host
  * framework that owns and pre-partitions all device memory, a real-time loop in which an allocation (and

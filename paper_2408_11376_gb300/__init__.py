@@ -9,8 +9,8 @@ diffusion is marched over a local window for one macro step to give that source'
 * ``synth``  -- seeded synthetic microstructures, diffusivity maps and initial fields.
 """
 from . import synth  # noqa: F401
-from .fdirw import (FDiRW, FdirwError, PRECISIONS, fdirw_create, fdirw_destroy, fdirw_get_info,  # noqa: F401
+from .fdirw import (FDiRW, FdirwError, Net, PRECISIONS, fdirw_create, fdirw_destroy, fdirw_get_info,  # noqa: F401
                     fdirw_kernels, fdirw_last_error, fdirw_mass, fdirw_read_kernels, fdirw_stable_dt, fdirw_step)
 
-__all__ = ["FDiRW", "FdirwError", "PRECISIONS", "fdirw_create", "fdirw_destroy", "fdirw_get_info", "fdirw_kernels",
+__all__ = ["FDiRW", "FdirwError", "Net", "PRECISIONS", "fdirw_create", "fdirw_destroy", "fdirw_get_info", "fdirw_kernels",
            "fdirw_last_error", "fdirw_mass", "fdirw_read_kernels", "fdirw_stable_dt", "fdirw_step", "synth"]

@@ -3,6 +3,7 @@
 // validates, allocates, copies and launches.
 #include "fdirw.h"
 #include "fdirw_internal.h"
+#include "ctx.h"
 
 #include <algorithm>
 #include <cmath>
@@ -13,35 +14,6 @@
 using fdirw::Grid;
 using fdirw::Store;
 
-struct fdirw_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    Grid g{};
-    double h = 1.0, dt_macro = 0.0, dt_sub = 0.0, lam = 0.0, max_face_sum = 0.0;
-    int R = 0, n_sub = 0;
-    int prec = FDIRW_FP32;
-    Store store = Store::F32;
-    int num_sms = 0;
-    int parts_req = 0, parts_used = 0;
-    uint64_t mem_limit = 0, allocated = 0;
-    void* coef[3] = {nullptr, nullptr, nullptr};   // lam * g: float (mixed) or double (FP64)
-    void* Q = nullptr;
-    uint64_t q_bytes = 0;
-    double* sigma = nullptr;
-    void* chat = nullptr;                           // padded sigma*c: double or float2
-    double* cbuf = nullptr;                         // staging for host fields
-    double* partials = nullptr;                     // kMassBlocks
-    double* dmass = nullptr;                        // 1 double
-    int64_t* dsrc = nullptr;
-    double* dkout = nullptr;
-    int64_t kcap = 0;
-    bool kernels_ready = false;
-    bool kernels_timed = false, gather_timed = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double window_cells = 0.0;
-    double mass_in = NAN, mass_out = NAN;
-    std::string err;
-};
 
 namespace {
 
@@ -164,12 +136,24 @@ void release(fdirw_ctx* c) {
     p = c->cbuf; dfree(p); c->cbuf = nullptr;
     p = c->partials; dfree(p); c->partials = nullptr;
     p = c->dmass; dfree(p); c->dmass = nullptr;
+    p = c->Dd; dfree(p); c->Dd = nullptr;
     p = c->dsrc; dfree(p); c->dsrc = nullptr;
     p = c->dkout; dfree(p); c->dkout = nullptr;
     for (auto& e : c->ev) if (e) { cudaEventDestroy(e); e = nullptr; }
 }
 
 }  // namespace
+
+int fdirw::ensure_cache(fdirw_ctx* c) {
+    if (c->Q) return FDIRW_OK;
+    const uint64_t W = (uint64_t)(2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
+    c->q_bytes = W * (uint64_t)c->g.n * (uint64_t)fdirw::store_bytes(c->store);
+    const int rc = dalloc(c, &c->Q, c->q_bytes, "kernel cache");
+    if (rc != FDIRW_OK) { c->q_bytes = 0; return rc; }
+    // Entries whose source lies outside the domain are never written by the march: zero them once.
+    FDIRW_CUDA(c, cudaMemsetAsync(c->Q, 0, c->q_bytes, c->stream));
+    return FDIRW_OK;
+}
 
 int fdirw::set_thread_error(int code, const std::string& msg) {
     g_err = msg;
@@ -274,6 +258,11 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
         }
     }
     const fdirw::Pad pad = fdirw::make_pad(c->g, c->R);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&c->Dd), n * 8, "D copy")) != FDIRW_OK) return bail(rc);
+    {
+        cudaError_t e = cudaMemcpyAsync(c->Dd, D_map, n * 8, cudaMemcpyDefault, c->stream);
+        if (e != cudaSuccess) { c->err = cuda_msg("copy D_map", e); return bail(FDIRW_ERR_CUDA); }
+    }
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->sigma), n * 8, "sigma")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, &c->chat, (uint64_t)pad.n * 8, "scaled field")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->cbuf), n * 8, "field staging")) != FDIRW_OK) return bail(rc);
@@ -292,14 +281,8 @@ int fdirw_kernels(fdirw_ctx* c) {
     if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
     DeviceGuard dg(c->device);
     if (c->R == 0) { c->kernels_ready = true; return FDIRW_OK; }
-    const uint64_t W = (uint64_t)(2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
-    if (!c->Q) {
-        c->q_bytes = W * (uint64_t)c->g.n * (uint64_t)fdirw::store_bytes(c->store);
-        const int rc = dalloc(c, &c->Q, c->q_bytes, "kernel cache");
-        if (rc != FDIRW_OK) { c->q_bytes = 0; return rc; }
-        // Entries whose source lies outside the domain are never written by the march: zero them once.
-        FDIRW_CUDA(c, cudaMemsetAsync(c->Q, 0, c->q_bytes, c->stream));
-    }
+    const int rc = fdirw::ensure_cache(c);
+    if (rc != FDIRW_OK) return rc;
     fdirw::MarchArgs a{};
     a.g = c->g;
     a.R = c->R;
@@ -318,6 +301,7 @@ int fdirw_kernels(fdirw_ctx* c) {
     a.sigma = c->sigma;
     a.src_begin = 0;
     a.src_end = c->g.n;
+    a.list = nullptr;
     FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     FDIRW_CUDA(c, fdirw::launch_march(a, c->num_sms, c->parts_req, c->stream, &c->parts_used));
     FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));

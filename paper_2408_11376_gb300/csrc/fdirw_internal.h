@@ -45,6 +45,7 @@ struct MarchArgs {
     Store store;
     double* sigma;        // N: 1 / FP64 sum of the stored values of each source
     int64_t src_begin, src_end;
+    const int64_t* list;  // nullable: march sources list[src_begin..src_end) instead of that range
 };
 // parts_req: threads per window column for the FP32 march (1..3), or 0 to autotune (timed once per
 // device, R and storage, then cached); parts_used receives the mapping launched.

@@ -79,14 +79,14 @@ __device__ __forceinline__ float put(void* Q, Store st, int64_t idx, float v) {
 // warp w takes slots w, w + nwarps, ...; lane l sums columns l, l + 32, ...; then a xor-butterfly.
 template <int COLS, int SPB>
 __device__ __forceinline__ void finish_sigma(const double* red, int64_t batch_first, int64_t src_end,
-                                             double* sigma) {
+                                             const int64_t* list, double* sigma) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int slot = warp; slot < SPB; slot += nwarps) {
         double acc = 0.0;
         for (int c = lane; c < COLS; c += 32) acc += red[slot * COLS + c];
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         const int64_t s = batch_first + slot;
-        if (lane == 0 && s < src_end) sigma[s] = acc > 0.0 ? 1.0 / acc : 0.0;
+        if (lane == 0 && s < src_end) sigma[list ? list[s] : s] = acc > 0.0 ? 1.0 / acc : 0.0;
     }
 }
 
@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
 
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
         const int64_t first = a.src_begin + b * SPB;
-        const int64_t s = first + slot;
+        int64_t s = first + slot;
         const bool src_ok = active && s < a.src_end;
+        if (src_ok && a.list) s = a.list[s];       // explicit source list (e.g. the surrogate's rejects)
         int sx = 0, sy = 0, sz = 0;
         if (src_ok) {
             sx = (int)(s % nx);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
             red[c] = colsum;
         }
         __syncthreads();
-        finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.list, a.sigma);
         __syncthreads();   // red and xbuf are reused by the next batch
     }
 }
@@ -253,8 +254,9 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
 
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
         const int64_t first = a.src_begin + b * SPB;
-        const int64_t s = first + slot;
+        int64_t s = first + slot;
         const bool src_ok = active && s < a.src_end;
+        if (src_ok && a.list) s = a.list[s];       // explicit source list (e.g. the surrogate's rejects)
         int sx = 0, sy = 0, sz = 0;
         if (src_ok) {
             sx = (int)(s % nx);
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
         }
         if (active) red[t] = colsum;
         __syncthreads();
-        finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.list, a.sigma);
         __syncthreads();
     }
 }
@@ -456,8 +458,9 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
 
     for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
         const int64_t first = a.src_begin + bt * SPB;
-        const int64_t s = first + slot;
+        int64_t s = first + slot;
         const bool src_ok = active && s < a.src_end;
+        if (src_ok && a.list) s = a.list[s];       // explicit source list (e.g. the surrogate's rejects)
         int sx = 0, sy = 0, sz = 0;
         if (src_ok) {
             sx = (int)(s % nx);
@@ -619,7 +622,7 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
             red[c] = colsum;
         }
         __syncthreads();
-        finish_sigma<COLS, SPB>(red, first, a.src_end, a.sigma);
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.list, a.sigma);
         __syncthreads();
     }
 

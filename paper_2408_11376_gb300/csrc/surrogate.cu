@@ -1,0 +1,720 @@
+// Learned surrogate of the per-source spreading kernel (the network itself has no counterpart in the
+// paper; what it predicts is the column of p of Sec. 3.1, and the explicit FD march stays its fallback).
+//
+// Network (per source s, a 17^3 patch centred on s): features [log10 D / 8 + 1, domain mask, source
+// marker] (16 channels, 13 zero) -> 4 x { conv3d 3^3, 16 -> 16 channels, zero padding, + bias } with
+// ReLU after layers 1-3 -> head y = exp(z_4[channel 0]) on in-domain cells.  Gate: accept the prediction
+// when |sum y - 1| <= 1e-3 (FP64); the stored kernel is then renormalised like the FD kernels.
+//
+// Tensor-core convolution (conv_kernel): implicit GEMM per 128-voxel tile, M = 128 voxels, N = 16 output
+// channels, K = 16 input channels per tap, 27 tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM)
+// per tile.  Activations are kept in a zero-halo 19^3 volume split into two 8-channel halves, so every
+// voxel row is 16 bytes and each of the 27 tap-shifted views of a plane ring is a valid K-major,
+// no-swizzle operand (LBO = distance between the halves, SBO = 8 rows) -- no im2col copy.  One thread
+// issues the MMAs, tcgen05.commit signals an mbarrier, and 4 warps drain the accumulators with
+// tcgen05.ld.  The same kernel runs the input gradient (flipped, transposed taps, ReLU mask in the
+// epilogue).  The weight gradient (a reduction over voxels with M = 16 channels, too thin for UMMA)
+// runs on the FP32 pipe with a fixed-order two-stage reduction.
+#include "ctx.h"
+#include "tc.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+using fdirw::Store;
+
+namespace fdirw {
+namespace net {
+
+constexpr int SP = 17, SH = 8, PP = 19, PLANE = PP * PP, VOL = PP * PLANE, KV = SP * SP * SP;
+constexpr int GUARD = 64, ROWS = GUARD + VOL + GUARD;            // rows per 8-channel half of a patch
+constexpr int64_t PATCH = 2 * (int64_t)ROWS * 8;                   // bf16 elements per patch activation
+constexpr int RSLOT = 4, RROWS = GUARD + RSLOT * PLANE + GUARD;    // plane ring in shared memory
+constexpr int NTILE = 3;                                           // 128-row tiles per plane (384 >= 361)
+constexpr int NL = 4, C = 16, TAPS = 27;
+constexpr int NW = NL * TAPS * C * C;                              // weights [layer][tap][co][ci]
+constexpr int NPARAM = NW + NL * C;                                // + biases [layer][co]
+constexpr int WCAN = TAPS * C * C;                                 // bf16 per layer, canonical layout
+constexpr int MAX_BATCH = 1024;
+constexpr size_t CONV_SMEM = (size_t)2 * RROWS * 16 + (size_t)TAPS * 512 + 16;
+constexpr uint32_t WAIT_LIMIT = 1u << 26;                          // mbarrier polls before giving up
+constexpr double GATE_TOL = 1e-3;
+
+enum Mode { FWD_RELU = 0, FWD_HEAD = 1, DGRAD = 2 };
+
+struct ConvArgs {
+    const __nv_bfloat16* in;        // [batch][PATCH]
+    __nv_bfloat16* out;             // [batch][PATCH] (FWD_RELU, DGRAD)
+    float* zhead;                   // [batch][KV]    (FWD_HEAD)
+    const __nv_bfloat16* mask_act;  // [batch][PATCH] (DGRAD: relu mask = this activation > 0)
+    const __nv_bfloat16* w;         // [TAPS][512 B] canonical layout of one layer
+    const float* bias;              // [C]
+    int batch;
+    int mode;
+    int* err;
+};
+
+__device__ __forceinline__ uint4 pack8(const float* v) {
+    uint4 r;
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    memcpy(&r, h, 16);
+    return r;
+}
+
+__global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t* ring0 = sm;
+    uint8_t* ring1 = sm + (size_t)RROWS * 16;
+    uint8_t* wsm = ring1 + (size_t)RROWS * 16;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(wsm + TAPS * 512);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    if (t == 0) {
+        tc::mbar_init(tc::smem_u32(mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const uint4* wsrc = reinterpret_cast<const uint4*>(a.w);
+    for (int i = t; i < TAPS * 512 / 16; i += 128) reinterpret_cast<uint4*>(wsm)[i] = wsrc[i];
+    const uint4 z4 = make_uint4(0, 0, 0, 0);
+    for (int i = t; i < GUARD; i += 128) {     // guard rows (read only by halo outputs, which are dropped)
+        reinterpret_cast<uint4*>(ring0)[i] = z4;
+        reinterpret_cast<uint4*>(ring1)[i] = z4;
+        reinterpret_cast<uint4*>(ring0)[RROWS - GUARD + i] = z4;
+        reinterpret_cast<uint4*>(ring1)[RROWS - GUARD + i] = z4;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t mb = tc::smem_u32(mbar);
+    const uint32_t r0 = tc::smem_u32(ring0), wsa = tc::smem_u32(wsm);
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 16);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int p = blockIdx.x; p < a.batch && ok; p += gridDim.x) {
+        const uint4* in0 = reinterpret_cast<const uint4*>(a.in + (int64_t)p * PATCH);
+        const uint4* in1 = in0 + ROWS;
+        auto load_plane = [&](int zz) {
+            const int slot = zz & 3;
+            for (int i = t; i < 2 * PLANE; i += 128) {
+                const int h = i >= PLANE, r = i - h * PLANE;
+                const uint4 v = (h ? in1 : in0)[GUARD + zz * PLANE + r];
+                reinterpret_cast<uint4*>(h ? ring1 : ring0)[GUARD + slot * PLANE + r] = v;
+            }
+        };
+        load_plane(0);
+        load_plane(1);
+        for (int z = 1; z <= SP && ok; z++) {
+            load_plane(z + 1);
+            tc::fence_async_smem();
+            __syncthreads();
+            if (t == 0) {
+                tc::fence_after_sync();
+#pragma unroll 1
+                for (int tile = 0; tile < NTILE; tile++) {
+#pragma unroll 1
+                    for (int tap = 0; tap < TAPS; tap++) {
+                        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                        const int row = GUARD + ((z + dz) & 3) * PLANE + tile * 128 + dx + PP * dy;
+                        const uint64_t ad = tc::smem_desc(r0 + (uint32_t)row * 16, RROWS * 16, 128);
+                        const uint64_t bd = tc::smem_desc(wsa + (uint32_t)tap * 512, 256, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(tile * 16), ad, bd, IDESC, tap > 0 ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(mb);
+            }
+            bool done = tc::mbar_wait(mb, phase, WAIT_LIMIT);
+            phase ^= 1u;
+            ok = __syncthreads_and(done ? 1 : 0) != 0;
+            if (!ok) {
+                if (t == 0) atomicExch(a.err, 1);
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int tile = 0; tile < NTILE; tile++) {
+                float v[16];
+                tc::tmem_ld16_wait(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(tile * 16), v);
+                const int r = tile * 128 + 32 * warp + lane;
+                if (r >= PLANE) continue;
+                const int x = r % PP, y = r / PP;
+                const bool interior = x >= 1 && x <= SP && y >= 1 && y <= SP;
+                const int64_t row = GUARD + (int64_t)z * PLANE + r;
+                if (a.mode == FWD_HEAD) {
+                    if (interior) a.zhead[(int64_t)p * KV + ((z - 1) * SP + (y - 1)) * SP + (x - 1)] = v[0] + a.bias[0];
+                    continue;
+                }
+                float o[16];
+                if (a.mode == FWD_RELU) {
+#pragma unroll
+                    for (int c = 0; c < 16; c++) o[c] = interior ? fmaxf(v[c] + a.bias[c], 0.f) : 0.f;
+                } else {
+                    const uint4* m = reinterpret_cast<const uint4*>(a.mask_act + (int64_t)p * PATCH);
+                    uint4 mv[2] = {m[row], m[ROWS + row]};
+                    const __nv_bfloat16* mb16 = reinterpret_cast<const __nv_bfloat16*>(mv);
+#pragma unroll
+                    for (int c = 0; c < 16; c++) o[c] = (interior && __bfloat162float(mb16[c]) > 0.f) ? v[c] : 0.f;
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.out + (int64_t)p * PATCH);
+                dst[row] = pack8(o);
+                dst[ROWS + row] = pack8(o + 8);
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+// Row of padded voxel (i, j, k) of the 17^3 patch (0-based interior coordinates).
+__device__ __forceinline__ int prow(int i, int j, int k) { return GUARD + (i + 1) + PP * ((j + 1) + PP * (k + 1)); }
+
+struct PatchPos {
+    int sx, sy, sz;
+};
+__device__ __forceinline__ PatchPos pos_of(int64_t s, const Grid& g) {
+    PatchPos q;
+    q.sx = (int)(s % g.nx);
+    const int64_t r = s / g.nx;
+    q.sy = (int)(r % g.ny);
+    q.sz = (int)(r / g.ny);
+    return q;
+}
+__device__ __forceinline__ bool in_domain(const PatchPos& q, int i, int j, int k, const Grid& g, int64_t* gi) {
+    const int x = q.sx - SH + i, y = q.sy - SH + j, z = q.sz - SH + k;
+    if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) return false;
+    *gi = (int64_t)x + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
+    return true;
+}
+
+// Feature patches (channels 0-2 of the first half; everything else stays zero from a prior memset).
+__global__ void features_kernel(const double* __restrict__ D, Grid g, const int64_t* __restrict__ src, int n,
+                                __nv_bfloat16* __restrict__ act) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * KV;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / KV), v = (int)(idx % KV);
+        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+        const PatchPos q = pos_of(src[b], g);
+        int64_t gi;
+        __nv_bfloat16* rowp = act + (int64_t)b * PATCH + (int64_t)prow(i, j, k) * 8;
+        if (in_domain(q, i, j, k, g, &gi)) {
+            const double d = D[gi];
+            double f = d > 0.0 ? log10(d) / 8.0 + 1.0 : -0.5;
+            f = f < -0.5 ? -0.5 : (f > 1.5 ? 1.5 : f);
+            rowp[0] = __float2bfloat16_rn((float)f);
+            rowp[1] = __float2bfloat16_rn(1.f);
+        }
+        if (i == SH && j == SH && k == SH) rowp[2] = __float2bfloat16_rn(1.f);
+    }
+}
+
+// Head for prediction: y = exp(z) in the domain, FP64 mass, gate; kernels_out [n][KV] (nullable).
+__global__ void __launch_bounds__(256) head_predict_kernel(const float* __restrict__ zhead, Grid g,
+                                                           const int64_t* __restrict__ src, double* __restrict__ kout,
+                                                           double* __restrict__ mass, int* __restrict__ accept) {
+    __shared__ double sh[8];
+    const int b = blockIdx.x;
+    const PatchPos q = pos_of(src[b], g);
+    double acc = 0.0;
+    for (int v = threadIdx.x; v < KV; v += blockDim.x) {
+        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+        int64_t gi;
+        const double y = in_domain(q, i, j, k, g, &gi) ? (double)expf(zhead[(int64_t)b * KV + v]) : 0.0;
+        if (kout) kout[(int64_t)b * KV + v] = y;
+        acc += y;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0) {
+            mass[b] = w;
+            accept[b] = fabs(w - 1.0) <= GATE_TOL ? 1 : 0;
+        }
+    }
+}
+
+// Head for training: loss sum_v (k + eps)(z - ln(k + eps))^2 over in-domain cells (a squared error on
+// ln y weighted by the target kernel's mass; a loss on y itself has dL/dz proportional to y, which
+// vanishes where the prediction is small) and its gradient 2 (k + eps)(z - ln(k + eps)) (channel 0).
+constexpr double LOSS_EPS = 1e-7;
+__global__ void __launch_bounds__(256) head_train_kernel(const float* __restrict__ zhead, Grid g,
+                                                         const int64_t* __restrict__ src, const double* __restrict__ tgt,
+                                                         __nv_bfloat16* __restrict__ grad, double* __restrict__ loss) {
+    __shared__ double sh[8];
+    const int b = blockIdx.x;
+    const PatchPos q = pos_of(src[b], g);
+    double acc = 0.0;
+    for (int v = threadIdx.x; v < KV; v += blockDim.x) {
+        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+        int64_t gi;
+        const bool ind = in_domain(q, i, j, k, g, &gi);
+        const double w = tgt[(int64_t)b * KV + v] + LOSS_EPS;
+        const double d = ind ? (double)zhead[(int64_t)b * KV + v] - log(w) : 0.0;
+        acc += w * d * d;
+        grad[(int64_t)b * PATCH + (int64_t)prow(i, j, k) * 8] = __float2bfloat16_rn((float)(2.0 * w * d));
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0) loss[b] = w;
+    }
+}
+
+// Head for the kernel cache: accepted predictions are rounded to the storage type and written into
+// Q[o][s + o]; sigma_s = 1 / FP64 sum of the stored values (the march's renormalisation).
+__global__ void __launch_bounds__(256) head_store_kernel(const float* __restrict__ zhead, Grid g,
+                                                         const int64_t* __restrict__ src, const int* __restrict__ accept,
+                                                         void* Q, Store st, double* __restrict__ sigma) {
+    __shared__ double sh[8];
+    const int b = blockIdx.x;
+    if (!accept[b]) return;
+    const int64_t s = src[b];
+    const PatchPos q = pos_of(s, g);
+    double acc = 0.0;
+    for (int v = threadIdx.x; v < KV; v += blockDim.x) {
+        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+        int64_t gi;
+        if (!in_domain(q, i, j, k, g, &gi)) continue;
+        const float y = expf(zhead[(int64_t)b * KV + v]);
+        const int64_t idx = (int64_t)v * g.n + gi;       // offset o = (i-8, j-8, k-8), destination gi
+        float stored;
+        if (st == Store::F32) { reinterpret_cast<float*>(Q)[idx] = y; stored = y; }
+        else if (st == Store::F16) { const __half h = __float2half_rn(y); reinterpret_cast<__half*>(Q)[idx] = h; stored = __half2float(h); }
+        else { const __nv_bfloat16 h = __float2bfloat16_rn(y); reinterpret_cast<__nv_bfloat16*>(Q)[idx] = h; stored = __bfloat162float(h); }
+        acc += (double)stored;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0) sigma[s] = w > 0.0 ? 1.0 / w : 0.0;
+    }
+}
+
+// Weight gradient of one layer: partial[tap][blk][co][ci] = sum over this block's voxels of
+// act[v + tap][ci] * grad[v][co]; the voxels of the batch (interior only) are split into fixed chunks.
+constexpr int WG_BLOCKS = 64, WG_CHUNK = 64;
+__global__ void __launch_bounds__(256) wgrad_partial_kernel(const __nv_bfloat16* __restrict__ act,
+                                                            const __nv_bfloat16* __restrict__ grad, int n,
+                                                            float* __restrict__ partial) {
+    __shared__ float As[WG_CHUNK][C + 1], Gs[WG_CHUNK][C + 1];
+    const int tap = blockIdx.x, blk = blockIdx.y;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int co = threadIdx.x / C, ci = threadIdx.x % C;
+    const int64_t total = (int64_t)n * KV;
+    const int64_t per = (total + WG_BLOCKS - 1) / WG_BLOCKS;
+    const int64_t lo = blk * per, hi = lo + per < total ? lo + per : total;
+    float acc = 0.f;
+    for (int64_t base = lo; base < hi; base += WG_CHUNK) {
+        for (int e = threadIdx.x; e < WG_CHUNK * C; e += blockDim.x) {
+            const int qv = e / C, c = e % C;
+            const int64_t u = base + qv;
+            float av = 0.f, gv = 0.f;
+            if (u < hi) {
+                const int b = (int)(u / KV), v = (int)(u % KV);
+                const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+                const int64_t half = c < 8 ? 0 : ROWS;
+                const __nv_bfloat16* pa = act + (int64_t)b * PATCH + (half + prow(i + dx, j + dy, k + dz)) * 8 + (c & 7);
+                const __nv_bfloat16* pg = grad + (int64_t)b * PATCH + (half + prow(i, j, k)) * 8 + (c & 7);
+                av = __bfloat162float(*pa);
+                gv = __bfloat162float(*pg);
+            }
+            As[qv][c] = av;
+            Gs[qv][c] = gv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int qv = 0; qv < WG_CHUNK; qv++) acc = fmaf(As[qv][ci], Gs[qv][co], acc);
+        __syncthreads();
+    }
+    partial[(((int64_t)tap * WG_BLOCKS + blk) * C + co) * C + ci] = acc;
+}
+
+// dW[layer][tap][co][ci] = sum over blocks (in order); db[layer][co] = sum of grad over interior voxels.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, float* __restrict__ dW) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= TAPS * C * C) return;
+    const int tap = e / (C * C), rc = e % (C * C);
+    float s = 0.f;
+    for (int b = 0; b < WG_BLOCKS; b++) s += partial[((int64_t)tap * WG_BLOCKS + b) * C * C + rc];
+    dW[e] = s;
+}
+
+__global__ void __launch_bounds__(256) bgrad_kernel(const __nv_bfloat16* __restrict__ grad, int n, float* __restrict__ db) {
+    __shared__ float sh[256];
+    const int c = blockIdx.x;                   // one block per channel, fixed-order tree
+    float acc = 0.f;
+    for (int64_t u = threadIdx.x; u < (int64_t)n * KV; u += blockDim.x) {
+        const int b = (int)(u / KV), v = (int)(u % KV);
+        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+        acc += __bfloat162float(grad[(int64_t)b * PATCH + ((c < 8 ? 0 : ROWS) + prow(i, j, k)) * 8 + (c & 7)]);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] = sh[0];
+}
+
+// Canonical UMMA layouts of the BF16 weights: per tap [kchunk 2][ngroup 2][8 n][8 k] (512 B).
+// Forward: n = co, k = ci.  Input gradient: tap -> 26 - tap (flip), n = ci, k = co (transpose).
+__global__ void canon_kernel(const float* __restrict__ params, __nv_bfloat16* __restrict__ wf,
+                             __nv_bfloat16* __restrict__ wd) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NW) return;
+    const int l = e / (TAPS * C * C), rem = e % (TAPS * C * C);
+    const int tap = rem / (C * C), co = (rem / C) % C, ci = rem % C;
+    const __nv_bfloat16 w = __float2bfloat16_rn(params[e]);
+    auto cidx = [](int tp, int n, int k) { return tp * 256 + (k >> 3) * 128 + (n >> 3) * 64 + (n & 7) * 8 + (k & 7); };
+    wf[(int64_t)l * WCAN + cidx(tap, co, ci)] = w;
+    wd[(int64_t)l * WCAN + cidx(TAPS - 1 - tap, ci, co)] = w;
+}
+
+// Adam on the FP32 master parameters (mean gradient over the batch); layer 4 keeps only channel 0.
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ grad, float scale, float lr, float b1t, float b2t) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NPARAM) return;
+    bool frozen;
+    if (e < NW) frozen = e / (TAPS * C * C) == NL - 1 && ((e % (C * C)) / C) != 0;
+    else frozen = (e - NW) / C == NL - 1 && ((e - NW) % C) != 0;
+    if (frozen) return;
+    const float gr = grad[e] * scale;
+    const float mm = 0.9f * m[e] + 0.1f * gr;
+    const float vv = 0.999f * v[e] + 0.001f * gr * gr;
+    m[e] = mm;
+    v[e] = vv;
+    p[e] -= lr * (mm / (1.f - b1t)) / (sqrtf(vv / (1.f - b2t)) + 1e-8f);
+}
+
+}  // namespace net
+}  // namespace fdirw
+
+using namespace fdirw::net;
+namespace tcx = fdirw::tc;
+
+struct fdirw_net {
+    int device = 0;
+    float* params = nullptr;   // device FP32 master [NPARAM]
+    float* m = nullptr;
+    float* v = nullptr;
+    int64_t step = 0;
+    __nv_bfloat16* wf = nullptr;   // [NL][WCAN]
+    __nv_bfloat16* wd = nullptr;
+    int cap = 0;
+    __nv_bfloat16* act[NL] = {};   // inputs of layers 1..4 (act[0] = features)
+    __nv_bfloat16* gbuf[2] = {};
+    float* zhead = nullptr;
+    int64_t* dsrc = nullptr;
+    double* dtgt = nullptr;
+    double* dkout = nullptr;
+    double* dmass = nullptr;
+    int* dacc = nullptr;
+    double* dloss = nullptr;
+    float* partial = nullptr;
+    float* grads = nullptr;
+    int* derr = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_net_err;
+
+int nfail(fdirw_net* net, int code, const std::string& msg) {
+    if (net) net->err = msg; else g_net_err = msg;
+    return fdirw::set_thread_error(code, msg);
+}
+
+#define NET_CUDA(net, call)                                                                     \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return nfail((net), FDIRW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int ensure_capacity(fdirw_net* net, int n) {
+    if (n <= net->cap) return FDIRW_OK;
+    const int cap = n;
+    for (auto& p : net->act) { cudaFree(p); p = nullptr; }
+    for (auto& p : net->gbuf) { cudaFree(p); p = nullptr; }
+    cudaFree(net->zhead); cudaFree(net->dsrc); cudaFree(net->dtgt); cudaFree(net->dkout);
+    cudaFree(net->dmass); cudaFree(net->dacc); cudaFree(net->dloss);
+    net->cap = 0;
+    const size_t ab = (size_t)cap * PATCH * 2;
+    for (auto& p : net->act) NET_CUDA(net, cudaMalloc(&p, ab));
+    for (auto& p : net->gbuf) NET_CUDA(net, cudaMalloc(&p, ab));
+    for (auto& p : net->act) NET_CUDA(net, cudaMemset(p, 0, ab));       // halos stay zero from here on
+    for (auto& p : net->gbuf) NET_CUDA(net, cudaMemset(p, 0, ab));
+    NET_CUDA(net, cudaMalloc(&net->zhead, (size_t)cap * KV * 4));
+    NET_CUDA(net, cudaMalloc(&net->dsrc, (size_t)cap * 8));
+    NET_CUDA(net, cudaMalloc(&net->dtgt, (size_t)cap * KV * 8));
+    NET_CUDA(net, cudaMalloc(&net->dkout, (size_t)cap * KV * 8));
+    NET_CUDA(net, cudaMalloc(&net->dmass, (size_t)cap * 8));
+    NET_CUDA(net, cudaMalloc(&net->dacc, (size_t)cap * 4));
+    NET_CUDA(net, cudaMalloc(&net->dloss, (size_t)cap * 8));
+    net->cap = cap;
+    return FDIRW_OK;
+}
+
+int launch_conv(fdirw_net* net, cudaStream_t st, int num_sms, const __nv_bfloat16* in, __nv_bfloat16* out,
+                float* zhead, const __nv_bfloat16* mask, const __nv_bfloat16* w, const float* bias, int n, int mode) {
+    ConvArgs a{in, out, zhead, mask, w, bias, n, mode, net->derr};
+    NET_CUDA(net, cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CONV_SMEM));
+    const int grid = n < num_sms * 3 ? n : num_sms * 3;
+    conv_kernel<<<grid, 128, CONV_SMEM, st>>>(a);
+    NET_CUDA(net, cudaGetLastError());
+    return FDIRW_OK;
+}
+
+// Features + the 4 convolutions for sources dsrc[0..n) (already on the device).  The first layer's
+// input keeps its halo zero; channels 3..15 and the out-of-domain rows are cleared every call.
+int forward(fdirw_ctx* c, fdirw_net* net, int n) {
+    cudaStream_t st = c->stream;
+    NET_CUDA(net, cudaMemsetAsync(net->act[0], 0, (size_t)n * PATCH * 2, st));
+    const int64_t work = (int64_t)n * KV;
+    const int fb = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
+    features_kernel<<<fb, 256, 0, st>>>(c->Dd, c->g, net->dsrc, n, net->act[0]);
+    NET_CUDA(net, cudaGetLastError());
+    for (int l = 0; l < NL; l++) {
+        const bool head = l == NL - 1;
+        const int rc = launch_conv(net, st, c->num_sms, net->act[l], head ? nullptr : net->act[l + 1],
+                                   head ? net->zhead : nullptr, nullptr, net->wf + (size_t)l * WCAN,
+                                   net->params + NW + l * C, n, head ? FWD_HEAD : FWD_RELU);
+        if (rc != FDIRW_OK) return rc;
+    }
+    return FDIRW_OK;
+}
+
+int check_err(fdirw_net* net, cudaStream_t st) {
+    int h = 0;
+    NET_CUDA(net, cudaMemcpyAsync(&h, net->derr, 4, cudaMemcpyDeviceToHost, st));
+    NET_CUDA(net, cudaStreamSynchronize(st));
+    if (h) {
+        cudaMemsetAsync(net->derr, 0, 4, st);
+        return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    }
+    return FDIRW_OK;
+}
+
+int upload_sources(fdirw_ctx* c, fdirw_net* net, const int64_t* sources, int64_t n) {
+    if (n < 0 || n > MAX_BATCH) return nfail(net, FDIRW_ERR_ARG, "batch size must be in [0, 1024]");
+    for (int64_t q = 0; q < n; q++)
+        if (sources[q] < 0 || sources[q] >= c->g.n) return nfail(net, FDIRW_ERR_ARG, "source index out of range");
+    int rc = ensure_capacity(net, (int)(n > 0 ? n : 1));
+    if (rc != FDIRW_OK) return rc;
+    NET_CUDA(net, cudaMemcpyAsync(net->dsrc, sources, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    return FDIRW_OK;
+}
+
+// Backward through the 4 layers into net->grads (sum over the batch); the head gradient is in gbuf[0].
+int backward(fdirw_ctx* c, fdirw_net* net, int n) {
+    cudaStream_t st = c->stream;
+    int cur = 0;
+    for (int l = NL - 1; l >= 0; l--) {
+        wgrad_partial_kernel<<<dim3(TAPS, WG_BLOCKS), 256, 0, st>>>(net->act[l], net->gbuf[cur], n, net->partial);
+        NET_CUDA(net, cudaGetLastError());
+        wgrad_reduce_kernel<<<(TAPS * C * C + 255) / 256, 256, 0, st>>>(net->partial, net->grads + (size_t)l * TAPS * C * C);
+        NET_CUDA(net, cudaGetLastError());
+        bgrad_kernel<<<C, 256, 0, st>>>(net->gbuf[cur], n, net->grads + NW + l * C);
+        NET_CUDA(net, cudaGetLastError());
+        if (l > 0) {
+            const int rc = launch_conv(net, st, c->num_sms, net->gbuf[cur], net->gbuf[cur ^ 1], nullptr, net->act[l],
+                                       net->wd + (size_t)l * WCAN, nullptr, n, DGRAD);
+            if (rc != FDIRW_OK) return rc;
+            cur ^= 1;
+        }
+    }
+    return FDIRW_OK;
+}
+
+int gradients(fdirw_ctx* c, fdirw_net* net, const int64_t* sources, int64_t n, const double* targets,
+              double* loss_out) {
+    int rc = upload_sources(c, net, sources, n);
+    if (rc != FDIRW_OK) return rc;
+    NET_CUDA(net, cudaMemcpyAsync(net->dtgt, targets, (size_t)n * KV * 8, cudaMemcpyDefault, c->stream));
+    if ((rc = forward(c, net, (int)n)) != FDIRW_OK) return rc;
+    NET_CUDA(net, cudaMemsetAsync(net->gbuf[0], 0, (size_t)n * PATCH * 2, c->stream));
+    head_train_kernel<<<(int)n, 256, 0, c->stream>>>(net->zhead, c->g, net->dsrc, net->dtgt, net->gbuf[0], net->dloss);
+    NET_CUDA(net, cudaGetLastError());
+    if ((rc = backward(c, net, (int)n)) != FDIRW_OK) return rc;
+    std::vector<double> lv((size_t)n);
+    NET_CUDA(net, cudaMemcpyAsync(lv.data(), net->dloss, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = check_err(net, c->stream)) != FDIRW_OK) return rc;
+    double s = 0.0;
+    for (double x : lv) s += x;
+    if (loss_out) *loss_out = n > 0 ? s / (double)n : 0.0;
+    return FDIRW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+FDIRW_API int fdirw_net_create(const float* params, int32_t device, fdirw_net** out) {
+    if (!out || !params) return nfail(nullptr, FDIRW_ERR_ARG, "NULL params or out");
+    *out = nullptr;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return nfail(nullptr, FDIRW_ERR_CUDA, "cannot select device");
+    fdirw_net* net = new fdirw_net();
+    cudaGetDevice(&net->device);
+    auto bail = [&](const std::string& m) {
+        std::string msg = m;
+        fdirw_net_destroy(net);
+        if (device >= 0) cudaSetDevice(prev);
+        return nfail(nullptr, FDIRW_ERR_CUDA, msg);
+    };
+    if (cudaMalloc(&net->params, NPARAM * 4) != cudaSuccess || cudaMalloc(&net->m, NPARAM * 4) != cudaSuccess ||
+        cudaMalloc(&net->v, NPARAM * 4) != cudaSuccess || cudaMalloc(&net->grads, NPARAM * 4) != cudaSuccess ||
+        cudaMalloc(&net->wf, (size_t)NL * WCAN * 2) != cudaSuccess || cudaMalloc(&net->wd, (size_t)NL * WCAN * 2) != cudaSuccess ||
+        cudaMalloc(&net->partial, (size_t)TAPS * WG_BLOCKS * C * C * 4) != cudaSuccess ||
+        cudaMalloc(&net->derr, 4) != cudaSuccess)
+        return bail("allocating the network");
+    if (cudaMemcpy(net->params, params, NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(net->m, 0, NPARAM * 4) != cudaSuccess || cudaMemset(net->v, 0, NPARAM * 4) != cudaSuccess ||
+        cudaMemset(net->derr, 0, 4) != cudaSuccess)
+        return bail("initialising the network");
+    canon_kernel<<<(NW + 255) / 256, 256>>>(net->params, net->wf, net->wd);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return bail("weight layout kernel");
+    if (device >= 0) cudaSetDevice(prev);
+    *out = net;
+    return FDIRW_OK;
+}
+
+FDIRW_API int fdirw_net_params(fdirw_net* net, float* params_out) {
+    if (!net || !params_out) return nfail(net, FDIRW_ERR_ARG, "NULL net or params_out");
+    NET_CUDA(net, cudaMemcpy(params_out, net->params, NPARAM * 4, cudaMemcpyDeviceToHost));
+    return FDIRW_OK;
+}
+
+FDIRW_API void fdirw_net_destroy(fdirw_net* net) {
+    if (!net) return;
+    cudaDeviceSynchronize();
+    for (auto& p : net->act) cudaFree(p);
+    for (auto& p : net->gbuf) cudaFree(p);
+    cudaFree(net->params); cudaFree(net->m); cudaFree(net->v); cudaFree(net->wf); cudaFree(net->wd);
+    cudaFree(net->zhead); cudaFree(net->dsrc); cudaFree(net->dtgt); cudaFree(net->dkout); cudaFree(net->dmass);
+    cudaFree(net->dacc); cudaFree(net->dloss); cudaFree(net->partial); cudaFree(net->grads); cudaFree(net->derr);
+    delete net;
+}
+
+FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                                double* kernels_out, double* mass_out, int32_t* accept_out) {
+    if (!ctx || !net || (n > 0 && !sources)) return nfail(net, FDIRW_ERR_ARG, "NULL ctx, net or sources");
+    if (n == 0) return FDIRW_OK;
+    int rc = upload_sources(ctx, net, sources, n);
+    if (rc != FDIRW_OK) return rc;
+    if ((rc = forward(ctx, net, (int)n)) != FDIRW_OK) return rc;
+    head_predict_kernel<<<(int)n, 256, 0, ctx->stream>>>(net->zhead, ctx->g, net->dsrc, net->dkout, net->dmass, net->dacc);
+    NET_CUDA(net, cudaGetLastError());
+    if (kernels_out) NET_CUDA(net, cudaMemcpyAsync(kernels_out, net->dkout, (size_t)n * KV * 8, cudaMemcpyDefault, ctx->stream));
+    if (mass_out) NET_CUDA(net, cudaMemcpyAsync(mass_out, net->dmass, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (accept_out) NET_CUDA(net, cudaMemcpyAsync(accept_out, net->dacc, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    return check_err(net, ctx->stream);
+}
+
+FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                                  const double* targets, float* grads_out, double* loss_out) {
+    if (!ctx || !net || n <= 0 || !sources || !targets) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
+    int rc = gradients(ctx, net, sources, n, targets, loss_out);
+    if (rc != FDIRW_OK) return rc;
+    if (grads_out) NET_CUDA(net, cudaMemcpy(grads_out, net->grads, NPARAM * 4, cudaMemcpyDeviceToHost));
+    return FDIRW_OK;
+}
+
+FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                                   const double* targets, float lr, double* loss_out) {
+    if (!ctx || !net || n <= 0 || !sources || !targets || !(lr > 0.f)) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
+    int rc = gradients(ctx, net, sources, n, targets, loss_out);
+    if (rc != FDIRW_OK) return rc;
+    net->step++;
+    const float b1t = (float)std::pow(0.9, (double)net->step), b2t = (float)std::pow(0.999, (double)net->step);
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, ctx->stream>>>(net->params, net->m, net->v, net->grads,
+                                                               1.f / (float)n, lr, b1t, b2t);
+    NET_CUDA(net, cudaGetLastError());
+    canon_kernel<<<(NW + 255) / 256, 256, 0, ctx->stream>>>(net->params, net->wf, net->wd);
+    NET_CUDA(net, cudaGetLastError());
+    return FDIRW_OK;
+}
+
+FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* c, fdirw_net* net, int64_t* accepted_out) {
+    if (!c || !net) return nfail(net, FDIRW_ERR_ARG, "NULL ctx or net");
+    if (c->R != SH) return nfail(net, FDIRW_ERR_ARG, "the surrogate predicts 17^3 kernels: window_R must be 8");
+    if (c->store == Store::F64) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves the FP32-march precisions only");
+    {
+        const int rc = fdirw::ensure_cache(c);
+        if (rc != FDIRW_OK) return nfail(net, rc, fdirw_last_error(c));
+    }
+    const int64_t N = c->g.n;
+    std::vector<int64_t> src(MAX_BATCH), rejected;
+    std::vector<int32_t> acc(MAX_BATCH);
+    rejected.reserve((size_t)(N / 4));
+    int64_t accepted = 0;
+    int rc = ensure_capacity(net, MAX_BATCH);
+    if (rc != FDIRW_OK) return rc;
+    for (int64_t b0 = 0; b0 < N; b0 += MAX_BATCH) {
+        const int n = (int)(N - b0 < MAX_BATCH ? N - b0 : MAX_BATCH);
+        for (int q = 0; q < n; q++) src[q] = b0 + q;
+        NET_CUDA(net, cudaMemcpyAsync(net->dsrc, src.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+        if ((rc = forward(c, net, n)) != FDIRW_OK) return rc;
+        head_predict_kernel<<<n, 256, 0, c->stream>>>(net->zhead, c->g, net->dsrc, nullptr, net->dmass, net->dacc);
+        NET_CUDA(net, cudaGetLastError());
+        head_store_kernel<<<n, 256, 0, c->stream>>>(net->zhead, c->g, net->dsrc, net->dacc, c->Q, c->store, c->sigma);
+        NET_CUDA(net, cudaGetLastError());
+        NET_CUDA(net, cudaMemcpyAsync(acc.data(), net->dacc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+        NET_CUDA(net, cudaStreamSynchronize(c->stream));
+        for (int q = 0; q < n; q++) {
+            if (acc[q]) accepted++;
+            else rejected.push_back(src[q]);
+        }
+    }
+    if ((rc = check_err(net, c->stream)) != FDIRW_OK) return rc;
+    if (!rejected.empty()) {
+        int64_t* dlist = nullptr;
+        NET_CUDA(net, cudaMalloc(&dlist, rejected.size() * 8));
+        cudaError_t e = cudaMemcpyAsync(dlist, rejected.data(), rejected.size() * 8, cudaMemcpyHostToDevice, c->stream);
+        fdirw::MarchArgs a{};
+        a.g = c->g;
+        a.R = c->R;
+        a.n_sub = c->n_sub;
+        a.ax = reinterpret_cast<const float*>(c->coef[0]);
+        a.ay = reinterpret_cast<const float*>(c->coef[1]);
+        a.az = reinterpret_cast<const float*>(c->coef[2]);
+        a.Q = c->Q;
+        a.store = c->store;
+        a.sigma = c->sigma;
+        a.src_begin = 0;
+        a.src_end = (int64_t)rejected.size();
+        a.list = dlist;
+        if (e == cudaSuccess) e = fdirw::launch_march(a, c->num_sms, c->parts_req, c->stream, &c->parts_used);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(dlist);
+        if (e != cudaSuccess) return nfail(net, FDIRW_ERR_CUDA, std::string("fallback march: ") + cudaGetErrorString(e));
+    }
+    c->kernels_ready = true;
+    if (accepted_out) *accepted_out = accepted;
+    return FDIRW_OK;
+}
+
+}  // extern "C"

@@ -29,7 +29,11 @@ FDIRW_FP32_STORE_BF16 = 3
 PRECISIONS = {"fp64": FDIRW_FP64, "fp32": FDIRW_FP32, "fp16": FDIRW_FP32_STORE_FP16, "bf16": FDIRW_FP32_STORE_BF16}
 
 EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "fdirw_mass", "fdirw_read_kernels",
-            "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc")
+            "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc", "fdirw_net_create",
+            "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
+            "fdirw_kernels_surrogate")
+NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
+NET_KV = 17 ** 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfdirw.so")
@@ -92,8 +96,16 @@ def load(path: str | None = None):
         lib.fdirw_last_error.argtypes = [vp]
         lib.fdirw_last_error.restype = ctypes.c_char_p
         lib.fdirw_mass_noalloc.argtypes = [vp, i64, vp, vp]
+        lib.fdirw_net_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        lib.fdirw_net_params.argtypes = [vp, vp]
+        lib.fdirw_net_destroy.argtypes = [vp]
+        lib.fdirw_net_destroy.restype = None
+        lib.fdirw_net_predict.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        lib.fdirw_net_gradients.argtypes = [vp, vp, vp, i64, vp, vp, dp]
+        lib.fdirw_net_train_step.argtypes = [vp, vp, vp, i64, vp, ctypes.c_float, dp]
+        lib.fdirw_kernels_surrogate.argtypes = [vp, vp, ctypes.POINTER(i64)]
         for name in EXPORTED:
-            if name not in ("fdirw_destroy", "fdirw_last_error"):
+            if name not in ("fdirw_destroy", "fdirw_last_error", "fdirw_net_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -259,3 +271,85 @@ class FDiRW:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- learned surrogate
+
+class Net:
+    """The surrogate network (C ABI fdirw_net_*).  params: float32 [NET_NPARAM] (weights [4][27][16][16]
+    as [layer][tap][co][ci], then biases [4][16])."""
+
+    def __init__(self, params, device: int = -1):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if p.size != NET_NPARAM:
+            raise ValueError(f"expected {NET_NPARAM} parameters")
+        h = ctypes.c_void_p(0)
+        _check(load().fdirw_net_create(ctypes.c_void_p(p.ctypes.data), int(device), ctypes.byref(h)))
+        self.h = h.value
+
+    def params(self) -> np.ndarray:
+        out = np.empty(NET_NPARAM, dtype=np.float32)
+        _check(load().fdirw_net_params(ctypes.c_void_p(self.h), ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    @staticmethod
+    def _src(sources):
+        return np.ascontiguousarray(sources, dtype=np.int64).reshape(-1)
+
+    def predict(self, ctx: int, sources):
+        """(kernels [n, 17, 17, 17] (unnormalised y), masses [n], accepted [n] bool)."""
+        src = self._src(sources)
+        k = np.empty((src.size, 17, 17, 17))
+        m = np.empty(src.size)
+        a = np.empty(src.size, dtype=np.int32)
+        _check(load().fdirw_net_predict(ctypes.c_void_p(ctx), ctypes.c_void_p(self.h), ctypes.c_void_p(src.ctypes.data),
+                                        src.size, ctypes.c_void_p(k.ctypes.data), ctypes.c_void_p(m.ctypes.data),
+                                        ctypes.c_void_p(a.ctypes.data)), ctypes.c_void_p(ctx))
+        return k, m, a.astype(bool)
+
+    def gradients(self, ctx: int, sources, targets):
+        src = self._src(sources)
+        t = np.ascontiguousarray(targets, dtype=np.float64)
+        g = np.empty(NET_NPARAM, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(load().fdirw_net_gradients(ctypes.c_void_p(ctx), ctypes.c_void_p(self.h), ctypes.c_void_p(src.ctypes.data),
+                                          src.size, ctypes.c_void_p(_ptr(t)), ctypes.c_void_p(g.ctypes.data),
+                                          ctypes.byref(loss)), ctypes.c_void_p(ctx))
+        return g, loss.value
+
+    def train_step(self, ctx: int, sources, targets, lr: float) -> float:
+        src = self._src(sources)
+        loss = ctypes.c_double(0.0)
+        t = targets if hasattr(targets, "data_ptr") else np.ascontiguousarray(targets, dtype=np.float64)
+        _check(load().fdirw_net_train_step(ctypes.c_void_p(ctx), ctypes.c_void_p(self.h), ctypes.c_void_p(src.ctypes.data),
+                                           src.size, ctypes.c_void_p(_ptr(t)), float(lr), ctypes.byref(loss)),
+               ctypes.c_void_p(ctx))
+        return loss.value
+
+    def build_kernels(self, ctx: int) -> int:
+        """fdirw_kernels_surrogate: returns the number of accepted sources."""
+        acc = ctypes.c_int64(0)
+        _check(load().fdirw_kernels_surrogate(ctypes.c_void_p(ctx), ctypes.c_void_p(self.h), ctypes.byref(acc)),
+               ctypes.c_void_p(ctx))
+        return acc.value
+
+    def close(self):
+        if self.h:
+            load().fdirw_net_destroy(ctypes.c_void_p(self.h))
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_params(Ws, bs) -> np.ndarray:
+    """Weights [4][27][16][16] and biases [4][16] (any float arrays) into the flat parameter vector."""
+    return np.concatenate([np.asarray(Ws, dtype=np.float32).reshape(-1), np.asarray(bs, dtype=np.float32).reshape(-1)])
+
+
+def unpack_params(p):
+    p = np.asarray(p, dtype=np.float64)
+    return p[:NET_NPARAM - 64].reshape(4, 27, 16, 16), p[NET_NPARAM - 64:].reshape(4, 16)

