@@ -314,10 +314,70 @@ def run_ours(args, w):
     }
     if fp64:
         line["speedup_vs_fp64_gpu"] = value / fp64["macro_steps_per_s"]
+    if args.surrogate:
+        line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec):
+    """Learned surrogate: trains on FD kernels of seeded packings (porosity U[0.3,0.5], per-sphere log10
+    ratio U[3,8]; 200k kernels by default), then builds the workload's kernel cache with the gate and FD
+    fallback and compares it with the FD-only build (time, acceptance, kernel and field error)."""
+    from paper_2408_11376_gb300 import surrogate as sg
+    t0 = time.perf_counter()
+    data = sg.training_set(args.surrogate_structures, args.surrogate_per_structure, 20240825, n_sub=w.n_sub)
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t0
+    net = fdirw.Net(sg.init_params(20240826))
+    t0 = time.perf_counter()
+    hist = sg.train(net, data, args.surrogate_epochs, batch=256, lr=args.surrogate_lr)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    n_train = sum(len(d.sources) for d in data)
+    for d in data:
+        d.ctx.close()
+    del data
+    torch.cuda.empty_cache()
+    N = c0.numel()
+    rng = np.random.default_rng(5)
+    probe = np.sort(rng.integers(0, N, 4096))
+    res = {}
+    for mode in ("fd", "surrogate"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            f = fdirw.FDiRW(shape, D, dt_macro, w.R, w.n_sub, prec, stream=stream)
+            if mode == "fd":
+                f.kernels()                    # warm the autotuner outside the timed build
+                stream.synchronize()
+            e0.record(stream)
+            acc = f.kernels() if mode == "fd" else net.build_kernels(f.ctx)
+            e1.record(stream)
+            stream.synchronize()
+            out = torch.empty_like(c0)
+            mass = f.step(c0, out, w.steps, want_mass=True)
+            k = f.read_kernels(probe)
+            f.close()
+        res[mode] = {"build_ms": e0.elapsed_time(e1), "accepted": acc if mode == "surrogate" else None,
+                     "field": out, "mass": mass, "kernels": k}
+    sgm, fd = res["surrogate"], res["fd"]
+    kd = np.linalg.norm((sgm["kernels"] - fd["kernels"]).reshape(len(probe), -1), axis=1)
+    kn = np.linalg.norm(fd["kernels"].reshape(len(probe), -1), axis=1)
+    changed = kd > 0
+    mass0 = float(c0.sum().item())
+    out = {"training_kernels": n_train, "epochs": args.surrogate_epochs, "loss_per_epoch": hist,
+           "data_gen_s": t_data, "train_s": t_train, "train_samples_per_s": n_train * len(hist) / t_train,
+           "fd_build_ms": fd["build_ms"], "surrogate_build_ms": sgm["build_ms"],
+           "gain_build": fd["build_ms"] / sgm["build_ms"],
+           "accepted_fraction": sgm["accepted"] / N,
+           "probe_accepted_kernel_rel_l2_max": float((kd / kn)[changed].max()) if changed.any() else 0.0,
+           "field_rel_l2_vs_fd_after_steps": float((torch.linalg.vector_norm(sgm["field"] - fd["field"]) /
+                                                     torch.linalg.vector_norm(fd["field"])).item()),
+           "mass_rel_err": abs(sgm["mass"] - mass0) / mass0}
+    net.close()
+    return out
 
 
 def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
@@ -378,6 +438,11 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU baseline and accuracy leg")
+    ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and compare its gated build")
+    ap.add_argument("--surrogate-structures", type=int, default=20)
+    ap.add_argument("--surrogate-per-structure", type=int, default=10000)
+    ap.add_argument("--surrogate-epochs", type=int, default=4)
+    ap.add_argument("--surrogate-lr", type=float, default=2e-3)
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per march launch from an ncu capture of the current kernel")

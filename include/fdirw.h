@@ -189,7 +189,7 @@ FDIRW_API void fdirw_net_destroy(fdirw_net* net);
  * decisions (host int32, nullable) for n sources of ctx's domain. */
 FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                                 double* kernels_out, double* mass_out, int32_t* accept_out);
-/* Gradients of the training loss sum_i sum_v (k_iv + 1e-7)(z_iv - ln(k_iv + 1e-7))^2 (k = targets, z = the
+/* Gradients of the training loss sum_i sum_v (k_iv + 1e-9)(z_iv - ln(k_iv + 1e-9))^2 (k = targets, z = the
  * head's pre-exponential output, in-domain cells only) with respect to the parameters (host,
  * FDIRW_NET_NPARAM floats, nullable) and the mean loss over the batch (host, nullable). */
 FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,

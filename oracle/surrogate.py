@@ -14,7 +14,7 @@ the prediction fails a mass/positivity gate.  Definition followed here (and by t
 * head: y = exp(z_4[channel 0]) on in-domain cells, 0 outside; mass m = sum y (FP64).
 * gate: accept when |m - 1| <= 1e-3 (y >= 0 holds by construction); the stored kernel is then y / m.
 * training loss per sample: sum_v (k_v + eps) (z_v - ln(k_v + eps))^2 over in-domain cells (z = z_4
-  channel 0, k the FD kernel, eps = 1e-7): a squared error on ln y weighted by the kernel's mass (a loss
+  channel 0, k the FD kernel, eps = 1e-9): a squared error on ln y weighted by the kernel's mass (a loss
   on y itself has dL/dz proportional to y, which vanishes wherever the prediction starts small).  Its
   gradient flows back through the relu layers (hand-derived below).
 
@@ -141,7 +141,7 @@ def backward(Ws, cache, dz, emulate_bf16=True):
     return dWs, dbs
 
 
-EPS = 1e-7
+EPS = 1e-9
 
 
 def loss_grad(cache, k):

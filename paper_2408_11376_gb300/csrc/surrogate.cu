@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256) head_predict_kernel(const float* __restri
 // Head for training: loss sum_v (k + eps)(z - ln(k + eps))^2 over in-domain cells (a squared error on
 // ln y weighted by the target kernel's mass; a loss on y itself has dL/dz proportional to y, which
 // vanishes where the prediction is small) and its gradient 2 (k + eps)(z - ln(k + eps)) (channel 0).
-constexpr double LOSS_EPS = 1e-7;
+constexpr double LOSS_EPS = 1e-9;
 __global__ void __launch_bounds__(256) head_train_kernel(const float* __restrict__ zhead, Grid g,
                                                          const int64_t* __restrict__ src, const double* __restrict__ tgt,
                                                          __nv_bfloat16* __restrict__ grad, double* __restrict__ loss) {

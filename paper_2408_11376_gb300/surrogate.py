@@ -5,8 +5,8 @@ libfdirw through the C ABI).
 Recipe: training structures are seeded sphere packings (porosity U[0.3, 0.5], per-sphere log10
 diffusivity ratio U[3, 8]); their FD kernels (window R = 8, n_sub substeps at the stability limit) are
 the targets; the network starts from a delta-kernel prior (the source marker routed to the head so that
-z = 0 at the source and ln(1e-7) elsewhere) plus N(0, 0.02) noise, and is trained with Adam on the
-mass-weighted log-space loss sum (k + 1e-7)(z - ln(k + 1e-7))^2.
+z = 0 at the source and ln(1e-9) elsewhere) plus N(0, 0.02) noise, and is trained with Adam on the
+mass-weighted log-space loss sum (k + 1e-9)(z - ln(k + 1e-9))^2.
 """
 from __future__ import annotations
 
@@ -17,7 +17,7 @@ import numpy as np
 
 from . import fdirw, synth
 
-EPS = 1e-7
+EPS = 1e-9
 LAYERS, TAPS, C = 4, 27, 16
 
 
