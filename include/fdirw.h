@@ -77,7 +77,9 @@ typedef struct {
     uint64_t mem_limit;   /* cap on the device bytes this context allocates; 0 = no cap */
     int32_t  march_parts; /* FP32 march thread mapping: 1..3 = threads per window column; 4 = one thread
                              per 2x2 block of window columns with the face coefficients in Tensor Memory;
-                             0 = autotune (each candidate timed once on the first build for a device, R
+                             5 = one thread per window column with its lateral face coefficients in
+                             Tensor Memory (the only mapping for window_R 9 and 10, chosen there
+                             whatever this field says); 0 = autotune (each candidate timed once on the first build for a device, R
                              and storage type, result cached for the process; that build synchronises the
                              stream) */
     int32_t  reserved;    /* must be 0 */
@@ -115,7 +117,7 @@ FDIRW_API int fdirw_stable_dt(const fdirw_grid* grid, const double* D_map, int32
  *   grid       : grid dimensions and cell size
  *   D_map      : N cell diffusivities (host or device), finite and >= 0; copied, not retained
  *   dt_macro   : macro step (>= 0, finite); dt_sub = dt_macro / n_sub
- *   window_R   : window radius, 0 <= R <= 8 (R = 0 gives the identity operator)
+ *   window_R   : window radius, 0 <= R <= 10; <= 8 with FDIRW_FP64 (R = 0 gives the identity operator)
  *   n_sub      : explicit substeps per macro step, >= 0 (0 gives the identity operator)
  *   opts       : NULL for defaults (FDIRW_FP32, current device, default stream, no cap, autotune)
  *   out        : receives the context (set to NULL on failure)

@@ -8,8 +8,9 @@
 
 namespace fdirw {
 
-// Largest window radius the register-resident march supports (window (2R+1)^3 = 4913 cells at R = 8).
-constexpr int kMaxR = 8;
+// Largest window radius: the FP32 march supports R <= 10 (window 21^3), the FP64 march R <= 8.
+constexpr int kMaxR = 10;
+constexpr int kMaxR64 = 8;
 
 enum class Store : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
 
@@ -37,7 +38,8 @@ cudaError_t launch_coef_f64(double* g, double lam, int64_t n, cudaStream_t st);
 // ---------------------------------------------------------------- march.cu
 struct MarchArgs {
     Grid g;
-    int R;
+    int R;                // window radius of the marched sources
+    int Rq;               // radius of the cache layout (Rq >= R; equal for a uniform window)
     int n_sub;
     const float* ax; const float* ay; const float* az;     // FP32 path: lam*g
     const double* dx; const double* dy; const double* dz;  // FP64 path: lam*g

@@ -58,6 +58,13 @@ struct Map32 {
     static constexpr size_t SMEM = (size_t)((2 * BUF * 4 + 15) / 16) * 16 + (size_t)SPB * COLS * 8;
 };
 
+// Plane of the kernel cache for window cell (x, y, k) of a radius-R window: the cache is laid out for
+// radius a.Rq >= R (offset o = (x - R, y - R, k - R), plane (ox + Rq) + Wq ((oy + Rq) + Wq (oz + Rq))).
+__device__ __forceinline__ int64_t qplane(const MarchArgs& a, int R, int x, int y, int k) {
+    const int Wq = 2 * a.Rq + 1, d = a.Rq - R;
+    return (int64_t)(x + d) + (int64_t)Wq * ((y + d) + (int64_t)Wq * (k + d));
+}
+
 // Rounds v to the storage type, writes it to Q[idx] and returns the stored value widened to float
 // (exact for every storage type).
 __device__ __forceinline__ float put(void* Q, Store st, int64_t idx, float v) {
@@ -205,8 +212,7 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
                     float st = 0.f;
                     if (col_ok && z >= 0 && z < nz) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                        const int64_t o = ci + W1 * (cj + W1 * k);
-                        st = put(a.Q, a.store, o * a.g.n + i, u[j]);
+                        st = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.g.n + i, u[j]);
                     }
                     sbuf[base + k] = st;
                 }
@@ -322,8 +328,7 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
                 const int z = sz - R + k;
                 if (z >= 0 && z < nz) {
                     const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                    const int64_t o = ci + W1 * (cj + W1 * k);
-                    reinterpret_cast<double*>(a.Q)[o * a.g.n + i] = u[k];
+                    reinterpret_cast<double*>(a.Q)[qplane(a, R, ci, cj, k) * a.g.n + i] = u[k];
                     colsum += u[k];
                 }
             }
@@ -603,8 +608,7 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
                 for (int k = 0; k < W1; k++) {
                     float stv = 0.f;
                     if (cell_ok(x, y, k)) {
-                        const int64_t o = x + W1 * (y + W1 * k);
-                        stv = put(a.Q, a.store, o * a.g.n + gidx(x, y, k), u[sc][k]);
+                        stv = put(a.Q, a.store, qplane(a, R, x, y, k) * a.g.n + gidx(x, y, k), u[sc][k]);
                     }
                     sbuf[k * LEVEL + sc * PLANE + t] = stv;
                 }
@@ -650,6 +654,197 @@ cudaError_t launch_tm(const MarchArgs& a, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------------
+// One thread per window column with the lateral face coefficients in TMEM (mapping id 5; any R <= 10).
+//
+// For R = 9, 10 a column of 2R+1 cells with 6 coefficients each no longer fits in registers next to
+// enough threads.  Here u, the diagonal and the z faces stay in registers and the 4 lateral faces of the
+// column (4(2R+1) words) live in the thread's TMEM lane, in groups of 4 cells (16 words, one
+// tcgen05.ld.32x32b.x16 each) fetched one group ahead of the compute.  Up to 4 threads share a TMEM lane
+// (128 columns each), so one CTA of up to 448 threads per SM owns all 512 columns.  The halo exchange
+// and the FP32 operations (and their order) are those of march_f32_kernel.
+template <int R>
+struct MapTmc {
+    static constexpr int W1 = 2 * R + 1;
+    static constexpr int COLS = W1 * W1;
+    static constexpr int THREADS = ((COLS + 31) / 32) * 32;
+    static constexpr int NG = (W1 + 3) / 4;               // TMEM groups of 4 cells
+    static constexpr int BUF = COLS * W1;
+    static constexpr size_t SMEM_USED = (size_t)((2 * BUF * 4 + 15) / 16) * 16 + (size_t)COLS * 8;
+    static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+    static_assert(16 * NG <= 128, "lateral faces of a column must fit a 128-column TMEM slot");
+    static_assert(THREADS <= 512, "at most 4 threads per TMEM lane");
+};
+
+template <int R>
+__global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchArgs a) {
+    using M = MapTmc<R>;
+    constexpr int W1 = M::W1, COLS = M::COLS, NG = M::NG, BUF = M::BUF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* xbuf = reinterpret_cast<float*>(smem_raw);                                  // [2][COLS][W1]
+    double* red = reinterpret_cast<double*>(smem_raw + ((2 * BUF * 4 + 15) / 16) * 16);  // [COLS]
+    __shared__ uint32_t s_taddr;
+
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(dst) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const uint32_t tbase = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+
+    const bool active = t < COLS;
+    const int col = active ? t : 0;
+    const int ci = col % W1, cj = col / W1;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t nbatch = a.src_end - a.src_begin;
+    const int base = col * W1;
+    const int xm = ci > 0 ? base - W1 : base;
+    const int xp = ci < 2 * R ? base + W1 : base;
+    const int ym = cj > 0 ? base - W1 * W1 : base;
+    const int yp = cj < 2 * R ? base + W1 * W1 : base;
+
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        const int64_t first = a.src_begin + b;
+        int64_t s = first;
+        const bool src_ok = active && s < a.src_end;
+        if (src_ok && a.list) s = a.list[s];
+        int sx = 0, sy = 0, sz = 0;
+        if (src_ok) {
+            sx = (int)(s % nx);
+            const int64_t r = s / nx;
+            sy = (int)(r % ny);
+            sz = (int)(r / ny);
+        }
+        const int x = sx - R + ci, y = sy - R + cj;
+        const bool col_ok = src_ok && x >= 0 && x < nx && y >= 0 && y < ny;
+
+        float u[W1], am[W1], cz[W1];
+        float zprev = 0.f;
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int k = 4 * g + q;
+                float vxm = 0.f, vxp = 0.f, vym = 0.f, vyp = 0.f, vz = 0.f;
+                if (k < W1) {
+                    const int z = sz - R + k;
+                    const bool ok = col_ok && z >= 0 && z < nz;
+                    if (ok) {
+                        const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                        if (ci > 0 && x > 0) vxm = __ldg(a.ax + i - 1);
+                        if (ci < 2 * R && x + 1 < nx) vxp = __ldg(a.ax + i);
+                        if (cj > 0 && y > 0) vym = __ldg(a.ay + i - nx);
+                        if (cj < 2 * R && y + 1 < ny) vyp = __ldg(a.ay + i);
+                        if (k < 2 * R && z + 1 < nz) vz = __ldg(a.az + i);
+                    }
+                    cz[k < W1 ? k : 0] = vz;
+                    am[k < W1 ? k : 0] = -(((vxm + vxp) + (vym + vyp)) + (zprev + vz));
+                    u[k < W1 ? k : 0] = (src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
+                    zprev = vz;
+                }
+                w[4 * q + 0] = __float_as_uint(vxm);
+                w[4 * q + 1] = __float_as_uint(vxp);
+                w[4 * q + 2] = __float_as_uint(vym);
+                w[4 * q + 3] = __float_as_uint(vyp);
+            }
+            tm_st16(tbase + (uint32_t)(16 * g), w);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+        for (int it = 0; it < a.n_sub; it++) {
+            float* buf = xbuf + (it & 1) * BUF;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < W1; k++) buf[base + k] = u[k];
+            }
+            __syncthreads();
+            uint32_t cc[16], cn[16];
+            tm_ld16(tbase, cc);
+            tm_wait_ld(cc);
+            float prev = 0.f;
+#pragma unroll
+            for (int g = 0; g < NG; g++) {
+                if (g + 1 < NG) tm_ld16(tbase + (uint32_t)(16 * (g + 1)), cn);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int k = 4 * g + q;
+                    if (k < W1) {
+                        const float cxm = __uint_as_float(cc[4 * q + 0]), cxp = __uint_as_float(cc[4 * q + 1]);
+                        const float cym = __uint_as_float(cc[4 * q + 2]), cyp = __uint_as_float(cc[4 * q + 3]);
+                        const float cur = u[k];
+                        float v = am[k] * cur;
+                        v = fmaf(cxm, buf[xm + k], v);
+                        v = fmaf(cxp, buf[xp + k], v);
+                        v = fmaf(cym, buf[ym + k], v);
+                        v = fmaf(cyp, buf[yp + k], v);
+                        v = fmaf(k > 0 ? cz[k > 0 ? k - 1 : 0] : 0.f, prev, v);
+                        v = fmaf(cz[k], k + 1 < W1 ? u[k + 1 < W1 ? k + 1 : k] : 0.f, v);
+                        prev = cur;
+                        u[k] = __fadd_rn(cur, v);
+                    }
+                }
+                if (g + 1 < NG) {
+                    tm_wait_ld(cn);
+#pragma unroll
+                    for (int q = 0; q < 16; q++) cc[q] = cn[q];
+                }
+            }
+        }
+
+        float* sbuf = xbuf + (a.n_sub & 1) * BUF;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                const int z = sz - R + k;
+                float stv = 0.f;
+                if (col_ok && z >= 0 && z < nz) {
+                    const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                    stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.g.n + i, u[k]);
+                }
+                sbuf[base + k] = stv;
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < COLS; c += blockDim.x) {
+            double colsum = 0.0;
+#pragma unroll
+            for (int k = 0; k < W1; k++) colsum += (double)sbuf[c * W1 + k];
+            red[c] = colsum;
+        }
+        __syncthreads();
+        finish_sigma<COLS, 1>(red, first, a.src_end, a.list, a.sigma);
+        __syncthreads();
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr) : "memory");
+}
+
+template <int R>
+cudaError_t launch_tmc(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    using M = MapTmc<R>;
+    const int64_t nsrc = a.src_end - a.src_begin;
+    if (nsrc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(march_tmc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmc_kernel<R>, M::THREADS, M::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm != 1) return cudaErrorInvalidConfiguration;   // TMEM allocation assumes one CTA per SM
+    const int64_t grid = nsrc < (int64_t)num_sms ? nsrc : (int64_t)num_sms;
+    march_tmc_kernel<R><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int R, int P>
 cudaError_t launch_f32(const MarchArgs& a, int num_sms, cudaStream_t st) {
     using M = Map32<R, P>;
@@ -674,6 +869,7 @@ cudaError_t launch_f32_p(const MarchArgs& a, int P, int num_sms, cudaStream_t st
         case 2: return launch_f32<R, 2>(a, num_sms, st);
         case 3: return launch_f32<R, 3>(a, num_sms, st);
         case 4: return launch_tm<R>(a, num_sms, st);
+        case 5: return launch_tmc<R>(a, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -719,6 +915,8 @@ cudaError_t dispatch(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
         case 6: return launch_f32_p<6>(a, P, num_sms, st);
         case 7: return launch_f32_p<7>(a, P, num_sms, st);
         case 8: return launch_f32_p<8>(a, P, num_sms, st);
+        case 9: return P == 5 ? launch_tmc<9>(a, num_sms, st) : cudaErrorInvalidValue;
+        case 10: return P == 5 ? launch_tmc<10>(a, num_sms, st) : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -745,8 +943,10 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     float best_ms = 1e30f;
     *best = default_parts(a.R);
-    for (int P = 1; P <= 4 && e == cudaSuccess; P++) {
+    for (int P = 1; P <= 5 && e == cudaSuccess; P++) {
         if (P <= 3 && P > W1) continue;
+        if (a.R > 8 && P != 5) continue;          // only the TMEM-face mapping covers R = 9, 10
+        if (P == 5 && a.R < 6) continue;          // one CTA of < 6 warps per SM: never the fastest there
         e = dispatch(warm, P, num_sms, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         if (e == cudaSuccess) e = dispatch(s, P, num_sms, st);
@@ -766,7 +966,9 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
     int P = 1;
     if (a.store != Store::F64) {
-        if (parts_req >= 1 && parts_req <= 4) {
+        if (a.R > 8) {
+            P = 5;
+        } else if (parts_req >= 1 && parts_req <= 5) {
             P = parts_req;
         } else {
             int dev = 0;

@@ -298,6 +298,8 @@ cudaError_t gather_ff(const void* Q, const void* chat, Grid g, int R, Pad p, dou
         case 6: return gather_ff_r<ST, 6>(Q, chat, g, p, out, st);
         case 7: return gather_ff_r<ST, 7>(Q, chat, g, p, out, st);
         case 8: return gather_ff_r<ST, 8>(Q, chat, g, p, out, st);
+        case 9: return gather_ff_r<ST, 9>(Q, chat, g, p, out, st);
+        case 10: return gather_ff_r<ST, 10>(Q, chat, g, p, out, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -339,7 +341,7 @@ cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, 
                           cudaStream_t st) {
     const Pad p = make_pad(g, R);
     const int vx = 16 / store_bytes(store);
-    if (R >= 1 && R <= kMaxR && g.nx % vx == 0) {
+    if (R >= 1 && R <= (store == Store::F64 ? kMaxR64 : kMaxR) && g.nx % vx == 0) {
         switch (store) {
             case Store::F64: return gather_f64(Q, chat, g, R, p, c_out, st);
             case Store::F32: return gather_ff<float>(Q, chat, g, R, p, c_out, st);

@@ -697,6 +697,7 @@ FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* c, fdirw_net* net, int64_t* acc
         fdirw::MarchArgs a{};
         a.g = c->g;
         a.R = c->R;
+        a.Rq = c->R;
         a.n_sub = c->n_sub;
         a.ax = reinterpret_cast<const float*>(c->coef[0]);
         a.ay = reinterpret_cast<const float*>(c->coef[1]);

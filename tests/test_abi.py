@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_host_side_argument_checks(lib):
     D = np.ones(64)
-    bad = [((0, 4, 4), 1.0, 2, 3, 1.0), ((4, 4, 4), float("nan"), 2, 3, 1.0), ((4, 4, 4), 1.0, 9, 3, 1.0),
+    bad = [((0, 4, 4), 1.0, 2, 3, 1.0), ((4, 4, 4), float("nan"), 2, 3, 1.0), ((4, 4, 4), 1.0, 11, 3, 1.0),
            ((4, 4, 4), 1.0, -1, 3, 1.0), ((4, 4, 4), 1.0, 2, -3, 1.0), ((4, 4, 4), -1.0, 2, 3, 1.0),
            ((4, 4, 4), 1.0, 2, 3, 0.0)]
     for shape, dt, R, n_sub, h in bad:
@@ -47,8 +47,9 @@ def test_host_side_argument_checks(lib):
         assert fdirw.fdirw_last_error()
     g = fdirw.fdirw_grid(4, 4, 4, 1.0)
     assert lib.fdirw_create(ctypes.byref(g), None, 1.0, 2, 3, None, ctypes.byref(ctypes.c_void_p())) == fdirw.FDIRW_ERR_ARG
-    for bad_opts in (fdirw.fdirw_opts(7, -1, None, 0, 0, 0), fdirw.fdirw_opts(1, -1, None, 0, 5, 0)):
-        rc = lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), 1.0, 2, 3, ctypes.byref(bad_opts),
+    for R, bad_opts in ((2, fdirw.fdirw_opts(7, -1, None, 0, 0, 0)), (2, fdirw.fdirw_opts(1, -1, None, 0, 6, 0)),
+                        (9, fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0))):
+        rc = lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), 1.0, R, 3, ctypes.byref(bad_opts),
                               ctypes.byref(ctypes.c_void_p()))
         assert rc == fdirw.FDIRW_ERR_ARG
     assert lib.fdirw_kernels(None) == fdirw.FDIRW_ERR_ARG

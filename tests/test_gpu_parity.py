@@ -91,6 +91,40 @@ def test_kernels_match_oracle(prec, shape, R, n_sub):
     assert ks.min() >= 0.0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("R", [9, 10])
+def test_large_radius_kernels_match_oracle(prec, R):
+    """R = 9, 10 (only the TMEM-face mapping): sampled kernels element by element, windows clipped by the
+    domain on some sides and not on others."""
+    shape = (25, 23, 22)
+    D = _case(shape, 12, "per_sphere")
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    src = np.arange(3, N, 37)
+    _, _, ks, info = _gpu_run(shape, D, lam, R, 45, np.zeros(N), 0, prec, src)
+    assert info["march_parts"] == 5
+    ref, _ = oracle.kernels(shape, D, lam, R, 45, src)
+    ks = ks.reshape(len(src), -1)
+    ref = ref.reshape(len(src), -1)
+    err = np.linalg.norm(ks - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= KERNEL_TOL[prec], (prec, err.max())
+    assert np.max(np.abs(ks.sum(axis=1) - 1.0)) <= 1e-12 and ks.min() >= 0.0
+
+
+@pytest.mark.parametrize("R", [9, 10])
+def test_large_radius_steps_match_oracle(R):
+    shape = (16, 13, 12)
+    D = _case(shape, 23, "two_phase")
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    c0 = synth.random_field(N, 24, 0.0, 2.0)
+    for prec in ("fp32", "bf16"):
+        got, m, _, _ = _gpu_run(shape, D, lam, R, 30, c0, 2, prec)
+        ref = _oracle_steps(shape, D, lam, R, 30, c0, 2)
+        assert _rel(got, ref) <= FIELD_TOL[prec], (prec, _rel(got, ref))
+        assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+
+
 # ------------------------------------------------------------------------- steps, element by element
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
@@ -166,18 +200,19 @@ def test_one_dimensional_chain():
 
 @pytest.mark.parametrize("R", [2, 5, 8])
 def test_thread_mappings_agree_bitwise(R):
-    """Every thread mapping of the FP32 march (1, 2 or 3 threads per window column, or 2x2 column blocks
-    with TMEM-resident coefficients) gives the same bits."""
+    """Every thread mapping of the FP32 march (1, 2 or 3 threads per window column, 2x2 column blocks
+    with TMEM-resident coefficients, or one column per thread with TMEM-resident lateral faces) gives the
+    same bits."""
     shape = (19, 17, 13)
     D = _case(shape, 81, "per_sphere")
     lam = oracle.stable_dt_sub(shape, D)
     N = int(np.prod(shape))
     c0 = synth.random_field(N, 82)
     src = np.arange(0, N, 7)
-    runs = [_gpu_run(shape, D, lam, R, 37, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4)]
+    runs = [_gpu_run(shape, D, lam, R, 37, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5)]
     for got, m, ks, info in runs[1:]:
         assert np.array_equal(got, runs[0][0]) and np.array_equal(ks, runs[0][2]) and m == runs[0][1]
-    assert [r[3]["march_parts"] for r in runs] == [1, 2, 3, 4]
+    assert [r[3]["march_parts"] for r in runs] == [1, 2, 3, 4, 5]
     ref, _ = oracle.kernels(shape, D, lam, R, 37, src)
     err = np.linalg.norm((runs[0][2] - ref).reshape(len(src), -1), axis=1) / np.linalg.norm(ref.reshape(len(src), -1), axis=1)
     assert err.max() <= KERNEL_TOL["fp32"]
