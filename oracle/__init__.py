@@ -38,6 +38,7 @@ _lib = None
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int32)
 
 
 def build(force: bool = False) -> str:
@@ -45,7 +46,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -71,6 +72,12 @@ def _load():
             lib.fo_superpose.restype = ctypes.c_int
             lib.fo_full_march.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, ctypes.c_int, _D, _D]
             lib.fo_full_march.restype = ctypes.c_int
+            lib.fo_radius_map.argtypes = [ctypes.c_int64, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, _I32]
+            lib.fo_radius_map.restype = None
+            lib.fo_superpose_rmap.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, _I32, ctypes.c_int,
+                                                                             _D, _D]
+            lib.fo_superpose_rmap.restype = ctypes.c_int
             lib.fo_mass.argtypes = [_D, ctypes.c_int64]
             lib.fo_mass.restype = ctypes.c_double
             _lib = lib
@@ -160,6 +167,28 @@ def superpose(shape, D, lam: float, R: int, n_sub: int, c, cond: Conductance | N
     out = np.empty_like(c)
     if _load().fo_superpose(*g.args, float(lam), int(R), int(n_sub), _p(c), _p(out)) != 0:
         raise ValueError("fo_superpose failed")
+    return out
+
+
+def radius_map(D, dt_macro: float, h: float, R_min: int, R_max: int) -> np.ndarray:
+    """Per-source window radius clamp(ceil(2 sqrt(2 D dt_macro) / h), R_min, R_max) (int32, FP64 rule)."""
+    D = _f64(D).reshape(-1)
+    out = np.empty(D.size, dtype=np.int32)
+    _load().fo_radius_map(D.size, _p(D), float(dt_macro), float(h), int(R_min), int(R_max),
+                          out.ctypes.data_as(_I32))
+    return out
+
+
+def superpose_rmap(shape, D, lam: float, Rmap, n_sub: int, c, cond: Conductance | None = None) -> np.ndarray:
+    """One macro step of Eq. 8 where source s uses its own window radius Rmap[s]."""
+    g = cond or Conductance(shape, D)
+    c = _f64(c).reshape(-1)
+    Rm = np.ascontiguousarray(Rmap, dtype=np.int32).reshape(-1)
+    if Rm.size != c.size:
+        raise ValueError("Rmap has the wrong size")
+    out = np.empty_like(c)
+    if _load().fo_superpose_rmap(*g.args, float(lam), Rm.ctypes.data_as(_I32), int(n_sub), _p(c), _p(out)) != 0:
+        raise ValueError("fo_superpose_rmap failed")
     return out
 
 

@@ -24,6 +24,7 @@
  * Compiled with -ffp-contract=off so that results agree bit for bit across x86-64 and AArch64 hosts.
  * Every sum below is a plain left-to-right FP64 sum in the loop order written.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -173,6 +174,65 @@ int fo_superpose(int nx, int ny, int nz, const double* gx, const double* gy, con
 /* Brute-force explicit FD march of a whole field over the full domain (no window), n_sub substeps:
  * the fine-mesh FD solver the paper compares against (Sec. 4.1).  By linearity (Eq. 8) it equals one
  * superposition step whenever every window covers the whole domain. */
+/* Per-source window radius from the local diffusivity (not in the paper, which has no window; reading
+ * of the batched variant): twice the diffusion length sqrt(2 D dt_macro) of the macro step, in cells,
+ * rounded up and clamped:  R(s) = clamp(ceil(2 sqrt(2 D(s) dt_macro) / h), R_min, R_max).
+ * Evaluated in FP64 in exactly this order: t = 2 D; t = t dt_macro; r = sqrt(t); r = 2 r; r = r / h. */
+void fo_radius_map(int64_t N, const double* D, double dt_macro, double h, int R_min, int R_max, int32_t* Rmap)
+{
+    for (int64_t s = 0; s < N; s++) {
+        double t = 2.0 * D[s];
+        t = t * dt_macro;
+        double r = sqrt(t);
+        r = 2.0 * r;
+        r = r / h;
+        double c = ceil(r);
+        int R = c > (double)R_max ? R_max : (int)c;
+        Rmap[s] = R < R_min ? R_min : R;
+    }
+}
+
+/* Eq. 8 with a radius per source: c_out(x) = sum_s c_in(s) k_s(x), k_s the kernel of s on its own
+ * window of radius Rmap[s] (scatter over sources, as fo_superpose). */
+int fo_superpose_rmap(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                      double lam, const int32_t* Rmap, int n_sub, const double* c_in, double* c_out)
+{
+    enum { CHUNK = 256 };
+    int64_t N = (int64_t)nx * ny * nz;
+    int Rmax = 0;
+    for (int64_t s = 0; s < N; s++) {
+        if (Rmap[s] < 0) return -1;
+        if (Rmap[s] > Rmax) Rmax = Rmap[s];
+    }
+    int64_t Wm = (int64_t)(2 * Rmax + 1) * (2 * Rmax + 1) * (2 * Rmax + 1);
+    double* k = (double*)malloc(sizeof(double) * (size_t)(Wm * CHUNK));
+    if (!k) return -1;
+    memset(c_out, 0, sizeof(double) * (size_t)N);
+    int bad = 0;
+    for (int64_t s0 = 0; s0 < N && !bad; s0 += CHUNK) {
+        int64_t s1 = s0 + CHUNK < N ? s0 + CHUNK : N;
+        /* kernels of a chunk of sources in parallel (independent), then the scatter in source order */
+        #pragma omp parallel for schedule(dynamic, 1) reduction(|:bad)
+        for (int64_t s = s0; s < s1; s++)
+            if (fo_source_kernel(nx, ny, nz, gx, gy, gz, lam, Rmap[s], n_sub, s, k + (s - s0) * Wm, NULL) != 0) bad = 1;
+        if (bad) break;
+        for (int64_t s = s0; s < s1; s++) {
+            const double* ks = k + (s - s0) * Wm;
+            int R = Rmap[s], W1 = 2 * R + 1;
+            int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
+            for (int oz = -R; oz <= R; oz++)
+                for (int oy = -R; oy <= R; oy++)
+                    for (int ox = -R; ox <= R; ox++) {
+                        int x = sx + ox, y = sy + oy, z = sz + oz;
+                        if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) continue;
+                        c_out[IDX(x, y, z, nx, ny)] += c_in[s] * ks[(ox + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (oz + R))];
+                    }
+        }
+    }
+    free(k);
+    return bad ? -1 : 0;
+}
+
 int fo_full_march(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                   double lam, int n_sub, const double* c_in, double* c_out)
 {
