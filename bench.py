@@ -163,6 +163,230 @@ def run_reference(args, w):
 
 # ----------------------------------------------------------------------------- CUDA path
 
+def march_kernel_name(prec: str, parts: int) -> str:
+    if prec == "fp64":
+        return "march_f64_kernel<R>"
+    return {4: "march_tm_kernel<R>", 5: "march_tmc_kernel<R>"}.get(parts, f"march_f32_kernel<R,{parts}>")
+
+
+def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: float, traffic, clocks, kname: str):
+    """Achieved FP32 flop rate of the march (13 flop per cell-substep over the clipped windows) against the
+    FP32 pipe peak at the measured maximum SM clock."""
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOP_PER_CELL_SUBSTEP * n_sub * window_cells / (march_ms * 1e-3) / 1e12
+    out = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": traffic,
+           "peak_source": f"FP32 pipe: {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz "
+                          f"(sm_max_mhz, {peak_src})",
+           "algorithmic": f"{FLOP_PER_CELL_SUBSTEP} flop per cell-substep x n_sub x sum of clipped window cells "
+                          f"({window_cells:.4g})"}
+    if clocks.get("sm_mhz"):
+        out["frac_at_sampled_clock"] = achieved / (num_sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    return out
+
+
+def run_batch(args, bw):
+    """The batched workload: every structure's radius map, kernels (chunk by chunk when they do not all
+    fit) and all macro steps through one fdirw_create_batch context; one step = create + step + destroy."""
+    import torch
+    from paper_2408_11376_gb300 import build as libbuild
+    from paper_2408_11376_gb300 import fdirw
+
+    ws, rank, local = _dist()
+    libbuild.build()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    t0 = time.perf_counter()
+    shapes, Ds_host, cs_host = bw.make()
+    t_gen = time.perf_counter() - t0
+    Ds = [torch.from_numpy(D).to(dev) for D in Ds_host]
+    c_host = np.concatenate(cs_host)
+    N = c_host.size
+    c0 = torch.from_numpy(c_host).to(dev)
+    c1 = torch.empty_like(c0)
+    stream = torch.cuda.Stream(device=dev)
+    dt_sub = min(fdirw.fdirw_stable_dt(s, D, device=local) for s, D in zip(shapes, Ds))
+    dt_macro = bw.n_sub * dt_sub
+    prec = args.prec if args.prec != "fp64" else "bf16"
+
+    def one_pass(times=None, p=prec, out=c1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            ctx = fdirw.fdirw_create_batch(shapes, Ds, dt_macro, bw.R_min, bw.R_max, bw.n_sub, p, device=local,
+                                           stream=stream)
+            ev[1].record(stream)
+            mass = fdirw.fdirw_step(ctx, c0, out, bw.steps, want_mass=True)
+            ev[2].record(stream)
+            info = fdirw.fdirw_get_info(ctx)
+            fdirw.fdirw_destroy(ctx)
+        if times is not None:
+            stream.synchronize()
+            times.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), info["kernels_ms"],
+                          info["last_gather_ms"], mass, info))
+        return mass
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    times = []
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            one_pass(times)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    total_ms = max_over_ranks(start.elapsed_time(end), pg, dev)
+    info = times[-1][5]
+    march_ms = statistics.mean(t[2] for t in times)
+    gather_ms = statistics.mean(t[3] for t in times)
+    mass0 = float(c_host.sum())
+
+    e2e = None
+    if not args.no_e2e:
+        Dp = [torch.from_numpy(D).pin_memory() for D in Ds_host]
+        cp = torch.from_numpy(c_host).pin_memory()
+        op = torch.empty_like(cp).pin_memory()
+
+        def e2e_pass():
+            with torch.cuda.stream(stream):
+                ctx = fdirw.fdirw_create_batch(shapes, Dp, dt_macro, bw.R_min, bw.R_max, bw.n_sub, prec,
+                                               device=local, stream=stream)
+                fdirw.fdirw_step(ctx, cp, op, bw.steps, want_mass=True)
+                fdirw.fdirw_destroy(ctx)
+
+        torch.cuda.synchronize(dev)
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_pass()
+        ee.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = max_over_ranks(es.elapsed_time(ee) / args.e2e_steps, pg, dev)
+        e2e = {"value": job_rate(ws, bw.steps, e_ms), "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+               "d2h_bytes_per_step": 8 * N + 8}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    accuracy = None
+    if not args.no_fp64 and ws == 1 and prec != "fp32":
+        ref = torch.empty_like(c0)
+        one_pass(p="fp32", out=ref)
+        stream.synchronize()
+        accuracy = {"vs": "fp32 storage, same batch", "rel_l2": float((torch.linalg.vector_norm(c1 - ref) /
+                                                                       torch.linalg.vector_norm(ref)).item())}
+        del ref
+
+    clocks = clk.summary()
+    roofline = fp32_alu_roofline(torch, dev, bw.n_sub, info["window_cells"], march_ms, args.traffic, clocks,
+                                 march_kernel_name(prec, info["march_parts"]))
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        t_src, threads, dt, ns = oracle_batch_sample(bw, shapes, Ds_host, dt_macro, args.ref_sample // 2)
+        cpu = {"value": 1.0 / (N * t_src), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{ns} seeded random sources of {bw.name}, each on its own radius ({dt:.1f} s of FP64 "
+                         f"windowed marches on {threads} host threads); macro-steps/s = 1/(N * seconds per source)"}
+    nch = info["n_chunks"]
+    n_launch = 5 * len(shapes) + 1 + nch * (2 + 2 * bw.steps) + 4
+    value = job_rate(ws, bw.steps * args.steps, total_ms)
+    n_src_pass = N
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": bw.name, "structures": len(shapes), "cells": N,
+                   "sides": sorted(set(s[0] for s in shapes)), "R": f"{bw.R_min}..{bw.R_max} by rule",
+                   "n_sub": bw.n_sub, "macro_steps": bw.steps, "prec": prec,
+                   "parallelism": "replicas" if ws > 1 else "single GPU", "chunks": nch,
+                   "l2": f"inputs larger than L2 (kernel cache {info['cache_bytes'] / 1e9:.1f} GB per chunk)"},
+        "source_kernels_per_s": n_src_pass / (march_ms * 1e-3),
+        "phase_ms": {"create": statistics.mean(t[0] for t in times), "step_call": statistics.mean(t[1] for t in times),
+                     "march_kernels": march_ms, "last_gather_per_chunk_sum": gather_ms, "host_generation_s": t_gen},
+        "graph_launches_per_pass": info["graph_launches"],
+        "mass_rel_err": abs(times[-1][4] - mass0) / mass0, "accuracy": accuracy,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": n_launch * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def oracle_batch_sample(bw, shapes, Ds, dt_macro, n_sources: int, seed: int = 9):
+    """Seconds per source of the FP64 oracle on a seeded sample of the batch's sources, each marched on
+    its own radius (all host threads)."""
+    import oracle
+    sizes = np.array([int(np.prod(s)) for s in shapes])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.integers(0, offs[-1], n_sources))
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    dt = 0.0
+    for i, shape in enumerate(shapes):
+        loc = pick[(pick >= offs[i]) & (pick < offs[i + 1])] - offs[i]
+        if loc.size == 0:
+            continue
+        R = oracle.radius_map(Ds[i], dt_macro, 1.0, bw.R_min, bw.R_max)
+        lam = dt_macro / bw.n_sub
+        cond = oracle.Conductance(shape, Ds[i])
+        for r in np.unique(R[loc]):
+            sel = loc[R[loc] == r]
+            t0 = time.perf_counter()
+            oracle.kernels(shape, Ds[i], lam, int(r), bw.n_sub, sel, cond)
+            dt += time.perf_counter() - t0
+    return dt / n_sources, threads, dt, n_sources
+
+
+def run_reference_batch(args, bw):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    shapes, Ds, _ = bw.make()
+    N = sum(int(np.prod(s)) for s in shapes)
+    dt_macro = bw.n_sub * min(oracle.stable_dt_sub(s, D) for s, D in zip(shapes, Ds))
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        t_src, threads, _, ns = oracle_batch_sample(bw, shapes, Ds, dt_macro, args.ref_sample // 2, seed=100 + i)
+        if i >= args.warmup:
+            per_step.append(t_src)
+    t_src = statistics.mean(per_step)
+    value = 1.0 / (N * t_src)
+    sample = (f"{args.ref_sample // 2} seeded random sources of {bw.name} per step, each on its own radius; "
+              "macro-steps/s = 1/(N * seconds per source), the oracle recomputing every kernel each step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * N * t_src, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": bw.name, "structures": len(shapes), "cells": N, "n_sub": bw.n_sub,
+                       "macro_steps": bw.steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, w):
     import torch
     from paper_2408_11376_gb300 import build as libbuild
@@ -267,24 +491,9 @@ def run_ours(args, w):
     if not args.no_fp64 and ws == 1:
         fp64 = fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec=prec)
 
-    peaks, peak_src = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak_tflops = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flops = FLOP_PER_CELL_SUBSTEP * w.n_sub * info["window_cells"]
-    achieved = flops / (march_ms * 1e-3) / 1e12
     clocks = clk.summary()
-    kname = ("march_f64_kernel<R>" if prec == "fp64" else
-             "march_tm_kernel<R>" if info["march_parts"] == 4 else f"march_f32_kernel<R,{info['march_parts']}>")
-    roofline = {"bound": "alu", "kernel": kname,
-                "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                "traffic": args.traffic,
-                "peak_source": f"FP32 pipe: {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz "
-                               f"(sm_max_mhz, {peak_src})",
-                "algorithmic": f"{FLOP_PER_CELL_SUBSTEP} flop per cell-substep x n_sub x sum of clipped window cells "
-                               f"({info['window_cells']:.4g})"}
-    if clocks.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = achieved / (num_sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    roofline = fp32_alu_roofline(torch, dev, w.n_sub, info["window_cells"], march_ms, args.traffic, clocks,
+                                 march_kernel_name(prec, info["march_parts"]))
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -450,6 +659,9 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     from paper_2408_11376_gb300 import synth
+    if args.workload in synth.BATCH_WORKLOADS:
+        bw = synth.BATCH_WORKLOADS[args.workload]
+        return run_reference_batch(args, bw) if args.impl == "reference" else run_batch(args, bw)
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

@@ -103,6 +103,10 @@ typedef struct {
     double   last_mass_out;  /* FP64 total of c_out after the last fdirw_step (if it was computed) */
     int32_t  march_parts;    /* thread mapping of the last kernel-cache build (see fdirw_opts) */
     int32_t  reserved;
+    int32_t  n_structures;   /* batch contexts: number of structures (0 for fdirw_create contexts) */
+    int32_t  n_chunks;       /* batch contexts: structure chunks whose kernels are built one at a time */
+    int32_t  window_R_min;   /* batch contexts: R_min of the radius rule */
+    int32_t  graph_launches; /* batch contexts: CUDA graph launches so far (one per fdirw_step call) */
 } fdirw_info;
 
 typedef struct fdirw_ctx fdirw_ctx;
@@ -158,6 +162,37 @@ FDIRW_API int fdirw_get_info(fdirw_ctx* ctx, fdirw_info* out);
 
 /* Release all device memory held by the context.  NULL-safe. */
 FDIRW_API void fdirw_destroy(fdirw_ctx* ctx);
+
+/* Create one context for a batch of n independent structures whose sources use per-source window radii
+ * (the paper has one domain and no window; Sec. 3.1 and Eq. 8 apply per structure).
+ *   n          : number of structures, >= 1; the total cell count must stay below 2^28
+ *   grids      : n grids (dimensions, cell size h_i)
+ *   D_maps     : n pointers to the structures' cell diffusivities (host or device, each 8-byte aligned,
+ *                finite, >= 0); copied, not retained
+ *   dt_macro   : macro step shared by all structures (dt_sub = dt_macro / n_sub; each structure is
+ *                checked against its own stability limit)
+ *   R_min/R_max: clamp of the radius rule R(s) = clamp(ceil(2 sqrt(2 D(s) dt_macro) / h_i), R_min,
+ *                R_max), evaluated in FP64 in that order; 0 <= R_min <= R_max <= 10
+ *   n_sub      : explicit substeps per macro step, >= 0
+ *   opts       : as for fdirw_create; prec must be FDIRW_FP32, FDIRW_FP32_STORE_FP16 or
+ *                FDIRW_FP32_STORE_BF16; mem_limit (or, when 0, the free device memory less a reserve)
+ *                bounds the kernel cache
+ * Fields passed to fdirw_step / fdirw_mass are the concatenation of the structures' fields, structure 0
+ * first, each x-fastest.  When the kernels of all structures do not fit the budget, the structures are
+ * split into chunks of consecutive structures and each fdirw_step call builds the kernels of one chunk,
+ * runs all n_steps macro steps on its cells and moves to the next (so pass all steps in one call); the
+ * device work of an fdirw_step call runs as one CUDA graph (captured on first use for the given fields
+ * and step count, replayed afterwards).  fdirw_read_kernels (sources as global cell indices, output on
+ * the (2 R_max + 1)^3 layout, zero outside a source's own window) needs a single chunk.
+ * Errors: FDIRW_ERR_ARG, FDIRW_ERR_UNSTABLE, FDIRW_ERR_NOMEM (a single structure's kernels exceed the
+ * budget), FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* D_maps, double dt_macro,
+                                 int32_t R_min, int32_t R_max, int32_t n_sub, const fdirw_opts* opts,
+                                 fdirw_ctx** out);
+
+/* Window radius of every source (n_cells int32 values, host): the radius rule's value for batch
+ * contexts, window_R for fdirw_create contexts.  Synchronises the context stream. */
+FDIRW_API int fdirw_read_radius(fdirw_ctx* ctx, int32_t* out);
 
 /* Message of the last failed call on ctx, or of the last failed call on this host thread when ctx is
  * NULL (for failures of fdirw_create / fdirw_stable_dt / fdirw_mass_noalloc).  Never NULL; the string

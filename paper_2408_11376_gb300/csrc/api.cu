@@ -15,7 +15,8 @@ using fdirw::Grid;
 using fdirw::Store;
 
 
-namespace {
+namespace fdirw {
+namespace host {
 
 thread_local std::string g_err;
 
@@ -27,25 +28,6 @@ int fail(fdirw_ctx* c, int code, const std::string& msg) {
 std::string cuda_msg(const char* what, cudaError_t e) {
     return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
 }
-
-#define FDIRW_CUDA(ctx, call)                                              \
-    do {                                                                   \
-        cudaError_t e_ = (call);                                           \
-        if (e_ != cudaSuccess) return fail((ctx), FDIRW_ERR_CUDA, cuda_msg(#call, e_)); \
-    } while (0)
-
-// Makes `dev` current for the duration of a call and restores the caller's device afterwards.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
-        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
-};
-
-enum class Kind { Host, Device, Foreign };
 
 // Host (pageable or pinned) vs device memory of `device`; managed memory counts as device.
 Kind classify(const void* p, int device) {
@@ -82,6 +64,13 @@ void dfree(void*& p) {
     if (p) cudaFree(p);
     p = nullptr;
 }
+
+}  // namespace host
+}  // namespace fdirw
+
+using namespace fdirw::host;
+
+namespace {
 
 // Sum over one axis of the clipped window extents: sum_x (min(x+R, n-1) - max(x-R, 0) + 1).
 double axis_window_sum(int n, int R) {
@@ -128,6 +117,7 @@ int conductances(fdirw_ctx* c, const double* D, double* g3[3], double* max_sum) 
 }
 
 void release(fdirw_ctx* c) {
+    fdirw::batch_release(c);
     for (auto& p : c->coef) dfree(p);
     dfree(c->Q);
     void* p;
@@ -282,6 +272,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
 int fdirw_kernels(fdirw_ctx* c) {
     if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
     DeviceGuard dg(c->device);
+    if (c->batch) return fdirw::batch_kernels(c);
     if (c->R == 0) { c->kernels_ready = true; return FDIRW_OK; }
     const int rc = fdirw::ensure_cache(c);
     if (rc != FDIRW_OK) return rc;
@@ -289,6 +280,7 @@ int fdirw_kernels(fdirw_ctx* c) {
     a.g = c->g;
     a.R = c->R;
     a.Rq = c->R;
+    a.q_stride = c->g.n;
     a.n_sub = c->n_sub;
     if (c->store == Store::F64) {
         a.dx = reinterpret_cast<const double*>(c->coef[0]);
@@ -320,6 +312,7 @@ int fdirw_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
     if (((reinterpret_cast<uintptr_t>(c_in) | reinterpret_cast<uintptr_t>(c_out)) & 7u) != 0)
         return fail(c, FDIRW_ERR_ARG, "c_in and c_out must be 8-byte aligned");
     DeviceGuard dg(c->device);
+    if (c->batch) return fdirw::batch_step(c, c_in, c_out, n_steps, mass_out);
     const Kind kin = classify(c_in, c->device), kout = classify(c_out, c->device);
     if (kin == Kind::Foreign || kout == Kind::Foreign)
         return fail(c, FDIRW_ERR_ARG, "c_in/c_out are device memory of another device");
@@ -391,6 +384,10 @@ int fdirw_read_kernels(fdirw_ctx* c, const int64_t* sources, int64_t n, double* 
         if (sources[q] < 0 || sources[q] >= c->g.n) return fail(c, FDIRW_ERR_ARG, "source index out of range");
     if (!c->kernels_ready) return fail(c, FDIRW_ERR_STATE, "kernel cache not built (call fdirw_kernels)");
     if (n == 0) return FDIRW_OK;
+    if (c->batch) {
+        DeviceGuard dg(c->device);
+        return fdirw::batch_read_kernels(c, sources, n, out);
+    }
     if (c->R == 0) {
         for (int64_t q = 0; q < n; q++) out[q] = 1.0;
         return FDIRW_OK;
@@ -444,6 +441,7 @@ int fdirw_get_info(fdirw_ctx* c, fdirw_info* out) {
         FDIRW_CUDA(c, cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
         out->last_gather_ms = ms;
     }
+    if (c->batch) return fdirw::batch_info(c, out);
     return FDIRW_OK;
 }
 

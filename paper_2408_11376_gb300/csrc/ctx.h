@@ -9,6 +9,10 @@
 #include "fdirw.h"
 #include "fdirw_internal.h"
 
+namespace fdirw {
+struct Batch;   // batch of structures with per-source window radii (batch.cu)
+}
+
 struct fdirw_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -37,10 +41,52 @@ struct fdirw_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double window_cells = 0.0;
     double mass_in = NAN, mass_out = NAN;
+    fdirw::Batch* batch = nullptr;                  // non-null for fdirw_create_batch contexts
     std::string err;
 };
 
 namespace fdirw {
+
+// Host helpers of the C ABI (api.cu).
+namespace host {
+// Records msg on the context (or as the thread's last error when c is NULL) and returns code.
+int fail(fdirw_ctx* c, int code, const std::string& msg);
+std::string cuda_msg(const char* what, cudaError_t e);
+// Makes `dev` current for the duration of a call and restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+enum class Kind { Host, Device, Foreign };
+// Host (pageable or pinned) vs device memory of `device`; managed memory counts as device.
+Kind classify(const void* p, int device);
+bool grid_ok(const fdirw_grid* g);
+// cudaMalloc that honours the context's mem_limit and keeps its byte count.
+int dalloc(fdirw_ctx* c, void** p, uint64_t bytes, const char* what);
+void dfree(void*& p);
+}  // namespace host
+
+#define FDIRW_CUDA(ctx, call)                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError();   /* a failed call must not surface again in a later check */    \
+            return fdirw::host::fail((ctx), FDIRW_ERR_CUDA, fdirw::host::cuda_msg(#call, e_));    \
+        }                                                                                         \
+    } while (0)
+
+// Batch contexts (batch.cu): the entry points of the C ABI forward to these when c->batch is set.
+int batch_kernels(fdirw_ctx* c);
+int batch_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps, double* mass_out);
+int batch_read_kernels(fdirw_ctx* c, const int64_t* sources, int64_t n, double* out);
+int batch_info(fdirw_ctx* c, fdirw_info* out);
+void batch_release(fdirw_ctx* c);
+
 // Allocates (once) and zeroes the kernel cache of a context; honours mem_limit.
 int ensure_cache(fdirw_ctx* c);
 }  // namespace fdirw

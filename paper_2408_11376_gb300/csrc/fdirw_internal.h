@@ -43,15 +43,29 @@ struct MarchArgs {
     int n_sub;
     const float* ax; const float* ay; const float* az;     // FP32 path: lam*g
     const double* dx; const double* dy; const double* dz;  // FP64 path: lam*g
-    void* Q;              // kernel cache, (2R+1)^3 planes of N values, destination-indexed
+    void* Q;              // kernel cache, (2Rq+1)^3 planes
     Store store;
     double* sigma;        // N: 1 / FP64 sum of the stored values of each source
     int64_t src_begin, src_end;
     const int64_t* list;  // nullable: march sources list[src_begin..src_end) instead of that range
+    // Batch of structures (nstruct > 0, FP32 march only): sources and coefficients index the
+    // concatenation; structure i holds global cells [s_base[i], s_base[i+1]) of dimensions s_dims[i].
+    int nstruct;
+    const int64_t* s_base;
+    const int4* s_dims;
+    // Q index = plane * q_stride + column; the column is the destination cell (src_major = 0) or the
+    // source's position in [src_begin, src_end) (src_major = 1, the per-radius buckets of a batch).
+    int64_t q_stride;
+    int src_major;
 };
-// parts_req: threads per window column for the FP32 march (1..3), or 0 to autotune (timed once per
-// device, R and storage, then cached); parts_used receives the mapping launched.
+// parts_req: FP32 march thread mapping (1..3 threads per window column, 4 = 2x2 column blocks with TMEM
+// faces, 5 = one column per thread with TMEM lateral faces), or 0 to autotune (timed once per device, R
+// and storage, then cached); parts_used receives the mapping launched.
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used);
+// The thread mapping launch_march would use for parts_req (timing the candidates on `a`'s sources when
+// autotuning and nothing is cached, which synchronises st and overwrites part of a.Q); launches nothing
+// else, so that the following launches can be captured into a graph.
+cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts);
 
 // ---------------------------------------------------------------- superpose.cu
 // Padded layout of the scaled field chat = sigma * c: (nx+2R) x (ny+2R) x (nz+2R), zero halo.

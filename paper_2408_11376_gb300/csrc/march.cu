@@ -65,6 +65,33 @@ __device__ __forceinline__ int64_t qplane(const MarchArgs& a, int R, int x, int 
     return (int64_t)(x + d) + (int64_t)Wq * ((y + d) + (int64_t)Wq * (k + d));
 }
 
+// Structure holding a source: its dimensions and first global cell (a batch concatenates structures;
+// a single grid is structure 0 with base 0).  s becomes the source's index within its structure.
+struct SrcLoc {
+    int nx, ny, nz;
+    int64_t base;
+};
+__device__ __forceinline__ SrcLoc locate(const MarchArgs& a, bool ok, int64_t& s) {
+    SrcLoc L{a.g.nx, a.g.ny, a.g.nz, 0};
+    if (ok && a.nstruct > 0) {
+        int lo = 0, hi = a.nstruct - 1;               // last structure whose first cell is <= s
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.s_base + mid) <= s) lo = mid; else hi = mid - 1;
+        }
+        const int4 d = __ldg(a.s_dims + lo);
+        L = SrcLoc{d.x, d.y, d.z, __ldg(a.s_base + lo)};
+        s -= L.base;
+    }
+    return L;
+}
+
+// Column of the kernel cache for a stored value: the destination cell (destination-indexed layout) or
+// the source's position in the launch's source range (source-indexed layout of the radius buckets).
+__device__ __forceinline__ int64_t qcol(const MarchArgs& a, int64_t dest, int64_t pos) {
+    return a.src_major ? pos - a.src_begin : dest;
+}
+
 // Rounds v to the storage type, writes it to Q[idx] and returns the stored value widened to float
 // (exact for every storage type).
 __device__ __forceinline__ float put(void* Q, Store st, int64_t idx, float v) {
@@ -114,8 +141,6 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
     const int ci = col % W1, cj = col / W1;
     const int k0 = part * KS;                                  // first own cell of the column
     const int kn = (W1 - k0) < KS ? (W1 - k0) : KS;            // number of own cells
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const int64_t nxy = (int64_t)nx * ny;
     const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
 
     const int base = (slot * COLS + col) * W1;
@@ -131,6 +156,13 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
         int64_t s = first + slot;
         const bool src_ok = active && s < a.src_end;
         if (src_ok && a.list) s = a.list[s];       // explicit source list (e.g. the surrogate's rejects)
+        const int64_t pos = first + slot;                     // position of the source in the launch range
+        const SrcLoc L = locate(a, src_ok, s);
+        const int nx = L.nx, ny = L.ny, nz = L.nz;
+        const int64_t nxy = (int64_t)nx * ny;
+        const float* ax = a.ax + L.base;   // coefficients of the source's structure
+        const float* ay = a.ay + L.base;
+        const float* az = a.az + L.base;
         int sx = 0, sy = 0, sz = 0;
         if (src_ok) {
             sx = (int)(s % nx);
@@ -155,12 +187,12 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
             float vxm = 0.f, vxp = 0.f, vym = 0.f, vyp = 0.f, vz = 0.f;
             if (ok) {
                 const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                if (ci > 0 && x > 0) vxm = __ldg(a.ax + i - 1);
-                if (ci < 2 * R && x + 1 < nx) vxp = __ldg(a.ax + i);
-                if (cj > 0 && y > 0) vym = __ldg(a.ay + i - nx);
-                if (cj < 2 * R && y + 1 < ny) vyp = __ldg(a.ay + i);
-                if (k < 2 * R && z + 1 < nz) vz = __ldg(a.az + i);
-                if (j == 0 && k > 0 && z > 0) czb = __ldg(a.az + i - nxy);
+                if (ci > 0 && x > 0) vxm = __ldg(ax + i - 1);
+                if (ci < 2 * R && x + 1 < nx) vxp = __ldg(ax + i);
+                if (cj > 0 && y > 0) vym = __ldg(ay + i - nx);
+                if (cj < 2 * R && y + 1 < ny) vyp = __ldg(ay + i);
+                if (k < 2 * R && z + 1 < nz) vz = __ldg(az + i);
+                if (j == 0 && k > 0 && z > 0) czb = __ldg(az + i - nxy);
             }
             cxm[j] = vxm; cxp[j] = vxp; cym[j] = vym; cyp[j] = vyp; cz[j] = vz;
             u[j] = (src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
@@ -212,7 +244,7 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
                     float st = 0.f;
                     if (col_ok && z >= 0 && z < nz) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                        st = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.g.n + i, u[j]);
+                        st = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.base + i, pos), u[j]);
                     }
                     sbuf[base + k] = st;
                 }
@@ -457,8 +489,6 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
     const int tr = (active && bi < NB - 1) ? t + 1 : t;
     const int tb = (active && bj > 0) ? t - NB : t;
     const int tt = (active && bj < NB - 1) ? t + NB : t;
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const int64_t nxy = (int64_t)nx * ny;
     const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
 
     for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
@@ -466,6 +496,13 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
         int64_t s = first + slot;
         const bool src_ok = active && s < a.src_end;
         if (src_ok && a.list) s = a.list[s];       // explicit source list (e.g. the surrogate's rejects)
+        const int64_t pos = first + slot;                     // position of the source in the launch range
+        const SrcLoc L = locate(a, src_ok, s);
+        const int nx = L.nx, ny = L.ny, nz = L.nz;
+        const int64_t nxy = (int64_t)nx * ny;
+        const float* ax = a.ax + L.base;   // coefficients of the source's structure
+        const float* ay = a.ay + L.base;
+        const float* az = a.az + L.base;
         int sx = 0, sy = 0, sz = 0;
         if (src_ok) {
             sx = (int)(s % nx);
@@ -483,13 +520,13 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
             return (int64_t)(sx - R + x) + (int64_t)nx * (sy - R + y) + nxy * (sz - R + k);
         };
         auto xface = [&](int x, int y, int k) -> float {   // face between window x and x+1
-            return (x + 1 < W1 && cell_ok(x, y, k) && sx - R + x + 1 < nx) ? __ldg(a.ax + gidx(x, y, k)) : 0.f;
+            return (x + 1 < W1 && cell_ok(x, y, k) && sx - R + x + 1 < nx) ? __ldg(ax + gidx(x, y, k)) : 0.f;
         };
         auto yface = [&](int x, int y, int k) -> float {
-            return (y + 1 < W1 && cell_ok(x, y, k) && sy - R + y + 1 < ny) ? __ldg(a.ay + gidx(x, y, k)) : 0.f;
+            return (y + 1 < W1 && cell_ok(x, y, k) && sy - R + y + 1 < ny) ? __ldg(ay + gidx(x, y, k)) : 0.f;
         };
         auto zface = [&](int x, int y, int k) -> float {
-            return (k + 1 < W1 && cell_ok(x, y, k) && sz - R + k + 1 < nz) ? __ldg(a.az + gidx(x, y, k)) : 0.f;
+            return (k + 1 < W1 && cell_ok(x, y, k) && sz - R + k + 1 < nz) ? __ldg(az + gidx(x, y, k)) : 0.f;
         };
 
         // Registers: state u[sub][k], z faces cz[sub][k] (+z face of the cell), diagonals of the levels
@@ -608,7 +645,7 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
                 for (int k = 0; k < W1; k++) {
                     float stv = 0.f;
                     if (cell_ok(x, y, k)) {
-                        stv = put(a.Q, a.store, qplane(a, R, x, y, k) * a.g.n + gidx(x, y, k), u[sc][k]);
+                        stv = put(a.Q, a.store, qplane(a, R, x, y, k) * a.q_stride + qcol(a, L.base + gidx(x, y, k), pos), u[sc][k]);
                     }
                     sbuf[k * LEVEL + sc * PLANE + t] = stv;
                 }
@@ -700,8 +737,6 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
     const bool active = t < COLS;
     const int col = active ? t : 0;
     const int ci = col % W1, cj = col / W1;
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const int64_t nxy = (int64_t)nx * ny;
     const int64_t nbatch = a.src_end - a.src_begin;
     const int base = col * W1;
     const int xm = ci > 0 ? base - W1 : base;
@@ -714,6 +749,13 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
         int64_t s = first;
         const bool src_ok = active && s < a.src_end;
         if (src_ok && a.list) s = a.list[s];
+        const int64_t pos = first;                     // position of the source in the launch range
+        const SrcLoc L = locate(a, src_ok, s);
+        const int nx = L.nx, ny = L.ny, nz = L.nz;
+        const int64_t nxy = (int64_t)nx * ny;
+        const float* ax = a.ax + L.base;   // coefficients of the source's structure
+        const float* ay = a.ay + L.base;
+        const float* az = a.az + L.base;
         int sx = 0, sy = 0, sz = 0;
         if (src_ok) {
             sx = (int)(s % nx);
@@ -738,11 +780,11 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                     const bool ok = col_ok && z >= 0 && z < nz;
                     if (ok) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                        if (ci > 0 && x > 0) vxm = __ldg(a.ax + i - 1);
-                        if (ci < 2 * R && x + 1 < nx) vxp = __ldg(a.ax + i);
-                        if (cj > 0 && y > 0) vym = __ldg(a.ay + i - nx);
-                        if (cj < 2 * R && y + 1 < ny) vyp = __ldg(a.ay + i);
-                        if (k < 2 * R && z + 1 < nz) vz = __ldg(a.az + i);
+                        if (ci > 0 && x > 0) vxm = __ldg(ax + i - 1);
+                        if (ci < 2 * R && x + 1 < nx) vxp = __ldg(ax + i);
+                        if (cj > 0 && y > 0) vym = __ldg(ay + i - nx);
+                        if (cj < 2 * R && y + 1 < ny) vyp = __ldg(ay + i);
+                        if (k < 2 * R && z + 1 < nz) vz = __ldg(az + i);
                     }
                     cz[k < W1 ? k : 0] = vz;
                     am[k < W1 ? k : 0] = -(((vxm + vxp) + (vym + vyp)) + (zprev + vz));
@@ -806,7 +848,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                 float stv = 0.f;
                 if (col_ok && z >= 0 && z < nz) {
                     const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                    stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.g.n + i, u[k]);
+                    stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.base + i, pos), u[k]);
                 }
                 sbuf[base + k] = stv;
             }
@@ -962,6 +1004,27 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
 }
 
 }  // namespace
+
+cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts) {
+    if (a.store == Store::F64) { *parts = 1; return cudaSuccess; }
+    if (a.R > 8) { *parts = 5; return cudaSuccess; }
+    if (parts_req >= 1 && parts_req <= 5) { *parts = parts_req; return cudaSuccess; }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, a.R, (int)a.store);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) { *parts = it->second; return cudaSuccess; }
+    }
+    int P = 0;
+    cudaError_t e = tune_parts(a, num_sms, st, &P);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = P;
+    *parts = P;
+    return cudaSuccess;
+}
 
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
     int P = 1;

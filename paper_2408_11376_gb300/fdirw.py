@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": FDIRW_FP64, "fp32": FDIRW_FP32, "fp16": FDIRW_FP32_STORE_F
 EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "fdirw_mass", "fdirw_read_kernels",
             "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc", "fdirw_net_create",
             "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
-            "fdirw_kernels_surrogate")
+            "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -61,7 +61,9 @@ class fdirw_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("window_cells", ctypes.c_double),
                 ("kernels_ms", ctypes.c_float), ("last_gather_ms", ctypes.c_float),
                 ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double),
-                ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_structures", ctypes.c_int32), ("n_chunks", ctypes.c_int32), ("window_R_min", ctypes.c_int32),
+                ("graph_launches", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -104,6 +106,9 @@ def load(path: str | None = None):
         lib.fdirw_net_gradients.argtypes = [vp, vp, vp, i64, vp, vp, dp]
         lib.fdirw_net_train_step.argtypes = [vp, vp, vp, i64, vp, ctypes.c_float, dp]
         lib.fdirw_kernels_surrogate.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        lib.fdirw_create_batch.argtypes = [i32, ctypes.POINTER(fdirw_grid), ctypes.POINTER(vp), ctypes.c_double, i32,
+                                           i32, i32, ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
+        lib.fdirw_read_radius.argtypes = [vp, vp]
         for name in EXPORTED:
             if name not in ("fdirw_destroy", "fdirw_last_error", "fdirw_net_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -169,6 +174,38 @@ def fdirw_create(shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp3
     _check(lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(_ptr(D)), float(dt_macro), int(window_R), int(n_sub),
                             ctypes.byref(o), ctypes.byref(ctx)))
     return ctx.value
+
+
+def fdirw_create_batch(shapes, Ds, dt_macro: float, R_min: int, R_max: int, n_sub: int, prec="fp32", hs=None,
+                       device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0) -> int:
+    """Context for a batch of structures with per-source radii; fields are the concatenation of the
+    structures' fields.  Returns the handle; release it with fdirw_destroy."""
+    lib = load()
+    n = len(shapes)
+    if len(Ds) != n:
+        raise ValueError("one D map per structure")
+    hs = [1.0] * n if hs is None else list(hs)
+    grids = (fdirw_grid * n)()
+    ptrs = (ctypes.c_void_p * n)()
+    for i, (shape, D) in enumerate(zip(shapes, Ds)):
+        nx, ny, nz = (int(v) for v in shape)
+        _check_f64(D, nx * ny * nz)
+        grids[i] = fdirw_grid(nx, ny, nz, float(hs[i]))
+        ptrs[i] = _ptr(D)
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), int(march_parts), 0)
+    ctx = ctypes.c_void_p(0)
+    _check(lib.fdirw_create_batch(int(n), grids, ptrs, float(dt_macro), int(R_min), int(R_max), int(n_sub),
+                                  ctypes.byref(o), ctypes.byref(ctx)))
+    return ctx.value
+
+
+def fdirw_read_radius(ctx: int, n_cells: int) -> np.ndarray:
+    """Window radius of every source (int32 [n_cells])."""
+    out = np.empty(int(n_cells), dtype=np.int32)
+    _check(load().fdirw_read_radius(ctypes.c_void_p(ctx), ctypes.c_void_p(out.ctypes.data)), ctypes.c_void_p(ctx))
+    return out
 
 
 def fdirw_kernels(ctx: int) -> None:
@@ -271,6 +308,24 @@ class FDiRW:
             self.close()
         except Exception:
             pass
+
+
+class FDiRWBatch(FDiRW):
+    """Owns one batch context: ``FDiRWBatch(shapes, Ds, dt_macro, R_min, R_max, n_sub, prec)``.  Fields are
+    the concatenation of the structures' fields (``offsets[i]`` is structure i's first cell)."""
+
+    def __init__(self, shapes, Ds, dt_macro: float, R_min: int, R_max: int, n_sub: int, prec="fp32", hs=None,
+                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0):
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        sizes = [a * b * c for a, b, c in self.shapes]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        self.R = int(R_max)
+        self.ctx = fdirw_create_batch(self.shapes, Ds, dt_macro, R_min, R_max, n_sub, prec, hs, device, stream,
+                                      mem_limit, march_parts)
+
+    def radius(self) -> np.ndarray:
+        return fdirw_read_radius(self.ctx, self.n)
 
 
 # --------------------------------------------------------------------------- learned surrogate

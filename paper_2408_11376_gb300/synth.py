@@ -179,3 +179,47 @@ WORKLOADS = {
     # 192^3, porosity 0.4, D 1 / 1e-6, R=8, n_sub=200, 20 steps, c = 1 in solid.
     "fdirw-192c-r8": Workload("fdirw-192c-r8", 192, 0.40, "two_phase", 1e-6, 8, 200, 20, "solid_one", _S0 + 2),
 }
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    """Many independent structures with per-source window radii: cube sides drawn uniformly from
+    `sides`, porosity from U[porosity_range], per-sphere log10 D ratio U[3, 8] (pore D = 1), c = 1 in
+    solid; the radius rule clamps to [R_min, R_max]; dt_macro = n_sub * (smallest stable substep)."""
+    name: str
+    n_struct: int
+    sides: tuple
+    porosity_range: tuple
+    R_min: int
+    R_max: int
+    n_sub: int
+    steps: int
+    seed: int
+
+    def layout(self):
+        """[(side, porosity, structure seed)] for every structure (cheap: no geometry)."""
+        rng = SplitMix64(self.seed)
+        out = []
+        for i in range(self.n_struct):
+            side = self.sides[min(int(rng.uniform(0.0, len(self.sides))), len(self.sides) - 1)]
+            por = rng.uniform(*self.porosity_range)
+            out.append((side, por, self.seed * 1000 + i))
+        return out
+
+    def make(self):
+        """Returns (shapes, Ds, c0s): one entry per structure."""
+        shapes, Ds, cs = [], [], []
+        for side, por, s in self.layout():
+            p = sphere_packing((side,) * 3, por, s)
+            shapes.append((side,) * 3)
+            Ds.append(diffusivity_per_sphere(p, 1.0))
+            cs.append(field_solid_one(p))
+        return shapes, Ds, cs
+
+
+BATCH_WORKLOADS = {
+    # 64 structures, sides 32..128 step 16, porosity U[0.35, 0.4], radius 3..10 by the rule, n_sub = 75
+    # at the stability limit (pore R = 10, solid R = 3), 10 macro steps.
+    "fdirw-batch64-r3to10": BatchWorkload("fdirw-batch64-r3to10", 64, (32, 48, 64, 80, 96, 112, 128), (0.35, 0.40),
+                                          3, 10, 75, 10, _S0 + 3),
+}

@@ -57,6 +57,30 @@ def test_host_side_argument_checks(lib):
     lib.fdirw_destroy(None)   # NULL-safe
 
 
+def test_batch_host_side_argument_checks(lib):
+    D = np.ones(64)
+    g = (fdirw.fdirw_grid * 2)(fdirw.fdirw_grid(4, 4, 4, 1.0), fdirw.fdirw_grid(4, 4, 4, 1.0))
+    ptrs = (ctypes.c_void_p * 2)(D.ctypes.data, D.ctypes.data)
+    huge = (fdirw.fdirw_grid * 1)(fdirw.fdirw_grid(1024, 1024, 256, 1.0))     # 2^28 cells
+    fp64 = fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)
+    parts6 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 6, 0)
+    bad_grid = (fdirw.fdirw_grid * 1)(fdirw.fdirw_grid(4, 0, 4, 1.0))
+    cases = [(0, g, ptrs, 1.0, 1, 3, 2, None), (2, None, ptrs, 1.0, 1, 3, 2, None), (2, g, None, 1.0, 1, 3, 2, None),
+             (2, g, ptrs, 1.0, 1, 11, 2, None), (2, g, ptrs, 1.0, 4, 3, 2, None), (2, g, ptrs, 1.0, -1, 3, 2, None),
+             (2, g, ptrs, -1.0, 1, 3, 2, None), (2, g, ptrs, 1.0, 1, 3, -2, None), (1, huge, ptrs, 1.0, 1, 3, 2, None),
+             (2, g, ptrs, 1.0, 1, 3, 2, fp64), (2, g, ptrs, 1.0, 1, 3, 2, parts6), (1, bad_grid, ptrs, 1.0, 1, 3, 2, None)]
+    for n, grids, dm, dt, rmin, rmax, n_sub, opts in cases:
+        ctx = ctypes.c_void_p(1234)
+        rc = lib.fdirw_create_batch(n, grids, dm, dt, rmin, rmax, n_sub, ctypes.byref(opts) if opts else None,
+                                    ctypes.byref(ctx))
+        assert rc == fdirw.FDIRW_ERR_ARG, (n, dt, rmin, rmax, n_sub)
+        assert ctx.value is None
+    null_ptrs = (ctypes.c_void_p * 2)(D.ctypes.data, None)
+    assert lib.fdirw_create_batch(2, g, null_ptrs, 1.0, 1, 3, 2, None, ctypes.byref(ctypes.c_void_p())) == \
+        fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_read_radius(None, None) == fdirw.FDIRW_ERR_ARG
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     saved = fdirw._lib
     try:
