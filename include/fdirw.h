@@ -107,6 +107,9 @@ typedef struct {
     int32_t  n_chunks;       /* batch contexts: structure chunks whose kernels are built one at a time */
     int32_t  window_R_min;   /* batch contexts: R_min of the radius rule */
     int32_t  graph_launches; /* batch contexts: CUDA graph launches so far (one per fdirw_step call) */
+    int32_t  dest_indexed_radii; /* batch contexts: bit r set when radius r's kernels are stored
+                                    destination-indexed (radii on >= 20% of the cells), else source-indexed */
+    int32_t  reserved2;
 } fdirw_info;
 
 typedef struct fdirw_ctx fdirw_ctx;

@@ -5,12 +5,16 @@
 //   radius     R(s) = clamp(ceil(2 sqrt(2 D(s) dt_macro) / h), R_min, R_max)   (FP64, this order)
 //   buckets    the sources of each radius r, in global cell order; code(s) = (r << 28) | position of s
 //              in its bucket
-//   kernels    radius r: K_r[plane][j], plane = offset in the (2r+1)^3 window, j = the source's position
-//              in the chunk's part of bucket r (source-indexed, so every stored value is a real kernel
-//              value: sum_s (2R(s)+1)^3 values instead of N (2 R_max + 1)^3)
-//   gather     c'(x) = sum over radii r (ascending), offsets o in the r-window (z, y rows), of
-//              K_r[o][j(x - o)] * chat(x - o) for the sources x - o of radius r: float-float per row,
-//              FP64 across rows, the same arithmetic as the uniform gather.
+//   kernels    per radius r, one of two layouts (planes = offsets of the (2r+1)^3 window):
+//              * destination-indexed, Q_r[plane][x] as in a uniform context (zero where the source x - o
+//                has another radius), for radii held by at least kDestFraction of the cells: the gather
+//                streams it with vector loads and needs no lookup;
+//              * source-indexed, K_r[plane][j], j = the source's position in the chunk's part of bucket
+//                r, for rare radii: only real kernel values are stored, and the gather finds j(x - o)
+//                through the bucket code of the source.
+//   gather     c'(x) = the source-indexed radii (ascending) in one pass, then each destination-indexed
+//              radius (ascending) accumulated on top; within a radius the rows (o_z, o_y) ascend and each
+//              row is a float-float sum added to the FP64 total, the arithmetic of the uniform gather.
 //   chunks     structures are independent, so when the kernels of all of them do not fit the memory
 //              budget they are processed in chunks of consecutive structures: build the chunk's kernels,
 //              run all requested macro steps on its cells, move on.
@@ -37,6 +41,7 @@ constexpr int kCodeShift = 28;
 constexpr uint32_t kCodeMask = (1u << kCodeShift) - 1u;
 constexpr int64_t kMaxBatchCells = (int64_t)1 << kCodeShift;   // bucket positions fit 28 bits
 constexpr int kTileX = 32, kTileY = 8;                           // gather block: 32 x 8 destinations
+constexpr double kDestFraction = 0.2;          // radii on at least this share of the cells: destination-indexed
 
 inline int64_t wcells(int r) { return (int64_t)(2 * r + 1) * (2 * r + 1) * (2 * r + 1); }
 inline uint64_t align256(uint64_t v) { return (v + 255u) & ~(uint64_t)255u; }
@@ -44,6 +49,7 @@ inline uint64_t align256(uint64_t v) { return (v + 255u) & ~(uint64_t)255u; }
 struct Chunk {
     int s0 = 0, s1 = 0;                          // structures [s0, s1)
     int64_t c0 = 0, c1 = 0;                      // their global cells
+    int64_t qn = 0;                              // columns of a destination-indexed plane (16-aligned slots)
     int64_t seg_begin[kMaxR + 1] = {}, seg_end[kMaxR + 1] = {};   // positions in each bucket list
     uint64_t k_off[kMaxR + 1] = {};              // byte offset of the radius-r kernels in the arena
     uint64_t k_bytes = 0;
@@ -66,6 +72,11 @@ struct Batch {
     std::vector<int64_t> before[kMaxR + 1];      // n + 1: bucket-r sources in structures < i
     int64_t* d_list[kMaxR + 1] = {};
     uint32_t* d_code = nullptr;
+    uint32_t dest_mask = 0;                      // bit r: radius r uses the destination-indexed layout
+    std::vector<int64_t> qbase;                  // n: first cache column of each structure within its chunk
+    int64_t* d_qbase = nullptr;
+    std::vector<int64_t> pbase;                  // n + 1: first element of each structure's padded chat
+    float2* chat_pad = nullptr;                  // sigma * c with a halo of R_max (destination-indexed radii)
     std::vector<Chunk> chunks;
     void* arena = nullptr;
     uint64_t arena_bytes = 0;
@@ -124,7 +135,10 @@ struct VarArgs {
     const int4* s_dims;
     const int64_t* blk;
     int s0, s1;
-    uint32_t rmask;                              // bit r set: radius r present
+    uint32_t rmask;                              // bit r set: radius r summed by gather_var_kernel
+    uint32_t dmask;                              // bit r set: radius r is destination-indexed
+    bool acc_in;                                 // add to out instead of overwriting it
+    const int64_t* qbase;
     const void* K[kMaxR + 1];
     int64_t jbase[kMaxR + 1];
     int64_t ncol[kMaxR + 1];
@@ -180,8 +194,8 @@ __global__ void __launch_bounds__(kTileX * kTileY) gather_var_kernel(VarArgs a) 
     const int z = (int)(t / ((int64_t)ntx * nty));
     if (x >= d.x || y >= d.y) return;
     const int64_t i = base + x + (int64_t)d.x * (y + (int64_t)d.y * z);
-    double acc = 0.0;
-    const uint32_t m = a.rmask;                   // radii present, summed in ascending order
+    double acc = a.acc_in ? a.out[i] : 0.0;
+    const uint32_t m = a.rmask;                   // radii summed here, in ascending order
     if (m & 1u) {                                 // radius 0: identity kernel, sigma = 1
         if ((__ldg(a.code + i) >> kCodeShift) == 0u) {
             const float2 ch = __ldg(a.chat + i);
@@ -233,7 +247,9 @@ __global__ void read_var_kernel(VarArgs a, const double* __restrict__ sigma, int
                 const int W1 = 2 * r + 1;
                 const int64_t plane = (ox + r) + (int64_t)W1 * ((oy + r) + (int64_t)W1 * (oz + r));
                 const ST* K = reinterpret_cast<const ST*>(a.K[r]);
-                v = (double)widen(K[plane * a.ncol[r] + ((int64_t)(code & kCodeMask) - a.jbase[r])]) * sigma[s];
+                const int64_t col = (a.dmask >> r) & 1u ? a.qbase[lo] + x + (int64_t)d.x * (y + (int64_t)d.y * z)
+                                                        : (int64_t)(code & kCodeMask) - a.jbase[r];
+                v = (double)widen(K[plane * a.ncol[r] + col]) * sigma[s];
             }
         }
         out[t] = v;
@@ -260,11 +276,15 @@ VarArgs var_args(const fdirw_ctx* c, const Chunk& ch, double* out) {
     a.s0 = ch.s0;
     a.s1 = ch.s1;
     a.rmask = 0;
+    a.dmask = b.dest_mask;
+    a.acc_in = false;
+    a.qbase = b.d_qbase;
     for (int r : b.radii) {
-        a.rmask |= 1u << r;
+        const bool dest = (b.dest_mask >> r) & 1u;
+        if (!dest) a.rmask |= 1u << r;
         a.K[r] = static_cast<const char*>(b.arena) + ch.k_off[r];
-        a.jbase[r] = ch.seg_begin[r];
-        a.ncol[r] = ch.seg_end[r] - ch.seg_begin[r];
+        a.jbase[r] = dest ? 0 : ch.seg_begin[r];
+        a.ncol[r] = dest ? ch.qn : ch.seg_end[r] - ch.seg_begin[r];
     }
     return a;
 }
@@ -288,8 +308,14 @@ MarchArgs march_args(const fdirw_ctx* c, const Chunk& ch, int r) {
     a.nstruct = b.n;
     a.s_base = b.d_base;
     a.s_dims = b.d_dims;
-    a.q_stride = ch.seg_end[r] - ch.seg_begin[r];
-    a.src_major = 1;
+    if ((b.dest_mask >> r) & 1u) {
+        a.s_qbase = b.d_qbase;
+        a.q_stride = ch.qn;
+        a.src_major = 0;
+    } else {
+        a.q_stride = ch.seg_end[r] - ch.seg_begin[r];
+        a.src_major = 1;
+    }
     return a;
 }
 
@@ -334,6 +360,11 @@ cudaError_t build_chunk(fdirw_ctx* c, int ci, cudaStream_t st, bool captured) {
     Batch& b = *c->batch;
     const Chunk& ch = b.chunks[ci];
     cudaError_t e = record(b.ev[4 * ci], st, captured);
+    for (int r : b.radii) {                     // destination-indexed planes: zero where another radius owns the source
+        if (e != cudaSuccess || r == 0 || !((b.dest_mask >> r) & 1u)) continue;
+        e = cudaMemsetAsync(static_cast<char*>(b.arena) + ch.k_off[r], 0,
+                            (size_t)wcells(r) * ch.qn * store_bytes(c->store), st);
+    }
     for (int r : b.radii) {
         if (e != cudaSuccess) break;
         if (r == 0 || ch.seg_end[r] == ch.seg_begin[r]) continue;
@@ -349,23 +380,41 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
                        bool captured) {
     Batch& b = *c->batch;
     const Chunk& ch = b.chunks[ci];
-    const VarArgs a = var_args(c, ch, dst);
+    VarArgs a = var_args(c, ch, dst);
     const int64_t nblk = b.blk[ch.s1] - b.blk[ch.s0];
+    const int Rm = c->R;
     cudaError_t e = cudaSuccess;
     const double* cur = src;
     for (int t = 0; t < n_steps && e == cudaSuccess; t++) {
-        scale_flat_kernel<<<grid_blocks(ch.c1 - ch.c0, 256), 256, 0, st>>>(cur, c->sigma, ch.c0, ch.c1, b.chat);
-        e = cudaGetLastError();
+        if (a.rmask) {
+            scale_flat_kernel<<<grid_blocks(ch.c1 - ch.c0, 256), 256, 0, st>>>(cur, c->sigma, ch.c0, ch.c1, b.chat);
+            e = cudaGetLastError();
+        }
+        for (int i = ch.s0; i < ch.s1 && e == cudaSuccess && b.dest_mask; i++)
+            e = launch_scale(cur + b.base[i], c->sigma + b.base[i], b.grids[i], Rm, b.chat_pad + b.pbase[i], true, st);
         const bool last = t + 1 == n_steps;
         if (e == cudaSuccess && last) e = record(b.ev[4 * ci + 2], st, captured);
         if (e != cudaSuccess) break;
-        if (nblk > 0) {
+        bool written = false;
+        if (a.rmask && nblk > 0) {
             switch (c->store) {
                 case Store::F32: gather_var_kernel<float><<<(unsigned)nblk, kTileX * kTileY, 0, st>>>(a); break;
                 case Store::F16: gather_var_kernel<__half><<<(unsigned)nblk, kTileX * kTileY, 0, st>>>(a); break;
                 default: gather_var_kernel<__nv_bfloat16><<<(unsigned)nblk, kTileX * kTileY, 0, st>>>(a); break;
             }
             e = cudaGetLastError();
+            written = true;
+        }
+        for (int r : b.radii) {
+            if (e != cudaSuccess) break;
+            if (r == 0 || !((b.dest_mask >> r) & 1u)) continue;
+            const size_t sb = store_bytes(c->store);
+            for (int i = ch.s0; i < ch.s1 && e == cudaSuccess; i++) {
+                const void* Q = static_cast<const char*>(a.K[r]) + (size_t)b.qbase[i] * sb;
+                e = launch_gather_part(Q, c->store, ch.qn, b.chat_pad + b.pbase[i], Rm, b.grids[i], r, written,
+                                       dst + b.base[i], st);
+            }
+            written = true;
         }
         if (e == cudaSuccess && last) e = record(b.ev[4 * ci + 3], st, captured);
         cur = dst;
@@ -453,8 +502,10 @@ void release_batch(fdirw_ctx* c) {
     p = b->d_blk; dfree(p);
     for (auto& l : b->d_list) { p = l; dfree(p); l = nullptr; }
     p = b->d_code; dfree(p);
+    p = b->d_qbase; dfree(p);
     dfree(b->arena);
     p = b->chat; dfree(p);
+    p = b->chat_pad; dfree(p);
     for (auto& e : b->ev) if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
@@ -567,6 +618,7 @@ int batch_info(fdirw_ctx* c, fdirw_info* out) {
     out->n_chunks = (int32_t)b.chunks.size();
     out->window_R_min = b.Rmin;
     out->graph_launches = b.graph_launches;
+    out->dest_indexed_radii = (int32_t)b.dest_mask;
     float km = 0.f, gm = 0.f;
     bool anyk = false, anyg = false;
     for (size_t ci = 0; ci < b.chunks.size(); ci++) {
@@ -767,6 +819,8 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
         b.before[r][n] = (int64_t)lists[r].size();
         b.count[r] = (int64_t)lists[r].size();
         if (b.count[r] > 0) b.radii.push_back(r);
+        if (r > 0 && b.count[r] > 0 && (double)b.count[r] >= fdirw::kDestFraction * (double)total)
+            b.dest_mask |= 1u << r;
     }
     if ((rc = dalloc(c, reinterpret_cast<void**>(&b.d_code), N * 4, "bucket codes")) != FDIRW_OK) return bail(rc);
     e = cudaMemcpy(b.d_code, code.data(), N * 4, cudaMemcpyHostToDevice);
@@ -787,12 +841,28 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->dmass), 8, "mass")) != FDIRW_OK) return bail(rc);
     fdirw::fill_kernel<<<fdirw::grid_blocks((int64_t)N, 256), 256, 0, c->stream>>>(c->sigma, (int64_t)N, 1.0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_bail("fill sigma", e);
+    if (b.dest_mask) {
+        // Padded scaled field: each structure with a zero halo of R_max cells (written once, never touched).
+        b.pbase.assign(n + 1, 0);
+        for (int i = 0; i < n; i++) {
+            const fdirw::Pad pd = fdirw::make_pad(b.grids[i], R_max);
+            b.pbase[i + 1] = b.pbase[i] + pd.n;
+        }
+        const uint64_t pbytes = (uint64_t)b.pbase[n] * 8;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&b.chat_pad), pbytes, "padded scaled field")) != FDIRW_OK) return bail(rc);
+        if ((e = cudaMemsetAsync(b.chat_pad, 0, pbytes, c->stream)) != cudaSuccess) return cuda_bail("zero padded field", e);
+    }
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&b.d_qbase), (uint64_t)n * 8, "structure table")) != FDIRW_OK) return bail(rc);
 
     // Chunks: consecutive structures whose kernels fit the budget together.
     const int sb = fdirw::store_bytes(c->store);
-    auto struct_bytes = [&](int i, int r) {
-        return r == 0 ? 0ull : (uint64_t)(b.before[r][i + 1] - b.before[r][i]) * (uint64_t)fdirw::wcells(r) * sb;
+    auto slot = [&](int i) { return (b.grids[i].n + 15) / 16 * 16; };   // 16-aligned destination columns
+    auto struct_bytes = [&](int i, int r) -> uint64_t {
+        if (r == 0) return 0;
+        const int64_t cols = (b.dest_mask >> r) & 1u ? slot(i) : b.before[r][i + 1] - b.before[r][i];
+        return (uint64_t)cols * (uint64_t)fdirw::wcells(r) * sb;
     };
+    b.qbase.assign(n, 0);
     uint64_t budget;
     if (c->mem_limit) {
         budget = c->mem_limit > c->allocated ? c->mem_limit - c->allocated : 0;
@@ -823,16 +893,24 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
         ch.s1 = i;
         ch.c0 = b.base[ch.s0];
         ch.c1 = b.base[ch.s1];
+        ch.qn = 0;
+        for (int k = ch.s0; k < ch.s1; k++) {
+            b.qbase[k] = ch.qn;
+            ch.qn += slot(k);
+        }
         uint64_t off = 0;
         for (int r : b.radii) {
             ch.seg_begin[r] = b.before[r][ch.s0];
             ch.seg_end[r] = b.before[r][ch.s1];
             ch.k_off[r] = off;
-            if (r > 0) off += fdirw::align256((uint64_t)(ch.seg_end[r] - ch.seg_begin[r]) * fdirw::wcells(r) * sb);
+            const int64_t cols = (b.dest_mask >> r) & 1u ? ch.qn : ch.seg_end[r] - ch.seg_begin[r];
+            if (r > 0) off += fdirw::align256((uint64_t)cols * fdirw::wcells(r) * sb);
         }
         ch.k_bytes = off;
         b.chunks.push_back(ch);
     }
+    if ((e = cudaMemcpyAsync(b.d_qbase, b.qbase.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_bail("copy structure tables", e);
     b.built.assign(b.chunks.size(), 0);
     b.stepped.assign(b.chunks.size(), 0);
     b.ev.assign(4 * b.chunks.size(), nullptr);

@@ -53,8 +53,10 @@ struct MarchArgs {
     int nstruct;
     const int64_t* s_base;
     const int4* s_dims;
-    // Q index = plane * q_stride + column; the column is the destination cell (src_major = 0) or the
-    // source's position in [src_begin, src_end) (src_major = 1, the per-radius buckets of a batch).
+    const int64_t* s_qbase;   // nullable: first cache column of each structure (destination-indexed layout)
+    // Q index = plane * q_stride + column; the column is the destination cell (src_major = 0: the cell's
+    // index within its structure plus s_qbase, or the global cell without s_qbase) or the source's
+    // position in [src_begin, src_end) (src_major = 1).
     int64_t q_stride;
     int src_major;
 };
@@ -85,6 +87,11 @@ cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, vo
 // c_out(x) = sum_o Q[o][x] * chat(x - o).
 cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
                           cudaStream_t st);
+// The radius-R part of the gather for one grid whose chat is padded with a halo of Rp >= R cells and
+// whose Q planes are qs values apart: c_out(x) = [c_out(x) +] sum_{|o| <= R} Q[o][x] * chat(x - o), the
+// rows (o_z, o_y) in ascending order as in launch_gather.
+cudaError_t launch_gather_part(const void* Q, Store store, int64_t qs, const void* chat, int Rp, Grid g, int R,
+                               bool accumulate, double* c_out, cudaStream_t st);
 // Deterministic FP64 total: partials[kMassBlocks] then one block.  partials must hold kMassBlocks doubles.
 constexpr int kMassBlocks = 1024;
 cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* out, cudaStream_t st);

@@ -67,12 +67,13 @@ __device__ __forceinline__ int64_t qplane(const MarchArgs& a, int R, int x, int 
 
 // Structure holding a source: its dimensions and first global cell (a batch concatenates structures;
 // a single grid is structure 0 with base 0).  s becomes the source's index within its structure.
+// qbase: first column of the structure in a destination-indexed cache (s_qbase, or base without it).
 struct SrcLoc {
     int nx, ny, nz;
-    int64_t base;
+    int64_t base, qbase;
 };
 __device__ __forceinline__ SrcLoc locate(const MarchArgs& a, bool ok, int64_t& s) {
-    SrcLoc L{a.g.nx, a.g.ny, a.g.nz, 0};
+    SrcLoc L{a.g.nx, a.g.ny, a.g.nz, 0, 0};
     if (ok && a.nstruct > 0) {
         int lo = 0, hi = a.nstruct - 1;               // last structure whose first cell is <= s
         while (lo < hi) {
@@ -80,7 +81,8 @@ __device__ __forceinline__ SrcLoc locate(const MarchArgs& a, bool ok, int64_t& s
             if (__ldg(a.s_base + mid) <= s) lo = mid; else hi = mid - 1;
         }
         const int4 d = __ldg(a.s_dims + lo);
-        L = SrcLoc{d.x, d.y, d.z, __ldg(a.s_base + lo)};
+        const int64_t b = __ldg(a.s_base + lo);
+        L = SrcLoc{d.x, d.y, d.z, b, a.s_qbase ? __ldg(a.s_qbase + lo) : b};
         s -= L.base;
     }
     return L;
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
                     float st = 0.f;
                     if (col_ok && z >= 0 && z < nz) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                        st = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.base + i, pos), u[j]);
+                        st = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.qbase + i, pos), u[j]);
                     }
                     sbuf[base + k] = st;
                 }
@@ -591,13 +593,16 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
                     for (int sc = 0; sc < 4; sc++) buf[k * LEVEL + sc * PLANE + t] = u[sc][k];
             }
             __syncthreads();
-            // cc: coefficients of level k (ready); cn: level k+1, loaded while level k computes.
-            uint32_t cc[16], cn[16];
-            tm_load_level<R>(tbase, 0, cc);
-            tm_wait_ld(cc);
+            // cb[k & 1]: coefficients of level k (ready); cb[(k + 1) & 1]: level k+1, loaded while level k
+            // computes (the loop is unrolled, so the two buffers are fixed registers and nothing is copied).
+            uint32_t cb[2][16];
+            tm_load_level<R>(tbase, 0, cb[0]);
+            tm_wait_ld(cb[0]);
             float prev[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < W1; k++) {
+                uint32_t (&cc)[16] = cb[k & 1];
+                uint32_t (&cn)[16] = cb[(k + 1) & 1];
                 if (k + 1 < W1) tm_load_level<R>(tbase, k + 1, cn);
                 const float* lv = buf + k * LEVEL;
                 const float l0 = lv[1 * PLANE + tl], l1 = lv[3 * PLANE + tl];
@@ -627,11 +632,7 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
                 }
 #pragma unroll
                 for (int sc = 0; sc < 4; sc++) { prev[sc] = u[sc][k]; u[sc][k] = nu[sc]; }
-                if (k + 1 < W1) {
-                    tm_wait_ld(cn);
-#pragma unroll
-                    for (int q = 0; q < 16; q++) cc[q] = cn[q];
-                }
+                if (k + 1 < W1) tm_wait_ld(cn);
             }
         }
 
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
                 for (int k = 0; k < W1; k++) {
                     float stv = 0.f;
                     if (cell_ok(x, y, k)) {
-                        stv = put(a.Q, a.store, qplane(a, R, x, y, k) * a.q_stride + qcol(a, L.base + gidx(x, y, k), pos), u[sc][k]);
+                        stv = put(a.Q, a.store, qplane(a, R, x, y, k) * a.q_stride + qcol(a, L.qbase + gidx(x, y, k), pos), u[sc][k]);
                     }
                     sbuf[k * LEVEL + sc * PLANE + t] = stv;
                 }
@@ -807,12 +808,14 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                 for (int k = 0; k < W1; k++) buf[base + k] = u[k];
             }
             __syncthreads();
-            uint32_t cc[16], cn[16];
-            tm_ld16(tbase, cc);
-            tm_wait_ld(cc);
+            uint32_t cb[2][16];                        // group g in cb[g & 1], g + 1 loading into the other
+            tm_ld16(tbase, cb[0]);
+            tm_wait_ld(cb[0]);
             float prev = 0.f;
 #pragma unroll
             for (int g = 0; g < NG; g++) {
+                uint32_t (&cc)[16] = cb[g & 1];
+                uint32_t (&cn)[16] = cb[(g + 1) & 1];
                 if (g + 1 < NG) tm_ld16(tbase + (uint32_t)(16 * (g + 1)), cn);
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
@@ -832,11 +835,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                         u[k] = __fadd_rn(cur, v);
                     }
                 }
-                if (g + 1 < NG) {
-                    tm_wait_ld(cn);
-#pragma unroll
-                    for (int q = 0; q < 16; q++) cc[q] = cn[q];
-                }
+                if (g + 1 < NG) tm_wait_ld(cn);
             }
         }
 
@@ -848,7 +847,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                 float stv = 0.f;
                 if (col_ok && z >= 0 && z < nz) {
                     const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                    stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.base + i, pos), u[k]);
+                    stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.qbase + i, pos), u[k]);
                 }
                 sbuf[base + k] = stv;
             }

@@ -46,7 +46,8 @@ __device__ __forceinline__ void load_q(const ST* p, float (&q)[VX]) {
 // Mixed path: ST in {float, half, bf16}, VX = 16 / sizeof(ST), chat as float2 (hi, lo).
 template <typename ST, int R>
 __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q, const float2* __restrict__ chat,
-                                                        Grid g, Pad p, double* __restrict__ out) {
+                                                        Grid g, Pad p, int64_t qs, bool acc_in,
+                                                        double* __restrict__ out) {
     constexpr int VX = 16 / sizeof(ST);
     constexpr int W1 = 2 * R + 1;
     constexpr int NC = VX + 2 * R;
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
 
     double acc[VX];
 #pragma unroll
-    for (int j = 0; j < VX; j++) acc[j] = 0.0;
+    for (int j = 0; j < VX; j++) acc[j] = acc_in ? out[i0 + j] : 0.0;
 
     for (int oz = -R; oz <= R; oz++) {
         for (int oy = -R; oy <= R; oy++) {
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
             float2 ch[NC];
 #pragma unroll
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
-            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + i0;
             // The FP32 pair restarts at zero on every row of 2R+1 terms, so its compensation term stays
             // within a few ulps of the row sum; the row is then added to the FP64 accumulator.
             float s[VX], c[VX];
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
 #pragma unroll
             for (int ox = -R; ox <= R; ox++) {
                 float q[VX];
-                load_q<ST, VX>(qrow + (int64_t)(ox + R) * g.n, q);
+                load_q<ST, VX>(qrow + (int64_t)(ox + R) * qs, q);
 #pragma unroll
                 for (int j = 0; j < VX; j++) ff_madd(s[j], c[j], q[j], ch[j - ox + R]);
             }
@@ -133,21 +134,22 @@ __global__ void __launch_bounds__(256) gather_f64_kernel(const double* __restric
 // Any nx (no vector alignment): one destination per thread, runtime R, same arithmetic as above.
 template <typename ST, bool FF>
 __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict__ Q, const void* __restrict__ chat,
-                                                            Grid g, Pad p, int R, double* __restrict__ out) {
+                                                            Grid g, Pad p, int R, int64_t qs, bool acc_in,
+                                                            double* __restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int x = (int)(i % g.nx);
     const int64_t r = i / g.nx;
     const int y = (int)(r % g.ny);
     const int z = (int)(r / g.ny);
-    double acc = 0.0;
+    double acc = acc_in ? out[i] : 0.0;
     int o = 0;
     for (int oz = -R; oz <= R; oz++)
         for (int oy = -R; oy <= R; oy++) {
             float s = 0.f, c = 0.f;
             for (int ox = -R; ox <= R; ox++, o++) {
                 const int64_t pi = ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + (x - ox + R);
-                const ST qv = Q[(int64_t)o * g.n + i];
+                const ST qv = Q[(int64_t)o * qs + i];
                 if constexpr (FF) {
                     ff_madd(s, c, widen(qv), reinterpret_cast<const float2*>(chat)[pi]);
                 } else {
@@ -264,27 +266,30 @@ int blocks_for(int64_t n, int threads) {
 }
 
 template <typename ST, int R>
-cudaError_t gather_ff_r(const void* Q, const void* chat, Grid g, Pad p, double* out, cudaStream_t st) {
+cudaError_t gather_ff_r(const void* Q, const void* chat, Grid g, Pad p, int64_t qs, bool acc_in, double* out,
+                        cudaStream_t st) {
     constexpr int VX = 16 / sizeof(ST);
     const int64_t nt = (int64_t)(g.nx / VX) * g.ny * g.nz;
     gather_ff_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q),
-                                                                   reinterpret_cast<const float2*>(chat), g, p, out);
+                                                                   reinterpret_cast<const float2*>(chat), g, p, qs,
+                                                                   acc_in, out);
     return cudaGetLastError();
 }
 
 template <typename ST>
-cudaError_t gather_ff(const void* Q, const void* chat, Grid g, int R, Pad p, double* out, cudaStream_t st) {
+cudaError_t gather_ff(const void* Q, const void* chat, Grid g, int R, Pad p, int64_t qs, bool acc_in, double* out,
+                      cudaStream_t st) {
     switch (R) {
-        case 1: return gather_ff_r<ST, 1>(Q, chat, g, p, out, st);
-        case 2: return gather_ff_r<ST, 2>(Q, chat, g, p, out, st);
-        case 3: return gather_ff_r<ST, 3>(Q, chat, g, p, out, st);
-        case 4: return gather_ff_r<ST, 4>(Q, chat, g, p, out, st);
-        case 5: return gather_ff_r<ST, 5>(Q, chat, g, p, out, st);
-        case 6: return gather_ff_r<ST, 6>(Q, chat, g, p, out, st);
-        case 7: return gather_ff_r<ST, 7>(Q, chat, g, p, out, st);
-        case 8: return gather_ff_r<ST, 8>(Q, chat, g, p, out, st);
-        case 9: return gather_ff_r<ST, 9>(Q, chat, g, p, out, st);
-        case 10: return gather_ff_r<ST, 10>(Q, chat, g, p, out, st);
+        case 1: return gather_ff_r<ST, 1>(Q, chat, g, p, qs, acc_in, out, st);
+        case 2: return gather_ff_r<ST, 2>(Q, chat, g, p, qs, acc_in, out, st);
+        case 3: return gather_ff_r<ST, 3>(Q, chat, g, p, qs, acc_in, out, st);
+        case 4: return gather_ff_r<ST, 4>(Q, chat, g, p, qs, acc_in, out, st);
+        case 5: return gather_ff_r<ST, 5>(Q, chat, g, p, qs, acc_in, out, st);
+        case 6: return gather_ff_r<ST, 6>(Q, chat, g, p, qs, acc_in, out, st);
+        case 7: return gather_ff_r<ST, 7>(Q, chat, g, p, qs, acc_in, out, st);
+        case 8: return gather_ff_r<ST, 8>(Q, chat, g, p, qs, acc_in, out, st);
+        case 9: return gather_ff_r<ST, 9>(Q, chat, g, p, qs, acc_in, out, st);
+        case 10: return gather_ff_r<ST, 10>(Q, chat, g, p, qs, acc_in, out, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -322,36 +327,51 @@ cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, vo
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
-                          cudaStream_t st) {
-    const Pad p = make_pad(g, R);
+cudaError_t launch_gather_part(const void* Q, Store store, int64_t qs, const void* chat, int Rp, Grid g, int R,
+                               bool accumulate, double* c_out, cudaStream_t st) {
+    if (R < 1 || R > Rp) return cudaErrorInvalidValue;
+    const Pad p = make_pad(g, Rp);
+    // The kernels index chat as if its halo were R: move the base by (Rp - R) on every axis.
+    const int64_t shift = ((int64_t)(Rp - R) * p.py + (Rp - R)) * p.px + (Rp - R);
+    const void* ch = static_cast<const char*>(chat) + shift * 8;   // chat element: double or float2, 8 bytes
     const int vx = 16 / store_bytes(store);
-    if (R >= 1 && R <= (store == Store::F64 ? kMaxR64 : kMaxR) && g.nx % vx == 0) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (qs * store_bytes(store)) % 16 == 0;
+    if (R <= (store == Store::F64 ? kMaxR64 : kMaxR) && g.nx % vx == 0 && aligned) {
         switch (store) {
-            case Store::F64: return gather_f64(Q, chat, g, R, p, c_out, st);
-            case Store::F32: return gather_ff<float>(Q, chat, g, R, p, c_out, st);
-            case Store::F16: return gather_ff<__half>(Q, chat, g, R, p, c_out, st);
-            case Store::BF16: return gather_ff<__nv_bfloat16>(Q, chat, g, R, p, c_out, st);
+            case Store::F64:
+                if (qs != g.n || accumulate) return cudaErrorInvalidValue;   // uniform FP64 contexts only
+                return gather_f64(Q, ch, g, R, p, c_out, st);
+            case Store::F32: return gather_ff<float>(Q, ch, g, R, p, qs, accumulate, c_out, st);
+            case Store::F16: return gather_ff<__half>(Q, ch, g, R, p, qs, accumulate, c_out, st);
+            case Store::BF16: return gather_ff<__nv_bfloat16>(Q, ch, g, R, p, qs, accumulate, c_out, st);
         }
         return cudaErrorInvalidValue;
     }
     const int b = blocks_for(g.n, 256);
     switch (store) {
         case Store::F64:
-            gather_scalar_kernel<double, false><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), chat, g, p, R, c_out);
+            gather_scalar_kernel<double, false><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), ch, g, p, R, qs,
+                                                                   accumulate, c_out);
             break;
         case Store::F32:
-            gather_scalar_kernel<float, true><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), chat, g, p, R, c_out);
+            gather_scalar_kernel<float, true><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
+                                                                 accumulate, c_out);
             break;
         case Store::F16:
-            gather_scalar_kernel<__half, true><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), chat, g, p, R, c_out);
+            gather_scalar_kernel<__half, true><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R, qs,
+                                                                  accumulate, c_out);
             break;
         case Store::BF16:
-            gather_scalar_kernel<__nv_bfloat16, true><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), chat,
-                                                                        g, p, R, c_out);
+            gather_scalar_kernel<__nv_bfloat16, true><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), ch,
+                                                                         g, p, R, qs, accumulate, c_out);
             break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
+                          cudaStream_t st) {
+    return launch_gather_part(Q, store, g.n, chat, R, g, R, false, c_out, st);
 }
 
 cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* out, cudaStream_t st) {

@@ -63,7 +63,7 @@ class fdirw_info(ctypes.Structure):
                 ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double),
                 ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("n_structures", ctypes.c_int32), ("n_chunks", ctypes.c_int32), ("window_R_min", ctypes.c_int32),
-                ("graph_launches", ctypes.c_int32)]
+                ("graph_launches", ctypes.c_int32), ("dest_indexed_radii", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

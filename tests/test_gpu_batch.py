@@ -130,6 +130,47 @@ def test_chunked_equals_resident_bitwise_and_graph_replays():
     assert abs(m - float(c0.sum())) <= 1e-12 * float(c0.sum())
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_layouts_match_oracle(prec):
+    """Log-uniform D gives radii 1..6 with one common radius (destination-indexed cache) and several rare
+    ones (source-indexed cache); fields, sampled kernels and chunked execution against the oracle."""
+    shapes = [(16, 12, 10), (11, 14, 9)]
+    Ds = [synth.random_diffusivity(s, 340 + i, 4.0) for i, s in enumerate(shapes)]
+    n_sub = 20
+    dt = n_sub * min(oracle.stable_dt_sub(s, D) for s, D in zip(shapes, Ds))
+    c0 = np.concatenate([synth.random_field(int(np.prod(s)), 350 + i) for i, s in enumerate(shapes)])
+    with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, prec) as b:
+        out = np.empty_like(c0)
+        m = b.step(c0, out, 2, want_mass=True)
+        Rmap = b.radius()
+        info = b.info()
+        src = np.arange(2, b.n, 9)
+        ks = b.read_kernels(src)
+    present = set(int(r) for r in np.unique(Rmap))
+    dest = {r for r in present if (info["dest_indexed_radii"] >> r) & 1}
+    assert dest and (present - dest), (present, dest)        # both cache layouts in use
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+    offs = b.offsets
+    for i, shape in enumerate(shapes):
+        sl = slice(int(offs[i]), int(offs[i + 1]))
+        ref = c0[sl]
+        for _ in range(2):
+            ref = oracle.superpose_rmap(shape, Ds[i], dt / n_sub, Rmap[sl], n_sub, ref)
+        assert _rel(out[sl], ref) <= FIELD_TOL[prec], (prec, i, _rel(out[sl], ref))
+    for q, s in enumerate(src):
+        i = int(np.searchsorted(offs, s, side="right") - 1)
+        r = int(Rmap[s])
+        ref, _ = oracle.source_kernel(shapes[i], Ds[i], dt / n_sub, r, n_sub, int(s - offs[i]))
+        got = ks[q][6 - r:7 + r, 6 - r:7 + r, 6 - r:7 + r]
+        assert _rel(got, ref) <= KERNEL_TOL[prec], (s, r)
+    limit = info["device_bytes"] - info["cache_bytes"] + info["cache_bytes"] * 2 // 3
+    with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, prec, mem_limit=limit) as b:
+        out2 = np.empty_like(c0)
+        b.step(c0, out2, 2)
+        assert b.info()["n_chunks"] == 2
+    assert np.array_equal(out, out2)
+
+
 @pytest.mark.parametrize("R", [3, 9])
 def test_single_structure_single_radius_equals_uniform_bitwise(R):
     shape = (20, 14, 12)
