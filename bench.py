@@ -224,7 +224,7 @@ def run_batch(args, bw):
         with torch.cuda.stream(stream):
             ev[0].record(stream)
             ctx = fdirw.fdirw_create_batch(shapes, Ds, dt_macro, bw.R_min, bw.R_max, bw.n_sub, p, device=local,
-                                           stream=stream)
+                                           stream=stream, march_parts=args.march_parts)
             ev[1].record(stream)
             mass = fdirw.fdirw_step(ctx, c0, out, bw.steps, want_mass=True)
             ev[2].record(stream)
@@ -268,7 +268,7 @@ def run_batch(args, bw):
         def e2e_pass():
             with torch.cuda.stream(stream):
                 ctx = fdirw.fdirw_create_batch(shapes, Dp, dt_macro, bw.R_min, bw.R_max, bw.n_sub, prec,
-                                               device=local, stream=stream)
+                                               device=local, stream=stream, march_parts=args.march_parts)
                 fdirw.fdirw_step(ctx, cp, op, bw.steps, want_mass=True)
                 fdirw.fdirw_destroy(ctx)
 
@@ -419,7 +419,8 @@ def run_ours(args, w):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         with torch.cuda.stream(stream):
             ev[0].record(stream)
-            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream)
+            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream,
+                                       march_parts=args.march_parts)
             ev[1].record(stream)
             fdirw.fdirw_kernels(ctx)
             ev[2].record(stream)
@@ -466,7 +467,8 @@ def run_ours(args, w):
 
         def e2e_pass():
             with torch.cuda.stream(stream):
-                ctx = fdirw.fdirw_create(shape, Dp, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream)
+                ctx = fdirw.fdirw_create(shape, Dp, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream,
+                                       march_parts=args.march_parts)
                 fdirw.fdirw_step(ctx, cp, op, w.steps, want_mass=True)
                 fdirw.fdirw_destroy(ctx)
 
@@ -653,6 +655,9 @@ def main(argv=None):
     ap.add_argument("--surrogate-epochs", type=int, default=4)
     ap.add_argument("--surrogate-lr", type=float, default=2e-3)
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
+    ap.add_argument("--march-parts", type=int, default=0,
+                    help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "
+                         "lateral faces); 0 = autotune")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per march launch from an ncu capture of the current kernel")
     args = ap.parse_args(argv)

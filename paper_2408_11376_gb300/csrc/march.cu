@@ -394,11 +394,14 @@ struct MapTm {
     static constexpr int COLS = W1 * W1;
     static constexpr int NB = R + 1;                      // blocks per window axis (last one half padding)
     static constexpr int TPS = NB * NB;                   // threads per source
-    static constexpr int THREADS = 256;
+    // R <= 8: 256 threads, two per TMEM lane (256 columns each); R = 9, 10: one source of 100 or 121
+    // threads per CTA, one per lane, so that every level's 16 words fit its 512 columns.
+    static constexpr int THREADS = TPS <= 81 ? 256 : 128;
+    static constexpr int TCOLS = THREADS == 256 ? 256 : 512;   // TMEM columns per thread
     static constexpr int SPB = THREADS / TPS;
     static constexpr int LEVEL = 4 * THREADS;             // floats per level: [sub-column][thread]
     static constexpr int BUF = W1 * LEVEL;                // floats per exchange buffer
-    static constexpr int LA0 = (256 - 12 * W1) / 4;
+    static constexpr int LA0 = (TCOLS - 12 * W1) / 4;
     static constexpr int LA = LA0 < W1 ? LA0 : W1;        // levels whose diagonals live in TMEM
     static constexpr int NR = W1 - LA;                    // levels whose diagonals live in registers
     static constexpr size_t SMEM_USED = (size_t)2 * BUF * 4 + (size_t)SPB * COLS * 8;
@@ -460,7 +463,7 @@ __device__ __forceinline__ void tm_load_level(uint32_t tbase, int k, uint32_t (&
 }
 
 template <int R>
-__global__ void __launch_bounds__(256, 1) march_tm_kernel(MarchArgs a) {
+__global__ void __launch_bounds__(MapTm<R>::THREADS, 1) march_tm_kernel(MarchArgs a) {
     using M = MapTm<R>;
     constexpr int W1 = M::W1, COLS = M::COLS, NB = M::NB, TPS = M::TPS, SPB = M::SPB;
     constexpr int LEVEL = M::LEVEL, PLANE = M::THREADS, BUF = M::BUF, LA = M::LA, NR = M::NR;
@@ -956,8 +959,8 @@ cudaError_t dispatch(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
         case 6: return launch_f32_p<6>(a, P, num_sms, st);
         case 7: return launch_f32_p<7>(a, P, num_sms, st);
         case 8: return launch_f32_p<8>(a, P, num_sms, st);
-        case 9: return P == 5 ? launch_tmc<9>(a, num_sms, st) : cudaErrorInvalidValue;
-        case 10: return P == 5 ? launch_tmc<10>(a, num_sms, st) : cudaErrorInvalidValue;
+        case 9: return P == 5 ? launch_tmc<9>(a, num_sms, st) : P == 4 ? launch_tm<9>(a, num_sms, st) : cudaErrorInvalidValue;
+        case 10: return P == 5 ? launch_tmc<10>(a, num_sms, st) : P == 4 ? launch_tm<10>(a, num_sms, st) : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -968,7 +971,7 @@ cudaError_t dispatch(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune;
 
-int default_parts(int R) { return R >= 4 ? 2 : 1; }
+int default_parts(int R) { return R > 8 ? 5 : R >= 4 ? 2 : 1; }
 
 cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* best) {
     const int W1 = 2 * a.R + 1, cols = W1 * W1;
@@ -986,7 +989,7 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
     *best = default_parts(a.R);
     for (int P = 1; P <= 5 && e == cudaSuccess; P++) {
         if (P <= 3 && P > W1) continue;
-        if (a.R > 8 && P != 5) continue;          // only the TMEM-face mapping covers R = 9, 10
+        if (a.R > 8 && P < 4) continue;           // only the TMEM mappings cover R = 9, 10
         if (P == 5 && a.R < 6) continue;          // one CTA of < 6 warps per SM: never the fastest there
         e = dispatch(warm, P, num_sms, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -1006,8 +1009,7 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
 
 cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts) {
     if (a.store == Store::F64) { *parts = 1; return cudaSuccess; }
-    if (a.R > 8) { *parts = 5; return cudaSuccess; }
-    if (parts_req >= 1 && parts_req <= 5) { *parts = parts_req; return cudaSuccess; }
+    if (parts_req >= 1 && parts_req <= 5 && (a.R <= 8 || parts_req >= 4)) { *parts = parts_req; return cudaSuccess; }
     int dev = 0;
     cudaGetDevice(&dev);
     const auto key = std::make_tuple(dev, a.R, (int)a.store);
@@ -1028,9 +1030,7 @@ cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStrea
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
     int P = 1;
     if (a.store != Store::F64) {
-        if (a.R > 8) {
-            P = 5;
-        } else if (parts_req >= 1 && parts_req <= 5) {
+        if (parts_req >= 1 && parts_req <= 5 && (a.R <= 8 || parts_req >= 4)) {
             P = parts_req;
         } else {
             int dev = 0;

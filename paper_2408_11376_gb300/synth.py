@@ -178,6 +178,10 @@ WORKLOADS = {
     "fdirw-96c-r6": Workload("fdirw-96c-r6", 96, 0.35, "per_sphere", 0.0, 6, 120, 10, "blob", _S0 + 1),
     # 192^3, porosity 0.4, D 1 / 1e-6, R=8, n_sub=200, 20 steps, c = 1 in solid.
     "fdirw-192c-r8": Workload("fdirw-192c-r8", 192, 0.40, "two_phase", 1e-6, 8, 200, 20, "solid_one", _S0 + 2),
+    # 256^3 with the 192^3 recipe (the surrogate's second size).
+    "fdirw-256c-r8": Workload("fdirw-256c-r8", 256, 0.40, "two_phase", 1e-6, 8, 200, 20, "solid_one", _S0 + 5),
+    # 64^3 with the 192^3 recipe: small profiling case of the same kernels.
+    "fdirw-64c-r8": Workload("fdirw-64c-r8", 64, 0.40, "two_phase", 1e-6, 8, 200, 2, "solid_one", _S0 + 6),
 }
 
 
@@ -222,4 +226,6 @@ BATCH_WORKLOADS = {
     # at the stability limit (pore R = 10, solid R = 3), 10 macro steps.
     "fdirw-batch64-r3to10": BatchWorkload("fdirw-batch64-r3to10", 64, (32, 48, 64, 80, 96, 112, 128), (0.35, 0.40),
                                           3, 10, 75, 10, _S0 + 3),
+    # Two 48^3 structures of the same recipe, one macro step: small profiling case of the batched kernels.
+    "fdirw-batch2x48c-r3to10": BatchWorkload("fdirw-batch2x48c-r3to10", 2, (48,), (0.35, 0.40), 3, 10, 75, 1, _S0 + 4),
 }

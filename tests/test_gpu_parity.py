@@ -91,6 +91,21 @@ def test_kernels_match_oracle(prec, shape, R, n_sub):
     assert ks.min() >= 0.0
 
 
+@pytest.mark.parametrize("R", [9, 10])
+def test_large_radius_mappings_agree_bitwise(R):
+    """R = 9, 10 run on mapping 4 (2x2 blocks, one source per CTA) and mapping 5 (one column per thread):
+    same bits."""
+    shape = (23, 22, 21)
+    D = _case(shape, 83, "per_sphere")
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    c0 = synth.random_field(N, 84)
+    src = np.arange(1, N, 29)
+    runs = [_gpu_run(shape, D, lam, R, 31, c0, 2, "fp32", src, parts=P) for P in (4, 5)]
+    assert [r[3]["march_parts"] for r in runs] == [4, 5]
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][2], runs[1][2])
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("R", [9, 10])
 def test_large_radius_kernels_match_oracle(prec, R):
@@ -102,7 +117,7 @@ def test_large_radius_kernels_match_oracle(prec, R):
     N = int(np.prod(shape))
     src = np.arange(3, N, 37)
     _, _, ks, info = _gpu_run(shape, D, lam, R, 45, np.zeros(N), 0, prec, src)
-    assert info["march_parts"] == 5
+    assert info["march_parts"] in (4, 5)
     ref, _ = oracle.kernels(shape, D, lam, R, 45, src)
     ks = ks.reshape(len(src), -1)
     ref = ref.reshape(len(src), -1)
