@@ -166,7 +166,8 @@ def run_reference(args, w):
 def march_kernel_name(prec: str, parts: int) -> str:
     if prec == "fp64":
         return "march_f64_kernel<R>"
-    return {4: "march_tm_kernel<R>", 5: "march_tmc_kernel<R>"}.get(parts, f"march_f32_kernel<R,{parts}>")
+    return {4: "march_tm_kernel<R>", 5: "march_tmc_kernel<R>", 6: "march_tmp_kernel<R>"}.get(
+        parts, f"march_f32_kernel<R,{parts}>")
 
 
 def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: float, traffic, clocks, kname: str):
@@ -302,7 +303,7 @@ def run_batch(args, bw):
                                  march_kernel_name(prec, info["march_parts"]))
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        t_src, threads, dt, ns = oracle_batch_sample(bw, shapes, Ds_host, dt_macro, args.ref_sample // 2)
+        t_src, threads, dt, ns = oracle_batch_sample(bw, shapes, Ds_host, dt_macro, args.ref_sample * 4)
         cpu = {"value": 1.0 / (N * t_src), "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{ns} seeded random sources of {bw.name}, each on its own radius ({dt:.1f} s of FP64 "
                          f"windowed marches on {threads} host threads); macro-steps/s = 1/(N * seconds per source)"}
@@ -369,12 +370,12 @@ def run_reference_batch(args, bw):
     dt_macro = bw.n_sub * min(oracle.stable_dt_sub(s, D) for s, D in zip(shapes, Ds))
     per_step = []
     for i in range(args.warmup + args.steps):
-        t_src, threads, _, ns = oracle_batch_sample(bw, shapes, Ds, dt_macro, args.ref_sample // 2, seed=100 + i)
+        t_src, threads, _, ns = oracle_batch_sample(bw, shapes, Ds, dt_macro, args.ref_sample * 4, seed=100 + i)
         if i >= args.warmup:
             per_step.append(t_src)
     t_src = statistics.mean(per_step)
     value = 1.0 / (N * t_src)
-    sample = (f"{args.ref_sample // 2} seeded random sources of {bw.name} per step, each on its own radius; "
+    sample = (f"{args.ref_sample * 4} seeded random sources of {bw.name} per step, each on its own radius; "
               "macro-steps/s = 1/(N * seconds per source), the oracle recomputing every kernel each step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * N * t_src, "higher_is_better": True,
@@ -657,7 +658,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
     ap.add_argument("--march-parts", type=int, default=0,
                     help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "
-                         "lateral faces); 0 = autotune")
+                         "lateral faces, 6 = source pairs in f32x2); 0 = autotune")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per march launch from an ncu capture of the current kernel")
     args = ap.parse_args(argv)

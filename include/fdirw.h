@@ -78,8 +78,10 @@ typedef struct {
     int32_t  march_parts; /* FP32 march thread mapping: 1..3 = threads per window column; 4 = one thread
                              per 2x2 block of window columns with the face coefficients in Tensor Memory;
                              5 = one thread per window column with its lateral face coefficients in
-                             Tensor Memory (window_R 9 and 10 take 4 or 5 only; another request is
-                             autotuned between those two); 0 = autotune (each candidate timed once on the first build for a device, R
+                             Tensor Memory; 6 = one thread per window column for a pair of sources,
+                             packed f32x2 arithmetic, lateral faces of both in Tensor Memory (R <= 8);
+                             window_R 9 and 10 take 4 or 5 only (another request is autotuned between
+                             those two); 0 = autotune (each candidate timed once on the first build for a device, R
                              and storage type, result cached for the process; that build synchronises the
                              stream) */
     int32_t  reserved;    /* must be 0 */

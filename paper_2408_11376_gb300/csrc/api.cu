@@ -186,7 +186,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     fdirw_opts o{FDIRW_FP32, -1, nullptr, 0, 0, 0};
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP64 || o.prec > FDIRW_FP32_STORE_BF16) return fail(nullptr, FDIRW_ERR_ARG, "unknown prec");
-    if (o.march_parts < 0 || o.march_parts > 5) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 5]");
+    if (o.march_parts < 0 || o.march_parts > 6) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 6]");
     if (o.prec == FDIRW_FP64 && window_R > fdirw::kMaxR64)
         return fail(nullptr, FDIRW_ERR_ARG, "FDIRW_FP64 supports window_R <= " + std::to_string(fdirw::kMaxR64));
 

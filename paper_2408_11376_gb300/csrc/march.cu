@@ -889,6 +889,260 @@ cudaError_t launch_tmc(const MarchArgs& a, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------------
+// Mapping 6: one window column per thread for a PAIR of sources, every FP32 operation packed (f32x2).
+//
+// The two sources of a pair have the same window shape, so each thread marches the same column of
+// both: the state, the diagonals and the z faces are register pairs (source A in the low half, B in
+// the high half), the exchange buffer holds one 8-byte pair per cell, and the four lateral faces of
+// both sources live in TMEM as aligned pairs (8 words per cell, 2 cells per 16-word load).  Each
+// packed mul.rn / fma.rn / add.rn.f32x2 rounds each half exactly like the scalar instruction, and the
+// operations come in the order of march_f32_kernel, so the kernels are bitwise those of mappings 1-5.
+// Per cell-substep of a pair: 1 store + 4 loads of 8 bytes and 8 packed FP32 instructions.
+template <int R>
+struct MapTmp {
+    static constexpr int W1 = 2 * R + 1;
+    static constexpr int COLS = W1 * W1;
+    static constexpr int PAIRS = (384 / COLS) > 0 ? (384 / COLS) : 1;   // source pairs per CTA
+    static constexpr int THREADS = ((PAIRS * COLS + 31) / 32) * 32;
+    static constexpr int SLOTS = (THREADS / 32 + 3) / 4;                // threads per TMEM lane
+    static constexpr int SLOT_COLS = (512 / SLOTS) / 16 * 16;           // TMEM columns per thread
+    static constexpr int NG = (W1 + 1) / 2;                             // 16-word groups of 2 cells
+    static constexpr int BUF = PAIRS * COLS * W1;                       // 8-byte pairs per buffer
+    static constexpr size_t SMEM_USED = (size_t)2 * BUF * 8 + (size_t)2 * PAIRS * COLS * 8;
+    static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+    static_assert(16 * NG <= SLOT_COLS, "the lateral faces of a column pair must fit the thread's TMEM slot");
+    static_assert(R <= 8, "mapping 6 covers R <= 8");
+};
+
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t u2pack(uint32_t lo, uint32_t hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2lo(uint64_t v) { float a, b; asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); return a; }
+__device__ __forceinline__ float f2hi(uint64_t v) { float a, b; asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); return b; }
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int R>
+__global__ void __launch_bounds__(MapTmp<R>::THREADS, 1) march_tmp_kernel(MarchArgs a) {
+    using M = MapTmp<R>;
+    constexpr int W1 = M::W1, COLS = M::COLS, NG = M::NG, BUF = M::BUF, PAIRS = M::PAIRS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* xbuf = reinterpret_cast<uint64_t*>(smem_raw);                        // [2][PAIRS*COLS][W1]
+    double* red = reinterpret_cast<double*>(smem_raw + (size_t)2 * BUF * 8);      // [2*PAIRS][COLS]
+    __shared__ uint32_t s_taddr;
+
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(dst) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const uint32_t tbase = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(M::SLOT_COLS * (warp >> 2));
+
+    const bool active = t < PAIRS * COLS;
+    const int pair = active ? t / COLS : 0;
+    const int col = active ? t - pair * COLS : 0;
+    const int ci = col % W1, cj = col / W1;
+    const int64_t nbatch = (a.src_end - a.src_begin + 2 * PAIRS - 1) / (2 * PAIRS);
+    const int base = (pair * COLS + col) * W1;
+    const int xm = ci > 0 ? base - W1 : base;
+    const int xp = ci < 2 * R ? base + W1 : base;
+    const int ym = cj > 0 ? base - W1 * W1 : base;
+    const int yp = cj < 2 * R ? base + W1 * W1 : base;
+
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        const int64_t first = a.src_begin + b * 2 * PAIRS;
+        // Per source of the pair (h = 0: low half, h = 1: high half): geometry and validity.
+        int64_t pos[2], sidx[2];
+        bool src_ok[2], col_ok[2];
+        int sx[2], sy[2], sz[2], xs[2], ys[2], nzs[2], nxs[2], nys[2];
+        int64_t nxy[2], cbase[2], qb[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            pos[h] = first + 2 * pair + h;
+            src_ok[h] = active && pos[h] < a.src_end;
+            int64_t s = pos[h];
+            if (src_ok[h] && a.list) s = a.list[s];
+            const SrcLoc L = locate(a, src_ok[h], s);
+            nxs[h] = L.nx; nys[h] = L.ny; nzs[h] = L.nz;
+            nxy[h] = (int64_t)L.nx * L.ny;
+            cbase[h] = L.base;
+            qb[h] = L.qbase;
+            sidx[h] = s;
+            sx[h] = sy[h] = sz[h] = 0;
+            if (src_ok[h]) {
+                sx[h] = (int)(s % L.nx);
+                const int64_t r = s / L.nx;
+                sy[h] = (int)(r % L.ny);
+                sz[h] = (int)(r / L.ny);
+            }
+            xs[h] = sx[h] - R + ci;
+            ys[h] = sy[h] - R + cj;
+            col_ok[h] = src_ok[h] && xs[h] >= 0 && xs[h] < L.nx && ys[h] >= 0 && ys[h] < L.ny;
+        }
+
+        uint64_t u[W1], am[W1], cz[W1];
+        float zprev[2] = {0.f, 0.f};
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int k = 2 * g + q;
+                float f[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};   // xm xp ym yp z+
+                if (k < W1) {
+                    float amv[2], uv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int z = sz[h] - R + k;
+                        const bool ok = col_ok[h] && z >= 0 && z < nzs[h];
+                        if (ok) {
+                            const int64_t i = cbase[h] + (int64_t)xs[h] + (int64_t)nxs[h] * ys[h] + nxy[h] * z;
+                            if (ci > 0 && xs[h] > 0) f[h][0] = __ldg(a.ax + i - 1);
+                            if (ci < 2 * R && xs[h] + 1 < nxs[h]) f[h][1] = __ldg(a.ax + i);
+                            if (cj > 0 && ys[h] > 0) f[h][2] = __ldg(a.ay + i - nxs[h]);
+                            if (cj < 2 * R && ys[h] + 1 < nys[h]) f[h][3] = __ldg(a.ay + i);
+                            if (k < 2 * R && z + 1 < nzs[h]) f[h][4] = __ldg(a.az + i);
+                        }
+                        amv[h] = -(((f[h][0] + f[h][1]) + (f[h][2] + f[h][3])) + (zprev[h] + f[h][4]));
+                        uv[h] = (src_ok[h] && ci == R && cj == R && k == R) ? 1.f : 0.f;
+                        zprev[h] = f[h][4];
+                    }
+                    const int kk = k < W1 ? k : 0;
+                    cz[kk] = f2pack(f[0][4], f[1][4]);
+                    am[kk] = f2pack(amv[0], amv[1]);
+                    u[kk] = f2pack(uv[0], uv[1]);
+                }
+#pragma unroll
+                for (int d = 0; d < 4; d++) {
+                    w[8 * q + 2 * d] = __float_as_uint(f[0][d]);
+                    w[8 * q + 2 * d + 1] = __float_as_uint(f[1][d]);
+                }
+            }
+            tm_st16(tbase + (uint32_t)(16 * g), w);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+        for (int it = 0; it < a.n_sub; it++) {
+            uint64_t* buf = xbuf + (it & 1) * BUF;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < W1; k++) buf[base + k] = u[k];
+            }
+            __syncthreads();
+            uint32_t cb[2][16];
+            tm_ld16(tbase, cb[0]);
+            tm_wait_ld(cb[0]);
+            uint64_t prev = 0ull;
+#pragma unroll
+            for (int g = 0; g < NG; g++) {
+                uint32_t (&cc)[16] = cb[g & 1];
+                uint32_t (&cn)[16] = cb[(g + 1) & 1];
+                if (g + 1 < NG) tm_ld16(tbase + (uint32_t)(16 * (g + 1)), cn);
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    const int k = 2 * g + q;
+                    if (k < W1) {
+                        const uint64_t cur = u[k];
+                        uint64_t v = mul2(am[k], cur);
+                        v = fma2(u2pack(cc[8 * q + 0], cc[8 * q + 1]), buf[xm + k], v);
+                        v = fma2(u2pack(cc[8 * q + 2], cc[8 * q + 3]), buf[xp + k], v);
+                        v = fma2(u2pack(cc[8 * q + 4], cc[8 * q + 5]), buf[ym + k], v);
+                        v = fma2(u2pack(cc[8 * q + 6], cc[8 * q + 7]), buf[yp + k], v);
+                        v = fma2(k > 0 ? cz[k > 0 ? k - 1 : 0] : 0ull, prev, v);
+                        v = fma2(cz[k], k + 1 < W1 ? u[k + 1 < W1 ? k + 1 : k] : 0ull, v);
+                        prev = cur;
+                        u[k] = add2(cur, v);
+                    }
+                }
+                if (g + 1 < NG) tm_wait_ld(cn);
+            }
+        }
+
+        uint64_t* sbuf = xbuf + (a.n_sub & 1) * BUF;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                float stv[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int z = sz[h] - R + k;
+                    stv[h] = 0.f;
+                    if (col_ok[h] && z >= 0 && z < nzs[h]) {
+                        const int64_t i = (int64_t)xs[h] + (int64_t)nxs[h] * ys[h] + nxy[h] * z;
+                        stv[h] = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, qb[h] + i, pos[h]),
+                                     h == 0 ? f2lo(u[k]) : f2hi(u[k]));
+                    }
+                }
+                sbuf[base + k] = f2pack(stv[0], stv[1]);
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < PAIRS * COLS; c += blockDim.x) {
+            const int pr = c / COLS, cl = c - pr * COLS;
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                const uint64_t v = sbuf[c * W1 + k];
+                s0 += (double)f2lo(v);
+                s1 += (double)f2hi(v);
+            }
+            red[(2 * pr) * COLS + cl] = s0;
+            red[(2 * pr + 1) * COLS + cl] = s1;
+        }
+        __syncthreads();
+        finish_sigma<COLS, 2 * PAIRS>(red, first, a.src_end, a.list, a.sigma);
+        __syncthreads();
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr) : "memory");
+}
+
+template <int R>
+cudaError_t launch_tmp(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    using M = MapTmp<R>;
+    const int64_t nsrc = a.src_end - a.src_begin;
+    if (nsrc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(march_tmp_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmp_kernel<R>, M::THREADS, M::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm != 1) return cudaErrorInvalidConfiguration;   // TMEM allocation assumes one CTA per SM
+    const int64_t nbatch = (nsrc + 2 * M::PAIRS - 1) / (2 * M::PAIRS);
+    const int64_t grid = nbatch < (int64_t)num_sms ? nbatch : (int64_t)num_sms;
+    march_tmp_kernel<R><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int R, int P>
 cudaError_t launch_f32(const MarchArgs& a, int num_sms, cudaStream_t st) {
     using M = Map32<R, P>;
@@ -914,6 +1168,7 @@ cudaError_t launch_f32_p(const MarchArgs& a, int P, int num_sms, cudaStream_t st
         case 3: return launch_f32<R, 3>(a, num_sms, st);
         case 4: return launch_tm<R>(a, num_sms, st);
         case 5: return launch_tmc<R>(a, num_sms, st);
+        case 6: return launch_tmp<R>(a, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -987,9 +1242,9 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     float best_ms = 1e30f;
     *best = default_parts(a.R);
-    for (int P = 1; P <= 5 && e == cudaSuccess; P++) {
+    for (int P = 1; P <= 6 && e == cudaSuccess; P++) {
         if (P <= 3 && P > W1) continue;
-        if (a.R > 8 && P < 4) continue;           // only the TMEM mappings cover R = 9, 10
+        if (a.R > 8 && (P < 4 || P > 5)) continue; // only mappings 4 and 5 cover R = 9, 10
         if (P == 5 && a.R < 6) continue;          // one CTA of < 6 warps per SM: never the fastest there
         e = dispatch(warm, P, num_sms, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -1009,7 +1264,7 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
 
 cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts) {
     if (a.store == Store::F64) { *parts = 1; return cudaSuccess; }
-    if (parts_req >= 1 && parts_req <= 5 && (a.R <= 8 || parts_req >= 4)) { *parts = parts_req; return cudaSuccess; }
+    if (parts_req >= 1 && parts_req <= 6 && (a.R <= 8 || parts_req == 4 || parts_req == 5)) { *parts = parts_req; return cudaSuccess; }
     int dev = 0;
     cudaGetDevice(&dev);
     const auto key = std::make_tuple(dev, a.R, (int)a.store);
@@ -1030,7 +1285,7 @@ cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStrea
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
     int P = 1;
     if (a.store != Store::F64) {
-        if (parts_req >= 1 && parts_req <= 5 && (a.R <= 8 || parts_req >= 4)) {
+        if (parts_req >= 1 && parts_req <= 6 && (a.R <= 8 || parts_req == 4 || parts_req == 5)) {
             P = parts_req;
         } else {
             int dev = 0;

@@ -216,18 +216,18 @@ def test_one_dimensional_chain():
 @pytest.mark.parametrize("R", [2, 5, 8])
 def test_thread_mappings_agree_bitwise(R):
     """Every thread mapping of the FP32 march (1, 2 or 3 threads per window column, 2x2 column blocks
-    with TMEM-resident coefficients, or one column per thread with TMEM-resident lateral faces) gives the
-    same bits."""
+    with TMEM-resident coefficients, one column per thread with TMEM-resident lateral faces, or one
+    column of a source pair per thread in packed f32x2 arithmetic) gives the same bits."""
     shape = (19, 17, 13)
     D = _case(shape, 81, "per_sphere")
     lam = oracle.stable_dt_sub(shape, D)
     N = int(np.prod(shape))
     c0 = synth.random_field(N, 82)
     src = np.arange(0, N, 7)
-    runs = [_gpu_run(shape, D, lam, R, 37, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5)]
+    runs = [_gpu_run(shape, D, lam, R, 37, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5, 6)]
     for got, m, ks, info in runs[1:]:
         assert np.array_equal(got, runs[0][0]) and np.array_equal(ks, runs[0][2]) and m == runs[0][1]
-    assert [r[3]["march_parts"] for r in runs] == [1, 2, 3, 4, 5]
+    assert [r[3]["march_parts"] for r in runs] == [1, 2, 3, 4, 5, 6]
     ref, _ = oracle.kernels(shape, D, lam, R, 37, src)
     err = np.linalg.norm((runs[0][2] - ref).reshape(len(src), -1), axis=1) / np.linalg.norm(ref.reshape(len(src), -1), axis=1)
     assert err.max() <= KERNEL_TOL["fp32"]
