@@ -170,6 +170,21 @@ def march_kernel_name(prec: str, parts: int) -> str:
         parts, f"march_f32_kernel<R,{parts}>")
 
 
+# DRAM bytes (read + write) per clipped window cell of march_tm_kernel<8> with BF16 storage, from one ncu
+# capture of the 64^3 case with the same recipe (profiles/march_tm_R8_64c.md: 1.209 GB read + 3.038 GB
+# written over 1.049e9 window cells); the traffic of a full launch scales with its window cells (the
+# stored kernel values dominate it).  Valid for that kernel, radius and storage only.
+TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL = (1.209124e9 + 3.037791e9) / 1.049e9
+
+
+def march_traffic(args, prec: str, parts: int, R: int, window_cells: float):
+    if args.traffic is not None:
+        return args.traffic
+    if prec == "bf16" and parts == 4 and R == 8:
+        return TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL * window_cells
+    return None
+
+
 def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: float, traffic, clocks, kname: str):
     """Achieved FP32 flop rate of the march (13 flop per cell-substep over the clipped windows) against the
     FP32 pipe peak at the measured maximum SM clock."""
@@ -495,8 +510,12 @@ def run_ours(args, w):
         fp64 = fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec=prec)
 
     clocks = clk.summary()
-    roofline = fp32_alu_roofline(torch, dev, w.n_sub, info["window_cells"], march_ms, args.traffic, clocks,
+    roofline = fp32_alu_roofline(torch, dev, w.n_sub, info["window_cells"], march_ms,
+                                 march_traffic(args, prec, info["march_parts"], w.R, info["window_cells"]), clocks,
                                  march_kernel_name(prec, info["march_parts"]))
+    if roofline["traffic"] is not None and args.traffic is None:
+        roofline["traffic_source"] = ("ncu capture of the 64^3 case (profiles/march_tm_R8_64c.md), DRAM bytes "
+                                      "scaled by window cells to this launch")
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
