@@ -78,6 +78,16 @@ def _load():
             lib.fo_superpose_rmap.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double, _I32, ctypes.c_int,
                                                                              _D, _D]
             lib.fo_superpose_rmap.restype = ctypes.c_int
+            _U8 = ctypes.POINTER(ctypes.c_uint8)
+            lib.fo_mask_faces.argtypes = [ctypes.c_int] * 3 + [_U8, _D, _D, _D]
+            lib.fo_mask_faces.restype = None
+            lib.fo_coarse_counts.argtypes = [ctypes.c_int] * 3 + [_U8, ctypes.c_int, _I64]
+            lib.fo_coarse_counts.restype = None
+            lib.fo_coarse_kernels.argtypes = [ctypes.c_int] * 3 + [_D] * 3 + [_U8, ctypes.c_int, ctypes.c_double,
+                                                                             ctypes.c_int, ctypes.c_int, _D]
+            lib.fo_coarse_kernels.restype = ctypes.c_int
+            lib.fo_coarse_step.argtypes = [ctypes.c_int] * 3 + [_U8, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+            lib.fo_coarse_step.restype = ctypes.c_int
             lib.fo_mass.argtypes = [_D, ctypes.c_int64]
             lib.fo_mass.restype = ctypes.c_double
             _lib = lib
@@ -93,9 +103,10 @@ def _f64(a) -> np.ndarray:
 
 
 class Conductance:
-    """Face conductances of a grid (gx, gy, gz: +x/+y/+z face of each cell)."""
+    """Face conductances of a grid (gx, gy, gz: +x/+y/+z face of each cell).  With a liquid mask, faces
+    with a non-liquid cell on either side carry none (the coarse-mesh path)."""
 
-    def __init__(self, shape, D):
+    def __init__(self, shape, D, liquid=None):
         self.shape = tuple(int(v) for v in shape)
         nx, ny, nz = self.shape
         self.D = _f64(D).reshape(-1)
@@ -105,6 +116,9 @@ class Conductance:
         self.gy = np.empty_like(self.D)
         self.gz = np.empty_like(self.D)
         _load().fo_face_conductance(nx, ny, nz, _p(self.D), _p(self.gx), _p(self.gy), _p(self.gz))
+        if liquid is not None:
+            self.liquid = _u8(liquid, self.D.size)
+            _load().fo_mask_faces(nx, ny, nz, _pu8(self.liquid), _p(self.gx), _p(self.gy), _p(self.gz))
 
     @property
     def args(self):
@@ -189,6 +203,57 @@ def superpose_rmap(shape, D, lam: float, Rmap, n_sub: int, c, cond: Conductance 
     out = np.empty_like(c)
     if _load().fo_superpose_rmap(*g.args, float(lam), Rm.ctypes.data_as(_I32), int(n_sub), _p(c), _p(out)) != 0:
         raise ValueError("fo_superpose_rmap failed")
+    return out
+
+
+def _u8(a, n: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
+    if a.size != n:
+        raise ValueError("liquid mask has the wrong size")
+    return a
+
+
+def _pu8(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def coarse_radius(R: int, B: int) -> int:
+    """Block radius of the coarse matrix band: ceil(R / B)."""
+    return (R + B - 1) // B
+
+
+def coarse_counts(shape, liquid, B: int) -> np.ndarray:
+    """Liquid cells per B^3 block (int64, block index bx + ncx (by + ncy bz))."""
+    nx, ny, nz = shape
+    nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
+    out = np.empty(nc, dtype=np.int64)
+    lq = _u8(liquid, nx * ny * nz)
+    _load().fo_coarse_counts(nx, ny, nz, _pu8(lq), int(B), out.ctypes.data_as(_I64))
+    return out
+
+
+def coarse_kernels(shape, D, liquid, B: int, lam: float, R: int, n_sub: int) -> np.ndarray:
+    """Coarse matrix P of Eq. 10 in its band layout [n_blocks, Wc, Wc, Wc] (source block J, offsets
+    [dz+Rc, dy+Rc, dx+Rc] to the destination block), Wc = 2 ceil(R/B) + 1."""
+    nx, ny, nz = shape
+    g = Conductance(shape, D, liquid)
+    Wc = 2 * coarse_radius(R, B) + 1
+    nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
+    out = np.empty((nc, Wc, Wc, Wc), dtype=np.float64)
+    if _load().fo_coarse_kernels(*g.args, _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub), _p(out)) != 0:
+        raise ValueError("fo_coarse_kernels rejected its arguments")
+    return out
+
+
+def coarse_step(shape, liquid, B: int, R: int, P_band, c) -> np.ndarray:
+    """One coarse-mesh FDiRW step (Eqs. 13-15, no boundary term)."""
+    nx, ny, nz = shape
+    lq = _u8(liquid, nx * ny * nz)
+    c = _f64(c).reshape(-1)
+    P = _f64(P_band)
+    out = np.empty_like(c)
+    if _load().fo_coarse_step(nx, ny, nz, _pu8(lq), int(B), int(R), _p(P), _p(c), _p(out)) != 0:
+        raise ValueError("fo_coarse_step failed")
     return out
 
 

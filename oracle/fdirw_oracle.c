@@ -233,6 +233,151 @@ int fo_superpose_rmap(int nx, int ny, int nz, const double* gx, const double* gy
     return bad ? -1 : 0;
 }
 
+/* ---- Coarse mesh (Sec. 3.1, Eqs. 10-15).  The coarsening rule is a reading (the paper takes it from its
+ * ref. [12]): the grid is cut into B x B x B blocks (the last ones clipped by the domain), and the
+ * liquid cells of block I form representative node I (N_I cells; a block without liquid has no node).
+ * Block index I = bx + ncx (by + ncy bz), ncx = ceil(nx / B).  The fast-diffusion phase is the liquid:
+ * faces with a non-liquid cell on either side carry no flux, and non-liquid cells keep their value. */
+
+/* Zeroes the face conductances of every face that has a non-liquid cell on either side. */
+void fo_mask_faces(int nx, int ny, int nz, const uint8_t* liquid, double* gx, double* gy, double* gz)
+{
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                if (!liquid[i] || x + 1 >= nx || !liquid[i + 1]) gx[i] = 0.0;
+                if (!liquid[i] || y + 1 >= ny || !liquid[i + nx]) gy[i] = 0.0;
+                if (!liquid[i] || z + 1 >= nz || !liquid[i + (int64_t)nx * ny]) gz[i] = 0.0;
+            }
+}
+
+/* Liquid-cell count of every block: cnt[ncx * ncy * ncz]. */
+void fo_coarse_counts(int nx, int ny, int nz, const uint8_t* liquid, int B, int64_t* cnt)
+{
+    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
+    memset(cnt, 0, sizeof(int64_t) * (size_t)ncx * ncy * ncz);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++)
+                if (liquid[IDX(x, y, z, nx, ny)]) cnt[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))]++;
+}
+
+/* Column J of the coarse matrix P (Eq. 10) for every block J with liquid cells: the remapped unit
+ * C_J = 1 (Eq. 12: 1 on each liquid cell of J) marched n_sub explicit substeps on the window of block J
+ * widened by R cells (clipped to the domain; zero flux through its faces and through non-liquid
+ * faces, which gx/gy/gz already carry), then mapped (Eq. 11): P[I][J] = N_J S_I / (m N_I), with S_I the
+ * marched mass on the liquid cells of block I and m the total (N_J in exact arithmetic, so each column
+ * conserves mass).  Stored source-major: P_band[J][d], d = I - J over [-Rc, Rc]^3, Rc = ceil(R / B),
+ * offset layout d_x fastest; 0 where block I is outside the grid or has no liquid.  OpenMP over J. */
+int fo_coarse_kernels(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                      const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
+{
+    if (B < 1 || R < 0 || n_sub < 0) return -1;
+    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
+    int64_t NC = (int64_t)ncx * ncy * ncz;
+    int Rc = (R + B - 1) / B, Wc = 2 * Rc + 1;
+    int64_t Wc3 = (int64_t)Wc * Wc * Wc;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
+    if (!cnt) return -1;
+    fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
+    memset(P_band, 0, sizeof(double) * (size_t)(NC * Wc3));
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t J = 0; J < NC; J++) {
+        if (cnt[J] == 0 || err) continue;
+        int bx = (int)(J % ncx), by = (int)((J / ncx) % ncy), bz = (int)(J / ((int64_t)ncx * ncy));
+        int x0 = bx * B - R < 0 ? 0 : bx * B - R, x1 = bx * B + B - 1 + R > nx - 1 ? nx - 1 : bx * B + B - 1 + R;
+        int y0 = by * B - R < 0 ? 0 : by * B - R, y1 = by * B + B - 1 + R > ny - 1 ? ny - 1 : by * B + B - 1 + R;
+        int z0 = bz * B - R < 0 ? 0 : bz * B - R, z1 = bz * B + B - 1 + R > nz - 1 ? nz - 1 : bz * B + B - 1 + R;
+        int wx = x1 - x0 + 1, wy = y1 - y0 + 1, wz = z1 - z0 + 1;
+        int64_t nb = (int64_t)wx * wy * wz;
+        double* u = (double*)calloc((size_t)nb, sizeof(double));
+        double* un = (double*)calloc((size_t)nb, sizeof(double));
+        double* S = (double*)calloc((size_t)Wc3, sizeof(double));
+        if (!u || !un || !S) { free(u); free(un); free(S); err = 1; continue; }
+        for (int l = 0; l < wz; l++)
+            for (int j = 0; j < wy; j++)
+                for (int i = 0; i < wx; i++) {
+                    int x = x0 + i, y = y0 + j, z = z0 + l;
+                    if (x / B == bx && y / B == by && z / B == bz && liquid[IDX(x, y, z, nx, ny)])
+                        u[i + (int64_t)wx * (j + (int64_t)wy * l)] = 1.0;
+                }
+        for (int k = 0; k < n_sub; k++) {
+            box_substep(nx, ny, gx, gy, gz, lam, x0, y0, z0, wx, wy, wz, u, un);
+            double* t = u; u = un; un = t;
+        }
+        double m = 0.0;
+        for (int64_t q = 0; q < nb; q++) m += u[q];
+        for (int l = 0; l < wz; l++)
+            for (int j = 0; j < wy; j++)
+                for (int i = 0; i < wx; i++) {
+                    int x = x0 + i, y = y0 + j, z = z0 + l;
+                    if (!liquid[IDX(x, y, z, nx, ny)]) continue;
+                    int dx = x / B - bx, dy = y / B - by, dz = z / B - bz;
+                    S[(dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc))] +=
+                        u[i + (int64_t)wx * (j + (int64_t)wy * l)];
+                }
+        for (int dz = -Rc; dz <= Rc; dz++)
+            for (int dy = -Rc; dy <= Rc; dy++)
+                for (int dx = -Rc; dx <= Rc; dx++) {
+                    int cx = bx + dx, cy = by + dy, cz = bz + dz;
+                    if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy || cz < 0 || cz >= ncz) continue;
+                    int64_t I = cx + (int64_t)ncx * (cy + (int64_t)ncy * cz);
+                    if (cnt[I] == 0) continue;
+                    int64_t o = (dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc));
+                    P_band[J * Wc3 + o] = ((double)cnt[J] * S[o]) / (m * (double)cnt[I]);
+                }
+        free(u); free(un); free(S);
+    }
+    free(cnt);
+    return err ? -1 : 0;
+}
+
+/* One coarse FDiRW step, Eqs. 13-15 without the boundary term: 'mapping' C_I = mean of c over the
+ * liquid cells of block I (Eq. 13), 'FDiRW calculation' C'_I = sum_J P[I][J] C_J (Eq. 14), 're-mapping'
+ * c'_i = C'_I for every liquid cell i of block I (Eq. 15); non-liquid cells keep c. */
+int fo_coarse_step(int nx, int ny, int nz, const uint8_t* liquid, int B, int R, const double* P_band,
+                   const double* c_in, double* c_out)
+{
+    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
+    int64_t NC = (int64_t)ncx * ncy * ncz;
+    int Rc = (R + B - 1) / B, Wc = 2 * Rc + 1;
+    int64_t Wc3 = (int64_t)Wc * Wc * Wc;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
+    double* C = (double*)calloc((size_t)NC, sizeof(double));
+    double* Cn = (double*)calloc((size_t)NC, sizeof(double));
+    if (!cnt || !C || !Cn) { free(cnt); free(C); free(Cn); return -1; }
+    fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                if (liquid[i]) C[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))] += c_in[i];
+            }
+    for (int64_t I = 0; I < NC; I++) if (cnt[I] > 0) C[I] /= (double)cnt[I];
+    for (int64_t J = 0; J < NC; J++) {
+        if (cnt[J] == 0) continue;
+        int bx = (int)(J % ncx), by = (int)((J / ncx) % ncy), bz = (int)(J / ((int64_t)ncx * ncy));
+        for (int dz = -Rc; dz <= Rc; dz++)
+            for (int dy = -Rc; dy <= Rc; dy++)
+                for (int dx = -Rc; dx <= Rc; dx++) {
+                    int cx = bx + dx, cy = by + dy, cz = bz + dz;
+                    if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy || cz < 0 || cz >= ncz) continue;
+                    int64_t I = cx + (int64_t)ncx * (cy + (int64_t)ncy * cz);
+                    Cn[I] += P_band[J * Wc3 + (dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc))] * C[J];
+                }
+    }
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                c_out[i] = liquid[i] ? Cn[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))] : c_in[i];
+            }
+    free(cnt); free(C); free(Cn);
+    return 0;
+}
+
 int fo_full_march(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                   double lam, int n_sub, const double* c_in, double* c_out)
 {

@@ -1,0 +1,99 @@
+"""Pins of the oracle's coarse-mesh FDiRW (Sec. 3.1, Eqs. 10-15): hand-worked chains, the reduction to
+the fine windowed FDiRW when every block is one cell, a single-block domain, and mass conservation with
+a liquid mask and clipped blocks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_11376_gb300 import synth
+
+
+def test_chain_two_blocks_by_hand():
+    """6 cells in a row, all liquid, D = 1 (face conductance 1), B = 3, one substep of lam:
+    u0 = 1 on block 0 -> [1, 1, 1 - lam, lam, 0, 0], so P[0][0] = 1 - lam/3 and P[1][0] = lam/3."""
+    lam = 0.2
+    shape = (6, 1, 1)
+    P = oracle.coarse_kernels(shape, np.ones(6), np.ones(6), 3, lam, 3, 1)
+    Rc = oracle.coarse_radius(3, 3)
+    assert P.shape == (2, 2 * Rc + 1, 2 * Rc + 1, 2 * Rc + 1)
+    assert P[0][Rc, Rc, Rc] == pytest.approx(1 - lam / 3, abs=1e-15)
+    assert P[0][Rc, Rc, Rc + 1] == pytest.approx(lam / 3, abs=1e-15)
+    assert P[1][Rc, Rc, Rc] == pytest.approx(1 - lam / 3, abs=1e-15)
+    assert P[1][Rc, Rc, Rc - 1] == pytest.approx(lam / 3, abs=1e-15)
+    assert np.count_nonzero(P) == 4
+    c = np.array([0.3, 0.9, 0.6, 2.0, 1.0, 0.0])
+    C = np.array([0.6, 1.0])                                     # block means (Eq. 13)
+    Cn = np.array([(1 - lam / 3) * C[0] + lam / 3 * C[1], lam / 3 * C[0] + (1 - lam / 3) * C[1]])
+    got = oracle.coarse_step(shape, np.ones(6), 3, 3, P, c)
+    assert np.allclose(got, np.repeat(Cn, 3), rtol=0, atol=1e-15)   # re-mapping (Eq. 15)
+
+
+def test_non_liquid_cell_blocks_flux_and_keeps_its_value():
+    """Chain [L, L, S, L], B = 1: the solid cell is no fast-diffusion node and cuts the chain."""
+    lam = 0.25
+    shape = (4, 1, 1)
+    liquid = np.array([1, 1, 0, 1])
+    P = oracle.coarse_kernels(shape, np.ones(4), liquid, 1, lam, 2, 1)
+    Rc = 2
+    assert P[0][Rc, Rc, Rc] == pytest.approx(1 - lam) and P[0][Rc, Rc, Rc + 1] == pytest.approx(lam)
+    assert P[3][Rc, Rc, Rc] == 1.0 and not P[2].any()
+    c = np.array([1.0, 0.0, 5.0, 2.0])
+    got = oracle.coarse_step(shape, liquid, 1, 2, P, c)
+    assert np.allclose(got, [1 - lam, lam, 5.0, 2.0], rtol=0, atol=1e-15)
+
+
+def test_unit_blocks_reduce_to_the_fine_windowed_fdirw():
+    """B = 1 with every cell liquid: the representative nodes are the cells and P is p (Eq. 8)."""
+    shape = (9, 8, 7)
+    D = synth.random_diffusivity(shape, 61, 4.0)
+    lam = oracle.stable_dt_sub(shape, D)
+    c = synth.random_field(D.size, 62)
+    liquid = np.ones(D.size)
+    P = oracle.coarse_kernels(shape, D, liquid, 1, lam, 3, 13)
+    ks, _ = oracle.kernels(shape, D, lam, 3, 13, np.arange(D.size))
+    assert np.allclose(P, ks, rtol=0, atol=1e-15)
+    got = oracle.coarse_step(shape, liquid, 1, 3, P, c)
+    assert np.allclose(got, oracle.superpose(shape, D, lam, 3, 13, c), rtol=1e-14, atol=0)
+
+
+def test_one_block_is_the_liquid_mean():
+    shape = (5, 4, 3)
+    D = synth.random_diffusivity(shape, 63, 3.0)
+    liquid = (np.random.default_rng(64).random(60) < 0.7).astype(np.uint8)
+    lam = oracle.stable_dt_sub(shape, D)
+    P = oracle.coarse_kernels(shape, D, liquid, 5, lam, 4, 9)
+    c = synth.random_field(60, 65)
+    got = oracle.coarse_step(shape, liquid, 5, 4, P, c)
+    Rc = oracle.coarse_radius(4, 5)
+    assert P[0][Rc, Rc, Rc] == pytest.approx(1.0, abs=1e-15)
+    lq = liquid.astype(bool)
+    assert np.allclose(got[lq], c[lq].mean(), rtol=1e-15) and np.array_equal(got[~lq], c[~lq])
+
+
+def test_mass_conservation_with_mask_and_clipped_blocks():
+    shape = (13, 12, 11)
+    p = synth.sphere_packing(shape, 0.4, 66, r_range=(1.5, 3.0))
+    D = synth.diffusivity_per_sphere(p)
+    liquid = ~p.solid
+    lam = oracle.stable_dt_sub(shape, D)
+    for B, R in ((5, 8), (3, 4)):
+        P = oracle.coarse_kernels(shape, D, liquid, B, lam, R, 20)
+        cnt = oracle.coarse_counts(shape, liquid, B)
+        # every column carries its block's mass: sum_I N_I P[I][J] = N_J
+        Rc = oracle.coarse_radius(R, B)
+        ncx, ncy, ncz = ((n + B - 1) // B for n in shape)
+        for J in np.flatnonzero(cnt)[::3]:
+            bx, by, bz = J % ncx, (J // ncx) % ncy, J // (ncx * ncy)
+            tot = 0.0
+            for dz in range(-Rc, Rc + 1):
+                for dy in range(-Rc, Rc + 1):
+                    for dx in range(-Rc, Rc + 1):
+                        cx, cy, cz = bx + dx, by + dy, bz + dz
+                        if 0 <= cx < ncx and 0 <= cy < ncy and 0 <= cz < ncz:
+                            I = cx + ncx * (cy + ncy * cz)
+                            tot += cnt[I] * P[J][dz + Rc, dy + Rc, dx + Rc]
+            assert tot == pytest.approx(cnt[J], rel=1e-13)
+        c = synth.random_field(D.size, 67, 0.0, 2.0)
+        got = oracle.coarse_step(shape, liquid, B, R, P, c)
+        assert abs(got.sum() - c.sum()) <= 1e-13 * c.sum()
+        assert P.min() >= 0.0
