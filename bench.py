@@ -420,7 +420,7 @@ def run_ours(args, w):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    _, D_host, c_host = w.make()
+    packing, D_host, c_host = w.make()
     shape = (w.n,) * 3
     N = w.n ** 3
     D = torch.from_numpy(D_host).to(dev)
@@ -547,6 +547,8 @@ def run_ours(args, w):
         line["speedup_vs_fp64_gpu"] = value / fp64["macro_steps_per_s"]
     if args.surrogate:
         line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec)
+    if args.coarse:
+        line["coarse_mesh"] = coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, ~packing.solid, dt_macro)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -609,6 +611,55 @@ def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, pr
            "mass_rel_err": abs(sgm["mass"] - mass0) / mass0}
     net.close()
     return out
+
+
+def coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, liquid, dt_macro):
+    """Coarse-mesh FDiRW (Eqs. 10-15) on the same geometry: the liquid (pore) cells of each B^3 block form
+    one node, R and n_sub as the fine path.  Times create + coarse matrix + all macro steps.  Accuracy: a
+    Gaussian blob (sigma = 10 cells) on the liquid cells, against the fine windowed FDiRW of the same
+    liquid phase (D = 0 in the non-liquid cells, which gives those faces zero conductance)."""
+    B = args.coarse
+    n = shape[0]
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r2 = ((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - n / 2) ** 2).reshape(-1)
+    c_liq = torch.from_numpy(np.where(liquid, np.exp(-r2 / (2 * 10.0 ** 2)), 0.0)).to(dev)
+    lq = torch.from_numpy(liquid.astype(np.uint8)).to(dev)
+    runs = []
+    for _ in range(3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        out = torch.empty_like(c_liq)
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            ctx = fdirw.fdirw_create_coarse(shape, D, lq, B, dt_macro, w.R, w.n_sub, args.prec, device=dev.index,
+                                            stream=stream)
+            ev[1].record(stream)
+            fdirw.fdirw_kernels(ctx)
+            ev[2].record(stream)
+            mass = fdirw.fdirw_step(ctx, c_liq, out, w.steps, want_mass=True)
+            ev[3].record(stream)
+            info = fdirw.fdirw_get_info(ctx)
+            fdirw.fdirw_destroy(ctx)
+        stream.synchronize()
+        runs.append((ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]), info, mass, out))
+    job_ms, build_ms, steps_ms, info, mass, out = runs[-1]
+    fine = torch.empty_like(c_liq)
+    with torch.cuda.stream(stream):
+        ctx = fdirw.fdirw_create(shape, D * lq.to(D.dtype), dt_macro, w.R, w.n_sub, args.prec, device=dev.index,
+                                 stream=stream)
+        fdirw.fdirw_step(ctx, c_liq, fine, w.steps)
+        fdirw.fdirw_destroy(ctx)
+    stream.synchronize()
+    mass0 = float(c_liq.sum().item())
+    lqb = lq.bool()
+    return {"block": B, "nodes": info["coarse_nodes"], "liquid_cells": int(liquid.sum()),
+            "macro_steps_per_s": 1000.0 * w.steps / job_ms, "job_ms": job_ms, "matrix_build_ms": build_ms,
+            "march_kernel_ms": info["kernels_ms"], "steps_ms": steps_ms,
+            "march_cell_substeps_per_s": w.n_sub * info["window_cells"] / (info["kernels_ms"] * 1e-3),
+            "matrix_bytes": info["cache_bytes"],
+            "field": "Gaussian blob sigma 10 on the liquid cells",
+            "rel_l2_vs_fine_liquid_phase": float((torch.linalg.vector_norm((out - fine)[lqb]) /
+                                                  torch.linalg.vector_norm(fine[lqb])).item()),
+            "mass_rel_err": abs(mass - mass0) / mass0}
 
 
 def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
@@ -674,6 +725,8 @@ def main(argv=None):
     ap.add_argument("--surrogate-per-structure", type=int, default=10000)
     ap.add_argument("--surrogate-epochs", type=int, default=4)
     ap.add_argument("--surrogate-lr", type=float, default=2e-3)
+    ap.add_argument("--coarse", type=int, default=0,
+                    help="also run the coarse-mesh FDiRW with this odd block side (e.g. 5) and compare it with the fine path")
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
     ap.add_argument("--march-parts", type=int, default=0,
                     help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "

@@ -111,7 +111,8 @@ typedef struct {
     int32_t  graph_launches; /* batch contexts: CUDA graph launches so far (one per fdirw_step call) */
     int32_t  dest_indexed_radii; /* batch contexts: bit r set when radius r's kernels are stored
                                     destination-indexed (radii on >= 20% of the cells), else source-indexed */
-    int32_t  reserved2;
+    int32_t  coarse_block;   /* coarse-mesh contexts: block side B (0 otherwise) */
+    int64_t  coarse_nodes;   /* coarse-mesh contexts: representative nodes (blocks with liquid cells) */
 } fdirw_info;
 
 typedef struct fdirw_ctx fdirw_ctx;
@@ -194,6 +195,31 @@ FDIRW_API void fdirw_destroy(fdirw_ctx* ctx);
 FDIRW_API int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* D_maps, double dt_macro,
                                  int32_t R_min, int32_t R_max, int32_t n_sub, const fdirw_opts* opts,
                                  fdirw_ctx** out);
+
+/* Coarse-mesh FDiRW (Sec. 3.1, Eqs. 10-15, without the boundary term p_BC c_far).  The liquid cells of
+ * each block x block x block cube of the grid (block odd; cubes clipped by the domain keep their cells)
+ * form one representative node I with N_I cells; faces with a non-liquid cell on either side carry no
+ * flux and non-liquid cells keep their value (the paper's liquid phase; its coarsening rule is in its
+ * ref. [12], this cube grouping is this library's reading).  Column J of the coarse matrix P (Eq. 10) is
+ * the remapped unit of node J (1 on its liquid cells, Eq. 12) marched n_sub explicit substeps on the
+ * node's cube widened by window_R cells (clipped; zero flux through its faces), then mapped (Eq. 11):
+ * P[I][J] = N_J S_I / (m N_I), S_I the marched mass on node I's cells and m the total, in FP64 from the
+ * FP32 march.  fdirw_step then applies, per macro step, the mapping C_I = mean of c over node I (Eq. 13),
+ * C' = P C (Eq. 14) and the re-mapping c'_i = C'_I on node I's liquid cells (Eq. 15); fdirw_kernels
+ * builds P (lazily otherwise), fdirw_mass and fdirw_get_info work as for fdirw_create contexts.
+ *   liquid   : N bytes (host or device), nonzero = liquid; NULL = every cell liquid; copied
+ *   block    : cube side B, odd, >= 1; window_R + (B - 1) / 2 must lie in [1, 10]
+ *   opts.prec: FDIRW_FP32, FDIRW_FP32_STORE_FP16 or FDIRW_FP32_STORE_BF16 (the march is FP32 in every
+ *              case and P is stored FP64)
+ * Errors: as fdirw_create. */
+FDIRW_API int fdirw_create_coarse(const fdirw_grid* grid, const double* D_map, const uint8_t* liquid, int32_t block,
+                                  double dt_macro, int32_t window_R, int32_t n_sub, const fdirw_opts* opts,
+                                  fdirw_ctx** out);
+
+/* Columns of the coarse matrix for listed nodes (block indices bx + ncx (by + ncy bz), ncx = ceil(nx / B)):
+ * out[n][(2 Rc + 1)^3] on the block-offset layout d = I - J (d_x fastest, Rc = ceil(window_R / B)), 0 where
+ * block J + d is outside the grid or has no liquid.  Needs the matrix built (FDIRW_ERR_STATE otherwise). */
+FDIRW_API int fdirw_read_coarse(fdirw_ctx* ctx, const int64_t* blocks, int64_t n, double* out);
 
 /* Window radius of every source (n_cells int32 values, host): the radius rule's value for batch
  * contexts, window_R for fdirw_create contexts.  Synchronises the context stream. */

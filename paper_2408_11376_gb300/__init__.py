@@ -9,10 +9,10 @@ diffusion is marched over a local window for one macro step to give that source'
 * ``synth``  -- seeded synthetic microstructures, diffusivity maps and initial fields.
 """
 from . import synth  # noqa: F401
-from .fdirw import (FDiRW, FDiRWBatch, FdirwError, Net, PRECISIONS, fdirw_create, fdirw_create_batch,  # noqa: F401
-                    fdirw_destroy, fdirw_get_info, fdirw_kernels, fdirw_last_error, fdirw_mass, fdirw_read_kernels,
+from .fdirw import (FDiRW, FDiRWBatch, FDiRWCoarse, FdirwError, Net, PRECISIONS, fdirw_create,  # noqa: F401
+                    fdirw_create_batch, fdirw_create_coarse, fdirw_read_coarse, fdirw_destroy, fdirw_get_info, fdirw_kernels, fdirw_last_error, fdirw_mass, fdirw_read_kernels,
                     fdirw_read_radius, fdirw_stable_dt, fdirw_step)
 
-__all__ = ["FDiRW", "FDiRWBatch", "FdirwError", "Net", "PRECISIONS", "fdirw_create", "fdirw_create_batch",
-           "fdirw_destroy", "fdirw_get_info", "fdirw_kernels", "fdirw_last_error", "fdirw_mass", "fdirw_read_kernels",
+__all__ = ["FDiRW", "FDiRWBatch", "FDiRWCoarse", "FdirwError", "Net", "PRECISIONS", "fdirw_create", "fdirw_create_batch",
+           "fdirw_create_coarse", "fdirw_read_coarse", "fdirw_destroy", "fdirw_get_info", "fdirw_kernels", "fdirw_last_error", "fdirw_mass", "fdirw_read_kernels",
            "fdirw_read_radius", "fdirw_stable_dt", "fdirw_step", "synth"]

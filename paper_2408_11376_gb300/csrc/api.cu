@@ -118,6 +118,7 @@ int conductances(fdirw_ctx* c, const double* D, double* g3[3], double* max_sum) 
 
 void release(fdirw_ctx* c) {
     fdirw::batch_release(c);
+    fdirw::coarse_release(c);
     for (auto& p : c->coef) dfree(p);
     dfree(c->Q);
     void* p;
@@ -273,6 +274,7 @@ int fdirw_kernels(fdirw_ctx* c) {
     if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
     DeviceGuard dg(c->device);
     if (c->batch) return fdirw::batch_kernels(c);
+    if (c->coarse) return fdirw::coarse_kernels(c);
     if (c->R == 0) { c->kernels_ready = true; return FDIRW_OK; }
     const int rc = fdirw::ensure_cache(c);
     if (rc != FDIRW_OK) return rc;
@@ -313,6 +315,7 @@ int fdirw_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
         return fail(c, FDIRW_ERR_ARG, "c_in and c_out must be 8-byte aligned");
     DeviceGuard dg(c->device);
     if (c->batch) return fdirw::batch_step(c, c_in, c_out, n_steps, mass_out);
+    if (c->coarse) return fdirw::coarse_step(c, c_in, c_out, n_steps, mass_out);
     const Kind kin = classify(c_in, c->device), kout = classify(c_out, c->device);
     if (kin == Kind::Foreign || kout == Kind::Foreign)
         return fail(c, FDIRW_ERR_ARG, "c_in/c_out are device memory of another device");
@@ -382,6 +385,7 @@ int fdirw_read_kernels(fdirw_ctx* c, const int64_t* sources, int64_t n, double* 
     if (n < 0 || (n > 0 && (!sources || !out))) return fail(c, FDIRW_ERR_ARG, "bad sources/out");
     for (int64_t q = 0; q < n; q++)
         if (sources[q] < 0 || sources[q] >= c->g.n) return fail(c, FDIRW_ERR_ARG, "source index out of range");
+    if (c->coarse) return fail(c, FDIRW_ERR_ARG, "a coarse-mesh context has no per-source kernels (fdirw_read_coarse)");
     if (!c->kernels_ready) return fail(c, FDIRW_ERR_STATE, "kernel cache not built (call fdirw_kernels)");
     if (n == 0) return FDIRW_OK;
     if (c->batch) {
@@ -442,6 +446,7 @@ int fdirw_get_info(fdirw_ctx* c, fdirw_info* out) {
         out->last_gather_ms = ms;
     }
     if (c->batch) return fdirw::batch_info(c, out);
+    if (c->coarse) return fdirw::coarse_info(c, out);
     return FDIRW_OK;
 }
 

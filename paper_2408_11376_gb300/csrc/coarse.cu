@@ -1,0 +1,377 @@
+// Coarse-mesh FDiRW (Sec. 3.1, Eqs. 10-15, without the boundary term p_BC c_far).
+//
+//   nodes      the liquid cells of each B x B x B block form one representative node (B odd; blocks
+//              clipped by the domain keep their cells); N_I = liquid cells of block I
+//   phase      faces with a non-liquid cell on either side carry no flux; non-liquid cells keep c
+//   P          column J: the remapped unit of block J (1 on its liquid cells, Eq. 12) marched n_sub
+//              explicit substeps on the block's window widened by R cells, then mapped (Eq. 11):
+//              P[I][J] = N_J S_I / (m N_I), S_I the marched mass on block I, m the total.  The march is
+//              mapping 5 in coarse mode (march.cu); P is stored FP64, destination-indexed over the
+//              (2 Rc + 1)^3 block offsets, Rc = ceil(R / B)
+//   step       mapping (Eq. 13): C_I = mean of c over the liquid cells of block I, FP64 in cell order;
+//              FDiRW calculation (Eq. 14): C'_I = sum_d P[I][I - d] C_{I - d}, FP64, d ascending;
+//              re-mapping (Eq. 15): c'_i = C'_I on every liquid cell of block I.
+#include "fdirw.h"
+#include "fdirw_internal.h"
+#include "ctx.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fdirw::host;
+
+namespace fdirw {
+
+struct Coarse {
+    int B = 1, Rc = 0, Rw = 0;                   // block side, band radius, march window radius
+    int ncx = 0, ncy = 0, ncz = 0;
+    int64_t nc = 0, nodes = 0;                   // blocks, blocks with liquid
+    uint8_t* liquid = nullptr;                   // N
+    int32_t* count = nullptr;                    // nc
+    int64_t* list = nullptr;                     // blocks with liquid, ascending
+    double* Qc = nullptr;                        // Wc^3 planes of nc values
+    double* C = nullptr;                         // nc
+    double* Cn = nullptr;                        // nc
+    bool built = false;
+};
+
+namespace {
+
+int grid_blocks(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// Zero the coefficient of every face with a non-liquid cell on either side.
+__global__ void mask_faces_kernel(Grid g, const uint8_t* __restrict__ liquid, float* __restrict__ ax,
+                                  float* __restrict__ ay, float* __restrict__ az) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx);
+        const int y = (int)((i / g.nx) % g.ny);
+        const int z = (int)(i / nxy);
+        const bool l = liquid[i] != 0;
+        if (!l || x + 1 >= g.nx || !liquid[i + 1]) ax[i] = 0.f;
+        if (!l || y + 1 >= g.ny || !liquid[i + g.nx]) ay[i] = 0.f;
+        if (!l || z + 1 >= g.nz || !liquid[i + nxy]) az[i] = 0.f;
+    }
+}
+
+// Liquid cells per block (one thread per block, cells in z, y, x order).
+__global__ void count_kernel(Grid g, const uint8_t* __restrict__ liquid, int B, int ncx, int ncy, int64_t nc,
+                             int32_t* __restrict__ count) {
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(I % ncx), by = (int)((I / ncx) % ncy), bz = (int)(I / ((int64_t)ncx * ncy));
+        int n = 0;
+        for (int z = bz * B; z < min(bz * B + B, g.nz); z++)
+            for (int y = by * B; y < min(by * B + B, g.ny); y++)
+                for (int x = bx * B; x < min(bx * B + B, g.nx); x++)
+                    n += liquid[x + (int64_t)g.nx * (y + (int64_t)g.ny * z)] ? 1 : 0;
+        count[I] = n;
+    }
+}
+
+// Eq. 13: C_I = (sum of c over the liquid cells of block I, z, y, x order) / N_I.
+__global__ void map_kernel(Grid g, const uint8_t* __restrict__ liquid, int B, int ncx, int ncy, int64_t nc,
+                           const int32_t* __restrict__ count, const double* __restrict__ c, double* __restrict__ C) {
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(I % ncx), by = (int)((I / ncx) % ncy), bz = (int)(I / ((int64_t)ncx * ncy));
+        double s = 0.0;
+        for (int z = bz * B; z < min(bz * B + B, g.nz); z++)
+            for (int y = by * B; y < min(by * B + B, g.ny); y++)
+                for (int x = bx * B; x < min(bx * B + B, g.nx); x++) {
+                    const int64_t i = x + (int64_t)g.nx * (y + (int64_t)g.ny * z);
+                    if (liquid[i]) s += c[i];
+                }
+        C[I] = count[I] > 0 ? s / (double)count[I] : 0.0;
+    }
+}
+
+// Eq. 14: C'_I = sum over block offsets d (ascending) of P[I][I - d] C_{I - d}, FP64.
+__global__ void coarse_gather_kernel(int ncx, int ncy, int ncz, int Rc, const double* __restrict__ Qc,
+                                     const double* __restrict__ C, double* __restrict__ Cn) {
+    const int64_t nc = (int64_t)ncx * ncy * ncz;
+    const int Wc = 2 * Rc + 1;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(I % ncx), by = (int)((I / ncx) % ncy), bz = (int)(I / ((int64_t)ncx * ncy));
+        double acc = 0.0;
+        int d = 0;
+        for (int dz = -Rc; dz <= Rc; dz++)
+            for (int dy = -Rc; dy <= Rc; dy++)
+                for (int dx = -Rc; dx <= Rc; dx++, d++) {
+                    const int jx = bx - dx, jy = by - dy, jz = bz - dz;
+                    if (jx < 0 || jx >= ncx || jy < 0 || jy >= ncy || jz < 0 || jz >= ncz) continue;
+                    const int64_t J = jx + (int64_t)ncx * (jy + (int64_t)ncy * jz);
+                    acc = fma(Qc[(int64_t)d * nc + I], C[J], acc);
+                }
+        Cn[I] = acc;
+        (void)Wc;
+    }
+}
+
+// Eq. 15: c'_i = C'_I on liquid cells, c'_i = c_i elsewhere (in place allowed: each cell reads itself).
+__global__ void remap_kernel(Grid g, const uint8_t* __restrict__ liquid, int B, int ncx, int ncy,
+                             const double* __restrict__ Cn, const double* c_in, double* c_out) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
+        c_out[i] = liquid[i] ? Cn[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))] : c_in[i];
+    }
+}
+
+// Columns of P for listed blocks on the source-major band layout [n][Wc^3] (offset d = I - J).
+__global__ void read_coarse_kernel(const double* __restrict__ Qc, int ncx, int ncy, int ncz, int Rc,
+                                   const int64_t* __restrict__ blocks, int64_t n, double* __restrict__ out) {
+    const int Wc = 2 * Rc + 1;
+    const int64_t W3 = (int64_t)Wc * Wc * Wc, nc = (int64_t)ncx * ncy * ncz;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * W3; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / W3;
+        const int d = (int)(t % W3);
+        const int64_t J = blocks[q];
+        const int bx = (int)(J % ncx), by = (int)((J / ncx) % ncy), bz = (int)(J / ((int64_t)ncx * ncy));
+        const int cx = bx + d % Wc - Rc, cy = by + (d / Wc) % Wc - Rc, cz = bz + d / (Wc * Wc) - Rc;
+        double v = 0.0;
+        if (cx >= 0 && cx < ncx && cy >= 0 && cy < ncy && cz >= 0 && cz < ncz)
+            v = Qc[(int64_t)d * nc + cx + (int64_t)ncx * (cy + (int64_t)ncy * cz)];
+        out[t] = v;
+    }
+}
+
+}  // namespace
+
+int coarse_kernels(fdirw_ctx* c) {
+    Coarse& k = *c->coarse;
+    if (k.built) return FDIRW_OK;
+    const uint64_t W3 = (uint64_t)(2 * k.Rc + 1) * (2 * k.Rc + 1) * (2 * k.Rc + 1);
+    FDIRW_CUDA(c, cudaMemsetAsync(k.Qc, 0, W3 * (uint64_t)k.nc * 8, c->stream));
+    MarchArgs a{};
+    a.g = c->g;
+    a.R = k.Rw;
+    a.Rq = k.Rw;
+    a.n_sub = c->n_sub;
+    a.ax = reinterpret_cast<const float*>(c->coef[0]);
+    a.ay = reinterpret_cast<const float*>(c->coef[1]);
+    a.az = reinterpret_cast<const float*>(c->coef[2]);
+    a.src_begin = 0;
+    a.src_end = k.nodes;
+    a.list = k.list;
+    a.coarse_B = k.B;
+    a.coarse_Rc = k.Rc;
+    a.ncx = k.ncx;
+    a.ncy = k.ncy;
+    a.ncz = k.ncz;
+    a.coarse_n = k.nc;
+    a.liquid = k.liquid;
+    a.ccount = k.count;
+    a.Qc = k.Qc;
+    FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    if (k.nodes > 0 && c->n_sub >= 0) FDIRW_CUDA(c, launch_march_coarse(a, k.Rw, c->num_sms, c->stream));
+    FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    c->kernels_timed = true;
+    c->parts_used = 5;
+    k.built = true;
+    c->kernels_ready = true;
+    return FDIRW_OK;
+}
+
+int coarse_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps, double* mass_out) {
+    Coarse& k = *c->coarse;
+    const Kind kin = classify(c_in, c->device), kout = classify(c_out, c->device);
+    if (kin == Kind::Foreign || kout == Kind::Foreign)
+        return fail(c, FDIRW_ERR_ARG, "c_in/c_out are device memory of another device");
+    if (!k.built) {
+        const int rc = coarse_kernels(c);
+        if (rc != FDIRW_OK) return rc;
+    }
+    const size_t bytes = (size_t)c->g.n * 8;
+    const double* src = c_in;
+    if (kin == Kind::Host) {
+        FDIRW_CUDA(c, cudaMemcpyAsync(c->cbuf, c_in, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = c->cbuf;
+    }
+    double* dst = kout == Kind::Device ? c_out : c->cbuf;
+    if (mass_out) {
+        FDIRW_CUDA(c, launch_mass(src, c->g.n, c->partials, c->dmass, c->stream));
+        FDIRW_CUDA(c, cudaMemcpyAsync(&c->mass_in, c->dmass, 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (n_steps == 0) {
+        if (dst != src) FDIRW_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        const double* cur = src;
+        for (int t = 0; t < n_steps; t++) {
+            map_kernel<<<grid_blocks(k.nc, 128), 128, 0, c->stream>>>(c->g, k.liquid, k.B, k.ncx, k.ncy, k.nc, k.count, cur, k.C);
+            FDIRW_CUDA(c, cudaGetLastError());
+            const bool last = t + 1 == n_steps;
+            if (last) FDIRW_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+            coarse_gather_kernel<<<grid_blocks(k.nc, 128), 128, 0, c->stream>>>(k.ncx, k.ncy, k.ncz, k.Rc, k.Qc, k.C, k.Cn);
+            FDIRW_CUDA(c, cudaGetLastError());
+            if (last) FDIRW_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+            remap_kernel<<<grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(c->g, k.liquid, k.B, k.ncx, k.ncy, k.Cn, cur, dst);
+            FDIRW_CUDA(c, cudaGetLastError());
+            cur = dst;
+        }
+        c->gather_timed = true;
+    }
+    if (mass_out) {
+        FDIRW_CUDA(c, launch_mass(dst, c->g.n, c->partials, c->dmass, c->stream));
+        FDIRW_CUDA(c, cudaMemcpyAsync(&c->mass_out, c->dmass, 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (kout == Kind::Host) FDIRW_CUDA(c, cudaMemcpyAsync(c_out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (mass_out || kout == Kind::Host) FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (mass_out) *mass_out = c->mass_out;
+    return FDIRW_OK;
+}
+
+int coarse_info(fdirw_ctx* c, fdirw_info* out) {
+    out->coarse_block = c->coarse->B;
+    out->coarse_nodes = c->coarse->nodes;
+    out->cache_bytes = (uint64_t)(2 * c->coarse->Rc + 1) * (2 * c->coarse->Rc + 1) * (2 * c->coarse->Rc + 1) *
+                       (uint64_t)c->coarse->nc * 8;
+    return FDIRW_OK;
+}
+
+void coarse_release(fdirw_ctx* c) {
+    Coarse* k = c->coarse;
+    if (!k) return;
+    void* p;
+    p = k->liquid; dfree(p);
+    p = k->count; dfree(p);
+    p = k->list; dfree(p);
+    p = k->Qc; dfree(p);
+    p = k->C; dfree(p);
+    p = k->Cn; dfree(p);
+    delete k;
+    c->coarse = nullptr;
+}
+
+}  // namespace fdirw
+
+extern "C" {
+
+int fdirw_create_coarse(const fdirw_grid* grid, const double* D_map, const uint8_t* liquid, int32_t block,
+                        double dt_macro, int32_t window_R, int32_t n_sub, const fdirw_opts* opts, fdirw_ctx** out) {
+    if (!out) return fail(nullptr, FDIRW_ERR_ARG, "NULL out");
+    *out = nullptr;
+    if (!grid_ok(grid)) return fail(nullptr, FDIRW_ERR_ARG, "invalid grid (dimensions >= 1, finite h > 0)");
+    if (!D_map) return fail(nullptr, FDIRW_ERR_ARG, "NULL D_map");
+    if (block < 1 || block % 2 == 0) return fail(nullptr, FDIRW_ERR_ARG, "block must be odd and >= 1");
+    if (window_R < 0 || window_R + (block - 1) / 2 > fdirw::kMaxR)
+        return fail(nullptr, FDIRW_ERR_ARG, "need 0 <= window_R and window_R + (block - 1) / 2 <= " + std::to_string(fdirw::kMaxR));
+    if (window_R + (block - 1) / 2 < 1) return fail(nullptr, FDIRW_ERR_ARG, "window_R + (block - 1) / 2 must be >= 1");
+    fdirw_opts o{FDIRW_FP32, -1, nullptr, 0, 0, 0};
+    if (opts) o = *opts;
+    if (o.prec < FDIRW_FP32 || o.prec > FDIRW_FP32_STORE_BF16)
+        return fail(nullptr, FDIRW_ERR_ARG, "the coarse path marches in FP32 (prec FP32, FP16 or BF16; P is FP64)");
+    // fdirw_create validates D, dt_macro, n_sub and stability and builds the face coefficients; the
+    // coarse path then masks them and replaces the kernel cache with the coarse matrix.
+    fdirw_opts o2 = o;
+    o2.prec = FDIRW_FP32;
+    fdirw_ctx* c = nullptr;
+    int rc = fdirw_create(grid, D_map, dt_macro, 0, n_sub, &o2, &c);
+    if (rc != FDIRW_OK) return rc;
+    DeviceGuard dg(c->device);
+    c->coarse = new fdirw::Coarse();
+    fdirw::Coarse& k = *c->coarse;
+    c->R = window_R;
+    c->prec = o.prec;
+    k.B = block;
+    k.Rc = (window_R + block - 1) / block;
+    k.Rw = window_R + (block - 1) / 2;
+    k.ncx = (grid->nx + block - 1) / block;
+    k.ncy = (grid->ny + block - 1) / block;
+    k.ncz = (grid->nz + block - 1) / block;
+    k.nc = (int64_t)k.ncx * k.ncy * k.ncz;
+    const uint64_t n = (uint64_t)c->g.n;
+    auto bail = [&](int code) {
+        std::string msg = c->err;
+        fdirw_destroy(c);
+        return fail(nullptr, code, msg);
+    };
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&k.liquid), n, "liquid mask")) != FDIRW_OK) return bail(rc);
+    cudaError_t e = cudaSuccess;
+    if (liquid) {
+        if (classify(liquid, c->device) == Kind::Foreign) { c->err = "liquid is device memory of another device"; return bail(FDIRW_ERR_ARG); }
+        e = cudaMemcpyAsync(k.liquid, liquid, n, cudaMemcpyDefault, c->stream);
+    } else {
+        e = cudaMemsetAsync(k.liquid, 1, n, c->stream);
+    }
+    if (e != cudaSuccess) { c->err = cuda_msg("copy liquid mask", e); return bail(FDIRW_ERR_CUDA); }
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&k.count), (uint64_t)k.nc * 4, "block counts")) != FDIRW_OK) return bail(rc);
+    const uint64_t W3 = (uint64_t)(2 * k.Rc + 1) * (2 * k.Rc + 1) * (2 * k.Rc + 1);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&k.Qc), W3 * (uint64_t)k.nc * 8, "coarse matrix")) != FDIRW_OK) return bail(rc);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&k.C), (uint64_t)k.nc * 8, "coarse field")) != FDIRW_OK) return bail(rc);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&k.Cn), (uint64_t)k.nc * 8, "coarse field")) != FDIRW_OK) return bail(rc);
+    fdirw::mask_faces_kernel<<<fdirw::grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(
+        c->g, k.liquid, reinterpret_cast<float*>(c->coef[0]), reinterpret_cast<float*>(c->coef[1]),
+        reinterpret_cast<float*>(c->coef[2]));
+    fdirw::count_kernel<<<fdirw::grid_blocks(k.nc, 128), 128, 0, c->stream>>>(c->g, k.liquid, k.B, k.ncx, k.ncy, k.nc, k.count);
+    if ((e = cudaGetLastError()) != cudaSuccess) { c->err = cuda_msg("coarse setup", e); return bail(FDIRW_ERR_CUDA); }
+    // Blocks with liquid, ascending (host pass over the counts).
+    std::vector<int32_t> cnt((size_t)k.nc);
+    if ((e = cudaMemcpyAsync(cnt.data(), k.count, (size_t)k.nc * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        c->err = cuda_msg("coarse setup", e);
+        return bail(FDIRW_ERR_CUDA);
+    }
+    std::vector<int64_t> list;
+    for (int64_t I = 0; I < k.nc; I++) if (cnt[(size_t)I] > 0) list.push_back(I);
+    k.nodes = (int64_t)list.size();
+    if (k.nodes > 0) {
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.list), (uint64_t)k.nodes * 8, "node list")) != FDIRW_OK) return bail(rc);
+        if ((e = cudaMemcpy(k.list, list.data(), (size_t)k.nodes * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            c->err = cuda_msg("copy node list", e);
+            return bail(FDIRW_ERR_CUDA);
+        }
+    }
+    c->kernels_ready = false;
+    // Sum over the nodes of their clipped march windows (cells), for the roofline's work count.
+    double wc = 0.0;
+    for (int64_t I : list) {
+        const int bx = (int)(I % k.ncx), by = (int)((I / k.ncx) % k.ncy), bz = (int)(I / ((int64_t)k.ncx * k.ncy));
+        auto ext = [&](int b, int n) {
+            return (double)(std::min(b * block + block - 1 + window_R, n - 1) - std::max(b * block - window_R, 0) + 1);
+        };
+        wc += ext(bx, grid->nx) * ext(by, grid->ny) * ext(bz, grid->nz);
+    }
+    c->window_cells = wc;
+    *out = c;
+    return FDIRW_OK;
+}
+
+int fdirw_read_coarse(fdirw_ctx* c, const int64_t* blocks, int64_t n, double* out) {
+    if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
+    if (!c->coarse) return fail(c, FDIRW_ERR_ARG, "not a coarse-mesh context");
+    if (n < 0 || (n > 0 && (!blocks || !out))) return fail(c, FDIRW_ERR_ARG, "bad blocks/out");
+    fdirw::Coarse& k = *c->coarse;
+    for (int64_t q = 0; q < n; q++)
+        if (blocks[q] < 0 || blocks[q] >= k.nc) return fail(c, FDIRW_ERR_ARG, "block index out of range");
+    if (!k.built) return fail(c, FDIRW_ERR_STATE, "coarse matrix not built (call fdirw_kernels)");
+    if (n == 0) return FDIRW_OK;
+    DeviceGuard dg(c->device);
+    const int64_t W3 = (int64_t)(2 * k.Rc + 1) * (2 * k.Rc + 1) * (2 * k.Rc + 1);
+    int64_t* db = nullptr;
+    double* dout = nullptr;
+    int rc = dalloc(c, reinterpret_cast<void**>(&db), (uint64_t)n * 8, "block list");
+    if (rc != FDIRW_OK) return rc;
+    rc = dalloc(c, reinterpret_cast<void**>(&dout), (uint64_t)(n * W3) * 8, "coarse readback");
+    if (rc != FDIRW_OK) { cudaFree(db); c->allocated -= (uint64_t)n * 8; return rc; }
+    cudaError_t e = cudaMemcpyAsync(db, blocks, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        fdirw::read_coarse_kernel<<<fdirw::grid_blocks(n * W3, 256), 256, 0, c->stream>>>(k.Qc, k.ncx, k.ncy, k.ncz, k.Rc,
+                                                                                         db, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, (size_t)(n * W3) * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(db);
+    cudaFree(dout);
+    c->allocated -= (uint64_t)n * 8 + (uint64_t)(n * W3) * 8;
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(c, FDIRW_ERR_CUDA, cuda_msg("read coarse matrix", e)); }
+    return FDIRW_OK;
+}
+
+}  // extern "C"

@@ -11,6 +11,7 @@
 
 namespace fdirw {
 struct Batch;   // batch of structures with per-source window radii (batch.cu)
+struct Coarse;  // coarse-mesh FDiRW (coarse.cu)
 }
 
 struct fdirw_ctx {
@@ -42,6 +43,7 @@ struct fdirw_ctx {
     double window_cells = 0.0;
     double mass_in = NAN, mass_out = NAN;
     fdirw::Batch* batch = nullptr;                  // non-null for fdirw_create_batch contexts
+    fdirw::Coarse* coarse = nullptr;                // non-null for fdirw_create_coarse contexts
     std::string err;
 };
 
@@ -86,6 +88,12 @@ int batch_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
 int batch_read_kernels(fdirw_ctx* c, const int64_t* sources, int64_t n, double* out);
 int batch_info(fdirw_ctx* c, fdirw_info* out);
 void batch_release(fdirw_ctx* c);
+
+// Coarse-mesh contexts (coarse.cu).
+int coarse_kernels(fdirw_ctx* c);
+int coarse_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps, double* mass_out);
+int coarse_info(fdirw_ctx* c, fdirw_info* out);
+void coarse_release(fdirw_ctx* c);
 
 // Allocates (once) and zeroes the kernel cache of a context; honours mem_limit.
 int ensure_cache(fdirw_ctx* c);

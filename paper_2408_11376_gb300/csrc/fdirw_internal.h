@@ -59,7 +59,17 @@ struct MarchArgs {
     // position in [src_begin, src_end) (src_major = 1).
     int64_t q_stride;
     int src_major;
+    // Coarse-mesh march (coarse_B > 0, mapping 5 only): list holds coarse block indices; see coarse.cu.
+    int coarse_B, coarse_Rc;
+    int ncx, ncy, ncz;
+    int64_t coarse_n;            // ncx * ncy * ncz
+    const uint8_t* liquid;       // N: 1 = liquid cell
+    const int32_t* ccount;       // coarse_n: liquid cells per block
+    double* Qc;                  // (2 Rc + 1)^3 planes of coarse_n values, destination-indexed
 };
+// Coarse-mesh march of the blocks a.list[src_begin..src_end): window radius R = window_R + (B - 1) / 2
+// (1..10), one source per CTA.
+cudaError_t launch_march_coarse(const MarchArgs& a, int R, int num_sms, cudaStream_t st);
 // parts_req: FP32 march thread mapping (1..3 threads per window column, 4 = 2x2 column blocks with TMEM
 // faces, 5 = one column per thread with TMEM lateral faces), or 0 to autotune (timed once per device, R
 // and storage, then cached); parts_used receives the mapping launched.

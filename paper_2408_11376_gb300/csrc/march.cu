@@ -715,9 +715,64 @@ struct MapTmc {
     static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
     static_assert(16 * NG <= 128, "lateral faces of a column must fit a 128-column TMEM slot");
     static_assert(THREADS <= 512, "at most 4 threads per TMEM lane");
+    // Coarse mode adds the per-block sums (at most W1^3 blocks in a window, plus the total).
+    static constexpr size_t SMEM_COARSE_USED = SMEM_USED + (size_t)(W1 * W1 * W1 + 1) * 8;
+    static constexpr size_t SMEM_COARSE = SMEM_COARSE_USED > SMEM ? SMEM_COARSE_USED : SMEM;
 };
 
+// Coarse epilogue (Eq. 11 applied to the marched unit of block J): S[d] = FP64 sum of the marched field
+// over the liquid cells of block J + d inside the window (z, y, x order; sbuf holds 0 elsewhere), m =
+// sum of S in a fixed order, and column J of P: Qc[d][J + d] = N_J S[d] / (m N_{J+d}) (0 where block
+// J + d has no liquid).  Every thread of the CTA takes part; S follows red in shared memory.
 template <int R>
+__device__ void coarse_epilogue(const MarchArgs& a, const float* sbuf, double* S, int64_t first) {
+    constexpr int W1 = 2 * R + 1;
+    const bool valid = first < a.src_end;                 // uniform over the CTA
+    const int64_t J = valid ? (a.list ? a.list[first] : first) : 0;
+    const int B = a.coarse_B, Rc = a.coarse_Rc, Wc = 2 * Rc + 1, Wc3 = Wc * Wc * Wc, bh = (B - 1) / 2;
+    const int bx = (int)(J % a.ncx), by = (int)((J / a.ncx) % a.ncy), bz = (int)(J / ((int64_t)a.ncx * a.ncy));
+    const int sx = bx * B + bh, sy = by * B + bh, sz = bz * B + bh;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    for (int d = threadIdx.x; d < Wc3; d += blockDim.x) {
+        double acc = 0.0;
+        if (valid) {
+            const int cx = bx + d % Wc - Rc, cy = by + (d / Wc) % Wc - Rc, cz = bz + d / (Wc * Wc) - Rc;
+            const int x0 = max(max(cx * B, sx - R), 0), x1 = min(min(cx * B + B - 1, sx + R), nx - 1);
+            const int y0 = max(max(cy * B, sy - R), 0), y1 = min(min(cy * B + B - 1, sy + R), ny - 1);
+            const int z0 = max(max(cz * B, sz - R), 0), z1 = min(min(cz * B + B - 1, sz + R), nz - 1);
+            for (int z = z0; z <= z1; z++)
+                for (int y = y0; y <= y1; y++)
+                    for (int x = x0; x <= x1; x++)
+                        acc += (double)sbuf[((x - (sx - R)) + W1 * (y - (sy - R))) * W1 + (z - (sz - R))];
+        }
+        S[d] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double m = 0.0;
+        for (int d = threadIdx.x; d < Wc3; d += 32) m += S[d];
+        for (int off = 16; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
+        if (threadIdx.x == 0) S[Wc3] = m;
+    }
+    __syncthreads();
+    const double m = S[Wc3];
+    if (valid) {
+        const double NJ = (double)a.ccount[J];
+        for (int d = threadIdx.x; d < Wc3; d += blockDim.x) {
+            const int cx = bx + d % Wc - Rc, cy = by + (d / Wc) % Wc - Rc, cz = bz + d / (Wc * Wc) - Rc;
+            if (cx < 0 || cx >= a.ncx || cy < 0 || cy >= a.ncy || cz < 0 || cz >= a.ncz) continue;
+            const int64_t I = cx + (int64_t)a.ncx * (cy + (int64_t)a.ncy * cz);
+            const int NI = a.ccount[I];
+            a.Qc[(int64_t)d * a.coarse_n + I] = (NI > 0 && m > 0.0) ? (NJ * S[d]) / (m * (double)NI) : 0.0;
+        }
+    }
+}
+
+// COARSE: the source is coarse block a.list[pos] (Eqs. 10-15): its window is centred on the block's
+// centre cell (radius R = window_R + (B - 1) / 2), the march starts from 1 on the block's liquid cells,
+// and the epilogue maps the marched field onto the blocks of the window (column J of the coarse matrix,
+// written destination-indexed) instead of storing a kernel.
+template <int R, bool COARSE>
 __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchArgs a) {
     using M = MapTmc<R>;
     constexpr int W1 = M::W1, COLS = M::COLS, NG = M::NG, BUF = M::BUF;
@@ -761,11 +816,22 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
         const float* ay = a.ay + L.base;
         const float* az = a.az + L.base;
         int sx = 0, sy = 0, sz = 0;
+        int bx = 0, by = 0, bz = 0;
+        const int bh = COARSE ? (a.coarse_B - 1) / 2 : 0;
         if (src_ok) {
-            sx = (int)(s % nx);
-            const int64_t r = s / nx;
-            sy = (int)(r % ny);
-            sz = (int)(r / ny);
+            if constexpr (COARSE) {
+                bx = (int)(s % a.ncx);
+                by = (int)((s / a.ncx) % a.ncy);
+                bz = (int)(s / ((int64_t)a.ncx * a.ncy));
+                sx = bx * a.coarse_B + bh;       // centre of the block (may lie past a clipped domain edge)
+                sy = by * a.coarse_B + bh;
+                sz = bz * a.coarse_B + bh;
+            } else {
+                sx = (int)(s % nx);
+                const int64_t r = s / nx;
+                sy = (int)(r % ny);
+                sz = (int)(r / ny);
+            }
         }
         const int x = sx - R + ci, y = sy - R + cj;
         const bool col_ok = src_ok && x >= 0 && x < nx && y >= 0 && y < ny;
@@ -782,8 +848,10 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                 if (k < W1) {
                     const int z = sz - R + k;
                     const bool ok = col_ok && z >= 0 && z < nz;
+                    float u0 = (!COARSE && src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
                     if (ok) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                        if (COARSE && a.liquid[i] && abs(ci - R) <= bh && abs(cj - R) <= bh && abs(k - R) <= bh) u0 = 1.f;
                         if (ci > 0 && x > 0) vxm = __ldg(ax + i - 1);
                         if (ci < 2 * R && x + 1 < nx) vxp = __ldg(ax + i);
                         if (cj > 0 && y > 0) vym = __ldg(ay + i - nx);
@@ -792,7 +860,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                     }
                     cz[k < W1 ? k : 0] = vz;
                     am[k < W1 ? k : 0] = -(((vxm + vxp) + (vym + vyp)) + (zprev + vz));
-                    u[k < W1 ? k : 0] = (src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
+                    u[k < W1 ? k : 0] = u0;
                     zprev = vz;
                 }
                 w[4 * q + 0] = __float_as_uint(vxm);
@@ -843,27 +911,40 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
         }
 
         float* sbuf = xbuf + (a.n_sub & 1) * BUF;
-        if (active) {
+        if constexpr (COARSE) {
+            if (active) {
 #pragma unroll
-            for (int k = 0; k < W1; k++) {
-                const int z = sz - R + k;
-                float stv = 0.f;
-                if (col_ok && z >= 0 && z < nz) {
-                    const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                    stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.qbase + i, pos), u[k]);
+                for (int k = 0; k < W1; k++) {
+                    const int z = sz - R + k;
+                    const bool ok = col_ok && z >= 0 && z < nz && a.liquid[(int64_t)x + (int64_t)nx * y + nxy * z];
+                    sbuf[base + k] = ok ? u[k] : 0.f;
                 }
-                sbuf[base + k] = stv;
             }
-        }
-        __syncthreads();
-        for (int c = t; c < COLS; c += blockDim.x) {
-            double colsum = 0.0;
+            __syncthreads();
+            coarse_epilogue<R>(a, sbuf, red + COLS, first);
+        } else {
+            if (active) {
 #pragma unroll
-            for (int k = 0; k < W1; k++) colsum += (double)sbuf[c * W1 + k];
-            red[c] = colsum;
+                for (int k = 0; k < W1; k++) {
+                    const int z = sz - R + k;
+                    float stv = 0.f;
+                    if (col_ok && z >= 0 && z < nz) {
+                        const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
+                        stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.qbase + i, pos), u[k]);
+                    }
+                    sbuf[base + k] = stv;
+                }
+            }
+            __syncthreads();
+            for (int c = t; c < COLS; c += blockDim.x) {
+                double colsum = 0.0;
+#pragma unroll
+                for (int k = 0; k < W1; k++) colsum += (double)sbuf[c * W1 + k];
+                red[c] = colsum;
+            }
+            __syncthreads();
+            finish_sigma<COLS, 1>(red, first, a.src_end, a.list, a.sigma);
         }
-        __syncthreads();
-        finish_sigma<COLS, 1>(red, first, a.src_end, a.list, a.sigma);
         __syncthreads();
     }
 
@@ -873,19 +954,19 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr) : "memory");
 }
 
-template <int R>
+template <int R, bool COARSE = false>
 cudaError_t launch_tmc(const MarchArgs& a, int num_sms, cudaStream_t st) {
     using M = MapTmc<R>;
     const int64_t nsrc = a.src_end - a.src_begin;
     if (nsrc <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(march_tmc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(march_tmc_kernel<R, COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(COARSE ? M::SMEM_COARSE : M::SMEM));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmc_kernel<R>, M::THREADS, M::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmc_kernel<R, COARSE>, M::THREADS, (COARSE ? M::SMEM_COARSE : M::SMEM));
     if (e != cudaSuccess) return e;
     if (per_sm != 1) return cudaErrorInvalidConfiguration;   // TMEM allocation assumes one CTA per SM
     const int64_t grid = nsrc < (int64_t)num_sms ? nsrc : (int64_t)num_sms;
-    march_tmc_kernel<R><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
+    march_tmc_kernel<R, COARSE><<<(unsigned)grid, M::THREADS, (COARSE ? M::SMEM_COARSE : M::SMEM), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -925,8 +1006,8 @@ __device__ __forceinline__ uint64_t u2pack(uint32_t lo, uint32_t hi) {
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
     return r;
 }
-__device__ __forceinline__ float f2lo(uint64_t v) { float a, b; asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); return a; }
-__device__ __forceinline__ float f2hi(uint64_t v) { float a, b; asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); return b; }
+__device__ __forceinline__ float f2lo(uint64_t v) { return __uint_as_float((uint32_t)(v & 0xffffffffull)); }
+__device__ __forceinline__ float f2hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
     uint64_t d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -1280,6 +1361,22 @@ cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStrea
     g_tune[key] = P;
     *parts = P;
     return cudaSuccess;
+}
+
+cudaError_t launch_march_coarse(const MarchArgs& a, int R, int num_sms, cudaStream_t st) {
+    switch (R) {
+        case 1: return launch_tmc<1, true>(a, num_sms, st);
+        case 2: return launch_tmc<2, true>(a, num_sms, st);
+        case 3: return launch_tmc<3, true>(a, num_sms, st);
+        case 4: return launch_tmc<4, true>(a, num_sms, st);
+        case 5: return launch_tmc<5, true>(a, num_sms, st);
+        case 6: return launch_tmc<6, true>(a, num_sms, st);
+        case 7: return launch_tmc<7, true>(a, num_sms, st);
+        case 8: return launch_tmc<8, true>(a, num_sms, st);
+        case 9: return launch_tmc<9, true>(a, num_sms, st);
+        case 10: return launch_tmc<10, true>(a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {

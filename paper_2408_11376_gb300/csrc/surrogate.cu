@@ -622,7 +622,7 @@ FDIRW_API void fdirw_net_destroy(fdirw_net* net) {
 FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                                 double* kernels_out, double* mass_out, int32_t* accept_out) {
     if (!ctx || !net || (n > 0 && !sources)) return nfail(net, FDIRW_ERR_ARG, "NULL ctx, net or sources");
-    if (ctx->batch) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
     if (n == 0) return FDIRW_OK;
     int rc = upload_sources(ctx, net, sources, n);
     if (rc != FDIRW_OK) return rc;
@@ -638,7 +638,7 @@ FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* s
 FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                                   const double* targets, float* grads_out, double* loss_out) {
     if (!ctx || !net || n <= 0 || !sources || !targets) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
-    if (ctx->batch) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
     int rc = gradients(ctx, net, sources, n, targets, loss_out);
     if (rc != FDIRW_OK) return rc;
     if (grads_out) NET_CUDA(net, cudaMemcpy(grads_out, net->grads, NPARAM * 4, cudaMemcpyDeviceToHost));
@@ -648,7 +648,7 @@ FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t*
 FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                                    const double* targets, float lr, double* loss_out) {
     if (!ctx || !net || n <= 0 || !sources || !targets || !(lr > 0.f)) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
-    if (ctx->batch) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
     int rc = gradients(ctx, net, sources, n, targets, loss_out);
     if (rc != FDIRW_OK) return rc;
     net->step++;
@@ -663,7 +663,7 @@ FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t
 
 FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* c, fdirw_net* net, int64_t* accepted_out) {
     if (!c || !net) return nfail(net, FDIRW_ERR_ARG, "NULL ctx or net");
-    if (c->batch) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (c->batch || c->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
     if (c->R != SH) return nfail(net, FDIRW_ERR_ARG, "the surrogate predicts 17^3 kernels: window_R must be 8");
     if (c->store == Store::F64) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves the FP32-march precisions only");
     {

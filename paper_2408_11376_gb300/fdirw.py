@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": FDIRW_FP64, "fp32": FDIRW_FP32, "fp16": FDIRW_FP32_STORE_F
 EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "fdirw_mass", "fdirw_read_kernels",
             "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc", "fdirw_net_create",
             "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
-            "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius")
+            "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius", "fdirw_create_coarse",
+            "fdirw_read_coarse")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -63,7 +64,8 @@ class fdirw_info(ctypes.Structure):
                 ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double),
                 ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("n_structures", ctypes.c_int32), ("n_chunks", ctypes.c_int32), ("window_R_min", ctypes.c_int32),
-                ("graph_launches", ctypes.c_int32), ("dest_indexed_radii", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("graph_launches", ctypes.c_int32), ("dest_indexed_radii", ctypes.c_int32),
+                ("coarse_block", ctypes.c_int32), ("coarse_nodes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,6 +111,9 @@ def load(path: str | None = None):
         lib.fdirw_create_batch.argtypes = [i32, ctypes.POINTER(fdirw_grid), ctypes.POINTER(vp), ctypes.c_double, i32,
                                            i32, i32, ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
         lib.fdirw_read_radius.argtypes = [vp, vp]
+        lib.fdirw_create_coarse.argtypes = [ctypes.POINTER(fdirw_grid), vp, vp, i32, ctypes.c_double, i32, i32,
+                                            ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
+        lib.fdirw_read_coarse.argtypes = [vp, vp, i64, vp]
         for name in EXPORTED:
             if name not in ("fdirw_destroy", "fdirw_last_error", "fdirw_net_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -199,6 +204,40 @@ def fdirw_create_batch(shapes, Ds, dt_macro: float, R_min: int, R_max: int, n_su
     _check(lib.fdirw_create_batch(int(n), grids, ptrs, float(dt_macro), int(R_min), int(R_max), int(n_sub),
                                   ctypes.byref(o), ctypes.byref(ctx)))
     return ctx.value
+
+
+def fdirw_create_coarse(shape, D, liquid, block: int, dt_macro: float, window_R: int, n_sub: int, prec="fp32",
+                        h: float = 1.0, device: int = -1, stream=None, mem_limit: int = 0) -> int:
+    """Coarse-mesh context (Eqs. 10-15): liquid = N bytes (nonzero = liquid) or None for all liquid."""
+    lib = load()
+    nx, ny, nz = (int(v) for v in shape)
+    _check_f64(D, nx * ny * nz)
+    lq_ptr = None
+    if liquid is not None:
+        if isinstance(liquid, np.ndarray):
+            liquid = np.ascontiguousarray(liquid, dtype=np.uint8).reshape(-1)
+        n = liquid.size if isinstance(liquid, np.ndarray) else liquid.numel()
+        if n != nx * ny * nz:
+            raise ValueError("liquid mask has the wrong size")
+        lq_ptr = ctypes.c_void_p(_ptr(liquid))
+    g = fdirw_grid(nx, ny, nz, float(h))
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), 0, 0)
+    ctx = ctypes.c_void_p(0)
+    _check(lib.fdirw_create_coarse(ctypes.byref(g), ctypes.c_void_p(_ptr(D)), lq_ptr, int(block), float(dt_macro),
+                                   int(window_R), int(n_sub), ctypes.byref(o), ctypes.byref(ctx)))
+    return ctx.value
+
+
+def fdirw_read_coarse(ctx: int, blocks, Rc: int) -> np.ndarray:
+    """Coarse-matrix columns of the listed blocks, [n, Wc, Wc, Wc] indexed [dz+Rc, dy+Rc, dx+Rc]."""
+    b = np.ascontiguousarray(blocks, dtype=np.int64).reshape(-1)
+    Wc = 2 * int(Rc) + 1
+    out = np.empty((b.size, Wc, Wc, Wc), dtype=np.float64)
+    _check(load().fdirw_read_coarse(ctypes.c_void_p(ctx), ctypes.c_void_p(b.ctypes.data), b.size,
+                                    ctypes.c_void_p(out.ctypes.data)), ctypes.c_void_p(ctx))
+    return out
 
 
 def fdirw_read_radius(ctx: int, n_cells: int) -> np.ndarray:
@@ -326,6 +365,23 @@ class FDiRWBatch(FDiRW):
 
     def radius(self) -> np.ndarray:
         return fdirw_read_radius(self.ctx, self.n)
+
+
+class FDiRWCoarse(FDiRW):
+    """Owns one coarse-mesh context: ``FDiRWCoarse(shape, D, liquid, block, dt_macro, R, n_sub)``."""
+
+    def __init__(self, shape, D, liquid, block: int, dt_macro: float, window_R: int, n_sub: int, prec="fp32",
+                 h: float = 1.0, device: int = -1, stream=None, mem_limit: int = 0):
+        self.shape = tuple(int(v) for v in shape)
+        self.n = self.shape[0] * self.shape[1] * self.shape[2]
+        self.R = int(window_R)
+        self.B = int(block)
+        self.ctx = fdirw_create_coarse(self.shape, D, liquid, block, dt_macro, window_R, n_sub, prec, h, device,
+                                       stream, mem_limit)
+        self.Rc = (self.R + self.B - 1) // self.B        # block >= 1 once the library accepted it
+
+    def read_coarse(self, blocks) -> np.ndarray:
+        return fdirw_read_coarse(self.ctx, blocks, self.Rc)
 
 
 # --------------------------------------------------------------------------- learned surrogate

@@ -1,0 +1,118 @@
+"""GPU parity of the coarse-mesh FDiRW (fdirw_create_coarse, Eqs. 10-15) against the FP64 oracle: every
+column of the coarse matrix, macro steps element by element (non-liquid cells bit for bit unchanged),
+unit blocks against the fine windowed FDiRW, the largest window, and argument errors."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_11376_gb300 import FDiRWCoarse, FdirwError, fdirw, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+P_TOL = 1e-5          # FP32 march, FP64 mapping: per-column relative L2
+FIELD_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_2408_11376_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(shape, seed):
+    p = synth.sphere_packing(shape, 0.4, seed, r_range=(1.5, 3.5))
+    D = synth.diffusivity_per_sphere(p)
+    return D, (~p.solid).astype(np.uint8)
+
+
+@pytest.mark.parametrize("shape,B,R,n_sub", [((23, 21, 19), 5, 3, 30), ((17, 16, 15), 3, 4, 25)])
+def test_coarse_matrix_matches_oracle(shape, B, R, n_sub):
+    """Clipped blocks on every face (sides not multiples of B), a liquid mask from a sphere packing."""
+    D, liquid = _case(shape, 70 + B)
+    lam = oracle.stable_dt_sub(shape, D)
+    ref = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub)
+    with FDiRWCoarse(shape, torch.from_numpy(D).to(DEV), torch.from_numpy(liquid).to(DEV), B, n_sub * lam, R,
+                     n_sub) as f:
+        f.kernels()
+        info = f.info()
+        got = f.read_coarse(np.arange(ref.shape[0]))
+    cnt = oracle.coarse_counts(shape, liquid, B)
+    assert info["coarse_block"] == B and info["coarse_nodes"] == int(np.count_nonzero(cnt))
+    for J in range(ref.shape[0]):
+        if cnt[J] == 0:
+            assert not got[J].any()
+            continue
+        assert _rel(got[J], ref[J]) <= P_TOL, (J, _rel(got[J], ref[J]))
+        assert (got[J] >= 0).all()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_coarse_steps_match_oracle(prec):
+    shape, B, R, n_sub = (24, 20, 18), 5, 4, 30
+    D, liquid = _case(shape, 80)
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(D.size, 81, 0.0, 2.0)
+    P = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub)
+    ref = c0
+    for _ in range(3):
+        ref = oracle.coarse_step(shape, liquid, B, R, P, ref)
+    with FDiRWCoarse(shape, D, liquid, B, n_sub * lam, R, n_sub, prec) as f:
+        cin = torch.from_numpy(c0).to(DEV)
+        cout = torch.empty_like(cin)
+        m = f.step(cin, cout, 3, want_mass=True)
+        got = cout.cpu().numpy()
+        host = np.empty_like(c0)
+        f.step(c0, host, 3)                       # host pointers, same result
+    assert np.array_equal(got, host)
+    assert _rel(got, ref) <= FIELD_TOL, _rel(got, ref)
+    solid = liquid == 0
+    assert np.array_equal(got[solid], c0[solid])
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+
+
+def test_unit_blocks_are_the_fine_windowed_fdirw():
+    shape = (14, 13, 12)
+    D = synth.random_diffusivity(shape, 82, 4.0)
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(D.size, 83)
+    with FDiRWCoarse(shape, D, None, 1, 20 * lam, 3, 20) as f:
+        out = np.empty_like(c0)
+        f.step(c0, out, 2)
+    ref = oracle.superpose(shape, D, lam, 3, 20, oracle.superpose(shape, D, lam, 3, 20, c0))
+    assert _rel(out, ref) <= FIELD_TOL
+
+
+def test_largest_window_matches_oracle():
+    """B = 5, R = 8: window radius 10 (21^3), the configuration of the 192^3 coarse leg."""
+    shape, B, R, n_sub = (26, 25, 24), 5, 8, 40
+    D, liquid = _case(shape, 84)
+    lam = oracle.stable_dt_sub(shape, D)
+    ref = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub)
+    blocks = np.flatnonzero(oracle.coarse_counts(shape, liquid, B))[::4]
+    with FDiRWCoarse(shape, D, liquid, B, n_sub * lam, R, n_sub) as f:
+        f.kernels()
+        got = f.read_coarse(blocks)
+    for q, J in enumerate(blocks):
+        assert _rel(got[q], ref[J]) <= P_TOL
+
+
+def test_coarse_argument_errors():
+    shape = (10, 10, 10)
+    D = np.ones(1000)
+    for B, R, prec in ((4, 2, "fp32"), (0, 2, "fp32"), (5, 9, "fp32"), (5, 2, "fp64"), (1, 0, "fp32")):
+        with pytest.raises(FdirwError):
+            FDiRWCoarse(shape, D, None, B, 0.1, R, 2, prec)
+    with FDiRWCoarse(shape, D, None, 5, 0.1, 2, 2) as f:
+        with pytest.raises(FdirwError) as e:
+            f.read_coarse([0])
+        assert e.value.code == fdirw.FDIRW_ERR_STATE
+        f.kernels()
+        with pytest.raises(FdirwError):
+            f.read_kernels([0])
+        with pytest.raises(FdirwError):
+            f.read_coarse([8])                    # 2 x 2 x 2 blocks
