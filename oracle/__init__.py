@@ -88,6 +88,17 @@ def _load():
             lib.fo_coarse_kernels.restype = ctypes.c_int
             lib.fo_coarse_step.argtypes = [ctypes.c_int] * 3 + [_U8, ctypes.c_int, ctypes.c_int, _D, _D, _D]
             lib.fo_coarse_step.restype = ctypes.c_int
+            lib.fo_boundary_conductance.argtypes = [ctypes.c_int] * 3 + [_D, _U8, _D]
+            lib.fo_boundary_conductance.restype = None
+            lib.fo_coarse_kernels_open.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [_U8, ctypes.c_int, ctypes.c_double,
+                                                                                  ctypes.c_int, ctypes.c_int, _D]
+            lib.fo_coarse_kernels_open.restype = ctypes.c_int
+            lib.fo_coarse_pbc.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [_U8, ctypes.c_int, ctypes.c_double,
+                                                                         ctypes.c_int, _D]
+            lib.fo_coarse_pbc.restype = ctypes.c_int
+            lib.fo_coarse_step_far.argtypes = [ctypes.c_int] * 3 + [_U8, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                                   ctypes.c_double, ctypes.c_double, _D, _D, _D]
+            lib.fo_coarse_step_far.restype = ctypes.c_int
             lib.fo_mass.argtypes = [_D, ctypes.c_int64]
             lib.fo_mass.restype = ctypes.c_double
             _lib = lib
@@ -255,6 +266,55 @@ def coarse_step(shape, liquid, B: int, R: int, P_band, c) -> np.ndarray:
     if _load().fo_coarse_step(nx, ny, nz, _pu8(lq), int(B), int(R), _p(P), _p(c), _p(out)) != 0:
         raise ValueError("fo_coarse_step failed")
     return out
+
+
+def boundary_conductance(shape, D, liquid) -> np.ndarray:
+    """Open-face conductance of every cell: D_i times its faces on the grid's outer surface (liquid only)."""
+    nx, ny, nz = shape
+    Dv = _f64(D).reshape(-1)
+    lq = _u8(liquid, Dv.size)
+    out = np.empty_like(Dv)
+    _load().fo_boundary_conductance(nx, ny, nz, _p(Dv), _pu8(lq), _p(out))
+    return out
+
+
+def coarse_kernels_open(shape, D, liquid, B: int, lam: float, R: int, n_sub: int) -> np.ndarray:
+    """Coarse matrix with the grid's outer faces open to the far field (no renormalisation)."""
+    nx, ny, nz = shape
+    g = Conductance(shape, D, liquid)
+    gb = boundary_conductance(shape, D, liquid)
+    Wc = 2 * coarse_radius(R, B) + 1
+    nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
+    out = np.empty((nc, Wc, Wc, Wc), dtype=np.float64)
+    if _load().fo_coarse_kernels_open(*g.args, _p(gb), _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub),
+                                      _p(out)) != 0:
+        raise ValueError("fo_coarse_kernels_open rejected its arguments")
+    return out
+
+
+def coarse_pbc(shape, D, liquid, B: int, lam: float, n_sub: int) -> np.ndarray:
+    """P_BC of Eq. 10 on the blocks: the liquid marched from 0 with every far-field ghost at 1, mapped."""
+    nx, ny, nz = shape
+    g = Conductance(shape, D, liquid)
+    gb = boundary_conductance(shape, D, liquid)
+    nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
+    out = np.empty(nc, dtype=np.float64)
+    if _load().fo_coarse_pbc(*g.args, _p(gb), _pu8(g.liquid), int(B), float(lam), int(n_sub), _p(out)) != 0:
+        raise ValueError("fo_coarse_pbc failed")
+    return out
+
+
+def coarse_step_far(shape, liquid, B: int, R: int, P_band, PBC, V_far: float, c_far: float, c):
+    """One coarse step with the far-field term and the Eq. 7 update: returns (c', c_far')."""
+    nx, ny, nz = shape
+    lq = _u8(liquid, nx * ny * nz)
+    c = _f64(c).reshape(-1)
+    out = np.empty_like(c)
+    cf = ctypes.c_double(0.0)
+    if _load().fo_coarse_step_far(nx, ny, nz, _pu8(lq), int(B), int(R), _p(_f64(P_band)), _p(_f64(PBC)),
+                                  float(V_far), float(c_far), _p(c), _p(out), ctypes.byref(cf)) != 0:
+        raise ValueError("fo_coarse_step_far failed")
+    return out, cf.value
 
 
 def full_march(shape, D, lam: float, n_sub: int, c, cond: Conductance | None = None) -> np.ndarray:

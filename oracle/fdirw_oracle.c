@@ -378,6 +378,158 @@ int fo_coarse_step(int nx, int ny, int nz, const uint8_t* liquid, int B, int R, 
     return 0;
 }
 
+/* ---- Far-field boundary (Eq. 7 and the p_BC c_far term of Eqs. 8, 10, 14), coarse path.  Reading: every
+ * face of a liquid cell on the outer surface of the grid opens onto the far-field liquid, represented by
+ * a ghost cell one cell width outside that holds c_far and has the cell's own diffusivity, so each open
+ * face has conductance D_i; gb[i] = D_i times the number of open faces of cell i (0 for non-liquid
+ * cells). */
+void fo_boundary_conductance(int nx, int ny, int nz, const double* D, const uint8_t* liquid, double* gb)
+{
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                int faces = (x == 0) + (x == nx - 1) + (y == 0) + (y == ny - 1) + (z == 0) + (z == nz - 1);
+                gb[i] = liquid[i] ? D[i] * (double)faces : 0.0;
+            }
+}
+
+/* One flux-form substep as box_substep plus the open faces: u_i += lam gb_i (ghost - u_i). */
+static void box_substep_open(int nx, int ny, const double* gx, const double* gy, const double* gz,
+                             const double* gb, double ghost, double lam, int x0, int y0, int z0, int bx, int by,
+                             int bz, const double* u, double* un)
+{
+    box_substep(nx, ny, gx, gy, gz, lam, x0, y0, z0, bx, by, bz, u, un);
+    for (int l = 0; l < bz; l++)
+        for (int j = 0; j < by; j++)
+            for (int i = 0; i < bx; i++) {
+                int64_t li = i + (int64_t)bx * (j + (int64_t)by * l);
+                int64_t gi = IDX(x0 + i, y0 + j, z0 + l, nx, ny);
+                un[li] += lam * (gb[gi] * (ghost - u[li]));
+            }
+}
+
+/* Coarse matrix with open faces: as fo_coarse_kernels, the march also losing mass through the open
+ * faces (ghost 0), and no renormalisation: P[I][J] = S_I / N_I (the column carries the mass that stays). */
+int fo_coarse_kernels_open(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                           const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
+                           double* P_band)
+{
+    if (B < 1 || R < 0 || n_sub < 0) return -1;
+    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
+    int64_t NC = (int64_t)ncx * ncy * ncz;
+    int Rc = (R + B - 1) / B, Wc = 2 * Rc + 1;
+    int64_t Wc3 = (int64_t)Wc * Wc * Wc;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
+    if (!cnt) return -1;
+    fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
+    memset(P_band, 0, sizeof(double) * (size_t)(NC * Wc3));
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t J = 0; J < NC; J++) {
+        if (cnt[J] == 0 || err) continue;
+        int bx = (int)(J % ncx), by = (int)((J / ncx) % ncy), bz = (int)(J / ((int64_t)ncx * ncy));
+        int x0 = bx * B - R < 0 ? 0 : bx * B - R, x1 = bx * B + B - 1 + R > nx - 1 ? nx - 1 : bx * B + B - 1 + R;
+        int y0 = by * B - R < 0 ? 0 : by * B - R, y1 = by * B + B - 1 + R > ny - 1 ? ny - 1 : by * B + B - 1 + R;
+        int z0 = bz * B - R < 0 ? 0 : bz * B - R, z1 = bz * B + B - 1 + R > nz - 1 ? nz - 1 : bz * B + B - 1 + R;
+        int wx = x1 - x0 + 1, wy = y1 - y0 + 1, wz = z1 - z0 + 1;
+        int64_t nb = (int64_t)wx * wy * wz;
+        double* u = (double*)calloc((size_t)nb, sizeof(double));
+        double* un = (double*)calloc((size_t)nb, sizeof(double));
+        double* S = (double*)calloc((size_t)Wc3, sizeof(double));
+        if (!u || !un || !S) { free(u); free(un); free(S); err = 1; continue; }
+        for (int l = 0; l < wz; l++)
+            for (int j = 0; j < wy; j++)
+                for (int i = 0; i < wx; i++) {
+                    int x = x0 + i, y = y0 + j, z = z0 + l;
+                    if (x / B == bx && y / B == by && z / B == bz && liquid[IDX(x, y, z, nx, ny)])
+                        u[i + (int64_t)wx * (j + (int64_t)wy * l)] = 1.0;
+                }
+        for (int k = 0; k < n_sub; k++) {
+            box_substep_open(nx, ny, gx, gy, gz, gb, 0.0, lam, x0, y0, z0, wx, wy, wz, u, un);
+            double* t = u; u = un; un = t;
+        }
+        for (int l = 0; l < wz; l++)
+            for (int j = 0; j < wy; j++)
+                for (int i = 0; i < wx; i++) {
+                    int x = x0 + i, y = y0 + j, z = z0 + l;
+                    if (!liquid[IDX(x, y, z, nx, ny)]) continue;
+                    int dx = x / B - bx, dy = y / B - by, dz = z / B - bz;
+                    S[(dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc))] +=
+                        u[i + (int64_t)wx * (j + (int64_t)wy * l)];
+                }
+        for (int dz = -Rc; dz <= Rc; dz++)
+            for (int dy = -Rc; dy <= Rc; dy++)
+                for (int dx = -Rc; dx <= Rc; dx++) {
+                    int cx = bx + dx, cy = by + dy, cz = bz + dz;
+                    if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy || cz < 0 || cz >= ncz) continue;
+                    int64_t I = cx + (int64_t)ncx * (cy + (int64_t)ncy * cz);
+                    if (cnt[I] == 0) continue;
+                    int64_t o = (dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc));
+                    P_band[J * Wc3 + o] = S[o] / (double)cnt[I];
+                }
+        free(u); free(un); free(S);
+    }
+    free(cnt);
+    return err ? -1 : 0;
+}
+
+/* P_BC of Eq. 10: the liquid phase marched n_sub substeps over the whole grid from 0 with every ghost at
+ * c_far = 1, then mapped to the blocks (Eq. 11): PBC[I] = mean over the liquid cells of block I. */
+int fo_coarse_pbc(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz, const double* gb,
+                  const uint8_t* liquid, int B, double lam, int n_sub, double* PBC)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
+    int64_t NC = (int64_t)ncx * ncy * ncz;
+    double* u = (double*)calloc((size_t)N, sizeof(double));
+    double* un = (double*)calloc((size_t)N, sizeof(double));
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
+    if (!u || !un || !cnt) { free(u); free(un); free(cnt); return -1; }
+    for (int k = 0; k < n_sub; k++) {
+        box_substep_open(nx, ny, gx, gy, gz, gb, 1.0, lam, 0, 0, 0, nx, ny, nz, u, un);
+        double* t = u; u = un; un = t;
+    }
+    fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
+    memset(PBC, 0, sizeof(double) * (size_t)NC);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                if (liquid[i]) PBC[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))] += u[i];
+            }
+    for (int64_t I = 0; I < NC; I++) if (cnt[I] > 0) PBC[I] /= (double)cnt[I];
+    free(u); free(un); free(cnt);
+    return 0;
+}
+
+/* One coarse step with the far field (Eqs. 13-15 with the P_BC c_far term of Eq. 14, then Eq. 7):
+ * C'_I = sum_J P[I][J] C_J + PBC[I] c_far, re-mapping, and c_far_out = (M0 - sum c_out) / V_far with
+ * M0 = sum c_in + V_far c_far (the total, near plus far field, that Eq. 7 conserves). */
+int fo_coarse_step_far(int nx, int ny, int nz, const uint8_t* liquid, int B, int R, const double* P_band,
+                       const double* PBC, double V_far, double c_far, const double* c_in, double* c_out,
+                       double* c_far_out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
+    int64_t NC = (int64_t)ncx * ncy * ncz;
+    if (fo_coarse_step(nx, ny, nz, liquid, B, R, P_band, c_in, c_out) != 0) return -1;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
+    if (!cnt) return -1;
+    fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                if (liquid[i]) c_out[i] += PBC[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))] * c_far;
+            }
+    free(cnt);
+    double m_in = 0.0, m_out = 0.0;
+    for (int64_t i = 0; i < N; i++) { m_in += c_in[i]; m_out += c_out[i]; }
+    *c_far_out = (m_in + V_far * c_far - m_out) / V_far;
+    return 0;
+}
+
 int fo_full_march(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                   double lam, int n_sub, const double* c_in, double* c_out)
 {

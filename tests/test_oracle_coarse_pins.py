@@ -97,3 +97,60 @@ def test_mass_conservation_with_mask_and_clipped_blocks():
         got = oracle.coarse_step(shape, liquid, B, R, P, c)
         assert abs(got.sum() - c.sum()) <= 1e-13 * c.sum()
         assert P.min() >= 0.0
+
+
+# ------------------------------------------------------------------ far-field boundary (Eq. 7, P_BC c_far)
+
+def test_open_chain_by_hand():
+    """3 x 1 x 1 grid, all liquid, D = 1: every cell has 4 open lateral faces and the end cells one more,
+    so gb = [5, 4, 5].  One substep: u = 1 - lam gb from the unit block (ghost 0), u = lam gb from the
+    ghosts at 1 (field 0); with one block of 3 cells P = (3 - 14 lam) / 3 and P_BC = 14 lam / 3."""
+    lam = 0.05
+    shape = (3, 1, 1)
+    assert np.array_equal(oracle.boundary_conductance(shape, np.ones(3), np.ones(3)), [5.0, 4.0, 5.0])
+    P = oracle.coarse_kernels_open(shape, np.ones(3), np.ones(3), 3, lam, 3, 1)
+    pbc = oracle.coarse_pbc(shape, np.ones(3), np.ones(3), 3, lam, 1)
+    Rc = oracle.coarse_radius(3, 3)
+    assert P[0][Rc, Rc, Rc] == pytest.approx((3 - 14 * lam) / 3, abs=1e-15)
+    assert pbc[0] == pytest.approx(14 * lam / 3, abs=1e-15)
+
+
+def test_uniform_far_field_is_a_fixed_point():
+    """With windows covering the grid, a liquid at c_far stays at c_far: P 1 + P_BC = 1 on every node."""
+    shape = (9, 8, 7)
+    D = synth.random_diffusivity(shape, 90, 3.0)
+    liquid = (np.random.default_rng(91).random(D.size) < 0.8).astype(np.uint8)
+    lam = 0.8 * oracle.stable_dt_sub(shape, D) * 4 / 5      # leave room for the open faces
+    B, R = 3, 9
+    P = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, 12)
+    pbc = oracle.coarse_pbc(shape, D, liquid, B, lam, 12)
+    c = np.where(liquid > 0, 0.7, 0.0)
+    out, _ = oracle.coarse_step_far(shape, liquid, B, R, P, pbc, 100.0, 0.7, c)
+    assert np.allclose(out[liquid > 0], 0.7, rtol=0, atol=1e-14)
+
+
+def test_far_field_conserves_the_total_and_closes_without_open_faces():
+    shape = (12, 11, 10)
+    p = synth.sphere_packing(shape, 0.4, 92, r_range=(1.5, 3.0))
+    D = synth.diffusivity_per_sphere(p)
+    liquid = (~p.solid).astype(np.uint8)
+    lam = 0.8 * oracle.stable_dt_sub(shape, D) * 4 / 5
+    B, R, n_sub, V_far = 3, 4, 15, 500.0
+    P = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub)
+    pbc = oracle.coarse_pbc(shape, D, liquid, B, lam, n_sub)
+    c = synth.random_field(D.size, 93, 0.0, 1.0)
+    cf = 0.25
+    total = c.sum() + V_far * cf
+    for _ in range(3):
+        c, cf = oracle.coarse_step_far(shape, liquid, B, R, P, pbc, V_far, cf, c)
+        assert c.sum() + V_far * cf == pytest.approx(total, rel=1e-14)
+    # A liquid phase that never touches the outer surface has no open face: P_BC = 0 and P is the
+    # closed coarse matrix.
+    inner = liquid.copy().reshape(shape[::-1])
+    inner[0, :, :] = inner[-1, :, :] = 0
+    inner[:, 0, :] = inner[:, -1, :] = 0
+    inner[:, :, 0] = inner[:, :, -1] = 0
+    inner = inner.reshape(-1)
+    assert not oracle.coarse_pbc(shape, D, inner, B, lam, n_sub).any()
+    assert np.allclose(oracle.coarse_kernels_open(shape, D, inner, B, lam, R, n_sub),
+                       oracle.coarse_kernels(shape, D, inner, B, lam, R, n_sub), rtol=1e-13, atol=1e-16)
