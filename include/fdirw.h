@@ -221,6 +221,27 @@ FDIRW_API int fdirw_create_coarse(const fdirw_grid* grid, const double* D_map, c
  * block J + d is outside the grid or has no liquid.  Needs the matrix built (FDIRW_ERR_STATE otherwise). */
 FDIRW_API int fdirw_read_coarse(fdirw_ctx* ctx, const int64_t* blocks, int64_t n, double* out);
 
+/* Far-field boundary of a coarse-mesh context (the p_BC c_far term of Eqs. 8, 10 and 14, and Eq. 7).
+ * Opens every face of a liquid cell on the grid's outer surface onto the far-field liquid, represented
+ * by a ghost cell one cell width outside that holds c_far and has the cell's own diffusivity
+ * (conductance D_i per open face; this ghost is this library's reading).  The coarse matrix is rebuilt
+ * with those faces (its columns then keep the mass that stays, unrenormalised), P_BC is the liquid
+ * marched from 0 with every ghost at 1 over the whole grid, mapped to the nodes, and each macro step
+ * becomes C' = P C + P_BC c_far followed by the Eq. 7 update c_far <- (m_in + V_far c_far - m_out) /
+ * V_far (m = FP64 total of the field before and after the step), so that the near- plus far-field total
+ * is conserved.  Calling it again only resets c_far.
+ *   V_far : far-field volume in cell volumes (> 0, finite); c_far: its current concentration (finite)
+ * Errors: FDIRW_ERR_ARG (not a coarse context, bad values), FDIRW_ERR_UNSTABLE (the open faces push
+ * dt_sub * max(sum g) / h^2 above 1), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_coarse_far_field(fdirw_ctx* ctx, double V_far, double c_far);
+
+/* Current far-field concentration (after the last fdirw_step).  Synchronises the context stream.
+ * Errors: FDIRW_ERR_ARG, FDIRW_ERR_STATE (no far field set). */
+FDIRW_API int fdirw_coarse_get_far_field(fdirw_ctx* ctx, double* c_far);
+
+/* P_BC of every block (n_blocks doubles, host), once built.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_STATE. */
+FDIRW_API int fdirw_read_coarse_pbc(fdirw_ctx* ctx, double* out);
+
 /* Window radius of every source (n_cells int32 values, host): the radius rule's value for batch
  * contexts, window_R for fdirw_create contexts.  Synchronises the context stream. */
 FDIRW_API int fdirw_read_radius(fdirw_ctx* ctx, int32_t* out);

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -36,6 +37,14 @@ struct Coarse {
     double* C = nullptr;                         // nc
     double* Cn = nullptr;                        // nc
     bool built = false;
+    // Far-field boundary (open outer surface): lam * open-face conductance per cell, P_BC per block,
+    // device scalars [c_far, mass before, mass after], FP32 ping-pong fields of the P_BC march.
+    bool open = false;
+    double V_far = 0.0;
+    float* abnd = nullptr;
+    double* pbc = nullptr;
+    double* far = nullptr;
+    float* ubuf = nullptr;
 };
 
 namespace {
@@ -91,9 +100,77 @@ __global__ void map_kernel(Grid g, const uint8_t* __restrict__ liquid, int B, in
     }
 }
 
-// Eq. 14: C'_I = sum over block offsets d (ascending) of P[I][I - d] C_{I - d}, FP64.
+// Open faces: gb_i = D_i times the faces of liquid cell i on the grid's outer surface; abnd = fp32(lam gb)
+// (one rounding, as the face coefficients); the largest per-cell sum of masked face conductances plus gb
+// (bits of a non-negative double, for atomicMax) for the stability check.
+__global__ void open_faces_kernel(Grid g, const double* __restrict__ D, const uint8_t* __restrict__ liquid,
+                                  double lam, float* __restrict__ abnd, unsigned long long* __restrict__ max_bits) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
+        double gb = 0.0, sum = 0.0;
+        if (liquid[i]) {
+            const int faces = (x == 0) + (x == g.nx - 1) + (y == 0) + (y == g.ny - 1) + (z == 0) + (z == g.nz - 1);
+            gb = D[i] * (double)faces;
+            auto face = [&](int64_t j) {
+                const double a = D[i], b = D[j];
+                return (liquid[j] && a + b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+            };
+            if (x > 0) sum += face(i - 1);
+            if (x + 1 < g.nx) sum += face(i + 1);
+            if (y > 0) sum += face(i - g.nx);
+            if (y + 1 < g.ny) sum += face(i + g.nx);
+            if (z > 0) sum += face(i - nxy);
+            if (z + 1 < g.nz) sum += face(i + nxy);
+            sum += gb;
+        }
+        abnd[i] = (float)(lam * gb);
+        atomicMax(max_bits, (unsigned long long)__double_as_longlong(sum));
+    }
+}
+
+// One explicit substep of the liquid phase over the whole grid with every far-field ghost at 1 (the
+// P_BC march): u' = u + (am u + sum c u_nb + abnd), am = -(sum of the cell's coefficients + abnd), in the
+// FP32 increment form and association of the windowed kernels.
+__global__ void pbc_substep_kernel(Grid g, const float* __restrict__ ax, const float* __restrict__ ay,
+                                   const float* __restrict__ az, const float* __restrict__ abnd,
+                                   const float* __restrict__ u, float* __restrict__ un) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
+        const float cxm = x > 0 ? ax[i - 1] : 0.f, cxp = x + 1 < g.nx ? ax[i] : 0.f;
+        const float cym = y > 0 ? ay[i - g.nx] : 0.f, cyp = y + 1 < g.ny ? ay[i] : 0.f;
+        const float czm = z > 0 ? az[i - nxy] : 0.f, czp = z + 1 < g.nz ? az[i] : 0.f;
+        const float vb = abnd[i];
+        const float cur = u[i];
+        const float am = -((((cxm + cxp) + (cym + cyp)) + (czm + czp)) + vb);
+        float v = am * cur;
+        v = fmaf(cxm, x > 0 ? u[i - 1] : 0.f, v);
+        v = fmaf(cxp, x + 1 < g.nx ? u[i + 1] : 0.f, v);
+        v = fmaf(cym, y > 0 ? u[i - g.nx] : 0.f, v);
+        v = fmaf(cyp, y + 1 < g.ny ? u[i + g.nx] : 0.f, v);
+        v = fmaf(czm, z > 0 ? u[i - nxy] : 0.f, v);
+        v = fmaf(czp, z + 1 < g.nz ? u[i + nxy] : 0.f, v);
+        v = __fadd_rn(v, vb);                           // inflow from the ghosts at c_far = 1
+        un[i] = __fadd_rn(cur, v);
+    }
+}
+
+__global__ void widen_kernel(const float* __restrict__ u, int64_t n, double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)u[i];
+}
+
+// Eq. 7 for the step just taken: c_far = (m_in + V_far c_far - m_out) / V_far.
+__global__ void far_update_kernel(double* far, double V_far) {
+    far[0] = ((far[1] + V_far * far[0]) - far[2]) / V_far;
+}
+
+// Eq. 14: C'_I = sum over block offsets d (ascending) of P[I][I - d] C_{I - d}, FP64, plus P_BC[I] c_far
+// when the outer surface is open.
 __global__ void coarse_gather_kernel(int ncx, int ncy, int ncz, int Rc, const double* __restrict__ Qc,
-                                     const double* __restrict__ C, double* __restrict__ Cn) {
+                                     const double* __restrict__ C, const double* __restrict__ pbc,
+                                     const double* __restrict__ far, double* __restrict__ Cn) {
     const int64_t nc = (int64_t)ncx * ncy * ncz;
     const int Wc = 2 * Rc + 1;
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
@@ -108,6 +185,7 @@ __global__ void coarse_gather_kernel(int ncx, int ncy, int ncz, int Rc, const do
                     const int64_t J = jx + (int64_t)ncx * (jy + (int64_t)ncy * jz);
                     acc = fma(Qc[(int64_t)d * nc + I], C[J], acc);
                 }
+        if (pbc) acc = __dadd_rn(acc, __dmul_rn(pbc[I], far[0]));
         Cn[I] = acc;
         (void)Wc;
     }
@@ -168,9 +246,26 @@ int coarse_kernels(fdirw_ctx* c) {
     a.liquid = k.liquid;
     a.ccount = k.count;
     a.Qc = k.Qc;
+    a.abnd = k.open ? k.abnd : nullptr;
     FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     if (k.nodes > 0 && c->n_sub >= 0) FDIRW_CUDA(c, launch_march_coarse(a, k.Rw, c->num_sms, c->stream));
     FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    if (k.open) {
+        // P_BC: the liquid from 0 with every ghost at 1, n_sub substeps over the whole grid, then Eq. 11.
+        float* u0 = k.ubuf;
+        float* u1 = k.ubuf + c->g.n;
+        FDIRW_CUDA(c, cudaMemsetAsync(u0, 0, (size_t)c->g.n * 4, c->stream));
+        for (int t = 0; t < c->n_sub; t++) {
+            pbc_substep_kernel<<<grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(
+                c->g, a.ax, a.ay, a.az, k.abnd, u0, u1);
+            FDIRW_CUDA(c, cudaGetLastError());
+            std::swap(u0, u1);
+        }
+        widen_kernel<<<grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(u0, c->g.n, c->cbuf);
+        map_kernel<<<grid_blocks(k.nc, 128), 128, 0, c->stream>>>(c->g, k.liquid, k.B, k.ncx, k.ncy, k.nc, k.count,
+                                                                  c->cbuf, k.pbc);
+        FDIRW_CUDA(c, cudaGetLastError());
+    }
     c->kernels_timed = true;
     c->parts_used = 5;
     k.built = true;
@@ -207,11 +302,18 @@ int coarse_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps
             FDIRW_CUDA(c, cudaGetLastError());
             const bool last = t + 1 == n_steps;
             if (last) FDIRW_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-            coarse_gather_kernel<<<grid_blocks(k.nc, 128), 128, 0, c->stream>>>(k.ncx, k.ncy, k.ncz, k.Rc, k.Qc, k.C, k.Cn);
+            if (k.open) FDIRW_CUDA(c, launch_mass(cur, c->g.n, c->partials, k.far + 1, c->stream));
+            coarse_gather_kernel<<<grid_blocks(k.nc, 128), 128, 0, c->stream>>>(k.ncx, k.ncy, k.ncz, k.Rc, k.Qc, k.C,
+                                                                                k.open ? k.pbc : nullptr, k.far, k.Cn);
             FDIRW_CUDA(c, cudaGetLastError());
             if (last) FDIRW_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
             remap_kernel<<<grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(c->g, k.liquid, k.B, k.ncx, k.ncy, k.Cn, cur, dst);
             FDIRW_CUDA(c, cudaGetLastError());
+            if (k.open) {
+                FDIRW_CUDA(c, launch_mass(dst, c->g.n, c->partials, k.far + 2, c->stream));
+                far_update_kernel<<<1, 1, 0, c->stream>>>(k.far, k.V_far);
+                FDIRW_CUDA(c, cudaGetLastError());
+            }
             cur = dst;
         }
         c->gather_timed = true;
@@ -244,6 +346,10 @@ void coarse_release(fdirw_ctx* c) {
     p = k->Qc; dfree(p);
     p = k->C; dfree(p);
     p = k->Cn; dfree(p);
+    p = k->abnd; dfree(p);
+    p = k->pbc; dfree(p);
+    p = k->far; dfree(p);
+    p = k->ubuf; dfree(p);
     delete k;
     c->coarse = nullptr;
 }
@@ -339,6 +445,73 @@ int fdirw_create_coarse(const fdirw_grid* grid, const double* D_map, const uint8
     }
     c->window_cells = wc;
     *out = c;
+    return FDIRW_OK;
+}
+
+int fdirw_coarse_far_field(fdirw_ctx* c, double V_far, double c_far) {
+    if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
+    if (!c->coarse) return fail(c, FDIRW_ERR_ARG, "not a coarse-mesh context");
+    if (!(std::isfinite(V_far) && V_far > 0.0) || !std::isfinite(c_far))
+        return fail(c, FDIRW_ERR_ARG, "V_far must be finite and > 0, c_far finite");
+    DeviceGuard dg(c->device);
+    fdirw::Coarse& k = *c->coarse;
+    const uint64_t n = (uint64_t)c->g.n;
+    int rc;
+    if (!k.abnd) {
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.abnd), n * 4, "open-face coefficients")) != FDIRW_OK) return rc;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.pbc), (uint64_t)k.nc * 8, "P_BC")) != FDIRW_OK) return rc;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.far), 3 * 8, "far field")) != FDIRW_OK) return rc;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.ubuf), 2 * n * 4, "P_BC march")) != FDIRW_OK) return rc;
+        unsigned long long* mx = nullptr;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&mx), 8, "flags")) != FDIRW_OK) return rc;
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemsetAsync(mx, 0, 8, c->stream);
+        if (e == cudaSuccess) {
+            fdirw::open_faces_kernel<<<fdirw::grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(c->g, c->Dd, k.liquid, c->lam,
+                                                                                           k.abnd, mx);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, mx, 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(mx);
+        c->allocated -= 8;
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, FDIRW_ERR_CUDA, cuda_msg("open faces", e)); }
+        double m;
+        std::memcpy(&m, &h, 8);
+        if (c->lam * m > 1.0 + 1e-12) {
+            char buf[200];
+            std::snprintf(buf, sizeof buf, "unstable with open faces: dt_sub*max(sum g)/h^2 = %.17g > 1", c->lam * m);
+            return fail(c, FDIRW_ERR_UNSTABLE, buf);
+        }
+    }
+    const double h3[3] = {c_far, 0.0, 0.0};
+    FDIRW_CUDA(c, cudaMemcpyAsync(k.far, h3, 24, cudaMemcpyHostToDevice, c->stream));
+    FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+    k.V_far = V_far;
+    if (!k.open) {
+        k.open = true;
+        k.built = false;                 // the coarse matrix changes with open faces
+        c->kernels_ready = false;
+    }
+    return FDIRW_OK;
+}
+
+int fdirw_coarse_get_far_field(fdirw_ctx* c, double* c_far) {
+    if (!c || !c_far) return fail(c, FDIRW_ERR_ARG, "NULL context or c_far");
+    if (!c->coarse || !c->coarse->open) return fail(c, FDIRW_ERR_STATE, "no far field set (fdirw_coarse_far_field)");
+    DeviceGuard dg(c->device);
+    FDIRW_CUDA(c, cudaMemcpyAsync(c_far, c->coarse->far, 8, cudaMemcpyDeviceToHost, c->stream));
+    FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+    return FDIRW_OK;
+}
+
+int fdirw_read_coarse_pbc(fdirw_ctx* c, double* out) {
+    if (!c || !out) return fail(c, FDIRW_ERR_ARG, "NULL context or out");
+    if (!c->coarse || !c->coarse->open) return fail(c, FDIRW_ERR_STATE, "no far field set (fdirw_coarse_far_field)");
+    if (!c->coarse->built) return fail(c, FDIRW_ERR_STATE, "coarse matrix not built (call fdirw_kernels)");
+    DeviceGuard dg(c->device);
+    FDIRW_CUDA(c, cudaMemcpyAsync(out, c->coarse->pbc, (size_t)c->coarse->nc * 8, cudaMemcpyDeviceToHost, c->stream));
+    FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
     return FDIRW_OK;
 }
 

@@ -66,6 +66,7 @@ struct MarchArgs {
     const uint8_t* liquid;       // N: 1 = liquid cell
     const int32_t* ccount;       // coarse_n: liquid cells per block
     double* Qc;                  // (2 Rc + 1)^3 planes of coarse_n values, destination-indexed
+    const float* abnd;           // nullable: lam * open-face conductance of each cell (far-field boundary)
 };
 // Coarse-mesh march of the blocks a.list[src_begin..src_end): window radius R = window_R + (B - 1) / 2
 // (1..10), one source per CTA.

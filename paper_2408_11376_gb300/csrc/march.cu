@@ -722,8 +722,9 @@ struct MapTmc {
 
 // Coarse epilogue (Eq. 11 applied to the marched unit of block J): S[d] = FP64 sum of the marched field
 // over the liquid cells of block J + d inside the window (z, y, x order; sbuf holds 0 elsewhere), m =
-// sum of S in a fixed order, and column J of P: Qc[d][J + d] = N_J S[d] / (m N_{J+d}) (0 where block
-// J + d has no liquid).  Every thread of the CTA takes part; S follows red in shared memory.
+// sum of S in a fixed order, and column J of P: Qc[d][J + d] = N_J S[d] / (m N_{J+d}), or S[d] / N_{J+d}
+// when the phase has open faces (a.abnd) and the column keeps the mass that stays (0 where block J + d
+// has no liquid).  Every thread of the CTA takes part; S follows red in shared memory.
 template <int R>
 __device__ void coarse_epilogue(const MarchArgs& a, const float* sbuf, double* S, int64_t first) {
     constexpr int W1 = 2 * R + 1;
@@ -763,7 +764,10 @@ __device__ void coarse_epilogue(const MarchArgs& a, const float* sbuf, double* S
             if (cx < 0 || cx >= a.ncx || cy < 0 || cy >= a.ncy || cz < 0 || cz >= a.ncz) continue;
             const int64_t I = cx + (int64_t)a.ncx * (cy + (int64_t)a.ncy * cz);
             const int NI = a.ccount[I];
-            a.Qc[(int64_t)d * a.coarse_n + I] = (NI > 0 && m > 0.0) ? (NJ * S[d]) / (m * (double)NI) : 0.0;
+            // Closed phase: renormalise the column to carry N_J; open faces: keep the mass that stays.
+            double v = 0.0;
+            if (NI > 0 && m > 0.0) v = a.abnd ? S[d] / (double)NI : (NJ * S[d]) / (m * (double)NI);
+            a.Qc[(int64_t)d * a.coarse_n + I] = v;
         }
     }
 }
@@ -849,9 +853,11 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                     const int z = sz - R + k;
                     const bool ok = col_ok && z >= 0 && z < nz;
                     float u0 = (!COARSE && src_ok && ci == R && cj == R && k == R) ? 1.f : 0.f;
+                    float vb = 0.f;                       // open faces of the cell (coarse, far field)
                     if (ok) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
                         if (COARSE && a.liquid[i] && abs(ci - R) <= bh && abs(cj - R) <= bh && abs(k - R) <= bh) u0 = 1.f;
+                        if (COARSE && a.abnd) vb = __ldg(a.abnd + i);
                         if (ci > 0 && x > 0) vxm = __ldg(ax + i - 1);
                         if (ci < 2 * R && x + 1 < nx) vxp = __ldg(ax + i);
                         if (cj > 0 && y > 0) vym = __ldg(ay + i - nx);
@@ -859,7 +865,10 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                         if (k < 2 * R && z + 1 < nz) vz = __ldg(az + i);
                     }
                     cz[k < W1 ? k : 0] = vz;
-                    am[k < W1 ? k : 0] = -(((vxm + vxp) + (vym + vyp)) + (zprev + vz));
+                    if constexpr (COARSE)
+                        am[k < W1 ? k : 0] = -((((vxm + vxp) + (vym + vyp)) + (zprev + vz)) + vb);
+                    else
+                        am[k < W1 ? k : 0] = -(((vxm + vxp) + (vym + vyp)) + (zprev + vz));
                     u[k < W1 ? k : 0] = u0;
                     zprev = vz;
                 }

@@ -32,7 +32,7 @@ EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "f
             "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc", "fdirw_net_create",
             "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
             "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius", "fdirw_create_coarse",
-            "fdirw_read_coarse")
+            "fdirw_read_coarse", "fdirw_coarse_far_field", "fdirw_coarse_get_far_field", "fdirw_read_coarse_pbc")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -114,6 +114,9 @@ def load(path: str | None = None):
         lib.fdirw_create_coarse.argtypes = [ctypes.POINTER(fdirw_grid), vp, vp, i32, ctypes.c_double, i32, i32,
                                             ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
         lib.fdirw_read_coarse.argtypes = [vp, vp, i64, vp]
+        lib.fdirw_coarse_far_field.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+        lib.fdirw_coarse_get_far_field.argtypes = [vp, dp]
+        lib.fdirw_read_coarse_pbc.argtypes = [vp, vp]
         for name in EXPORTED:
             if name not in ("fdirw_destroy", "fdirw_last_error", "fdirw_net_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -382,6 +385,25 @@ class FDiRWCoarse(FDiRW):
 
     def read_coarse(self, blocks) -> np.ndarray:
         return fdirw_read_coarse(self.ctx, blocks, self.Rc)
+
+    def far_field(self, V_far: float, c_far: float) -> None:
+        """Open the outer surface onto a far field of V_far cell volumes at c_far (Eqs. 7, 10, 14)."""
+        _check(load().fdirw_coarse_far_field(ctypes.c_void_p(self.ctx), float(V_far), float(c_far)),
+               ctypes.c_void_p(self.ctx))
+
+    def c_far(self) -> float:
+        v = ctypes.c_double(0.0)
+        _check(load().fdirw_coarse_get_far_field(ctypes.c_void_p(self.ctx), ctypes.byref(v)), ctypes.c_void_p(self.ctx))
+        return v.value
+
+    def read_pbc(self) -> np.ndarray:
+        nb = 1
+        for n in self.shape:
+            nb *= (n + self.B - 1) // self.B
+        out = np.empty(nb, dtype=np.float64)
+        _check(load().fdirw_read_coarse_pbc(ctypes.c_void_p(self.ctx), ctypes.c_void_p(out.ctypes.data)),
+               ctypes.c_void_p(self.ctx))
+        return out
 
 
 # --------------------------------------------------------------------------- learned surrogate

@@ -116,3 +116,56 @@ def test_coarse_argument_errors():
             f.read_kernels([0])
         with pytest.raises(FdirwError):
             f.read_coarse([8])                    # 2 x 2 x 2 blocks
+
+
+# ------------------------------------------------------------------ far-field boundary (Eq. 7, P_BC c_far)
+
+def test_far_field_matches_oracle():
+    shape, B, R, n_sub, V_far, cf0 = (22, 19, 17), 5, 4, 24, 3000.0, 0.4
+    D, liquid = _case(shape, 95)
+    lam = 0.8 * oracle.stable_dt_sub(shape, D) * 4 / 5
+    P = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub)
+    pbc = oracle.coarse_pbc(shape, D, liquid, B, lam, n_sub)
+    c0 = synth.random_field(D.size, 96, 0.0, 1.0)
+    ref, cf = c0, cf0
+    refs = []
+    for _ in range(3):
+        ref, cf = oracle.coarse_step_far(shape, liquid, B, R, P, pbc, V_far, cf, ref)
+        refs.append((ref, cf))
+    with FDiRWCoarse(shape, D, liquid, B, n_sub * lam, R, n_sub) as f:
+        f.far_field(V_far, cf0)
+        f.kernels()
+        gotP = f.read_coarse(np.arange(P.shape[0]))
+        gotpbc = f.read_pbc()
+        out = np.empty_like(c0)
+        cur = c0
+        for t in range(3):
+            f.step(cur, out, 1)
+            cur = out.copy()
+            assert _rel(cur, refs[t][0]) <= FIELD_TOL
+            # c_far moves by the step's mass change over V_far, so its error is the field's mass error / V_far
+            assert abs(f.c_far() - refs[t][1]) <= FIELD_TOL * np.abs(refs[t][0]).sum() / V_far
+            assert cur.sum() + V_far * f.c_far() == pytest.approx(c0.sum() + V_far * cf0, rel=1e-12)
+    cnt = oracle.coarse_counts(shape, liquid, B)
+    for J in np.flatnonzero(cnt):
+        assert _rel(gotP[J], P[J]) <= P_TOL
+    assert _rel(gotpbc, pbc) <= P_TOL
+    assert np.array_equal(cur[liquid == 0], c0[liquid == 0])
+
+
+def test_far_field_errors():
+    shape = (10, 10, 10)
+    D = np.full((10, 10, 10), 1e-3)
+    D[0], D[-1], D[:, 0], D[:, -1], D[:, :, 0], D[:, :, -1] = 1.0, 1.0, 1.0, 1.0, 1.0, 1.0
+    D = D.reshape(-1)
+    dt = oracle.stable_dt_sub(shape, D)          # closed limit, set by the outer layer's in-layer faces
+    with FDiRWCoarse(shape, D, None, 5, dt, 2, 1) as f:
+        with pytest.raises(FdirwError) as e:
+            f.far_field(100.0, 0.0)              # the open faces of the outer layer push it over
+        assert e.value.code == fdirw.FDIRW_ERR_UNSTABLE
+    D = np.ones(1000)
+    with FDiRWCoarse(shape, D, None, 5, 0.1, 2, 1) as f:
+        with pytest.raises(FdirwError):
+            f.c_far()
+        with pytest.raises(FdirwError):
+            f.far_field(0.0, 1.0)
