@@ -81,6 +81,25 @@ def test_batch_host_side_argument_checks(lib):
     assert lib.fdirw_read_radius(None, None) == fdirw.FDIRW_ERR_ARG
 
 
+def test_coarse_host_side_argument_checks(lib):
+    D = np.ones(64)
+    g = fdirw.fdirw_grid(4, 4, 4, 1.0)
+    fp64 = fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)
+    for block, R, opts in ((2, 2, None), (0, 2, None), (-1, 2, None), (5, 9, None), (1, 0, None), (3, -1, None),
+                           (3, 2, fp64)):
+        ctx = ctypes.c_void_p(1234)
+        rc = lib.fdirw_create_coarse(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), None, block, 0.1, R, 2,
+                                     ctypes.byref(opts) if opts else None, ctypes.byref(ctx))
+        assert rc == fdirw.FDIRW_ERR_ARG, (block, R)
+        assert ctx.value is None
+    assert lib.fdirw_create_coarse(ctypes.byref(g), None, None, 3, 0.1, 2, 2, None,
+                                   ctypes.byref(ctypes.c_void_p())) == fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_read_coarse(None, None, 0, None) == fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_coarse_far_field(None, 1.0, 0.0) == fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_coarse_get_far_field(None, None) == fdirw.FDIRW_ERR_ARG
+    assert lib.fdirw_read_coarse_pbc(None, None) == fdirw.FDIRW_ERR_ARG
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     saved = fdirw._lib
     try:
