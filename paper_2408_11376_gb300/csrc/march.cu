@@ -587,6 +587,7 @@ __global__ void __launch_bounds__(MapTm<R>::THREADS, 1) march_tm_kernel(MarchArg
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
+        #pragma unroll(R <= 8 ? 2 : 1)   // two substeps per iteration: no register copies at the back edge
         for (int it = 0; it < a.n_sub; it++) {
             float* buf = xbuf + (it & 1) * BUF;
             if (active) {
@@ -1337,12 +1338,16 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
         if (a.R > 8 && (P < 4 || P > 5)) continue; // only mappings 4 and 5 cover R = 9, 10
         if (P == 5 && a.R < 6) continue;          // one CTA of < 6 warps per SM: never the fastest there
         e = dispatch(warm, P, num_sms, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess) e = dispatch(s, P, num_sms, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {      // the faster of two timings
+            float t = 0.f;
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = dispatch(s, P, num_sms, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && t < ms) ms = t;
+        }
         if (e == cudaSuccess && ms < best_ms) { best_ms = ms; *best = P; }
     }
     cudaEventDestroy(e0);
