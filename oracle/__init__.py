@@ -99,6 +99,10 @@ def _load():
             lib.fo_coarse_step_far.argtypes = [ctypes.c_int] * 3 + [_U8, ctypes.c_int, ctypes.c_int, _D, _D,
                                                                    ctypes.c_double, ctypes.c_double, _D, _D, _D]
             lib.fo_coarse_step_far.restype = ctypes.c_int
+            lib.fo_absorb.argtypes = [ctypes.c_int] * 3 + [_U8] + [ctypes.c_double] * 4 + [_D, _D]
+            lib.fo_absorb.restype = None
+            lib.fo_solid_march.argtypes = [ctypes.c_int] * 3 + [_D, _U8, ctypes.c_double, ctypes.c_int, _D, _D]
+            lib.fo_solid_march.restype = ctypes.c_int
             lib.fo_mass.argtypes = [_D, ctypes.c_int64]
             lib.fo_mass.restype = ctypes.c_double
             _lib = lib
@@ -315,6 +319,37 @@ def coarse_step_far(shape, liquid, B: int, R: int, P_band, PBC, V_far: float, c_
                                   float(V_far), float(c_far), _p(c), _p(out), ctypes.byref(cf)) != 0:
         raise ValueError("fo_coarse_step_far failed")
     return out, cf.value
+
+
+def absorb(shape, liquid, k: float, cS_eq: float, cL_eq: float, dt: float, c) -> np.ndarray:
+    """Interface exchange of Eqs. 4-6 over one macro step on every liquid/solid face."""
+    nx, ny, nz = shape
+    lq = _u8(liquid, nx * ny * nz)
+    c = _f64(c).reshape(-1)
+    out = np.empty_like(c)
+    _load().fo_absorb(nx, ny, nz, _pu8(lq), float(k), float(cS_eq), float(cL_eq), float(dt), _p(c), _p(out))
+    return out
+
+
+def solid_march(shape, D, liquid, lam: float, n_sub: int, c) -> np.ndarray:
+    """Slow diffusion of the solid phase: explicit flux-form march over solid-solid faces only."""
+    nx, ny, nz = shape
+    Dv = _f64(D).reshape(-1)
+    lq = _u8(liquid, Dv.size)
+    c = _f64(c).reshape(-1)
+    out = np.empty_like(c)
+    if _load().fo_solid_march(nx, ny, nz, _p(Dv), _pu8(lq), float(lam), int(n_sub), _p(c), _p(out)) != 0:
+        raise ValueError("fo_solid_march failed")
+    return out
+
+
+def coupled_step(shape, D, liquid, B: int, R: int, P_band, PBC, V_far: float, c_far: float, k: float,
+                 cS_eq: float, cL_eq: float, dt: float, lam_s: float, n_sub_s: int, c):
+    """One coupled macro step: interface exchange, slow solid march, coarse FDiRW with the far field.
+    Returns (c', c_far')."""
+    c1 = absorb(shape, liquid, k, cS_eq, cL_eq, dt, c)
+    c2 = solid_march(shape, D, liquid, lam_s, n_sub_s, c1)
+    return coarse_step_far(shape, liquid, B, R, P_band, PBC, V_far, c_far, c2)
 
 
 def full_march(shape, D, lam: float, n_sub: int, c, cond: Conductance | None = None) -> np.ndarray:

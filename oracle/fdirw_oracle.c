@@ -530,6 +530,72 @@ int fo_coarse_step_far(int nx, int ny, int nz, const uint8_t* liquid, int B, int
     return 0;
 }
 
+/* ---- Coupled macro step (Sec. 2, Eqs. 1-7) around the coarse FDiRW.  Readings: the field c holds the
+ * liquid concentration on liquid cells and the solid one on the others; D is the effective diffusivity
+ * D_m A_m / RT of each cell's phase (Eqs. 1-3: the flux D grad(mu/RT) with mu = A (c - c_eq)); the
+ * interface exchange of Eqs. 4-6 acts on every face between a liquid cell and a solid cell, with the
+ * pre-step values on both sides and the rate applied over the macro step dt (the reaction runs only
+ * while c_L > cL_eq and c_S < cS_eq, as the text after Eq. 6 states, so f_S is clamped at 0 too):
+ *   f_L = max(0, (c_L - cL_eq) / cL_eq),  f_S = max(0, (cS_eq - c_S) / cS_eq),  m = k f_L f_S dt,
+ *   c_S += m, c_L -= m  (cell volumes equal);
+ * the slow solid diffusion is the explicit flux-form march of the solid phase (faces between solid
+ * cells only) with n_sub_s substeps of lam_s = (dt / n_sub_s) / h^2; then the fast liquid diffusion is
+ * one coarse FDiRW step with the far field (fo_coarse_step_far). */
+void fo_absorb(int nx, int ny, int nz, const uint8_t* liquid, double k, double cS_eq, double cL_eq, double dt,
+               const double* c_in, double* c_out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    memcpy(c_out, c_in, sizeof(double) * (size_t)N);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int64_t i = IDX(x, y, z, nx, ny);
+                int64_t nb[3];
+                int has[3] = {x + 1 < nx, y + 1 < ny, z + 1 < nz};
+                nb[0] = i + 1; nb[1] = i + nx; nb[2] = i + (int64_t)nx * ny;
+                for (int a = 0; a < 3; a++) {
+                    if (!has[a]) continue;
+                    int64_t j = nb[a];
+                    if (liquid[i] == liquid[j]) continue;
+                    int64_t l = liquid[i] ? i : j, sd = liquid[i] ? j : i;
+                    double fL = c_in[l] > cL_eq ? (c_in[l] - cL_eq) / cL_eq : 0.0;
+                    double fS = c_in[sd] < cS_eq ? (cS_eq - c_in[sd]) / cS_eq : 0.0;
+                    double m = k * fL * fS * dt;
+                    c_out[sd] += m;
+                    c_out[l] -= m;
+                }
+            }
+}
+
+/* Slow solid diffusion: the flux-form march of the solid phase (faces between two solid cells, harmonic
+ * mean of D), n_sub substeps of lam. */
+int fo_solid_march(int nx, int ny, int nz, const double* D, const uint8_t* liquid, double lam, int n_sub,
+                   const double* c_in, double* c_out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    double* gx = (double*)malloc(sizeof(double) * (size_t)N);
+    double* gy = (double*)malloc(sizeof(double) * (size_t)N);
+    double* gz = (double*)malloc(sizeof(double) * (size_t)N);
+    double* u = (double*)malloc(sizeof(double) * (size_t)N);
+    double* un = (double*)malloc(sizeof(double) * (size_t)N);
+    uint8_t* solid = (uint8_t*)malloc((size_t)N);
+    if (!gx || !gy || !gz || !u || !un || !solid) {
+        free(gx); free(gy); free(gz); free(u); free(un); free(solid);
+        return -1;
+    }
+    for (int64_t i = 0; i < N; i++) solid[i] = liquid[i] ? 0 : 1;
+    fo_face_conductance(nx, ny, nz, D, gx, gy, gz);
+    fo_mask_faces(nx, ny, nz, solid, gx, gy, gz);
+    memcpy(u, c_in, sizeof(double) * (size_t)N);
+    for (int k = 0; k < n_sub; k++) {
+        box_substep(nx, ny, gx, gy, gz, lam, 0, 0, 0, nx, ny, nz, u, un);
+        double* t = u; u = un; un = t;
+    }
+    memcpy(c_out, u, sizeof(double) * (size_t)N);
+    free(gx); free(gy); free(gz); free(u); free(un); free(solid);
+    return 0;
+}
+
 int fo_full_march(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                   double lam, int n_sub, const double* c_in, double* c_out)
 {

@@ -154,3 +154,62 @@ def test_far_field_conserves_the_total_and_closes_without_open_faces():
     assert not oracle.coarse_pbc(shape, D, inner, B, lam, n_sub).any()
     assert np.allclose(oracle.coarse_kernels_open(shape, D, inner, B, lam, R, n_sub),
                        oracle.coarse_kernels(shape, D, inner, B, lam, R, n_sub), rtol=1e-13, atol=1e-16)
+
+
+# ------------------------------------------------------------------ coupled macro step (Eqs. 1-7)
+
+def test_absorption_by_hand():
+    """Liquid cell at 3 cL_eq next to a solid cell at cS_eq / 4: f_L = 2, f_S = 3/4, m = k f_L f_S dt."""
+    k, cS, cL, dt = 0.05, 1.0, 1e-5, 1e-4
+    c = np.array([3e-5, 0.25])
+    got = oracle.absorb((2, 1, 1), [1, 0], k, cS, cL, dt, c)
+    m = k * 2.0 * 0.75 * dt
+    assert got[0] == pytest.approx(3e-5 - m, rel=1e-14) and got[1] == pytest.approx(0.25 + m, rel=1e-15)
+    # no reaction below the liquid equilibrium or at / above the solid one
+    assert np.array_equal(oracle.absorb((2, 1, 1), [1, 0], k, cS, cL, dt, np.array([0.5e-5, 0.25])), [0.5e-5, 0.25])
+    assert np.array_equal(oracle.absorb((2, 1, 1), [1, 0], k, cS, cL, dt, np.array([3e-5, 1.2])), [3e-5, 1.2])
+
+
+def test_absorption_counts_every_interface_face_and_conserves():
+    """A liquid cell between two solid cells loses to both; the total is unchanged."""
+    k, cS, cL, dt = 0.01, 1.0, 1e-3, 0.1
+    c = np.array([0.5, 5e-3, 0.2])
+    got = oracle.absorb((3, 1, 1), [0, 1, 0], k, cS, cL, dt, c)
+    fL = (5e-3 - 1e-3) / 1e-3
+    m0, m2 = k * fL * 0.5 * dt, k * fL * 0.8 * dt
+    assert got == pytest.approx([0.5 + m0, 5e-3 - m0 - m2, 0.2 + m2], abs=1e-17)
+    shape = (9, 8, 7)
+    liquid = (np.random.default_rng(97).random(504) < 0.5).astype(np.uint8)
+    c = synth.random_field(504, 98, 0.0, 1e-2)
+    assert oracle.absorb(shape, liquid, k, cS, cL, dt, c).sum() == pytest.approx(c.sum(), rel=1e-14)
+
+
+def test_solid_march_is_the_full_march_of_the_solid():
+    shape = (7, 6, 5)
+    D = synth.random_diffusivity(shape, 99, 3.0)
+    lam = oracle.stable_dt_sub(shape, D)
+    c = synth.random_field(D.size, 100)
+    none_liquid = np.zeros(D.size)
+    assert np.allclose(oracle.solid_march(shape, D, none_liquid, lam, 9, c), oracle.full_march(shape, D, lam, 9, c),
+                       rtol=1e-14, atol=0)
+    all_liquid = np.ones(D.size)
+    assert np.array_equal(oracle.solid_march(shape, D, all_liquid, lam, 9, c), c)   # no solid face: unchanged
+
+
+def test_coupled_step_conserves_the_total():
+    shape = (12, 11, 10)
+    p = synth.sphere_packing(shape, 0.45, 101, r_range=(1.5, 3.0))
+    liquid = (~p.solid).astype(np.uint8)
+    D = np.where(liquid > 0, 1.0, 1e-3)
+    lam = 0.6 * oracle.stable_dt_sub(shape, D)
+    B, R, n_sub, V_far = 3, 4, 12, 800.0
+    P = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub)
+    pbc = oracle.coarse_pbc(shape, D, liquid, B, lam, n_sub)
+    c = np.where(liquid > 0, 2e-3, 1e-6)
+    cf = 2e-3
+    total = c.sum() + V_far * cf
+    for _ in range(3):
+        c, cf = oracle.coupled_step(shape, D, liquid, B, R, P, pbc, V_far, cf, 1e-7, 1.0, 1e-5, n_sub * lam,
+                                    lam, 2, c)
+        assert c.sum() + V_far * cf == pytest.approx(total, rel=1e-13)
+    assert c[liquid == 0].sum() > 1e-6 * (liquid == 0).sum()       # the solid absorbed
