@@ -549,6 +549,8 @@ def run_ours(args, w):
         line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec)
     if args.coarse:
         line["coarse_mesh"] = coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, ~packing.solid, dt_macro)
+    if args.coupled:
+        line["coupled"] = coupled_leg(args, fdirw, torch, dev, stream, w, shape, D, ~packing.solid, dt_macro)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -651,7 +653,25 @@ def coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, liquid, dt_macro):
     stream.synchronize()
     mass0 = float(c_liq.sum().item())
     lqb = lq.bool()
-    return {"block": B, "nodes": info["coarse_nodes"], "liquid_cells": int(liquid.sum()),
+    # Far-field boundary (Eqs. 7, 10, 14): outer surface open onto V_far = the liquid volume, c_far = 0.
+    V_far = float(liquid.sum())
+    far = torch.empty_like(c_liq)
+    fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        f = fdirw.FDiRWCoarse(shape, D, lq, B, dt_macro, w.R, w.n_sub, args.prec, device=dev.index, stream=stream)
+        f.far_field(V_far, 0.0)
+        fe[0].record(stream)
+        f.kernels()
+        f.step(c_liq, far, w.steps)
+        fe[1].record(stream)
+        c_far = f.c_far()
+        f.close()
+    stream.synchronize()
+    far_total = float(far.sum().item()) + V_far * c_far
+    far_leg = {"V_far_cells": V_far, "c_far0": 0.0, "c_far_after": c_far,
+               "near_field_mass_after": float(far.sum().item()),
+               "total_rel_err": abs(far_total - mass0) / mass0, "matrix_pbc_and_steps_ms": fe[0].elapsed_time(fe[1])}
+    return {"block": B, "nodes": info["coarse_nodes"], "liquid_cells": int(liquid.sum()), "far_field": far_leg,
             "macro_steps_per_s": 1000.0 * w.steps / job_ms, "job_ms": job_ms, "matrix_build_ms": build_ms,
             "march_kernel_ms": info["kernels_ms"], "steps_ms": steps_ms,
             "march_cell_substeps_per_s": w.n_sub * info["window_cells"] / (info["kernels_ms"] * 1e-3),
@@ -660,6 +680,37 @@ def coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, liquid, dt_macro):
             "rel_l2_vs_fine_liquid_phase": float((torch.linalg.vector_norm((out - fine)[lqb]) /
                                                   torch.linalg.vector_norm(fine[lqb])).item()),
             "mass_rel_err": abs(mass - mass0) / mass0}
+
+
+def coupled_leg(args, fdirw, torch, dev, stream, w, shape, D, liquid, dt_macro):
+    """Coupled macro step (Sec. 2): interface exchange, slow solid march and the coarse liquid FDiRW with
+    the far field, on the workload's geometry (liquid = pore; the D map read as the effective D_m A_m/RT).
+    Kinetics in lattice units chosen so that no face moves more than a percent of its liquid cell per step:
+    k = 1e-7, cS_eq = 1, cL_eq = 1e-5; initial liquid 2.12e-3, solid 1e-6, far field 2.12e-3 over the
+    liquid's volume (the proportions of the paper's Table 1)."""
+    B = args.coarse or 5
+    lq = torch.from_numpy(liquid.astype(np.uint8)).to(dev)
+    c_init = torch.from_numpy(np.where(liquid, 2.12e-3, 1e-6)).to(dev)
+    V_far = float(liquid.sum())
+    cf0 = 2.12e-3
+    field = c_init.clone()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(stream):
+        f = fdirw.FDiRWCoarse(shape, D, lq, B, dt_macro, w.R, w.n_sub, args.prec, device=dev.index, stream=stream)
+        f.far_field(V_far, cf0)
+        ev[0].record(stream)
+        f.kernels()
+        ev[1].record(stream)
+        QL, QS, c_far = f.coupled_step(field, w.steps, 1e-7, 1.0, 1e-5, dt_macro, 1)
+        ev[2].record(stream)
+        f.close()
+    stream.synchronize()
+    total0 = float(c_init.sum().item()) + V_far * cf0
+    total = float(field.sum().item()) + V_far * c_far
+    steps_ms = ev[1].elapsed_time(ev[2])
+    return {"block": B, "macro_steps": w.steps, "matrix_and_pbc_ms": ev[0].elapsed_time(ev[1]),
+            "steps_ms": steps_ms, "coupled_macro_steps_per_s": 1000.0 * w.steps / steps_ms,
+            "Q_L": [QL[0], QL[-1]], "Q_S": [QS[0], QS[-1]], "c_far_after": c_far, "total_rel_err": abs(total - total0) / total0}
 
 
 def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
@@ -727,6 +778,8 @@ def main(argv=None):
     ap.add_argument("--surrogate-lr", type=float, default=2e-3)
     ap.add_argument("--coarse", type=int, default=0,
                     help="also run the coarse-mesh FDiRW with this odd block side (e.g. 5) and compare it with the fine path")
+    ap.add_argument("--coupled", action="store_true",
+                    help="also run the coupled macro step (exchange, solid march, coarse FDiRW with far field)")
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
     ap.add_argument("--march-parts", type=int, default=0,
                     help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "

@@ -242,6 +242,35 @@ FDIRW_API int fdirw_coarse_get_far_field(fdirw_ctx* ctx, double* c_far);
 /* P_BC of every block (n_blocks doubles, host), once built.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_STATE. */
 FDIRW_API int fdirw_read_coarse_pbc(fdirw_ctx* ctx, double* out);
 
+/* Parameters of the coupled macro step (Sec. 2): interface exchange (Eqs. 4-6) and slow solid diffusion
+ * around the coarse FDiRW.  k: rate constant; cS_eq, cL_eq: equilibrium concentrations (> 0); dt: the
+ * macro step; n_sub_solid: explicit substeps of the solid march within dt (0 = no solid diffusion). */
+typedef struct {
+    double  k;
+    double  cS_eq;
+    double  cL_eq;
+    double  dt;
+    int32_t n_sub_solid;
+    int32_t reserved;      /* must be 0 */
+} fdirw_coupled_params;
+
+/* n_steps coupled macro steps on a coarse-mesh context with a far field (fdirw_coarse_far_field), in
+ * place on field (N float64, host or device; each cell holds the concentration of its own phase: liquid
+ * cells the liquid one, the others the solid one).  The context's D map is read as the effective
+ * diffusivity D_m A_m / RT of each cell's phase (Eqs. 1-3).  Each step: (1) interface exchange on every
+ * liquid/solid face with the pre-step values, m = k f_L f_S dt, f_L = max(0, (c_L - cL_eq) / cL_eq),
+ * f_S = max(0, (cS_eq - c_S) / cS_eq) (the reaction runs only while c_L > cL_eq and c_S < cS_eq), the
+ * solid cell gaining m and the liquid cell losing it; (2) the solid phase marched n_sub_solid FP64
+ * flux-form substeps of lam = (dt / n_sub_solid) / h^2 over solid-solid faces (harmonic mean of D);
+ * (3) one coarse FDiRW step of the liquid with the far-field term and the Eq. 7 update.  QL, QS
+ * (nullable, host, n_steps each): FP64 totals of the liquid and solid cells after every step; c_far
+ * (nullable): the far-field concentration after the last step.  The exchange and the solid march are
+ * explicit: parameters that move more than a cell holds within dt are the caller's to avoid.
+ * Errors: FDIRW_ERR_ARG, FDIRW_ERR_STATE (not a coarse context with a far field), FDIRW_ERR_UNSTABLE
+ * (the solid march), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_coupled_step(fdirw_ctx* ctx, const fdirw_coupled_params* params, double* field, int32_t n_steps,
+                                 double* QL, double* QS, double* c_far);
+
 /* Window radius of every source (n_cells int32 values, host): the radius rule's value for batch
  * contexts, window_R for fdirw_create contexts.  Synchronises the context stream. */
 FDIRW_API int fdirw_read_radius(fdirw_ctx* ctx, int32_t* out);

@@ -45,6 +45,12 @@ struct Coarse {
     double* pbc = nullptr;
     double* far = nullptr;
     float* ubuf = nullptr;
+    // Coupled macro step: FP64 solid-phase face conductances, a scratch field, phase-mass partials.
+    double* gs = nullptr;                        // 3 N: +x/+y/+z solid-solid faces
+    double* tmp = nullptr;                       // 2 N
+    double* qpart = nullptr;                     // kMassBlocks
+    double* qout = nullptr;                      // [Q_L, Q_S] per step, n_steps_cap * 2
+    int64_t qcap = 0;
 };
 
 namespace {
@@ -159,6 +165,105 @@ __global__ void pbc_substep_kernel(Grid g, const float* __restrict__ ax, const f
 __global__ void widen_kernel(const float* __restrict__ u, int64_t n, double* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (double)u[i];
+}
+
+// Interface exchange of Eqs. 4-6 on every liquid/solid face, pre-step values, rate over dt; each cell adds
+// its faces' transfers in the order -z, -y, -x, +x, +y, +z (the order in which a raster sweep over the
+// lower cell of each face reaches them), f_L and f_S clamped at 0.  FP64 without contraction.
+__device__ __forceinline__ double exchange(const double* c, const uint8_t* liquid, int64_t a, int64_t b, double k,
+                                           double cS, double cL, double dt) {
+    // transfer from the liquid cell to the solid one across face (a, b); 0 unless the phases differ
+    if (liquid[a] == liquid[b]) return 0.0;
+    const int64_t l = liquid[a] ? a : b, s = liquid[a] ? b : a;
+    const double fL = c[l] > cL ? __ddiv_rn(__dadd_rn(c[l], -cL), cL) : 0.0;
+    const double fS = c[s] < cS ? __ddiv_rn(__dadd_rn(cS, -c[s]), cS) : 0.0;
+    return __dmul_rn(__dmul_rn(__dmul_rn(k, fL), fS), dt);
+}
+
+__global__ void absorb_kernel(Grid g, const uint8_t* __restrict__ liquid, double k, double cS, double cL, double dt,
+                              const double* __restrict__ c, double* __restrict__ out) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
+        const double sgn = liquid[i] ? -1.0 : 1.0;       // the liquid side loses, the solid side gains
+        double v = c[i];
+        if (z > 0) v = __dadd_rn(v, sgn * exchange(c, liquid, i - nxy, i, k, cS, cL, dt));
+        if (y > 0) v = __dadd_rn(v, sgn * exchange(c, liquid, i - g.nx, i, k, cS, cL, dt));
+        if (x > 0) v = __dadd_rn(v, sgn * exchange(c, liquid, i - 1, i, k, cS, cL, dt));
+        if (x + 1 < g.nx) v = __dadd_rn(v, sgn * exchange(c, liquid, i, i + 1, k, cS, cL, dt));
+        if (y + 1 < g.ny) v = __dadd_rn(v, sgn * exchange(c, liquid, i, i + g.nx, k, cS, cL, dt));
+        if (z + 1 < g.nz) v = __dadd_rn(v, sgn * exchange(c, liquid, i, i + nxy, k, cS, cL, dt));
+        out[i] = v;
+    }
+}
+
+// FP64 harmonic conductances of the faces between two solid cells (+x, +y, +z of each cell).
+__global__ void solid_faces_kernel(Grid g, const double* __restrict__ D, const uint8_t* __restrict__ liquid,
+                                   double* __restrict__ gx, double* __restrict__ gy, double* __restrict__ gz) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
+        auto h = [&](int64_t j) {
+            const double a = D[i], b = D[j];
+            return (!liquid[i] && !liquid[j] && __dadd_rn(a, b) > 0.0)
+                       ? __ddiv_rn(__dmul_rn(__dmul_rn(2.0, a), b), __dadd_rn(a, b)) : 0.0;
+        };
+        gx[i] = x + 1 < g.nx ? h(i + 1) : 0.0;
+        gy[i] = y + 1 < g.ny ? h(i + g.nx) : 0.0;
+        gz[i] = z + 1 < g.nz ? h(i + nxy) : 0.0;
+    }
+}
+
+// One flux-form substep of the solid phase, FP64, faces in the order -x, +x, -y, +y, -z, +z.
+__global__ void solid_substep_kernel(Grid g, const double* __restrict__ gx, const double* __restrict__ gy,
+                                     const double* __restrict__ gz, double lam, const double* __restrict__ u,
+                                     double* __restrict__ un) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
+        const double ui = u[i];
+        double acc = 0.0;
+        if (x > 0) acc = __dadd_rn(acc, __dmul_rn(gx[i - 1], __dadd_rn(u[i - 1], -ui)));
+        if (x + 1 < g.nx) acc = __dadd_rn(acc, __dmul_rn(gx[i], __dadd_rn(u[i + 1], -ui)));
+        if (y > 0) acc = __dadd_rn(acc, __dmul_rn(gy[i - g.nx], __dadd_rn(u[i - g.nx], -ui)));
+        if (y + 1 < g.ny) acc = __dadd_rn(acc, __dmul_rn(gy[i], __dadd_rn(u[i + g.nx], -ui)));
+        if (z > 0) acc = __dadd_rn(acc, __dmul_rn(gz[i - nxy], __dadd_rn(u[i - nxy], -ui)));
+        if (z + 1 < g.nz) acc = __dadd_rn(acc, __dmul_rn(gz[i], __dadd_rn(u[i + nxy], -ui)));
+        un[i] = __dadd_rn(ui, __dmul_rn(lam, acc));
+    }
+}
+
+// Fixed-order FP64 total of the cells of one phase: block b sums chunk b, then one block sums the partials.
+__global__ void __launch_bounds__(256) phase_partial_kernel(const double* __restrict__ c, const uint8_t* __restrict__ liquid,
+                                                            int want_liquid, int64_t n, double* __restrict__ partials) {
+    __shared__ double sh[8];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = lo + chunk < n ? lo + chunk : n;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        if ((liquid[i] != 0) == (want_liquid != 0)) acc += c[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kMassBlocks) phase_final_kernel(const double* __restrict__ partials, double* __restrict__ out) {
+    __shared__ double sh[kMassBlocks / 32];
+    double v = partials[threadIdx.x];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = sh[threadIdx.x];
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0) *out = w;
+    }
 }
 
 // Eq. 7 for the step just taken: c_far = (m_in + V_far c_far - m_out) / V_far.
@@ -350,6 +455,10 @@ void coarse_release(fdirw_ctx* c) {
     p = k->pbc; dfree(p);
     p = k->far; dfree(p);
     p = k->ubuf; dfree(p);
+    p = k->gs; dfree(p);
+    p = k->tmp; dfree(p);
+    p = k->qpart; dfree(p);
+    p = k->qout; dfree(p);
     delete k;
     c->coarse = nullptr;
 }
@@ -512,6 +621,100 @@ int fdirw_read_coarse_pbc(fdirw_ctx* c, double* out) {
     DeviceGuard dg(c->device);
     FDIRW_CUDA(c, cudaMemcpyAsync(out, c->coarse->pbc, (size_t)c->coarse->nc * 8, cudaMemcpyDeviceToHost, c->stream));
     FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+    return FDIRW_OK;
+}
+
+int fdirw_coupled_step(fdirw_ctx* c, const fdirw_coupled_params* p, double* field, int32_t n_steps, double* QL,
+                       double* QS, double* c_far) {
+    if (!c || !p || !field) return fail(c, FDIRW_ERR_ARG, "NULL context, params or field");
+    if (!c->coarse || !c->coarse->open)
+        return fail(c, FDIRW_ERR_STATE, "the coupled step needs a coarse-mesh context with a far field");
+    if (n_steps < 0) return fail(c, FDIRW_ERR_ARG, "n_steps must be >= 0");
+    if (!(std::isfinite(p->k) && p->k >= 0.0) || !(std::isfinite(p->cS_eq) && p->cS_eq > 0.0) ||
+        !(std::isfinite(p->cL_eq) && p->cL_eq > 0.0) || !(std::isfinite(p->dt) && p->dt >= 0.0) || p->n_sub_solid < 0)
+        return fail(c, FDIRW_ERR_ARG, "need k >= 0, cS_eq > 0, cL_eq > 0, dt >= 0, n_sub_solid >= 0");
+    if ((reinterpret_cast<uintptr_t>(field) & 7u) != 0) return fail(c, FDIRW_ERR_ARG, "field must be 8-byte aligned");
+    DeviceGuard dg(c->device);
+    fdirw::Coarse& k = *c->coarse;
+    const Kind kf = classify(field, c->device);
+    if (kf == Kind::Foreign) return fail(c, FDIRW_ERR_ARG, "field is device memory of another device");
+    const uint64_t n = (uint64_t)c->g.n;
+    int rc;
+    const double lam_s = p->n_sub_solid > 0 ? (p->dt / p->n_sub_solid) / (c->h * c->h) : 0.0;
+    if (!k.gs) {
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.gs), 3 * n * 8, "solid faces")) != FDIRW_OK) return rc;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.tmp), 2 * n * 8, "coupled scratch")) != FDIRW_OK) return rc;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.qpart), fdirw::kMassBlocks * 8, "phase partials")) != FDIRW_OK) return rc;
+        fdirw::solid_faces_kernel<<<fdirw::grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(c->g, c->Dd, k.liquid, k.gs,
+                                                                                        k.gs + n, k.gs + 2 * n);
+        FDIRW_CUDA(c, cudaGetLastError());
+    }
+    if (lam_s > 0.0) {
+        // stability of the solid march: lam_s * max(sum of solid faces) <= 1, checked on the host once per call
+        std::vector<double> gh(3 * n);
+        FDIRW_CUDA(c, cudaMemcpyAsync(gh.data(), k.gs, 3 * n * 8, cudaMemcpyDeviceToHost, c->stream));
+        FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int nx = c->g.nx, ny = c->g.ny;
+        const int64_t nxy = (int64_t)nx * ny;
+        double mx = 0.0;
+        for (int64_t i = 0; i < c->g.n; i++) {
+            const int x = (int)(i % nx), y = (int)((i / nx) % ny);
+            const int64_t z = i / nxy;
+            double sum = gh[i] + gh[n + i] + gh[2 * n + i];
+            if (x > 0) sum += gh[i - 1];
+            if (y > 0) sum += gh[n + i - nx];
+            if (z > 0) sum += gh[2 * n + i - nxy];
+            mx = std::max(mx, sum);
+        }
+        if (lam_s * mx > 1.0 + 1e-12) return fail(c, FDIRW_ERR_UNSTABLE, "solid march unstable: raise n_sub_solid");
+    }
+    if ((QL || QS) && n_steps > k.qcap) {
+        void* q = k.qout; dfree(q); k.qout = nullptr;
+        c->allocated -= (uint64_t)k.qcap * 16;
+        k.qcap = 0;
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&k.qout), (uint64_t)n_steps * 16, "phase masses")) != FDIRW_OK) return rc;
+        k.qcap = n_steps;
+    }
+    if (!k.built) {
+        if ((rc = fdirw::coarse_kernels(c)) != FDIRW_OK) return rc;
+    }
+    double* cur = field;
+    if (kf == Kind::Host) {
+        FDIRW_CUDA(c, cudaMemcpyAsync(c->cbuf, field, n * 8, cudaMemcpyHostToDevice, c->stream));
+        cur = c->cbuf;
+    }
+    const int gb = fdirw::grid_blocks(c->g.n, 256);
+    for (int t = 0; t < n_steps; t++) {
+        fdirw::absorb_kernel<<<gb, 256, 0, c->stream>>>(c->g, k.liquid, p->k, p->cS_eq, p->cL_eq, p->dt, cur, k.tmp);
+        FDIRW_CUDA(c, cudaGetLastError());
+        double* a = k.tmp;
+        double* b = k.tmp + n;
+        for (int s = 0; s < p->n_sub_solid; s++) {
+            fdirw::solid_substep_kernel<<<gb, 256, 0, c->stream>>>(c->g, k.gs, k.gs + n, k.gs + 2 * n, lam_s, a, b);
+            FDIRW_CUDA(c, cudaGetLastError());
+            std::swap(a, b);
+        }
+        if ((rc = fdirw::coarse_step(c, a, cur, 1, nullptr)) != FDIRW_OK) return rc;
+        if (QL || QS) {
+            for (int ph = 0; ph < 2; ph++) {
+                fdirw::phase_partial_kernel<<<fdirw::kMassBlocks, 256, 0, c->stream>>>(cur, k.liquid, ph == 0, c->g.n, k.qpart);
+                fdirw::phase_final_kernel<<<1, fdirw::kMassBlocks, 0, c->stream>>>(k.qpart, k.qout + 2 * t + ph);
+                FDIRW_CUDA(c, cudaGetLastError());
+            }
+        }
+    }
+    if (kf == Kind::Host) FDIRW_CUDA(c, cudaMemcpyAsync(field, cur, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if ((QL || QS) && n_steps > 0) {
+        std::vector<double> q((size_t)n_steps * 2);
+        FDIRW_CUDA(c, cudaMemcpyAsync(q.data(), k.qout, (size_t)n_steps * 16, cudaMemcpyDeviceToHost, c->stream));
+        FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int t = 0; t < n_steps; t++) {
+            if (QL) QL[t] = q[2 * t];
+            if (QS) QS[t] = q[2 * t + 1];
+        }
+    }
+    if (c_far) FDIRW_CUDA(c, cudaMemcpyAsync(c_far, k.far, 8, cudaMemcpyDeviceToHost, c->stream));
+    if (c_far || kf == Kind::Host) FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
     return FDIRW_OK;
 }
 

@@ -32,7 +32,8 @@ EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "f
             "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc", "fdirw_net_create",
             "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
             "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius", "fdirw_create_coarse",
-            "fdirw_read_coarse", "fdirw_coarse_far_field", "fdirw_coarse_get_far_field", "fdirw_read_coarse_pbc")
+            "fdirw_read_coarse", "fdirw_coarse_far_field", "fdirw_coarse_get_far_field", "fdirw_read_coarse_pbc",
+            "fdirw_coupled_step")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -53,6 +54,11 @@ class fdirw_grid(ctypes.Structure):
 class fdirw_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("mem_limit", ctypes.c_uint64), ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fdirw_coupled_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("cS_eq", ctypes.c_double), ("cL_eq", ctypes.c_double), ("dt", ctypes.c_double),
+                ("n_sub_solid", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fdirw_info(ctypes.Structure):
@@ -117,6 +123,7 @@ def load(path: str | None = None):
         lib.fdirw_coarse_far_field.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         lib.fdirw_coarse_get_far_field.argtypes = [vp, dp]
         lib.fdirw_read_coarse_pbc.argtypes = [vp, vp]
+        lib.fdirw_coupled_step.argtypes = [vp, ctypes.POINTER(fdirw_coupled_params), vp, i32, vp, vp, dp]
         for name in EXPORTED:
             if name not in ("fdirw_destroy", "fdirw_last_error", "fdirw_net_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -395,6 +402,18 @@ class FDiRWCoarse(FDiRW):
         v = ctypes.c_double(0.0)
         _check(load().fdirw_coarse_get_far_field(ctypes.c_void_p(self.ctx), ctypes.byref(v)), ctypes.c_void_p(self.ctx))
         return v.value
+
+    def coupled_step(self, field, n_steps: int, k: float, cS_eq: float, cL_eq: float, dt: float, n_sub_solid: int):
+        """n_steps coupled macro steps in place on field; returns (QL [n], QS [n], c_far)."""
+        _check_f64(field, self.n)
+        prm = fdirw_coupled_params(float(k), float(cS_eq), float(cL_eq), float(dt), int(n_sub_solid), 0)
+        QL = np.empty(max(int(n_steps), 0))
+        QS = np.empty(max(int(n_steps), 0))
+        cf = ctypes.c_double(0.0)
+        _check(load().fdirw_coupled_step(ctypes.c_void_p(self.ctx), ctypes.byref(prm), ctypes.c_void_p(_ptr(field)),
+                                         int(n_steps), ctypes.c_void_p(QL.ctypes.data), ctypes.c_void_p(QS.ctypes.data),
+                                         ctypes.byref(cf)), ctypes.c_void_p(self.ctx))
+        return QL, QS, cf.value
 
     def read_pbc(self) -> np.ndarray:
         nb = 1

@@ -169,3 +169,54 @@ def test_far_field_errors():
             f.c_far()
         with pytest.raises(FdirwError):
             f.far_field(0.0, 1.0)
+
+
+# ------------------------------------------------------------------ coupled macro step (Eqs. 1-7)
+
+def test_coupled_steps_match_oracle():
+    shape, B, R, n_sub, V_far = (20, 18, 16), 5, 4, 20, 2000.0
+    p = synth.sphere_packing(shape, 0.45, 102, r_range=(1.5, 3.0))
+    liquid = (~p.solid).astype(np.uint8)
+    D = np.where(liquid > 0, 1.0, 1e-3)                      # effective D_m A_m / RT per phase
+    lam = 0.6 * oracle.stable_dt_sub(shape, D)
+    dt = n_sub * lam
+    kin = dict(k=1e-7, cS_eq=1.0, cL_eq=1e-5)
+    P = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub)
+    pbc = oracle.coarse_pbc(shape, D, liquid, B, lam, n_sub)
+    c0 = np.where(liquid > 0, 2e-3, 1e-6)
+    cf0 = 2e-3
+    ref, cf = c0.copy(), cf0
+    QLr, QSr = [], []
+    for _ in range(3):
+        ref, cf = oracle.coupled_step(shape, D, liquid, B, R, P, pbc, V_far, cf, kin["k"], kin["cS_eq"], kin["cL_eq"],
+                                      dt, dt / 2 / 1.0, 2, ref)
+        QLr.append(ref[liquid > 0].sum())
+        QSr.append(ref[liquid == 0].sum())
+    with FDiRWCoarse(shape, D, liquid, B, dt, R, n_sub) as f:
+        f.far_field(V_far, cf0)
+        field = torch.from_numpy(c0).to(DEV)
+        QL, QS, c_far = f.coupled_step(field, 3, kin["k"], kin["cS_eq"], kin["cL_eq"], dt, 2)
+        got = field.cpu().numpy()
+    assert _rel(got, ref) <= FIELD_TOL, _rel(got, ref)
+    assert np.allclose(QS, QSr, rtol=FIELD_TOL) and np.allclose(QL, QLr, rtol=FIELD_TOL)
+    assert abs(c_far - cf) <= FIELD_TOL * np.abs(ref).sum() / V_far
+    total0 = c0.sum() + V_far * cf0
+    assert got.sum() + V_far * c_far == pytest.approx(total0, rel=1e-12)
+    assert QS[-1] > QS[0] > (liquid == 0).sum() * 1e-6          # the solid keeps absorbing
+
+
+def test_coupled_exchange_and_solid_march_are_exact():
+    """With unit blocks and no substeps the FDiRW part is the identity, so the step is exchange + solid
+    march, both FP64 in the oracle's order: bit for bit."""
+    shape, B, R = (9, 8, 7), 1, 2
+    liquid = np.zeros(504, dtype=np.uint8)
+    liquid[::5] = 1
+    D = np.where(liquid > 0, 1.0, 0.05)
+    dt = 0.4
+    c0 = np.where(liquid > 0, 3e-5, 0.3) + synth.random_field(504, 103, 0.0, 1e-6)
+    ref = oracle.solid_march(shape, D, liquid, dt / 2, 2, oracle.absorb(shape, liquid, 0.02, 1.0, 1e-5, dt, c0))
+    with FDiRWCoarse(shape, D, liquid, B, dt, R, 0) as f:         # B = 1, n_sub = 0: the liquid step is the identity
+        f.far_field(100.0, 0.0)
+        field = c0.copy()
+        f.coupled_step(field, 1, 0.02, 1.0, 1e-5, dt, 2)
+    assert np.array_equal(field, ref)
