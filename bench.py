@@ -171,10 +171,10 @@ def march_kernel_name(prec: str, parts: int) -> str:
 
 
 # DRAM bytes (read + write) per clipped window cell of march_tm_kernel<8> with BF16 storage, from one ncu
-# capture of the 64^3 case with the same recipe (profiles/march_tm_R8_64c.md: 1.209 GB read + 3.038 GB
+# capture of the 64^3 case with the same recipe (profiles/march_tm_R8_64c.md: 1.262 GB read + 3.117 GB
 # written over 1.049e9 window cells); the traffic of a full launch scales with its window cells (the
 # stored kernel values dominate it).  Valid for that kernel, radius and storage only.
-TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL = (1.209124e9 + 3.037791e9) / 1.049e9
+TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL = (1.261629e9 + 3.116823e9) / 1.049e9
 
 
 def march_traffic(args, prec: str, parts: int, R: int, window_cells: float):
