@@ -232,3 +232,36 @@ def test_batch_argument_errors():
     bad[3] = -1.0
     with pytest.raises(FdirwError):
         FDiRWBatch([shape, shape], [D, bad], 0.1, 1, 3, 2, "fp32")
+
+
+def test_batch_workload_full_size():
+    """The benchmark's batched workload at full size (64 structures, 5.4e7 cells, chunked): one macro step,
+    the mass budget, and three structures checked against single-structure contexts bit for bit and, for
+    sampled sources of every radius, against the oracle's kernels."""
+    bw = synth.BATCH_WORKLOADS["fdirw-batch64-r3to10"]
+    shapes, Ds, cs = bw.make()
+    dt = bw.n_sub * min(oracle.stable_dt_sub(s, D) for s, D in zip(shapes, Ds))
+    c0 = torch.from_numpy(np.concatenate(cs)).to(DEV)
+    with FDiRWBatch(shapes, [torch.from_numpy(D).to(DEV) for D in Ds], dt, bw.R_min, bw.R_max, bw.n_sub, "bf16") as b:
+        out = torch.empty_like(c0)
+        m = b.step(c0, out, 1, want_mass=True)
+        info = b.info()
+        offs = b.offsets
+    assert info["n_structures"] == 64 and info["n_chunks"] >= 2
+    assert abs(m - float(c0.sum())) <= 1e-12 * float(c0.sum())
+    rng = np.random.default_rng(105)
+    for i in (0, 31, 63):
+        sl = slice(int(offs[i]), int(offs[i + 1]))
+        with FDiRWBatch([shapes[i]], [Ds[i]], dt, bw.R_min, bw.R_max, bw.n_sub, "bf16") as one:
+            single = torch.empty_like(c0[sl])
+            one.step(c0[sl].contiguous(), single, 1)
+            Rmap = one.radius()
+            src = np.concatenate([rng.choice(np.flatnonzero(Rmap == r), 2, replace=False) for r in np.unique(Rmap)])
+            ks = one.read_kernels(src)
+        assert torch.equal(out[sl], single)
+        lam = dt / bw.n_sub
+        for q, s in enumerate(src):
+            r = int(Rmap[s])
+            ref, _ = oracle.source_kernel(shapes[i], Ds[i], lam, r, bw.n_sub, int(s))
+            got = ks[q][10 - r:11 + r, 10 - r:11 + r, 10 - r:11 + r]
+            assert _rel(got, ref) <= KERNEL_TOL["bf16"], (i, s, r)

@@ -325,6 +325,25 @@ def test_workload_96_sampled(prec):
     assert np.max(np.abs(got[dests] - ref_at)) <= FIELD_TOL[prec] * np.abs(ref_at).max()
 
 
+def test_workload_256_sampled():
+    """256^3 with the 192^3 recipe (the surrogate comparison's second size), BF16 storage: sampled kernels
+    and destinations against the oracle, mass budget."""
+    w = synth.WORKLOADS["fdirw-256c-r8"]
+    _, D, c0 = w.make()
+    shape = (w.n,) * 3
+    lam = oracle.stable_dt_sub(shape, D)
+    src = _sample_sources(shape, 16, 256)
+    got, m, ks, info = _gpu_run(shape, D, lam, w.R, w.n_sub, c0, 1, "bf16", src)
+    ref, _ = oracle.kernels(shape, D, lam, w.R, w.n_sub, src)
+    err = np.linalg.norm((ks - ref).reshape(len(src), -1), axis=1) / np.linalg.norm(ref.reshape(len(src), -1), axis=1)
+    assert err.max() <= KERNEL_TOL["bf16"]
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+    N = w.n ** 3
+    dests = np.array([7, N - 8, (w.n // 2) * (1 + w.n + w.n * w.n)])
+    ref_at = _oracle_at(shape, D, lam, w.R, w.n_sub, c0, dests)
+    assert np.max(np.abs(got[dests] - ref_at)) <= FIELD_TOL["bf16"] * np.abs(ref_at).max()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_workload_192_sampled(prec):
     """192^3, porosity 0.4, D 1/1e-6, R=8, n_sub=200, c=1 in solid: the benchmark's launch configuration."""
