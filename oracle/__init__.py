@@ -103,6 +103,13 @@ def _load():
             lib.fo_absorb.restype = None
             lib.fo_solid_march.argtypes = [ctypes.c_int] * 3 + [_D, _U8, ctypes.c_double, ctypes.c_int, _D, _D]
             lib.fo_solid_march.restype = ctypes.c_int
+            lib.fo_source_kernel_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, ctypes.c_double,
+                                                                                ctypes.c_int, ctypes.c_int,
+                                                                                ctypes.c_int64, _D, _D]
+            lib.fo_source_kernel_adv.restype = ctypes.c_int
+            lib.fo_superpose_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, ctypes.c_double,
+                                                                            ctypes.c_int, ctypes.c_int, _D, _D]
+            lib.fo_superpose_adv.restype = ctypes.c_int
             lib.fo_mass.argtypes = [_D, ctypes.c_int64]
             lib.fo_mass.restype = ctypes.c_double
             _lib = lib
@@ -350,6 +357,32 @@ def coupled_step(shape, D, liquid, B: int, R: int, P_band, PBC, V_far: float, c_
     c1 = absorb(shape, liquid, k, cS_eq, cL_eq, dt, c)
     c2 = solid_march(shape, D, liquid, lam_s, n_sub_s, c1)
     return coarse_step_far(shape, liquid, B, R, P_band, PBC, V_far, c_far, c2)
+
+
+def source_kernel_adv(shape, D, w, lam: float, lama: float, R: int, n_sub: int, s: int):
+    """(kernel, mass_before) with convection: w = (wx, wy, wz) face velocities (+a face of each cell),
+    lama = dt_sub / h; kernel indexed [oz+R, oy+R, ox+R]."""
+    g = Conductance(shape, D)
+    wx, wy, wz = (_f64(a).reshape(-1) for a in w)
+    W1 = 2 * R + 1
+    out = np.empty(W1 ** 3, dtype=np.float64)
+    m = ctypes.c_double(0.0)
+    if _load().fo_source_kernel_adv(*g.args, _p(wx), _p(wy), _p(wz), float(lam), float(lama), int(R), int(n_sub),
+                                    int(s), _p(out), ctypes.byref(m)) != 0:
+        raise ValueError("fo_source_kernel_adv rejected its arguments")
+    return out.reshape(W1, W1, W1), m.value
+
+
+def superpose_adv(shape, D, w, lam: float, lama: float, R: int, n_sub: int, c) -> np.ndarray:
+    """One macro step of Eq. 8 whose kernels include the upwind convection of face velocities w."""
+    g = Conductance(shape, D)
+    wx, wy, wz = (_f64(a).reshape(-1) for a in w)
+    c = _f64(c).reshape(-1)
+    out = np.empty_like(c)
+    if _load().fo_superpose_adv(*g.args, _p(wx), _p(wy), _p(wz), float(lam), float(lama), int(R), int(n_sub),
+                                _p(c), _p(out)) != 0:
+        raise ValueError("fo_superpose_adv failed")
+    return out
 
 
 def full_march(shape, D, lam: float, n_sub: int, c, cond: Conductance | None = None) -> np.ndarray:

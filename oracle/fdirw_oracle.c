@@ -596,6 +596,120 @@ int fo_solid_march(int nx, int ny, int nz, const double* D, const uint8_t* liqui
     return 0;
 }
 
+/* ---- Convection (Sec. 5: a steady flow folded into the computation of p).  Reading: w[a][i] is the
+ * velocity through the +a face of cell i (toward +a when positive), the advective flux through a face is
+ * upwind, lam_a (w+ u_lower - w- u_upper) from the lower cell to the upper one with lam_a = dt_sub / h,
+ * and it adds to the diffusive flux of box_substep.  Faces on a window's or the domain's edge carry
+ * neither. */
+static void box_substep_adv(int nx, int ny, const double* gx, const double* gy, const double* gz,
+                            const double* wx, const double* wy, const double* wz, double lam, double lama,
+                            int x0, int y0, int z0, int bx, int by, int bz, const double* u, double* un)
+{
+    for (int l = 0; l < bz; l++)
+        for (int j = 0; j < by; j++)
+            for (int i = 0; i < bx; i++) {
+                int64_t li = i + (int64_t)bx * (j + (int64_t)by * l);
+                int64_t gi = IDX(x0 + i, y0 + j, z0 + l, nx, ny);
+                int64_t sy = nx, sz = (int64_t)nx * ny, ly = bx, lz = (int64_t)bx * by;
+                double ui = u[li], acc = 0.0, adv = 0.0;
+                if (i > 0) {
+                    acc += gx[gi - 1] * (u[li - 1] - ui);
+                    double w = wx[gi - 1];
+                    adv += (w > 0.0 ? w * u[li - 1] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
+                }
+                if (i + 1 < bx) {
+                    acc += gx[gi] * (u[li + 1] - ui);
+                    double w = wx[gi];
+                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + 1] : 0.0);
+                }
+                if (j > 0) {
+                    acc += gy[gi - sy] * (u[li - ly] - ui);
+                    double w = wy[gi - sy];
+                    adv += (w > 0.0 ? w * u[li - ly] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
+                }
+                if (j + 1 < by) {
+                    acc += gy[gi] * (u[li + ly] - ui);
+                    double w = wy[gi];
+                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + ly] : 0.0);
+                }
+                if (l > 0) {
+                    acc += gz[gi - sz] * (u[li - lz] - ui);
+                    double w = wz[gi - sz];
+                    adv += (w > 0.0 ? w * u[li - lz] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
+                }
+                if (l + 1 < bz) {
+                    acc += gz[gi] * (u[li + lz] - ui);
+                    double w = wz[gi];
+                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + lz] : 0.0);
+                }
+                un[li] = ui + lam * acc + lama * adv;
+            }
+}
+
+/* Spreading kernel with convection: fo_source_kernel with box_substep_adv (renormalised the same way). */
+int fo_source_kernel_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                         const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
+                         int n_sub, int64_t s, double* k_out, double* mass_before)
+{
+    if (R < 0 || n_sub < 0 || s < 0 || s >= (int64_t)nx * ny * nz) return -1;
+    int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
+    int x0 = sx - R < 0 ? 0 : sx - R, x1 = sx + R > nx - 1 ? nx - 1 : sx + R;
+    int y0 = sy - R < 0 ? 0 : sy - R, y1 = sy + R > ny - 1 ? ny - 1 : sy + R;
+    int z0 = sz - R < 0 ? 0 : sz - R, z1 = sz + R > nz - 1 ? nz - 1 : sz + R;
+    int bx = x1 - x0 + 1, by = y1 - y0 + 1, bz = z1 - z0 + 1;
+    int64_t nb = (int64_t)bx * by * bz;
+    double* u = (double*)calloc((size_t)nb, sizeof(double));
+    double* un = (double*)calloc((size_t)nb, sizeof(double));
+    if (!u || !un) { free(u); free(un); return -1; }
+    u[(sx - x0) + (int64_t)bx * ((sy - y0) + (int64_t)by * (sz - z0))] = 1.0;
+    for (int k = 0; k < n_sub; k++) {
+        box_substep_adv(nx, ny, gx, gy, gz, wx, wy, wz, lam, lama, x0, y0, z0, bx, by, bz, u, un);
+        double* t = u; u = un; un = t;
+    }
+    double m = 0.0;
+    for (int64_t q = 0; q < nb; q++) m += u[q];
+    if (mass_before) *mass_before = m;
+    int W1 = 2 * R + 1;
+    memset(k_out, 0, sizeof(double) * (size_t)W1 * W1 * W1);
+    for (int l = 0; l < bz; l++)
+        for (int j = 0; j < by; j++)
+            for (int i = 0; i < bx; i++) {
+                int ox = x0 + i - sx, oy = y0 + j - sy, oz = z0 + l - sz;
+                k_out[(ox + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (oz + R))] =
+                    u[i + (int64_t)bx * (j + (int64_t)by * l)] / m;
+            }
+    free(u); free(un);
+    return 0;
+}
+
+/* Eq. 8 with convection: c_out = sum_s c_in(s) k_s (scatter), kernels from fo_source_kernel_adv. */
+int fo_superpose_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                     const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
+                     int n_sub, const double* c_in, double* c_out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int W1 = 2 * R + 1;
+    double* k = (double*)malloc(sizeof(double) * (size_t)W1 * W1 * W1);
+    if (!k) return -1;
+    memset(c_out, 0, sizeof(double) * (size_t)N);
+    for (int64_t s = 0; s < N; s++) {
+        if (fo_source_kernel_adv(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, R, n_sub, s, k, NULL) != 0) {
+            free(k);
+            return -1;
+        }
+        int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
+        for (int oz = -R; oz <= R; oz++)
+            for (int oy = -R; oy <= R; oy++)
+                for (int ox = -R; ox <= R; ox++) {
+                    int x = sx + ox, y = sy + oy, z = sz + oz;
+                    if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) continue;
+                    c_out[IDX(x, y, z, nx, ny)] += c_in[s] * k[(ox + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (oz + R))];
+                }
+    }
+    free(k);
+    return 0;
+}
+
 int fo_full_march(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                   double lam, int n_sub, const double* c_in, double* c_out)
 {
