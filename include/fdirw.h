@@ -271,6 +271,21 @@ typedef struct {
 FDIRW_API int fdirw_coupled_step(fdirw_ctx* ctx, const fdirw_coupled_params* params, double* field, int32_t n_steps,
                                  double* QL, double* QS, double* c_far);
 
+/* Convection (Sec. 5, where a steady flow is said to change only the computation of the spreading
+ * kernels p, not the superposition of Eq. 8).  w: 3 * n_cells float64 (host or device, 8-byte aligned),
+ * w[a * n_cells + i] the velocity through the +a face of cell i (a = 0, 1, 2 for x, y, z; positive toward
+ * +a; the value on a cell of the last plane of axis a is ignored).  Every substep of the per-source march
+ * then carries, across each interior face, the diffusive flux lam g (u_lower - u_upper) plus the upwind
+ * advective flux lam_a (w+ u_lower - w- u_upper), lam = dt_sub / h^2, lam_a = dt_sub / h, w+ = max(w, 0),
+ * w- = max(-w, 0); window and domain edges stay closed.  The face coefficients are rounded once to FP32
+ * and the march runs mapping 5 (direction-dependent faces); the superposition is unchanged.  A second
+ * call replaces the velocity; the kernels are recomputed by the next fdirw_kernels / fdirw_step.  With
+ * w = 0 the kernels and steps are bit for bit those without a velocity.  Synchronises the context
+ * stream.  Errors: FDIRW_ERR_ARG (NULL or misaligned w, a batch or coarse context, FDIRW_FP64
+ * precision), FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
+ * any, stays in place), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_set_velocity(fdirw_ctx* ctx, const double* w);
+
 /* Window radius of every source (n_cells int32 values, host): the radius rule's value for batch
  * contexts, window_R for fdirw_create contexts.  Synchronises the context stream. */
 FDIRW_API int fdirw_read_radius(fdirw_ctx* ctx, int32_t* out);

@@ -11,8 +11,8 @@ diffusion is marched over a local window for one macro step to give that source'
 from . import synth  # noqa: F401
 from .fdirw import (FDiRW, FDiRWBatch, FDiRWCoarse, FdirwError, Net, PRECISIONS, fdirw_create,  # noqa: F401
                     fdirw_create_batch, fdirw_create_coarse, fdirw_read_coarse, fdirw_destroy, fdirw_get_info, fdirw_kernels, fdirw_last_error, fdirw_mass, fdirw_read_kernels,
-                    fdirw_read_radius, fdirw_stable_dt, fdirw_step)
+                    fdirw_read_radius, fdirw_set_velocity, fdirw_stable_dt, fdirw_step)
 
 __all__ = ["FDiRW", "FDiRWBatch", "FDiRWCoarse", "FdirwError", "Net", "PRECISIONS", "fdirw_create", "fdirw_create_batch",
            "fdirw_create_coarse", "fdirw_read_coarse", "fdirw_destroy", "fdirw_get_info", "fdirw_kernels", "fdirw_last_error", "fdirw_mass", "fdirw_read_kernels",
-           "fdirw_read_radius", "fdirw_stable_dt", "fdirw_step", "synth"]
+           "fdirw_read_radius", "fdirw_set_velocity", "fdirw_stable_dt", "fdirw_step", "synth"]

@@ -120,6 +120,7 @@ void release(fdirw_ctx* c) {
     fdirw::batch_release(c);
     fdirw::coarse_release(c);
     for (auto& p : c->coef) dfree(p);
+    for (auto& p : c->coefb) dfree(p);
     dfree(c->Q);
     void* p;
     p = c->sigma; dfree(p); c->sigma = nullptr;
@@ -299,6 +300,11 @@ int fdirw_kernels(fdirw_ctx* c) {
     a.src_begin = 0;
     a.src_end = c->g.n;
     a.list = nullptr;
+    if (c->flow) {                                    // convection: direction-dependent faces (mapping 5)
+        a.bx = reinterpret_cast<const float*>(c->coefb[0]);
+        a.by = reinterpret_cast<const float*>(c->coefb[1]);
+        a.bz = reinterpret_cast<const float*>(c->coefb[2]);
+    }
     FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     FDIRW_CUDA(c, fdirw::launch_march(a, c->num_sms, c->parts_req, c->stream, &c->parts_used));
     FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));

@@ -26,6 +26,8 @@ struct fdirw_ctx {
     int parts_req = 0, parts_used = 0;
     uint64_t mem_limit = 0, allocated = 0;
     void* coef[3] = {nullptr, nullptr, nullptr};   // lam * g: float (mixed) or double (FP64)
+    void* coefb[3] = {nullptr, nullptr, nullptr};  // convection: upper-into-lower face coefficients (flow.cu)
+    bool flow = false;                              // coef / coefb hold direction-dependent coefficients
     void* Q = nullptr;
     uint64_t q_bytes = 0;
     double* sigma = nullptr;

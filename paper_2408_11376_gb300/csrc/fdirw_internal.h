@@ -67,6 +67,9 @@ struct MarchArgs {
     const int32_t* ccount;       // coarse_n: liquid cells per block
     double* Qc;                  // (2 Rc + 1)^3 planes of coarse_n values, destination-indexed
     const float* abnd;           // nullable: lam * open-face conductance of each cell (far-field boundary)
+    // Convection (nullable; mapping 5 only): ax/ay/az then hold the coefficient of the lower cell in the
+    // upper cell's update across each +face, bx/by/bz that of the upper cell in the lower cell's update.
+    const float* bx; const float* by; const float* bz;
 };
 // Coarse-mesh march of the blocks a.list[src_begin..src_end): window radius R = window_R + (B - 1) / 2
 // (1..10), one source per CTA.

@@ -777,7 +777,10 @@ __device__ void coarse_epilogue(const MarchArgs& a, const float* sbuf, double* S
 // centre cell (radius R = window_R + (B - 1) / 2), the march starts from 1 on the block's liquid cells,
 // and the epilogue maps the marched field onto the blocks of the window (column J of the coarse matrix,
 // written destination-indexed) instead of storing a kernel.
-template <int R, bool COARSE>
+// ADV: the face coefficients differ by direction (convection): a.ax/ay/az hold the coefficient of the
+// lower cell in the upper cell's update and a.bx/by/bz that of the upper cell in the lower one's; the
+// diagonal is minus the sum of the cell's outflow coefficients.  Without ADV both are a.ax/ay/az.
+template <int R, bool COARSE, bool ADV>
 __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchArgs a) {
     using M = MapTmc<R>;
     constexpr int W1 = M::W1, COLS = M::COLS, NG = M::NG, BUF = M::BUF;
@@ -842,7 +845,11 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
         const bool col_ok = src_ok && x >= 0 && x < nx && y >= 0 && y < ny;
 
         float u[W1], am[W1], cz[W1];
-        float zprev = 0.f;
+        float czb[ADV ? W1 : 1];              // ADV: coefficient of the upper z neighbour (cz: of the lower)
+        float zprev = 0.f, zprevb = 0.f;
+        const float* bxp = ADV ? a.bx + L.base : nullptr;
+        const float* byp = ADV ? a.by + L.base : nullptr;
+        const float* bzp = ADV ? a.bz + L.base : nullptr;
 #pragma unroll
         for (int g = 0; g < NG; g++) {
             uint32_t w[16];
@@ -850,6 +857,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
             for (int q = 0; q < 4; q++) {
                 const int k = 4 * g + q;
                 float vxm = 0.f, vxp = 0.f, vym = 0.f, vyp = 0.f, vz = 0.f;
+                float oxm = 0.f, oxp = 0.f, oym = 0.f, oyp = 0.f, vzb = 0.f;   // ADV: outflows, upper-z inflow
                 if (k < W1) {
                     const int z = sz - R + k;
                     const bool ok = col_ok && z >= 0 && z < nz;
@@ -860,16 +868,30 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                         if (COARSE && a.liquid[i] && abs(ci - R) <= bh && abs(cj - R) <= bh && abs(k - R) <= bh) u0 = 1.f;
                         if (COARSE && a.abnd) vb = __ldg(a.abnd + i);
                         if (ci > 0 && x > 0) vxm = __ldg(ax + i - 1);
-                        if (ci < 2 * R && x + 1 < nx) vxp = __ldg(ax + i);
+                        if (ci < 2 * R && x + 1 < nx) vxp = __ldg(ADV ? bxp + i : ax + i);
                         if (cj > 0 && y > 0) vym = __ldg(ay + i - nx);
-                        if (cj < 2 * R && y + 1 < ny) vyp = __ldg(ay + i);
+                        if (cj < 2 * R && y + 1 < ny) vyp = __ldg(ADV ? byp + i : ay + i);
                         if (k < 2 * R && z + 1 < nz) vz = __ldg(az + i);
+                        if constexpr (ADV) {
+                            if (ci > 0 && x > 0) oxm = __ldg(bxp + i - 1);
+                            if (ci < 2 * R && x + 1 < nx) oxp = __ldg(ax + i);
+                            if (cj > 0 && y > 0) oym = __ldg(byp + i - nx);
+                            if (cj < 2 * R && y + 1 < ny) oyp = __ldg(ay + i);
+                            if (k < 2 * R && z + 1 < nz) vzb = __ldg(bzp + i);
+                        }
                     }
                     cz[k < W1 ? k : 0] = vz;
-                    if constexpr (COARSE)
+                    if constexpr (ADV) {
+                        // outflow through the -z face: the lower cell's upper-z inflow coefficient
+                        czb[k < W1 ? k : 0] = vzb;
+                        const float diag = ((oxm + oxp) + (oym + oyp)) + (zprevb + vz);
+                        am[k < W1 ? k : 0] = COARSE ? -(diag + vb) : -diag;
+                        zprevb = vzb;
+                    } else if constexpr (COARSE) {
                         am[k < W1 ? k : 0] = -((((vxm + vxp) + (vym + vyp)) + (zprev + vz)) + vb);
-                    else
+                    } else {
                         am[k < W1 ? k : 0] = -(((vxm + vxp) + (vym + vyp)) + (zprev + vz));
+                    }
                     u[k < W1 ? k : 0] = u0;
                     zprev = vz;
                 }
@@ -911,7 +933,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                         v = fmaf(cym, buf[ym + k], v);
                         v = fmaf(cyp, buf[yp + k], v);
                         v = fmaf(k > 0 ? cz[k > 0 ? k - 1 : 0] : 0.f, prev, v);
-                        v = fmaf(cz[k], k + 1 < W1 ? u[k + 1 < W1 ? k + 1 : k] : 0.f, v);
+                        v = fmaf(ADV ? czb[ADV ? k : 0] : cz[k], k + 1 < W1 ? u[k + 1 < W1 ? k + 1 : k] : 0.f, v);
                         prev = cur;
                         u[k] = __fadd_rn(cur, v);
                     }
@@ -964,19 +986,19 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr) : "memory");
 }
 
-template <int R, bool COARSE = false>
+template <int R, bool COARSE = false, bool ADV = false>
 cudaError_t launch_tmc(const MarchArgs& a, int num_sms, cudaStream_t st) {
     using M = MapTmc<R>;
     const int64_t nsrc = a.src_end - a.src_begin;
     if (nsrc <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(march_tmc_kernel<R, COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(COARSE ? M::SMEM_COARSE : M::SMEM));
+    cudaError_t e = cudaFuncSetAttribute(march_tmc_kernel<R, COARSE, ADV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(COARSE ? M::SMEM_COARSE : M::SMEM));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmc_kernel<R, COARSE>, M::THREADS, (COARSE ? M::SMEM_COARSE : M::SMEM));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmc_kernel<R, COARSE, ADV>, M::THREADS, (COARSE ? M::SMEM_COARSE : M::SMEM));
     if (e != cudaSuccess) return e;
     if (per_sm != 1) return cudaErrorInvalidConfiguration;   // TMEM allocation assumes one CTA per SM
     const int64_t grid = nsrc < (int64_t)num_sms ? nsrc : (int64_t)num_sms;
-    march_tmc_kernel<R, COARSE><<<(unsigned)grid, M::THREADS, (COARSE ? M::SMEM_COARSE : M::SMEM), st>>>(a);
+    march_tmc_kernel<R, COARSE, ADV><<<(unsigned)grid, M::THREADS, (COARSE ? M::SMEM_COARSE : M::SMEM), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1258,7 +1280,7 @@ cudaError_t launch_f32_p(const MarchArgs& a, int P, int num_sms, cudaStream_t st
         case 2: return launch_f32<R, 2>(a, num_sms, st);
         case 3: return launch_f32<R, 3>(a, num_sms, st);
         case 4: return launch_tm<R>(a, num_sms, st);
-        case 5: return launch_tmc<R>(a, num_sms, st);
+        case 5: return a.bx ? launch_tmc<R, false, true>(a, num_sms, st) : launch_tmc<R>(a, num_sms, st);
         case 6: return launch_tmp<R>(a, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
@@ -1305,8 +1327,10 @@ cudaError_t dispatch(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
         case 6: return launch_f32_p<6>(a, P, num_sms, st);
         case 7: return launch_f32_p<7>(a, P, num_sms, st);
         case 8: return launch_f32_p<8>(a, P, num_sms, st);
-        case 9: return P == 5 ? launch_tmc<9>(a, num_sms, st) : P == 4 ? launch_tm<9>(a, num_sms, st) : cudaErrorInvalidValue;
-        case 10: return P == 5 ? launch_tmc<10>(a, num_sms, st) : P == 4 ? launch_tm<10>(a, num_sms, st) : cudaErrorInvalidValue;
+        case 9: return P == 5 ? (a.bx ? launch_tmc<9, false, true>(a, num_sms, st) : launch_tmc<9>(a, num_sms, st))
+                       : P == 4 ? launch_tm<9>(a, num_sms, st) : cudaErrorInvalidValue;
+        case 10: return P == 5 ? (a.bx ? launch_tmc<10, false, true>(a, num_sms, st) : launch_tmc<10>(a, num_sms, st))
+                        : P == 4 ? launch_tm<10>(a, num_sms, st) : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1395,6 +1419,10 @@ cudaError_t launch_march_coarse(const MarchArgs& a, int R, int num_sms, cudaStre
 
 cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts_used) {
     int P = 1;
+    if (a.bx && a.store != Store::F64) {          // direction-dependent coefficients: mapping 5 only
+        if (parts_used) *parts_used = 5;
+        return dispatch(a, 5, num_sms, st);
+    }
     if (a.store != Store::F64) {
         if (parts_req >= 1 && parts_req <= 6 && (a.R <= 8 || parts_req == 4 || parts_req == 5)) {
             P = parts_req;

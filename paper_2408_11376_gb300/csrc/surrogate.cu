@@ -663,7 +663,7 @@ FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t
 
 FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* c, fdirw_net* net, int64_t* accepted_out) {
     if (!c || !net) return nfail(net, FDIRW_ERR_ARG, "NULL ctx or net");
-    if (c->batch || c->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (c->batch || c->coarse || c->flow) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves diffusion-only fdirw_create contexts");
     if (c->R != SH) return nfail(net, FDIRW_ERR_ARG, "the surrogate predicts 17^3 kernels: window_R must be 8");
     if (c->store == Store::F64) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves the FP32-march precisions only");
     {

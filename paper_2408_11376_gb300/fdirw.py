@@ -33,7 +33,7 @@ EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "f
             "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
             "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius", "fdirw_create_coarse",
             "fdirw_read_coarse", "fdirw_coarse_far_field", "fdirw_coarse_get_far_field", "fdirw_read_coarse_pbc",
-            "fdirw_coupled_step")
+            "fdirw_coupled_step", "fdirw_set_velocity")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -124,6 +124,7 @@ def load(path: str | None = None):
         lib.fdirw_coarse_get_far_field.argtypes = [vp, dp]
         lib.fdirw_read_coarse_pbc.argtypes = [vp, vp]
         lib.fdirw_coupled_step.argtypes = [vp, ctypes.POINTER(fdirw_coupled_params), vp, i32, vp, vp, dp]
+        lib.fdirw_set_velocity.argtypes = [vp, vp]
         for name in EXPORTED:
             if name not in ("fdirw_destroy", "fdirw_last_error", "fdirw_net_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -305,6 +306,19 @@ def fdirw_mass_noalloc(c, mass_out, stream=None) -> None:
                                      ctypes.c_void_p(st)))
 
 
+def fdirw_set_velocity(ctx: int, w, n: int) -> None:
+    """Face velocities w (3 * n float64, host or device; w[a * n + i] through the +a face of cell i)."""
+    if hasattr(w, "data_ptr"):
+        if str(w.dtype) != "torch.float64" or w.numel() != 3 * n:
+            raise ValueError("w must be a float64 tensor of 3 * n_cells values")
+        _check(load().fdirw_set_velocity(ctypes.c_void_p(ctx), ctypes.c_void_p(_ptr(w))), ctx)
+        return
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+    if a.size != 3 * n:
+        raise ValueError("w must hold 3 * n_cells values")
+    _check(load().fdirw_set_velocity(ctypes.c_void_p(ctx), ctypes.c_void_p(a.ctypes.data)), ctx)
+
+
 def fdirw_last_error(ctx: int | None = None) -> str:
     m = load().fdirw_last_error(ctypes.c_void_p(ctx) if ctx else None)
     return m.decode() if m else ""
@@ -337,6 +351,10 @@ class FDiRW:
 
     def read_kernels(self, sources) -> np.ndarray:
         return fdirw_read_kernels(self.ctx, sources, self.R)
+
+    def set_velocity(self, w):
+        """Steady face velocities (3, n) or (3 * n,) float64, host or device (Sec. 5 convection)."""
+        fdirw_set_velocity(self.ctx, w, self.n)
 
     def info(self) -> dict:
         return fdirw_get_info(self.ctx)

@@ -143,6 +143,22 @@ def random_diffusivity(shape, seed: int, decades: float = 6.0, d_max: float = 1.
     return d_max * np.power(10.0, -rng.uniform(0.0, decades, size=nx * ny * nz))
 
 
+def face_velocity(shape, seed: int, mean=(0.0, 0.0, 0.0), amp: float = 0.0, solid=None) -> np.ndarray:
+    """A seeded steady face-velocity field, (3, n): a uniform mean flow plus independent uniform noise in
+    [-amp, amp] on every face, w[a, i] through the +a face of cell i; zero on faces touching a solid cell
+    when a solid mask is given (the flow runs in the pore space)."""
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    rng = np.random.default_rng(seed)
+    w = np.asarray(mean, dtype=np.float64)[:, None] + rng.uniform(-amp, amp, size=(3, n))
+    if solid is not None:
+        sol = np.asarray(solid, dtype=bool).reshape(nz, ny, nx)
+        for a, axis in enumerate((2, 1, 0)):
+            touch = sol | np.roll(sol, -1, axis=axis)        # cell i or its +a neighbour is solid
+            w[a][touch.reshape(-1)] = 0.0
+    return w
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """One synthetic FDiRW workload: geometry, diffusivity recipe, method parameters, initial field."""
