@@ -549,6 +549,8 @@ def run_ours(args, w):
         line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec)
     if args.coarse:
         line["coarse_mesh"] = coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, ~packing.solid, dt_macro)
+    if args.flow:
+        line["convection"] = flow_leg(args, fdirw, torch, dev, stream, w, shape, D, packing.solid, dt_macro)
     if args.coupled:
         line["coupled"] = coupled_leg(args, fdirw, torch, dev, stream, w, shape, D, ~packing.solid, dt_macro)
     print(json.dumps(line), flush=True)
@@ -713,6 +715,55 @@ def coupled_leg(args, fdirw, torch, dev, stream, w, shape, D, liquid, dt_macro):
             "Q_L": [QL[0], QL[-1]], "Q_S": [QS[0], QS[-1]], "c_far_after": c_far, "total_rel_err": abs(total - total0) / total0}
 
 
+def flow_leg(args, fdirw, torch, dev, stream, w, shape, D, solid, dt_macro):
+    """Convection (Sec. 5): a steady face-velocity field folded into every source's march (upwind faces,
+    mapping 5), the superposition unchanged.  Flow: a mean of 0.03 cells per unit time along +x plus
+    uniform noise of 0.03 on every face, zero on faces touching a solid cell; n_sub raised by a tenth so
+    that the diffusive part leaves room for the advective outflow within the same macro step.  Field: a
+    Gaussian blob (sigma 10 cells) on the pore cells.  Times create + velocity + kernels + macro steps
+    with the flow, and the same n_sub on mapping 5 without it (the march's cost of the upwind faces)."""
+    from paper_2408_11376_gb300 import synth
+    n_sub = -(-11 * w.n_sub // 10)
+    N = shape[0] * shape[1] * shape[2]
+    vel = torch.from_numpy(synth.face_velocity(shape, w.seed + 40, (0.03, 0.0, 0.0), 0.03, solid).reshape(-1)).to(dev)
+    n = shape[0]
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r2 = ((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - n / 2) ** 2).reshape(-1)
+    c_in = torch.from_numpy(np.where(solid, 0.0, np.exp(-r2 / (2 * 10.0 ** 2)))).to(dev)
+    xs = torch.from_numpy(x.reshape(-1).astype(np.float64)).to(dev)
+    res = {}
+    for flow in (True, False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        out = torch.empty_like(c_in)
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, n_sub, args.prec, device=dev.index, stream=stream,
+                                     march_parts=5)
+            if flow:
+                fdirw.fdirw_set_velocity(ctx, vel, N)
+            ev[1].record(stream)
+            fdirw.fdirw_kernels(ctx)
+            ev[2].record(stream)
+            mass = fdirw.fdirw_step(ctx, c_in, out, w.steps, want_mass=True)
+            ev[3].record(stream)
+            info = fdirw.fdirw_get_info(ctx)
+            fdirw.fdirw_destroy(ctx)
+        stream.synchronize()
+        res[flow] = (ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]), info, mass,
+                     float((out * xs).sum().item() / out.sum().item()))
+    job_ms, build_ms, steps_ms, info, mass, xc = res[True]
+    mass0 = float(c_in.sum().item())
+    roof = fp32_alu_roofline(torch, dev, n_sub, info["window_cells"], info["kernels_ms"], None, {},
+                             "march_tmc_kernel<R, ADV>")
+    return {"n_sub": n_sub, "velocity": "mean 0.03 along +x, noise 0.03, 0 on solid faces",
+            "macro_steps_per_s": 1000.0 * w.steps / job_ms, "job_ms": job_ms, "kernels_ms": build_ms,
+            "steps_ms": steps_ms, "march_kernel_ms": info["kernels_ms"],
+            "march_kernel_ms_no_flow_same_mapping": res[False][3]["kernels_ms"],
+            "march_tflops": roof["achieved"], "march_frac_fp32": roof["frac"],
+            "mass_rel_err": abs(mass - mass0) / mass0,
+            "x_centroid_shift_vs_no_flow_cells": xc - res[False][5]}
+
+
 def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
     """The plain FP64 GPU FDiRW (FP64 march, FP64 cache, FP64 gather) run once over the workload, timed
     with CUDA events, keeping its field after every macro step; then every reduced-precision mode is run
@@ -780,6 +831,8 @@ def main(argv=None):
                     help="also run the coarse-mesh FDiRW with this odd block side (e.g. 5) and compare it with the fine path")
     ap.add_argument("--coupled", action="store_true",
                     help="also run the coupled macro step (exchange, solid march, coarse FDiRW with far field)")
+    ap.add_argument("--flow", action="store_true",
+                    help="also time the convection path (steady face velocities folded into the march)")
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
     ap.add_argument("--march-parts", type=int, default=0,
                     help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "
