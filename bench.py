@@ -436,7 +436,7 @@ def run_ours(args, w):
         with torch.cuda.stream(stream):
             ev[0].record(stream)
             ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream,
-                                       march_parts=args.march_parts)
+                                       march_parts=args.march_parts, accum=args.accum)
             ev[1].record(stream)
             fdirw.fdirw_kernels(ctx)
             ev[2].record(stream)
@@ -484,7 +484,7 @@ def run_ours(args, w):
         def e2e_pass():
             with torch.cuda.stream(stream):
                 ctx = fdirw.fdirw_create(shape, Dp, dt_macro, w.R, w.n_sub, prec, device=local, stream=stream,
-                                       march_parts=args.march_parts)
+                                       march_parts=args.march_parts, accum=args.accum)
                 fdirw.fdirw_step(ctx, cp, op, w.steps, want_mass=True)
                 fdirw.fdirw_destroy(ctx)
 
@@ -526,13 +526,16 @@ def run_ours(args, w):
                          "recomputing every kernel each step"}
 
     n_launch = 4 + 1 + 2 + 2 * w.steps + 2      # conductance + 3 coef, march, mass(in), scale+gather per step, mass(out)
+    if args.accum == "fp32":
+        n_launch += 2 + 3 * w.steps             # the input's FP64 total, then the mass restoration per step
     value = job_rate(ws, w.steps * args.steps, total_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": w.name, "grid": f"{w.n}^3", "R": w.R, "n_sub": w.n_sub, "macro_steps": w.steps,
-                   "prec": prec, "porosity": w.porosity, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "prec": prec, "accum": args.accum, "porosity": w.porosity,
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
                    "march_threads_per_column": info["march_parts"],
                    "l2": f"inputs larger than L2 (kernel cache {info['cache_bytes'] / 1e9:.1f} GB, read every step)"},
         "source_kernels_per_s": N / (march_ms * 1e-3),
@@ -791,9 +794,9 @@ def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
            "steps_ms": ev[2].elapsed_time(ev[3]), "cache_gb": info["cache_bytes"] / 1e9, "rel_l2_vs_fp64": {}}
     mass0 = float(c0.sum().item())
     out["mass_rel_err"] = abs(float(ref[-1].sum().item()) - mass0) / mass0
-    for p in ("fp32", "fp16", "bf16"):
+    for p, acc in (("fp32", "ff"), ("fp16", "ff"), ("bf16", "ff"), ("fp32", "fp32"), ("bf16", "fp32")):
         with torch.cuda.stream(stream):
-            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, p, stream=stream)
+            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, p, stream=stream, accum=acc)
             a = torch.empty_like(c0)
             errs = []
             cur = c0
@@ -803,7 +806,8 @@ def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
                 cur = a.clone()
             m = fdirw.fdirw_mass(ctx, a)
             fdirw.fdirw_destroy(ctx)
-        out["rel_l2_vs_fp64"][p] = {"max_over_steps": max(errs), "last": errs[-1], "mass_rel_err": abs(m - mass0) / mass0}
+        out["rel_l2_vs_fp64"][p if acc == "ff" else p + "_fp32acc"] = {
+            "max_over_steps": max(errs), "last": errs[-1], "mass_rel_err": abs(m - mass0) / mass0}
     del ref
     torch.cuda.empty_cache()
     return out
@@ -831,6 +835,8 @@ def main(argv=None):
                     help="also run the coarse-mesh FDiRW with this odd block side (e.g. 5) and compare it with the fine path")
     ap.add_argument("--coupled", action="store_true",
                     help="also run the coupled macro step (exchange, solid march, coarse FDiRW with far field)")
+    ap.add_argument("--accum", choices=["ff", "fp32"], default="ff",
+                    help="superposition accumulation: float-float rows, or FP32 rows with the mass restored")
     ap.add_argument("--flow", action="store_true",
                     help="also time the convection path (steady face velocities folded into the march)")
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")

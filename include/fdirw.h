@@ -65,6 +65,21 @@ typedef enum {
     FDIRW_FP32_STORE_BF16 = 3   /* FP32 march, BF16 storage of the kernel cache, same renorm/accumulation */
 } fdirw_prec;
 
+/* Accumulation of the superposition for the FP32-march precisions (fdirw_opts.accum; Sec. 3.3: the
+ * products in the storage precision, the sums in a higher one).  Both keep the fixed summation order, so
+ * results are reproducible bit for bit. */
+typedef enum {
+    FDIRW_ACCUM_FF   = 0,  /* every row of 2R+1 products summed as an error-free FP32 pair (exact products,
+                              TwoSum), the rows of a destination as a double-float pair: within a few 1e-15
+                              of FP64 summation; the total mass follows from the per-source renormalisation */
+    FDIRW_ACCUM_FP32 = 1   /* FP32 products and FP32 sums along each row (2 operations per term, so the
+                              step runs at the HBM rate of the cache stream), the rows as a double-float
+                              pair; the rounding of the row sums is not mass-neutral, so after every macro
+                              step the field's FP64 total is restored to the total of the call's input:
+                              c'(x) += (M_in - S) |c'(x)| / A with S = sum c', A = sum |c'| (FP64,
+                              fixed order), a change of the size of the FP32 rounding (~1e-8 relative) */
+} fdirw_accum;
+
 typedef struct {
     int32_t nx, ny, nz;   /* cells per axis, each >= 1 */
     double  h;            /* cell size, > 0 */
@@ -84,7 +99,8 @@ typedef struct {
                              those two); 0 = autotune (each candidate timed once on the first build for a device, R
                              and storage type, result cached for the process; that build synchronises the
                              stream) */
-    int32_t  reserved;    /* must be 0 */
+    int32_t  accum;       /* fdirw_accum; FDIRW_ACCUM_FP32 needs an FP32-march precision and an fdirw_create
+                             context (batch and coarse-mesh contexts take FDIRW_ACCUM_FF only) */
 } fdirw_opts;
 
 typedef struct {
@@ -104,7 +120,7 @@ typedef struct {
     double   last_mass_in;   /* FP64 total of c_in at the last fdirw_step */
     double   last_mass_out;  /* FP64 total of c_out after the last fdirw_step (if it was computed) */
     int32_t  march_parts;    /* thread mapping of the last kernel-cache build (see fdirw_opts) */
-    int32_t  reserved;
+    int32_t  accum;          /* fdirw_accum in use */
     int32_t  n_structures;   /* batch contexts: number of structures (0 for fdirw_create contexts) */
     int32_t  n_chunks;       /* batch contexts: structure chunks whose kernels are built one at a time */
     int32_t  window_R_min;   /* batch contexts: R_min of the radius rule */

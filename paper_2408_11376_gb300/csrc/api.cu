@@ -128,6 +128,7 @@ void release(fdirw_ctx* c) {
     p = c->cbuf; dfree(p); c->cbuf = nullptr;
     p = c->partials; dfree(p); c->partials = nullptr;
     p = c->dmass; dfree(p); c->dmass = nullptr;
+    p = c->dfix; dfree(p); c->dfix = nullptr;
     p = c->Dd; dfree(p); c->Dd = nullptr;
     p = c->dsrc; dfree(p); c->dsrc = nullptr;
     p = c->dkout; dfree(p); c->dkout = nullptr;
@@ -189,6 +190,9 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP64 || o.prec > FDIRW_FP32_STORE_BF16) return fail(nullptr, FDIRW_ERR_ARG, "unknown prec");
     if (o.march_parts < 0 || o.march_parts > 6) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 6]");
+    if (o.accum != FDIRW_ACCUM_FF && o.accum != FDIRW_ACCUM_FP32) return fail(nullptr, FDIRW_ERR_ARG, "unknown accum");
+    if (o.accum == FDIRW_ACCUM_FP32 && o.prec == FDIRW_FP64)
+        return fail(nullptr, FDIRW_ERR_ARG, "FDIRW_ACCUM_FP32 needs an FP32-march precision");
     if (o.prec == FDIRW_FP64 && window_R > fdirw::kMaxR64)
         return fail(nullptr, FDIRW_ERR_ARG, "FDIRW_FP64 supports window_R <= " + std::to_string(fdirw::kMaxR64));
 
@@ -199,6 +203,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     c->stream = reinterpret_cast<cudaStream_t>(o.stream);
     c->mem_limit = o.mem_limit;
     c->parts_req = o.march_parts;
+    c->accum = o.accum;
     c->g = Grid{grid->nx, grid->ny, grid->nz, (int64_t)grid->nx * grid->ny * grid->nz};
     c->h = grid->h;
     c->dt_macro = dt_macro;
@@ -260,8 +265,9 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->sigma), n * 8, "sigma")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, &c->chat, (uint64_t)pad.n * 8, "scaled field")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->cbuf), n * 8, "field staging")) != FDIRW_OK) return bail(rc);
-    if ((rc = dalloc(c, reinterpret_cast<void**>(&c->partials), fdirw::kMassBlocks * 8, "mass partials")) != FDIRW_OK) return bail(rc);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&c->partials), 2 * fdirw::kMassBlocks * 8, "mass partials")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->dmass), 8, "mass")) != FDIRW_OK) return bail(rc);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&c->dfix), 16, "mass restoration")) != FDIRW_OK) return bail(rc);
     cudaError_t e = cudaMemsetAsync(c->chat, 0, (size_t)pad.n * 8, c->stream);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&c->ev[i]);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -344,14 +350,23 @@ int fdirw_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
     if (identity) {
         if (dst != src) FDIRW_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
     } else {
-        const bool split = c->store != Store::F64;
+        const bool fp32acc = c->accum == FDIRW_ACCUM_FP32;
+        const int mode = c->store == Store::F64 ? 0 : fp32acc ? 2 : 1;
+        // FDIRW_ACCUM_FP32: the FP64 total of the call's input, the target of every step's restoration.
+        if (fp32acc) FDIRW_CUDA(c, fdirw::launch_mass(src, c->g.n, c->partials, c->dfix, c->stream));
         const double* cur = src;
         for (int t = 0; t < n_steps; t++) {
-            FDIRW_CUDA(c, fdirw::launch_scale(cur, c->sigma, c->g, c->R, c->chat, split, c->stream));
+            FDIRW_CUDA(c, fdirw::launch_scale(cur, c->sigma, c->g, c->R, c->chat, mode, c->stream));
             const bool last = t + 1 == n_steps;
             if (last) FDIRW_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-            FDIRW_CUDA(c, fdirw::launch_gather(c->Q, c->store, c->chat, c->g, c->R, dst, c->stream));
+            if (fp32acc) {
+                FDIRW_CUDA(c, fdirw::launch_gather_fp32(c->Q, c->store, reinterpret_cast<const float*>(c->chat), c->g,
+                                                        c->R, dst, c->stream));
+            } else {
+                FDIRW_CUDA(c, fdirw::launch_gather(c->Q, c->store, c->chat, c->g, c->R, dst, c->stream));
+            }
             if (last) FDIRW_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+            if (fp32acc) FDIRW_CUDA(c, fdirw::launch_restore_mass(dst, c->g.n, c->partials, c->dfix, c->stream));
             cur = dst;
         }
         c->gather_timed = true;
@@ -440,6 +455,7 @@ int fdirw_get_info(fdirw_ctx* c, fdirw_info* out) {
     out->last_mass_in = c->mass_in;
     out->last_mass_out = c->mass_out;
     out->march_parts = c->parts_used;
+    out->accum = c->accum;
     float ms = 0.f;
     if (c->kernels_timed) {
         FDIRW_CUDA(c, cudaEventSynchronize(c->ev[1]));

@@ -147,7 +147,8 @@ struct VarArgs {
 // Contribution of the radius-R sources around destination (x, y, z) of a structure of dimensions d whose
 // first global cell is base.
 template <typename ST, int R>
-__device__ __forceinline__ void acc_radius(const VarArgs& a, int4 d, int64_t base, int x, int y, int z, double& acc) {
+__device__ __forceinline__ void acc_radius(const VarArgs& a, int4 d, int64_t base, int x, int y, int z, float& A,
+                                           float& B) {
     constexpr int W1 = 2 * R + 1;
     const ST* __restrict__ K = reinterpret_cast<const ST*>(a.K[R]);
     const int64_t jb = a.jbase[R], nc = a.ncol[R];
@@ -172,7 +173,7 @@ __device__ __forceinline__ void acc_radius(const VarArgs& a, int4 d, int64_t bas
                     }
                 }
             }
-            acc += (double)s + (double)c;
+            ff_add(A, B, s, c);
         }
     }
 }
@@ -194,25 +195,25 @@ __global__ void __launch_bounds__(kTileX * kTileY) gather_var_kernel(VarArgs a) 
     const int z = (int)(t / ((int64_t)ntx * nty));
     if (x >= d.x || y >= d.y) return;
     const int64_t i = base + x + (int64_t)d.x * (y + (int64_t)d.y * z);
-    double acc = a.acc_in ? a.out[i] : 0.0;
+    float A = 0.f, B = 0.f;                       // running double-float sum of the destination
     const uint32_t m = a.rmask;                   // radii summed here, in ascending order
     if (m & 1u) {                                 // radius 0: identity kernel, sigma = 1
         if ((__ldg(a.code + i) >> kCodeShift) == 0u) {
             const float2 ch = __ldg(a.chat + i);
-            acc += (double)ch.x + (double)ch.y;
+            ff_add(A, B, ch.x, ch.y);
         }
     }
-    if (m & (1u << 1)) acc_radius<ST, 1>(a, d, base, x, y, z, acc);
-    if (m & (1u << 2)) acc_radius<ST, 2>(a, d, base, x, y, z, acc);
-    if (m & (1u << 3)) acc_radius<ST, 3>(a, d, base, x, y, z, acc);
-    if (m & (1u << 4)) acc_radius<ST, 4>(a, d, base, x, y, z, acc);
-    if (m & (1u << 5)) acc_radius<ST, 5>(a, d, base, x, y, z, acc);
-    if (m & (1u << 6)) acc_radius<ST, 6>(a, d, base, x, y, z, acc);
-    if (m & (1u << 7)) acc_radius<ST, 7>(a, d, base, x, y, z, acc);
-    if (m & (1u << 8)) acc_radius<ST, 8>(a, d, base, x, y, z, acc);
-    if (m & (1u << 9)) acc_radius<ST, 9>(a, d, base, x, y, z, acc);
-    if (m & (1u << 10)) acc_radius<ST, 10>(a, d, base, x, y, z, acc);
-    a.out[i] = acc;
+    if (m & (1u << 1)) acc_radius<ST, 1>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 2)) acc_radius<ST, 2>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 3)) acc_radius<ST, 3>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 4)) acc_radius<ST, 4>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 5)) acc_radius<ST, 5>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 6)) acc_radius<ST, 6>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 7)) acc_radius<ST, 7>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 8)) acc_radius<ST, 8>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 9)) acc_radius<ST, 9>(a, d, base, x, y, z, A, B);
+    if (m & (1u << 10)) acc_radius<ST, 10>(a, d, base, x, y, z, A, B);
+    a.out[i] = (a.acc_in ? a.out[i] : 0.0) + ((double)A + (double)B);
 }
 
 // Renormalised kernels of listed global sources on the (2 R_max + 1)^3 offset layout (zero outside the
@@ -391,7 +392,7 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
             e = cudaGetLastError();
         }
         for (int i = ch.s0; i < ch.s1 && e == cudaSuccess && b.dest_mask; i++)
-            e = launch_scale(cur + b.base[i], c->sigma + b.base[i], b.grids[i], Rm, b.chat_pad + b.pbase[i], true, st);
+            e = launch_scale(cur + b.base[i], c->sigma + b.base[i], b.grids[i], Rm, b.chat_pad + b.pbase[i], 1, st);
         const bool last = t + 1 == n_steps;
         if (e == cudaSuccess && last) e = record(b.ev[4 * ci + 2], st, captured);
         if (e != cudaSuccess) break;
@@ -674,6 +675,7 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
     if (o.prec < FDIRW_FP32 || o.prec > FDIRW_FP32_STORE_BF16)
         return fail(nullptr, FDIRW_ERR_ARG, "a batch needs an FP32-march precision (FP32, FP16 or BF16 storage)");
     if (o.march_parts < 0 || o.march_parts > 6) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 6]");
+    if (o.accum != FDIRW_ACCUM_FF) return fail(nullptr, FDIRW_ERR_ARG, "batch contexts take FDIRW_ACCUM_FF only");
 
     DeviceGuard dg(o.device);
     if (!dg.ok) return fail(nullptr, FDIRW_ERR_CUDA, "cannot select CUDA device " + std::to_string(o.device));

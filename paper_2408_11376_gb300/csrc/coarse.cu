@@ -481,6 +481,7 @@ int fdirw_create_coarse(const fdirw_grid* grid, const double* D_map, const uint8
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP32 || o.prec > FDIRW_FP32_STORE_BF16)
         return fail(nullptr, FDIRW_ERR_ARG, "the coarse path marches in FP32 (prec FP32, FP16 or BF16; P is FP64)");
+    if (o.accum != FDIRW_ACCUM_FF) return fail(nullptr, FDIRW_ERR_ARG, "coarse contexts take FDIRW_ACCUM_FF only");
     // fdirw_create validates D, dt_macro, n_sub and stability and builds the face coefficients; the
     // coarse path then masks them and replaces the kernel cache with the coarse matrix.
     fdirw_opts o2 = o;

@@ -33,8 +33,10 @@ struct fdirw_ctx {
     double* sigma = nullptr;
     void* chat = nullptr;                           // padded sigma*c: double or float2
     double* cbuf = nullptr;                         // staging for host fields
-    double* partials = nullptr;                     // kMassBlocks
+    double* partials = nullptr;                     // 2 * kMassBlocks
     double* dmass = nullptr;                        // 1 double
+    double* dfix = nullptr;                         // FDIRW_ACCUM_FP32: [M_in, f] of the mass restoration
+    int accum = 0;                                  // fdirw_accum
     double* Dd = nullptr;                           // device copy of D (surrogate features)
     int64_t* dsrc = nullptr;
     double* dkout = nullptr;

@@ -94,9 +94,9 @@ inline Pad make_pad(const Grid& g, int R) {
     p.n = (int64_t)p.px * p.py * p.pz;
     return p;
 }
-// chat = sigma * c into the interior of the padded buffer; FP64 (split == false) or as a float2 (hi, lo)
-// pair with hi = fp32(v), lo = fp32(v - hi) (split == true).
-cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, bool split,
+// chat = sigma * c into the interior of the padded buffer (zero halo of R cells): mode 0 FP64, mode 1 a
+// float2 (hi, lo) pair with hi = fp32(v), lo = fp32(v - hi), mode 2 fp32(v).
+cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, int mode,
                          cudaStream_t st);
 // c_out(x) = sum_o Q[o][x] * chat(x - o).
 cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
@@ -109,6 +109,14 @@ cudaError_t launch_gather_part(const void* Q, Store store, int64_t qs, const voi
 // Deterministic FP64 total: partials[kMassBlocks] then one block.  partials must hold kMassBlocks doubles.
 constexpr int kMassBlocks = 1024;
 cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* out, cudaStream_t st);
+// FDIRW_ACCUM_FP32 superposition of a uniform context: FP32 chat (launch_scale mode 2), FP32 products
+// and row sums, double-float row accumulation.
+cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Grid g, int R, double* c_out,
+                               cudaStream_t st);
+// Restores the FP64 total of c to *m_in: c[i] += f |c[i]|, f = (m_in - sum c) / sum |c| (0 when the
+// field is zero), both sums in a fixed order.  partials: 2 * kMassBlocks doubles; fix: 2 doubles
+// (fix[0] = m_in on entry, fix[1] = f on exit).
+cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* fix, cudaStream_t st);
 // Renormalised kernels of listed sources on the (2R+1)^3 offset layout.
 cudaError_t launch_read_kernels(const void* Q, Store store, const double* sigma, Grid g, int R,
                                 const int64_t* sources, int64_t n_src, double* out, cudaStream_t st);

@@ -13,8 +13,10 @@
 //   - FP32/FP16/BF16 storage: GB300 issues FP64 FMAs at 1/73 of the FP32 rate (measured), so each row of
 //     2R+1 terms is summed as an unevaluated pair of FP32 values (s, c) -- error-free product (FMA
 //     residual) and error-free addition (Knuth TwoSum), with chat split into hi = fp32(v),
-//     lo = fp32(v - hi) -- and the row result is added to an FP64 accumulator (2 FP64 adds per row
-//     instead of 2R+1 FP64 FMAs).
+//     lo = fp32(v - hi) -- and the rows of a destination are summed as a second FP32 pair (ff_add);
+//     one FP64 addition per destination forms the result.
+//   - FDIRW_ACCUM_FP32: FP32 products and row sums (one FMA per term), rows as above; the caller then
+//     restores the step's FP64 mass budget (launch_restore_mass).
 // The work per step is HBM-bound in the cache read (N * (2R+1)^3 * storage bytes).
 #include "fdirw_internal.h"
 #include "ff.cuh"
@@ -62,9 +64,9 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
     const int x0 = xv * VX;
     const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
 
-    double acc[VX];
+    float A[VX], B[VX];                       // running double-float sum of each destination
 #pragma unroll
-    for (int j = 0; j < VX; j++) acc[j] = acc_in ? out[i0 + j] : 0.0;
+    for (int j = 0; j < VX; j++) { A[j] = 0.f; B[j] = 0.f; }
 
     for (int oz = -R; oz <= R; oz++) {
         for (int oy = -R; oy <= R; oy++) {
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
             const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + i0;
             // The FP32 pair restarts at zero on every row of 2R+1 terms, so its compensation term stays
-            // within a few ulps of the row sum; the row is then added to the FP64 accumulator.
+            // within a few ulps of the row sum; the row is then added to the destination's pair.
             float s[VX], c[VX];
 #pragma unroll
             for (int j = 0; j < VX; j++) { s[j] = 0.f; c[j] = 0.f; }
@@ -87,11 +89,58 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
                 for (int j = 0; j < VX; j++) ff_madd(s[j], c[j], q[j], ch[j - ox + R]);
             }
 #pragma unroll
-            for (int j = 0; j < VX; j++) acc[j] += (double)s[j] + (double)c[j];
+            for (int j = 0; j < VX; j++) ff_add(A[j], B[j], s[j], c[j]);
         }
     }
 #pragma unroll
-    for (int j = 0; j < VX; j++) out[i0 + j] = acc[j];
+    for (int j = 0; j < VX; j++) out[i0 + j] = (acc_in ? out[i0 + j] : 0.0) + ((double)A[j] + (double)B[j]);
+}
+
+// FDIRW_ACCUM_FP32: the loop of gather_ff_kernel with FP32 products and row sums (one FMA per term) and an
+// FP32 chat; the rows still go into a double-float pair per destination.  The caller restores the mass.
+template <typename ST, int R>
+__global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__ Q, const float* __restrict__ chat,
+                                                          Grid g, Pad p, double* __restrict__ out) {
+    constexpr int VX = 16 / sizeof(ST);
+    constexpr int W1 = 2 * R + 1;
+    constexpr int NC = VX + 2 * R;
+    const int nxv = g.nx / VX;
+    const int64_t nthreads = (int64_t)nxv * g.ny * g.nz;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= nthreads) return;
+    const int xv = (int)(tid % nxv);
+    const int64_t r = tid / nxv;
+    const int y = (int)(r % g.ny);
+    const int z = (int)(r / g.ny);
+    const int x0 = xv * VX;
+    const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
+
+    float A[VX], B[VX];
+#pragma unroll
+    for (int j = 0; j < VX; j++) { A[j] = 0.f; B[j] = 0.f; }
+    for (int oz = -R; oz <= R; oz++) {
+        for (int oy = -R; oy <= R; oy++) {
+            const float* row = chat + ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + x0;
+            float ch[NC];
+#pragma unroll
+            for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
+            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+            float s[VX];
+#pragma unroll
+            for (int j = 0; j < VX; j++) s[j] = 0.f;
+#pragma unroll
+            for (int ox = -R; ox <= R; ox++) {
+                float q[VX];
+                load_q<ST, VX>(qrow + (int64_t)(ox + R) * g.n, q);
+#pragma unroll
+                for (int j = 0; j < VX; j++) s[j] = fmaf(q[j], ch[j - ox + R], s[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < VX; j++) ff_add(A[j], B[j], s[j], 0.f);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < VX; j++) out[i0 + j] = (double)A[j] + (double)B[j];
 }
 
 // FP64 path: FP64 storage, FP64 chat, FP64 FMA accumulation, VX = 2.
@@ -132,7 +181,7 @@ __global__ void __launch_bounds__(256) gather_f64_kernel(const double* __restric
 }
 
 // Any nx (no vector alignment): one destination per thread, runtime R, same arithmetic as above.
-template <typename ST, bool FF>
+template <typename ST, int MODE>
 __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict__ Q, const void* __restrict__ chat,
                                                             Grid g, Pad p, int R, int64_t qs, bool acc_in,
                                                             double* __restrict__ out) {
@@ -142,7 +191,8 @@ __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict
     const int64_t r = i / g.nx;
     const int y = (int)(r % g.ny);
     const int z = (int)(r / g.ny);
-    double acc = acc_in ? out[i] : 0.0;
+    double acc = (MODE == 0 && acc_in) ? out[i] : 0.0;   // FP64 path: plain FMA accumulation
+    float A = 0.f, B = 0.f;                               // FP32 paths: running double-float sum
     int o = 0;
     for (int oz = -R; oz <= R; oz++)
         for (int oy = -R; oy <= R; oy++) {
@@ -150,19 +200,22 @@ __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict
             for (int ox = -R; ox <= R; ox++, o++) {
                 const int64_t pi = ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + (x - ox + R);
                 const ST qv = Q[(int64_t)o * qs + i];
-                if constexpr (FF) {
+                if constexpr (MODE == 1) {
                     ff_madd(s, c, widen(qv), reinterpret_cast<const float2*>(chat)[pi]);
+                } else if constexpr (MODE == 2) {
+                    s = fmaf(widen(qv), reinterpret_cast<const float*>(chat)[pi], s);
                 } else {
                     acc = fma((double)qv, reinterpret_cast<const double*>(chat)[pi], acc);
                 }
             }
-            if constexpr (FF) acc += (double)s + (double)c;
+            if constexpr (MODE != 0) ff_add(A, B, s, c);
         }
-    out[i] = acc;
+    if constexpr (MODE != 0) out[i] = (acc_in ? out[i] : 0.0) + ((double)A + (double)B);
+    else out[i] = acc;
 }
 
 __global__ void scale_kernel(const double* __restrict__ c, const double* __restrict__ sigma, Grid g, int R, Pad p,
-                             void* __restrict__ chat, bool split) {
+                             void* __restrict__ chat, int mode) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % g.nx);
         const int64_t r = i / g.nx;
@@ -170,10 +223,12 @@ __global__ void scale_kernel(const double* __restrict__ c, const double* __restr
         const int z = (int)(r / g.ny);
         const int64_t pi = ((int64_t)(z + R) * p.py + (y + R)) * p.px + (x + R);
         const double v = sigma[i] * c[i];
-        if (split) {
+        if (mode == 1) {
             const float hi = (float)v;
             const float lo = (float)(v - (double)hi);
             reinterpret_cast<float2*>(chat)[pi] = make_float2(hi, lo);
+        } else if (mode == 2) {
+            reinterpret_cast<float*>(chat)[pi] = (float)v;
         } else {
             reinterpret_cast<double*>(chat)[pi] = v;
         }
@@ -212,6 +267,64 @@ __global__ void __launch_bounds__(kMassBlocks) mass_final_kernel(const double* _
         for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
         if (threadIdx.x == 0) *out = w;
     }
+}
+
+// Mass restoration, pass 1: block b sums c and |c| over the contiguous chunk b (as mass_partial_kernel).
+__global__ void __launch_bounds__(256) mass_abs_partial_kernel(const double* __restrict__ c, int64_t n,
+                                                               double* __restrict__ partials) {
+    __shared__ double sh[2][8];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = lo + chunk < n ? lo + chunk : n;
+    double acc = 0.0, aab = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double v = c[i];
+        acc += v;
+        aab += fabs(v);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        aab += __shfl_xor_sync(0xffffffffu, aab, off);
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = acc; sh[1][threadIdx.x >> 5] = aab; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? sh[0][threadIdx.x] : 0.0;
+        double w = threadIdx.x < (blockDim.x >> 5) ? sh[1][threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, off);
+            w += __shfl_xor_sync(0xffffffffu, w, off);
+        }
+        if (threadIdx.x == 0) { partials[blockIdx.x] = v; partials[kMassBlocks + blockIdx.x] = w; }
+    }
+}
+
+// Pass 2: one block sums both partial sets and writes f = (m_in - S) / A into fix[1] (0 when A = 0).
+__global__ void __launch_bounds__(kMassBlocks) mass_fix_kernel(const double* __restrict__ partials,
+                                                               double* __restrict__ fix) {
+    __shared__ double sh[2][kMassBlocks / 32];
+    double v = partials[threadIdx.x], w = partials[kMassBlocks + threadIdx.x];
+    for (int off = 16; off > 0; off >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+        w += __shfl_xor_sync(0xffffffffu, w, off);
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = v; sh[1][threadIdx.x >> 5] = w; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double S = sh[0][threadIdx.x], A = sh[1][threadIdx.x];
+        for (int off = 16; off > 0; off >>= 1) {
+            S += __shfl_xor_sync(0xffffffffu, S, off);
+            A += __shfl_xor_sync(0xffffffffu, A, off);
+        }
+        if (threadIdx.x == 0) fix[1] = A > 0.0 ? (fix[0] - S) / A : 0.0;
+    }
+}
+
+// Pass 3: c[i] += f |c[i]|.
+__global__ void mass_apply_kernel(double* __restrict__ c, int64_t n, const double* __restrict__ fix) {
+    const double f = fix[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c[i] = fma(f, fabs(c[i]), c[i]);
 }
 
 template <typename ST>
@@ -318,12 +431,12 @@ cudaError_t gather_f64(const void* Q, const void* chat, Grid g, int R, Pad p, do
 
 }  // namespace
 
-cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, bool split,
+cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, int mode,
                          cudaStream_t st) {
     const Pad p = make_pad(g, R);
     int b = blocks_for(g.n, 256);
     if (b > 152 * 16) b = 152 * 16;
-    scale_kernel<<<b, 256, 0, st>>>(c, sigma, g, R, p, chat, split);
+    scale_kernel<<<b, 256, 0, st>>>(c, sigma, g, R, p, chat, mode);
     return cudaGetLastError();
 }
 
@@ -350,19 +463,19 @@ cudaError_t launch_gather_part(const void* Q, Store store, int64_t qs, const voi
     const int b = blocks_for(g.n, 256);
     switch (store) {
         case Store::F64:
-            gather_scalar_kernel<double, false><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), ch, g, p, R, qs,
+            gather_scalar_kernel<double, 0><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), ch, g, p, R, qs,
                                                                    accumulate, c_out);
             break;
         case Store::F32:
-            gather_scalar_kernel<float, true><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
+            gather_scalar_kernel<float, 1><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
                                                                  accumulate, c_out);
             break;
         case Store::F16:
-            gather_scalar_kernel<__half, true><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R, qs,
+            gather_scalar_kernel<__half, 1><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R, qs,
                                                                   accumulate, c_out);
             break;
         case Store::BF16:
-            gather_scalar_kernel<__nv_bfloat16, true><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), ch,
+            gather_scalar_kernel<__nv_bfloat16, 1><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), ch,
                                                                          g, p, R, qs, accumulate, c_out);
             break;
     }
@@ -379,6 +492,77 @@ cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* ou
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     mass_final_kernel<<<1, kMassBlocks, 0, st>>>(partials, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* fix, cudaStream_t st) {
+    mass_abs_partial_kernel<<<kMassBlocks, 256, 0, st>>>(c, n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mass_fix_kernel<<<1, kMassBlocks, 0, st>>>(partials, fix);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int b = blocks_for(n, 256);
+    if (b > 152 * 16) b = 152 * 16;
+    mass_apply_kernel<<<b, 256, 0, st>>>(c, n, fix);
+    return cudaGetLastError();
+}
+
+template <typename ST, int R>
+cudaError_t gather_fp32_r(const void* Q, const float* chat, Grid g, Pad p, double* out, cudaStream_t st) {
+    constexpr int VX = 16 / sizeof(ST);
+    const int64_t nt = (int64_t)(g.nx / VX) * g.ny * g.nz;
+    gather_fp32_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q), chat, g, p, out);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t gather_fp32_st(const void* Q, const float* chat, Grid g, int R, Pad p, double* out, cudaStream_t st) {
+    switch (R) {
+        case 1: return gather_fp32_r<ST, 1>(Q, chat, g, p, out, st);
+        case 2: return gather_fp32_r<ST, 2>(Q, chat, g, p, out, st);
+        case 3: return gather_fp32_r<ST, 3>(Q, chat, g, p, out, st);
+        case 4: return gather_fp32_r<ST, 4>(Q, chat, g, p, out, st);
+        case 5: return gather_fp32_r<ST, 5>(Q, chat, g, p, out, st);
+        case 6: return gather_fp32_r<ST, 6>(Q, chat, g, p, out, st);
+        case 7: return gather_fp32_r<ST, 7>(Q, chat, g, p, out, st);
+        case 8: return gather_fp32_r<ST, 8>(Q, chat, g, p, out, st);
+        case 9: return gather_fp32_r<ST, 9>(Q, chat, g, p, out, st);
+        case 10: return gather_fp32_r<ST, 10>(Q, chat, g, p, out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Grid g, int R, double* c_out,
+                               cudaStream_t st) {
+    if (R < 1 || R > kMaxR || store == Store::F64) return cudaErrorInvalidValue;
+    const Pad p = make_pad(g, R);
+    const int vx = 16 / store_bytes(store);
+    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (g.n * store_bytes(store)) % 16 == 0;
+    if (g.nx % vx == 0 && aligned) {
+        switch (store) {
+            case Store::F32: return gather_fp32_st<float>(Q, chat, g, R, p, c_out, st);
+            case Store::F16: return gather_fp32_st<__half>(Q, chat, g, R, p, c_out, st);
+            case Store::BF16: return gather_fp32_st<__nv_bfloat16>(Q, chat, g, R, p, c_out, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    const int b = blocks_for(g.n, 256);
+    switch (store) {
+        case Store::F32:
+            gather_scalar_kernel<float, 2><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), chat, g, p, R, g.n,
+                                                              false, c_out);
+            break;
+        case Store::F16:
+            gather_scalar_kernel<__half, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), chat, g, p, R, g.n,
+                                                               false, c_out);
+            break;
+        case Store::BF16:
+            gather_scalar_kernel<__nv_bfloat16, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), chat,
+                                                                      g, p, R, g.n, false, c_out);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -27,6 +27,9 @@ FDIRW_FP32 = 1
 FDIRW_FP32_STORE_FP16 = 2
 FDIRW_FP32_STORE_BF16 = 3
 PRECISIONS = {"fp64": FDIRW_FP64, "fp32": FDIRW_FP32, "fp16": FDIRW_FP32_STORE_FP16, "bf16": FDIRW_FP32_STORE_BF16}
+FDIRW_ACCUM_FF = 0
+FDIRW_ACCUM_FP32 = 1
+ACCUMS = {"ff": FDIRW_ACCUM_FF, "fp32": FDIRW_ACCUM_FP32}
 
 EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "fdirw_mass", "fdirw_read_kernels",
             "fdirw_get_info", "fdirw_destroy", "fdirw_last_error", "fdirw_mass_noalloc", "fdirw_net_create",
@@ -53,7 +56,7 @@ class fdirw_grid(ctypes.Structure):
 
 class fdirw_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("mem_limit", ctypes.c_uint64), ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mem_limit", ctypes.c_uint64), ("march_parts", ctypes.c_int32), ("accum", ctypes.c_int32)]
 
 
 class fdirw_coupled_params(ctypes.Structure):
@@ -68,7 +71,7 @@ class fdirw_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("window_cells", ctypes.c_double),
                 ("kernels_ms", ctypes.c_float), ("last_gather_ms", ctypes.c_float),
                 ("last_mass_in", ctypes.c_double), ("last_mass_out", ctypes.c_double),
-                ("march_parts", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("march_parts", ctypes.c_int32), ("accum", ctypes.c_int32),
                 ("n_structures", ctypes.c_int32), ("n_chunks", ctypes.c_int32), ("window_R_min", ctypes.c_int32),
                 ("graph_launches", ctypes.c_int32), ("dest_indexed_radii", ctypes.c_int32),
                 ("coarse_block", ctypes.c_int32), ("coarse_nodes", ctypes.c_int64)]
@@ -177,15 +180,17 @@ def fdirw_stable_dt(shape, D, h: float = 1.0, device: int = -1) -> float:
 
 
 def fdirw_create(shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp32", h: float = 1.0,
-                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0) -> int:
-    """Returns the context handle (an integer address); release it with fdirw_destroy."""
+                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0, accum="ff") -> int:
+    """Returns the context handle (an integer address); release it with fdirw_destroy.  accum: "ff"
+    (float-float rows, the default) or "fp32" (FP32 rows with the mass restored every step)."""
     lib = load()
     nx, ny, nz = (int(v) for v in shape)
     _check_f64(D, nx * ny * nz)
     g = fdirw_grid(nx, ny, nz, float(h))
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
-    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), int(march_parts), 0)
+    acc = ACCUMS[accum] if isinstance(accum, str) else int(accum)
+    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), int(march_parts), acc)
     ctx = ctypes.c_void_p(0)
     _check(lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(_ptr(D)), float(dt_macro), int(window_R), int(n_sub),
                             ctypes.byref(o), ctypes.byref(ctx)))
@@ -330,12 +335,12 @@ class FDiRW:
     """Owns one context: ``FDiRW(shape, D, dt_macro, R, n_sub, prec)``; ``step(c_in, c_out, n)``; ``close()``."""
 
     def __init__(self, shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp32", h: float = 1.0,
-                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0):
+                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0, accum="ff"):
         self.shape = tuple(int(v) for v in shape)
         self.R = int(window_R)
         self.n = self.shape[0] * self.shape[1] * self.shape[2]
         self.ctx = fdirw_create(self.shape, D, dt_macro, window_R, n_sub, prec, h, device, stream, mem_limit,
-                                march_parts)
+                                march_parts, accum)
 
     def kernels(self):
         fdirw_kernels(self.ctx)

@@ -48,7 +48,9 @@ def test_host_side_argument_checks(lib):
     g = fdirw.fdirw_grid(4, 4, 4, 1.0)
     assert lib.fdirw_create(ctypes.byref(g), None, 1.0, 2, 3, None, ctypes.byref(ctypes.c_void_p())) == fdirw.FDIRW_ERR_ARG
     for R, bad_opts in ((2, fdirw.fdirw_opts(7, -1, None, 0, 0, 0)), (2, fdirw.fdirw_opts(1, -1, None, 0, 7, 0)),
-                        (9, fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0))):
+                        (9, fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)),
+                        (2, fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, 2)),                  # unknown accum
+                        (2, fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, fdirw.FDIRW_ACCUM_FP32))):
         rc = lib.fdirw_create(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), 1.0, R, 3, ctypes.byref(bad_opts),
                               ctypes.byref(ctypes.c_void_p()))
         assert rc == fdirw.FDIRW_ERR_ARG
@@ -65,10 +67,12 @@ def test_batch_host_side_argument_checks(lib):
     fp64 = fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)
     parts7 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 7, 0)
     bad_grid = (fdirw.fdirw_grid * 1)(fdirw.fdirw_grid(4, 0, 4, 1.0))
+    acc32 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, fdirw.FDIRW_ACCUM_FP32)
     cases = [(0, g, ptrs, 1.0, 1, 3, 2, None), (2, None, ptrs, 1.0, 1, 3, 2, None), (2, g, None, 1.0, 1, 3, 2, None),
              (2, g, ptrs, 1.0, 1, 11, 2, None), (2, g, ptrs, 1.0, 4, 3, 2, None), (2, g, ptrs, 1.0, -1, 3, 2, None),
              (2, g, ptrs, -1.0, 1, 3, 2, None), (2, g, ptrs, 1.0, 1, 3, -2, None), (1, huge, ptrs, 1.0, 1, 3, 2, None),
-             (2, g, ptrs, 1.0, 1, 3, 2, fp64), (2, g, ptrs, 1.0, 1, 3, 2, parts7), (1, bad_grid, ptrs, 1.0, 1, 3, 2, None)]
+             (2, g, ptrs, 1.0, 1, 3, 2, fp64), (2, g, ptrs, 1.0, 1, 3, 2, parts7), (1, bad_grid, ptrs, 1.0, 1, 3, 2, None),
+             (2, g, ptrs, 1.0, 1, 3, 2, acc32)]
     for n, grids, dm, dt, rmin, rmax, n_sub, opts in cases:
         ctx = ctypes.c_void_p(1234)
         rc = lib.fdirw_create_batch(n, grids, dm, dt, rmin, rmax, n_sub, ctypes.byref(opts) if opts else None,
@@ -85,8 +89,9 @@ def test_coarse_host_side_argument_checks(lib):
     D = np.ones(64)
     g = fdirw.fdirw_grid(4, 4, 4, 1.0)
     fp64 = fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)
+    acc32 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, fdirw.FDIRW_ACCUM_FP32)
     for block, R, opts in ((2, 2, None), (0, 2, None), (-1, 2, None), (5, 9, None), (1, 0, None), (3, -1, None),
-                           (3, 2, fp64)):
+                           (3, 2, fp64), (3, 2, acc32)):
         ctx = ctypes.c_void_p(1234)
         rc = lib.fdirw_create_coarse(ctypes.byref(g), ctypes.c_void_p(D.ctypes.data), None, block, 0.1, R, 2,
                                      ctypes.byref(opts) if opts else None, ctypes.byref(ctx))
