@@ -185,6 +185,22 @@ def march_traffic(args, prec: str, parts: int, R: int, window_cells: float):
     return None
 
 
+def gather_roofline(prec: str, accum: str, N: int, R: int, gather_ms: float):
+    """HBM roofline of one superposition launch: algorithmic bytes = the kernel cache (N (2R+1)^3 stored
+    values, each read once) + the scaled field it multiplies (FP32, or FP32 pairs) + the FP64 output."""
+    peaks, peak_src = _peaks()
+    qb = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec]
+    chat_b = 8 if prec == "fp64" else (4 if accum == "fp32" else 8)
+    nbytes = N * (2 * R + 1) ** 3 * qb + N * chat_b + N * 8
+    achieved = nbytes / (gather_ms * 1e-3) / 1e9
+    kname = ("gather_f64_kernel<R>" if prec == "fp64" else
+             "gather_fp32_kernel<ST,R>" if accum == "fp32" else "gather_ff_kernel<ST,R>")
+    return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({peak_src})",
+            "algorithmic": f"cache {N}x{(2 * R + 1) ** 3}x{qb} B + field {chat_b} B + output 8 B per cell "
+                           f"= {nbytes / 1e9:.2f} GB per launch"}
+
+
 def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: float, traffic, clocks, kname: str):
     """Achieved FP32 flop rate of the march (13 flop per cell-substep over the clipped windows) against the
     FP32 pipe peak at the measured maximum SM clock."""
@@ -543,7 +559,8 @@ def run_ours(args, w):
         "phase_ms": {"create": statistics.mean(t[0] for t in times), "kernels": statistics.mean(t[1] for t in times),
                      "march_kernel": march_ms, "steps": steps_ms, "gather_kernel": gather_ms},
         "mass_rel_err": abs(times[-1][6] - mass0) / mass0,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu_baseline": fp64,
+        "roofline": roofline, "gather_roofline": gather_roofline(prec, args.accum, N, w.R, gather_ms),
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu_baseline": fp64,
         "gpu_launches": n_launch * args.steps, "clocks": clocks,
     }
     if fp64:
@@ -835,7 +852,7 @@ def main(argv=None):
                     help="also run the coarse-mesh FDiRW with this odd block side (e.g. 5) and compare it with the fine path")
     ap.add_argument("--coupled", action="store_true",
                     help="also run the coupled macro step (exchange, solid march, coarse FDiRW with far field)")
-    ap.add_argument("--accum", choices=["ff", "fp32"], default="ff",
+    ap.add_argument("--accum", choices=["ff", "fp32"], default="fp32",
                     help="superposition accumulation: float-float rows, or FP32 rows with the mass restored")
     ap.add_argument("--flow", action="store_true",
                     help="also time the convection path (steady face velocities folded into the march)")
@@ -849,6 +866,8 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     from paper_2408_11376_gb300 import synth
+    if args.prec == "fp64" or args.workload in synth.BATCH_WORKLOADS:
+        args.accum = "ff"            # the FP64 path and batch contexts sum in FP64 / float-float only
     if args.workload in synth.BATCH_WORKLOADS:
         bw = synth.BATCH_WORKLOADS[args.workload]
         return run_reference_batch(args, bw) if args.impl == "reference" else run_batch(args, bw)
