@@ -57,6 +57,8 @@ struct Chunk {
 
 }  // namespace
 
+constexpr int kAux = 8;                          // parallel branches for per-structure gathers
+
 struct Batch {
     int n = 0;
     std::vector<Grid> grids;
@@ -85,6 +87,8 @@ struct Batch {
     float2* chat = nullptr;
     cudaStream_t gs = nullptr;                   // capture stream
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t aux[kAux] = {};                 // branches of the captured graph: per-structure gathers
+    cudaEvent_t afork = nullptr, ajoin[kAux] = {};
     std::vector<cudaEvent_t> ev;                 // 4 per chunk: march begin/end, last gather begin/end
     std::vector<char> built, stepped;            // per chunk, in the last call
     cudaGraphExec_t exec = nullptr;
@@ -406,14 +410,28 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
             e = cudaGetLastError();
             written = true;
         }
-        for (int r : b.radii) {
-            if (e != cudaSuccess) break;
-            if (r == 0 || !((b.dest_mask >> r) & 1u)) continue;
+        if (e == cudaSuccess && b.dest_mask) {
+            // Structures are independent: their destination-indexed gathers run as kAux parallel branches
+            // of the graph (one structure alone fills a fraction of the GPU), each structure's radii in
+            // ascending order on its branch, so every destination sums in the same order as before.
             const size_t sb = store_bytes(c->store);
+            e = cudaEventRecord(b.afork, st);
+            for (int k = 0; k < kAux && e == cudaSuccess; k++) e = cudaStreamWaitEvent(b.aux[k], b.afork, 0);
             for (int i = ch.s0; i < ch.s1 && e == cudaSuccess; i++) {
-                const void* Q = static_cast<const char*>(a.K[r]) + (size_t)b.qbase[i] * sb;
-                e = launch_gather_part(Q, c->store, ch.qn, b.chat_pad + b.pbase[i], Rm, b.grids[i], r, written,
-                                       dst + b.base[i], st);
+                cudaStream_t sx = b.aux[(i - ch.s0) % kAux];
+                bool w = written;
+                for (int r : b.radii) {
+                    if (r == 0 || !((b.dest_mask >> r) & 1u)) continue;
+                    const void* Q = static_cast<const char*>(a.K[r]) + (size_t)b.qbase[i] * sb;
+                    e = launch_gather_part(Q, c->store, ch.qn, b.chat_pad + b.pbase[i], Rm, b.grids[i], r, w,
+                                           dst + b.base[i], sx);
+                    if (e != cudaSuccess) break;
+                    w = true;
+                }
+            }
+            for (int k = 0; k < kAux && e == cudaSuccess; k++) {
+                e = cudaEventRecord(b.ajoin[k], b.aux[k]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b.ajoin[k], 0);
             }
             written = true;
         }
@@ -511,6 +529,11 @@ void release_batch(fdirw_ctx* c) {
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
     if (b->gs) cudaStreamDestroy(b->gs);
+    if (b->afork) cudaEventDestroy(b->afork);
+    for (int k = 0; k < kAux; k++) {
+        if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+        if (b->ajoin[k]) cudaEventDestroy(b->ajoin[k]);
+    }
     delete b;
     c->batch = nullptr;
 }
@@ -921,6 +944,11 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
     if ((e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming)) != cudaSuccess) return cuda_bail("cudaEventCreate", e);
     if ((e = cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming)) != cudaSuccess) return cuda_bail("cudaEventCreate", e);
     if ((e = cudaStreamCreateWithFlags(&b.gs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_bail("cudaStreamCreate", e);
+    if ((e = cudaEventCreateWithFlags(&b.afork, cudaEventDisableTiming)) != cudaSuccess) return cuda_bail("cudaEventCreate", e);
+    for (int k = 0; k < fdirw::kAux; k++) {
+        if ((e = cudaStreamCreateWithFlags(&b.aux[k], cudaStreamNonBlocking)) != cudaSuccess) return cuda_bail("cudaStreamCreate", e);
+        if ((e = cudaEventCreateWithFlags(&b.ajoin[k], cudaEventDisableTiming)) != cudaSuccess) return cuda_bail("cudaEventCreate", e);
+    }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_bail("batch setup", e);
     *out = c;
     return FDIRW_OK;
