@@ -251,12 +251,12 @@ def run_batch(args, bw):
     dt_macro = bw.n_sub * dt_sub
     prec = args.prec if args.prec != "fp64" else "bf16"
 
-    def one_pass(times=None, p=prec, out=c1):
+    def one_pass(times=None, p=prec, out=c1, acc=args.accum):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         with torch.cuda.stream(stream):
             ev[0].record(stream)
             ctx = fdirw.fdirw_create_batch(shapes, Ds, dt_macro, bw.R_min, bw.R_max, bw.n_sub, p, device=local,
-                                           stream=stream, march_parts=args.march_parts)
+                                           stream=stream, march_parts=args.march_parts, accum=acc)
             ev[1].record(stream)
             mass = fdirw.fdirw_step(ctx, c0, out, bw.steps, want_mass=True)
             ev[2].record(stream)
@@ -300,7 +300,8 @@ def run_batch(args, bw):
         def e2e_pass():
             with torch.cuda.stream(stream):
                 ctx = fdirw.fdirw_create_batch(shapes, Dp, dt_macro, bw.R_min, bw.R_max, bw.n_sub, prec,
-                                               device=local, stream=stream, march_parts=args.march_parts)
+                                               device=local, stream=stream, march_parts=args.march_parts,
+                                               accum=args.accum)
                 fdirw.fdirw_step(ctx, cp, op, bw.steps, want_mass=True)
                 fdirw.fdirw_destroy(ctx)
 
@@ -323,9 +324,9 @@ def run_batch(args, bw):
     accuracy = None
     if not args.no_fp64 and ws == 1 and prec != "fp32":
         ref = torch.empty_like(c0)
-        one_pass(p="fp32", out=ref)
+        one_pass(p="fp32", out=ref, acc="ff")
         stream.synchronize()
-        accuracy = {"vs": "fp32 storage, same batch", "rel_l2": float((torch.linalg.vector_norm(c1 - ref) /
+        accuracy = {"vs": "fp32 storage, float-float sums, same batch", "rel_l2": float((torch.linalg.vector_norm(c1 - ref) /
                                                                        torch.linalg.vector_norm(ref)).item())}
         del ref
 
@@ -340,6 +341,8 @@ def run_batch(args, bw):
                          f"windowed marches on {threads} host threads); macro-steps/s = 1/(N * seconds per source)"}
     nch = info["n_chunks"]
     n_launch = 5 * len(shapes) + 1 + nch * (2 + 2 * bw.steps) + 4
+    if args.accum == "fp32":
+        n_launch += 2 + 3 * nch * bw.steps       # structure totals, then the restoration per chunk and step
     value = job_rate(ws, bw.steps * args.steps, total_ms)
     n_src_pass = N
     line = {
@@ -348,7 +351,7 @@ def run_batch(args, bw):
         "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": bw.name, "structures": len(shapes), "cells": N,
                    "sides": sorted(set(s[0] for s in shapes)), "R": f"{bw.R_min}..{bw.R_max} by rule",
-                   "n_sub": bw.n_sub, "macro_steps": bw.steps, "prec": prec,
+                   "n_sub": bw.n_sub, "macro_steps": bw.steps, "prec": prec, "accum": args.accum,
                    "parallelism": "replicas" if ws > 1 else "single GPU", "chunks": nch,
                    "l2": f"inputs larger than L2 (kernel cache {info['cache_bytes'] / 1e9:.1f} GB per chunk)"},
         "source_kernels_per_s": n_src_pass / (march_ms * 1e-3),
@@ -866,8 +869,8 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     from paper_2408_11376_gb300 import synth
-    if args.prec == "fp64" or args.workload in synth.BATCH_WORKLOADS:
-        args.accum = "ff"            # the FP64 path and batch contexts sum in FP64 / float-float only
+    if args.prec == "fp64":
+        args.accum = "ff"            # the FP64 path sums in FP64
     if args.workload in synth.BATCH_WORKLOADS:
         bw = synth.BATCH_WORKLOADS[args.workload]
         return run_reference_batch(args, bw) if args.impl == "reference" else run_batch(args, bw)

@@ -77,7 +77,9 @@ typedef enum {
                               pair; the rounding of the row sums is not mass-neutral, so after every macro
                               step the field's FP64 total is restored to the total of the call's input:
                               c'(x) += (M_in - S) |c'(x)| / A with S = sum c', A = sum |c'| (FP64,
-                              fixed order), a change of the size of the FP32 rounding (~1e-8 relative) */
+                              fixed order), a change of the size of the FP32 rounding (~1e-8 relative).
+                              Batch contexts restore every structure's total separately, and their rare
+                              radii (source-indexed cache) keep the float-float sums */
 } fdirw_accum;
 
 typedef struct {
@@ -100,7 +102,7 @@ typedef struct {
                              and storage type, result cached for the process; that build synchronises the
                              stream) */
     int32_t  accum;       /* fdirw_accum; FDIRW_ACCUM_FP32 needs an FP32-march precision and an fdirw_create
-                             context (batch and coarse-mesh contexts take FDIRW_ACCUM_FF only) */
+                             or batch context (coarse-mesh contexts take FDIRW_ACCUM_FF only) */
 } fdirw_opts;
 
 typedef struct {

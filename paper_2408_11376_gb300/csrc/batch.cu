@@ -79,6 +79,8 @@ struct Batch {
     int64_t* d_qbase = nullptr;
     std::vector<int64_t> pbase;                  // n + 1: first element of each structure's padded chat
     float2* chat_pad = nullptr;                  // sigma * c with a halo of R_max (destination-indexed radii)
+    double* seg_part = nullptr;                  // FDIRW_ACCUM_FP32: 2 * kSegBlocks partial sums per structure
+    double* seg_fix = nullptr;                   // FDIRW_ACCUM_FP32: [target total, factor] per structure
     std::vector<Chunk> chunks;
     void* arena = nullptr;
     uint64_t arena_bytes = 0;
@@ -387,6 +389,7 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
     const Chunk& ch = b.chunks[ci];
     VarArgs a = var_args(c, ch, dst);
     const int64_t nblk = b.blk[ch.s1] - b.blk[ch.s0];
+    const bool fp32acc = c->accum == FDIRW_ACCUM_FP32;   // destination-indexed radii only; see the header
     const int Rm = c->R;
     cudaError_t e = cudaSuccess;
     const double* cur = src;
@@ -396,7 +399,8 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
             e = cudaGetLastError();
         }
         for (int i = ch.s0; i < ch.s1 && e == cudaSuccess && b.dest_mask; i++)
-            e = launch_scale(cur + b.base[i], c->sigma + b.base[i], b.grids[i], Rm, b.chat_pad + b.pbase[i], 1, st);
+            e = launch_scale(cur + b.base[i], c->sigma + b.base[i], b.grids[i], Rm, b.chat_pad + b.pbase[i],
+                             fp32acc ? 2 : 1, st);
         const bool last = t + 1 == n_steps;
         if (e == cudaSuccess && last) e = record(b.ev[4 * ci + 2], st, captured);
         if (e != cudaSuccess) break;
@@ -423,8 +427,11 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
                 for (int r : b.radii) {
                     if (r == 0 || !((b.dest_mask >> r) & 1u)) continue;
                     const void* Q = static_cast<const char*>(a.K[r]) + (size_t)b.qbase[i] * sb;
-                    e = launch_gather_part(Q, c->store, ch.qn, b.chat_pad + b.pbase[i], Rm, b.grids[i], r, w,
-                                           dst + b.base[i], sx);
+                    e = fp32acc ? launch_gather_part_fp32(Q, c->store, ch.qn,
+                                                          reinterpret_cast<const float*>(b.chat_pad + b.pbase[i]), Rm,
+                                                          b.grids[i], r, w, dst + b.base[i], sx)
+                                : launch_gather_part(Q, c->store, ch.qn, b.chat_pad + b.pbase[i], Rm, b.grids[i], r, w,
+                                                     dst + b.base[i], sx);
                     if (e != cudaSuccess) break;
                     w = true;
                 }
@@ -436,6 +443,7 @@ cudaError_t step_chunk(fdirw_ctx* c, int ci, const double* src, double* dst, int
             written = true;
         }
         if (e == cudaSuccess && last) e = record(b.ev[4 * ci + 3], st, captured);
+        if (e == cudaSuccess && fp32acc) e = launch_seg_restore(dst, b.d_base, ch.s0, ch.s1, b.seg_part, b.seg_fix, st);
         cur = dst;
     }
     return e;
@@ -447,6 +455,8 @@ cudaError_t issue_all(fdirw_ctx* c, const double* src, double* dst, int n_steps,
     Batch& b = *c->batch;
     cudaError_t e = cudaSuccess;
     const int nch = (int)b.chunks.size();
+    // FDIRW_ACCUM_FP32: every structure's FP64 total of the call's input, the target of its restoration.
+    if (c->accum == FDIRW_ACCUM_FP32) e = launch_seg_target(src, b.d_base, 0, b.n, b.seg_part, b.seg_fix, b.gs);
     for (int ci = 0; ci < nch && e == cudaSuccess; ci++) {
         const bool build = nch > 1 || build_single;
         if (build) e = build_chunk(c, ci, b.gs, true);
@@ -525,6 +535,8 @@ void release_batch(fdirw_ctx* c) {
     dfree(b->arena);
     p = b->chat; dfree(p);
     p = b->chat_pad; dfree(p);
+    p = b->seg_part; dfree(p);
+    p = b->seg_fix; dfree(p);
     for (auto& e : b->ev) if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
@@ -698,7 +710,7 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
     if (o.prec < FDIRW_FP32 || o.prec > FDIRW_FP32_STORE_BF16)
         return fail(nullptr, FDIRW_ERR_ARG, "a batch needs an FP32-march precision (FP32, FP16 or BF16 storage)");
     if (o.march_parts < 0 || o.march_parts > 6) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 6]");
-    if (o.accum != FDIRW_ACCUM_FF) return fail(nullptr, FDIRW_ERR_ARG, "batch contexts take FDIRW_ACCUM_FF only");
+    if (o.accum != FDIRW_ACCUM_FF && o.accum != FDIRW_ACCUM_FP32) return fail(nullptr, FDIRW_ERR_ARG, "unknown accum");
 
     DeviceGuard dg(o.device);
     if (!dg.ok) return fail(nullptr, FDIRW_ERR_CUDA, "cannot select CUDA device " + std::to_string(o.device));
@@ -709,6 +721,7 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
     c->stream = reinterpret_cast<cudaStream_t>(o.stream);
     c->mem_limit = o.mem_limit;
     c->parts_req = o.march_parts;
+    c->accum = o.accum;
     c->g = fdirw::Grid{(int)std::min<int64_t>(total, 0x7fffffff), 1, 1, total};   // flat view for fields
     c->h = grids[0].h;
     c->dt_macro = dt_macro;
@@ -878,6 +891,12 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
         if ((e = cudaMemsetAsync(b.chat_pad, 0, pbytes, c->stream)) != cudaSuccess) return cuda_bail("zero padded field", e);
     }
     if ((rc = dalloc(c, reinterpret_cast<void**>(&b.d_qbase), (uint64_t)n * 8, "structure table")) != FDIRW_OK) return bail(rc);
+    if (c->accum == FDIRW_ACCUM_FP32) {
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&b.seg_part), (uint64_t)n * 2 * fdirw::kSegBlocks * 8,
+                         "mass restoration partials")) != FDIRW_OK) return bail(rc);
+        if ((rc = dalloc(c, reinterpret_cast<void**>(&b.seg_fix), (uint64_t)n * 2 * 8, "mass restoration")) != FDIRW_OK)
+            return bail(rc);
+    }
 
     // Chunks: consecutive structures whose kernels fit the budget together.
     const int sb = fdirw::store_bytes(c->store);

@@ -117,6 +117,18 @@ cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Gr
 // field is zero), both sums in a fixed order.  partials: 2 * kMassBlocks doubles; fix: 2 doubles
 // (fix[0] = m_in on entry, fix[1] = f on exit).
 cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* fix, cudaStream_t st);
+// launch_gather_part with the FDIRW_ACCUM_FP32 arithmetic (FP32 chat with a halo of Rp).
+cudaError_t launch_gather_part_fp32(const void* Q, Store store, int64_t qs, const float* chat, int Rp, Grid g, int R,
+                                    bool accumulate, double* c_out, cudaStream_t st);
+// Per-structure mass restoration of structures [s0, s1) whose cells are [base[i], base[i + 1]) (base on
+// the device): launch_seg_target stores each structure's FP64 total of c in fix[2 i]; launch_seg_restore
+// then adds f_i |c| to every cell of structure i, f_i = (fix[2 i] - sum c) / sum |c|.  partials holds
+// 2 * kSegBlocks doubles per structure of the range.
+constexpr int kSegBlocks = 32;
+cudaError_t launch_seg_target(const double* c, const int64_t* base, int s0, int s1, double* partials, double* fix,
+                              cudaStream_t st);
+cudaError_t launch_seg_restore(double* c, const int64_t* base, int s0, int s1, double* partials, double* fix,
+                               cudaStream_t st);
 // Renormalised kernels of listed sources on the (2R+1)^3 offset layout.
 cudaError_t launch_read_kernels(const void* Q, Store store, const double* sigma, Grid g, int R,
                                 const int64_t* sources, int64_t n_src, double* out, cudaStream_t st);

@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
 // FP32 chat; the rows still go into a double-float pair per destination.  The caller restores the mass.
 template <typename ST, int R>
 __global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__ Q, const float* __restrict__ chat,
-                                                          Grid g, Pad p, double* __restrict__ out) {
+                                                          Grid g, Pad p, int64_t qs, bool acc_in,
+                                                          double* __restrict__ out) {
     constexpr int VX = 16 / sizeof(ST);
     constexpr int W1 = 2 * R + 1;
     constexpr int NC = VX + 2 * R;
@@ -124,14 +125,14 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__
             float ch[NC];
 #pragma unroll
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
-            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + i0;
             float s[VX];
 #pragma unroll
             for (int j = 0; j < VX; j++) s[j] = 0.f;
 #pragma unroll
             for (int ox = -R; ox <= R; ox++) {
                 float q[VX];
-                load_q<ST, VX>(qrow + (int64_t)(ox + R) * g.n, q);
+                load_q<ST, VX>(qrow + (int64_t)(ox + R) * qs, q);
 #pragma unroll
                 for (int j = 0; j < VX; j++) s[j] = fmaf(q[j], ch[j - ox + R], s[j]);
             }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__
         }
     }
 #pragma unroll
-    for (int j = 0; j < VX; j++) out[i0 + j] = (double)A[j] + (double)B[j];
+    for (int j = 0; j < VX; j++) out[i0 + j] = (acc_in ? out[i0 + j] : 0.0) + ((double)A[j] + (double)B[j]);
 }
 
 // FP64 path: FP64 storage, FP64 chat, FP64 FMA accumulation, VX = 2.
@@ -327,6 +328,69 @@ __global__ void mass_apply_kernel(double* __restrict__ c, int64_t n, const doubl
         c[i] = fma(f, fabs(c[i]), c[i]);
 }
 
+// Per-structure mass restoration of batch contexts: kSegBlocks blocks per structure, block p summing the
+// p-th contiguous part of its cells (c and |c|); then one warp per structure sums the parts in order.
+__global__ void __launch_bounds__(256) seg_sums_kernel(const double* __restrict__ c, const int64_t* __restrict__ base,
+                                                       int s0, double* __restrict__ partials) {
+    __shared__ double sh[2][8];
+    const int i = s0 + (int)(blockIdx.x / kSegBlocks), part = (int)(blockIdx.x % kSegBlocks);
+    const int64_t b0 = base[i], n = base[i + 1] - b0;
+    const int64_t chunk = (n + kSegBlocks - 1) / kSegBlocks;
+    const int64_t lo = b0 + part * chunk;
+    const int64_t hi = lo + chunk < b0 + n ? lo + chunk : b0 + n;
+    double acc = 0.0, aab = 0.0;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double v = c[j];
+        acc += v;
+        aab += fabs(v);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        aab += __shfl_xor_sync(0xffffffffu, aab, off);
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = acc; sh[1][threadIdx.x >> 5] = aab; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? sh[0][threadIdx.x] : 0.0;
+        double w = threadIdx.x < (blockDim.x >> 5) ? sh[1][threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, off);
+            w += __shfl_xor_sync(0xffffffffu, w, off);
+        }
+        if (threadIdx.x == 0) { partials[2 * blockIdx.x] = v; partials[2 * blockIdx.x + 1] = w; }
+    }
+}
+
+// One warp per structure i in [s0, s0 + nseg): target == true stores its total in fix[2 i]; otherwise
+// fix[2 i + 1] = (fix[2 i] - S_i) / A_i (0 when A_i = 0).
+__global__ void seg_fix_kernel(const double* __restrict__ partials, int s0, int nseg, double* __restrict__ fix,
+                               bool target) {
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= nseg) return;
+    static_assert(kSegBlocks == 32, "one part per lane");
+    double S = partials[2 * (w * kSegBlocks + lane)], A = partials[2 * (w * kSegBlocks + lane) + 1];
+    for (int off = 16; off > 0; off >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, off);
+        A += __shfl_xor_sync(0xffffffffu, A, off);
+    }
+    const int i = s0 + w;
+    if (lane == 0) {
+        if (target) fix[2 * i] = S;
+        else fix[2 * i + 1] = A > 0.0 ? (fix[2 * i] - S) / A : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) seg_apply_kernel(double* __restrict__ c, const int64_t* __restrict__ base, int s0,
+                                                        const double* __restrict__ fix) {
+    const int i = s0 + (int)(blockIdx.x / kSegBlocks), part = (int)(blockIdx.x % kSegBlocks);
+    const int64_t b0 = base[i], n = base[i + 1] - b0;
+    const int64_t chunk = (n + kSegBlocks - 1) / kSegBlocks;
+    const int64_t lo = b0 + part * chunk;
+    const int64_t hi = lo + chunk < b0 + n ? lo + chunk : b0 + n;
+    const double f = fix[2 * i + 1];
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) c[j] = fma(f, fabs(c[j]), c[j]);
+}
+
 template <typename ST>
 __global__ void read_kernels_kernel(const ST* __restrict__ Q, const double* __restrict__ sigma, Grid g, int R,
                                     const int64_t* __restrict__ sources, int64_t n_src, double* __restrict__ out) {
@@ -495,6 +559,31 @@ cudaError_t launch_mass(const double* c, int64_t n, double* partials, double* ou
     return cudaGetLastError();
 }
 
+cudaError_t launch_seg_target(const double* c, const int64_t* base, int s0, int s1, double* partials, double* fix,
+                              cudaStream_t st) {
+    const int nseg = s1 - s0;
+    if (nseg <= 0) return cudaSuccess;
+    seg_sums_kernel<<<nseg * kSegBlocks, 256, 0, st>>>(c, base, s0, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    seg_fix_kernel<<<(nseg * 32 + 255) / 256, 256, 0, st>>>(partials, s0, nseg, fix, true);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_restore(double* c, const int64_t* base, int s0, int s1, double* partials, double* fix,
+                               cudaStream_t st) {
+    const int nseg = s1 - s0;
+    if (nseg <= 0) return cudaSuccess;
+    seg_sums_kernel<<<nseg * kSegBlocks, 256, 0, st>>>(c, base, s0, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    seg_fix_kernel<<<(nseg * 32 + 255) / 256, 256, 0, st>>>(partials, s0, nseg, fix, false);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    seg_apply_kernel<<<nseg * kSegBlocks, 256, 0, st>>>(c, base, s0, fix);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* fix, cudaStream_t st) {
     mass_abs_partial_kernel<<<kMassBlocks, 256, 0, st>>>(c, n, partials);
     cudaError_t e = cudaGetLastError();
@@ -509,61 +598,71 @@ cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* 
 }
 
 template <typename ST, int R>
-cudaError_t gather_fp32_r(const void* Q, const float* chat, Grid g, Pad p, double* out, cudaStream_t st) {
+cudaError_t gather_fp32_r(const void* Q, const float* chat, Grid g, Pad p, int64_t qs, bool acc_in, double* out,
+                          cudaStream_t st) {
     constexpr int VX = 16 / sizeof(ST);
     const int64_t nt = (int64_t)(g.nx / VX) * g.ny * g.nz;
-    gather_fp32_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q), chat, g, p, out);
+    gather_fp32_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q), chat, g, p, qs,
+                                                                     acc_in, out);
     return cudaGetLastError();
 }
 
 template <typename ST>
-cudaError_t gather_fp32_st(const void* Q, const float* chat, Grid g, int R, Pad p, double* out, cudaStream_t st) {
+cudaError_t gather_fp32_st(const void* Q, const float* chat, Grid g, int R, Pad p, int64_t qs, bool acc_in,
+                           double* out, cudaStream_t st) {
     switch (R) {
-        case 1: return gather_fp32_r<ST, 1>(Q, chat, g, p, out, st);
-        case 2: return gather_fp32_r<ST, 2>(Q, chat, g, p, out, st);
-        case 3: return gather_fp32_r<ST, 3>(Q, chat, g, p, out, st);
-        case 4: return gather_fp32_r<ST, 4>(Q, chat, g, p, out, st);
-        case 5: return gather_fp32_r<ST, 5>(Q, chat, g, p, out, st);
-        case 6: return gather_fp32_r<ST, 6>(Q, chat, g, p, out, st);
-        case 7: return gather_fp32_r<ST, 7>(Q, chat, g, p, out, st);
-        case 8: return gather_fp32_r<ST, 8>(Q, chat, g, p, out, st);
-        case 9: return gather_fp32_r<ST, 9>(Q, chat, g, p, out, st);
-        case 10: return gather_fp32_r<ST, 10>(Q, chat, g, p, out, st);
+        case 1: return gather_fp32_r<ST, 1>(Q, chat, g, p, qs, acc_in, out, st);
+        case 2: return gather_fp32_r<ST, 2>(Q, chat, g, p, qs, acc_in, out, st);
+        case 3: return gather_fp32_r<ST, 3>(Q, chat, g, p, qs, acc_in, out, st);
+        case 4: return gather_fp32_r<ST, 4>(Q, chat, g, p, qs, acc_in, out, st);
+        case 5: return gather_fp32_r<ST, 5>(Q, chat, g, p, qs, acc_in, out, st);
+        case 6: return gather_fp32_r<ST, 6>(Q, chat, g, p, qs, acc_in, out, st);
+        case 7: return gather_fp32_r<ST, 7>(Q, chat, g, p, qs, acc_in, out, st);
+        case 8: return gather_fp32_r<ST, 8>(Q, chat, g, p, qs, acc_in, out, st);
+        case 9: return gather_fp32_r<ST, 9>(Q, chat, g, p, qs, acc_in, out, st);
+        case 10: return gather_fp32_r<ST, 10>(Q, chat, g, p, qs, acc_in, out, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Grid g, int R, double* c_out,
-                               cudaStream_t st) {
-    if (R < 1 || R > kMaxR || store == Store::F64) return cudaErrorInvalidValue;
-    const Pad p = make_pad(g, R);
+cudaError_t launch_gather_part_fp32(const void* Q, Store store, int64_t qs, const float* chat, int Rp, Grid g, int R,
+                                    bool accumulate, double* c_out, cudaStream_t st) {
+    if (R < 1 || R > Rp || R > kMaxR || store == Store::F64) return cudaErrorInvalidValue;
+    const Pad p = make_pad(g, Rp);
+    // The kernels index chat as if its halo were R: move the base by (Rp - R) on every axis.
+    const float* ch = chat + ((int64_t)(Rp - R) * p.py + (Rp - R)) * p.px + (Rp - R);
     const int vx = 16 / store_bytes(store);
-    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (g.n * store_bytes(store)) % 16 == 0;
+    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (qs * store_bytes(store)) % 16 == 0;
     if (g.nx % vx == 0 && aligned) {
         switch (store) {
-            case Store::F32: return gather_fp32_st<float>(Q, chat, g, R, p, c_out, st);
-            case Store::F16: return gather_fp32_st<__half>(Q, chat, g, R, p, c_out, st);
-            case Store::BF16: return gather_fp32_st<__nv_bfloat16>(Q, chat, g, R, p, c_out, st);
+            case Store::F32: return gather_fp32_st<float>(Q, ch, g, R, p, qs, accumulate, c_out, st);
+            case Store::F16: return gather_fp32_st<__half>(Q, ch, g, R, p, qs, accumulate, c_out, st);
+            case Store::BF16: return gather_fp32_st<__nv_bfloat16>(Q, ch, g, R, p, qs, accumulate, c_out, st);
             default: return cudaErrorInvalidValue;
         }
     }
     const int b = blocks_for(g.n, 256);
     switch (store) {
         case Store::F32:
-            gather_scalar_kernel<float, 2><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), chat, g, p, R, g.n,
-                                                              false, c_out);
+            gather_scalar_kernel<float, 2><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
+                                                              accumulate, c_out);
             break;
         case Store::F16:
-            gather_scalar_kernel<__half, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), chat, g, p, R, g.n,
-                                                               false, c_out);
+            gather_scalar_kernel<__half, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R, qs,
+                                                               accumulate, c_out);
             break;
         case Store::BF16:
-            gather_scalar_kernel<__nv_bfloat16, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), chat,
-                                                                      g, p, R, g.n, false, c_out);
+            gather_scalar_kernel<__nv_bfloat16, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), ch,
+                                                                      g, p, R, qs, accumulate, c_out);
             break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Grid g, int R, double* c_out,
+                               cudaStream_t st) {
+    return launch_gather_part_fp32(Q, store, g.n, chat, R, g, R, false, c_out, st);
 }
 
 cudaError_t launch_read_kernels(const void* Q, Store store, const double* sigma, Grid g, int R,

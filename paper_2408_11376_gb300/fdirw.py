@@ -198,7 +198,7 @@ def fdirw_create(shape, D, dt_macro: float, window_R: int, n_sub: int, prec="fp3
 
 
 def fdirw_create_batch(shapes, Ds, dt_macro: float, R_min: int, R_max: int, n_sub: int, prec="fp32", hs=None,
-                       device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0) -> int:
+                       device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0, accum="ff") -> int:
     """Context for a batch of structures with per-source radii; fields are the concatenation of the
     structures' fields.  Returns the handle; release it with fdirw_destroy."""
     lib = load()
@@ -215,7 +215,8 @@ def fdirw_create_batch(shapes, Ds, dt_macro: float, R_min: int, R_max: int, n_su
         ptrs[i] = _ptr(D)
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     st = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
-    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), int(march_parts), 0)
+    acc = ACCUMS[accum] if isinstance(accum, str) else int(accum)
+    o = fdirw_opts(p, int(device), ctypes.c_void_p(st), int(mem_limit), int(march_parts), acc)
     ctx = ctypes.c_void_p(0)
     _check(lib.fdirw_create_batch(int(n), grids, ptrs, float(dt_macro), int(R_min), int(R_max), int(n_sub),
                                   ctypes.byref(o), ctypes.byref(ctx)))
@@ -387,14 +388,14 @@ class FDiRWBatch(FDiRW):
     the concatenation of the structures' fields (``offsets[i]`` is structure i's first cell)."""
 
     def __init__(self, shapes, Ds, dt_macro: float, R_min: int, R_max: int, n_sub: int, prec="fp32", hs=None,
-                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0):
+                 device: int = -1, stream=None, mem_limit: int = 0, march_parts: int = 0, accum="ff"):
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         sizes = [a * b * c for a, b, c in self.shapes]
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         self.n = int(self.offsets[-1])
         self.R = int(R_max)
         self.ctx = fdirw_create_batch(self.shapes, Ds, dt_macro, R_min, R_max, n_sub, prec, hs, device, stream,
-                                      mem_limit, march_parts)
+                                      mem_limit, march_parts, accum)
 
     def radius(self) -> np.ndarray:
         return fdirw_read_radius(self.ctx, self.n)

@@ -67,12 +67,12 @@ def test_batch_host_side_argument_checks(lib):
     fp64 = fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)
     parts7 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 7, 0)
     bad_grid = (fdirw.fdirw_grid * 1)(fdirw.fdirw_grid(4, 0, 4, 1.0))
-    acc32 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, fdirw.FDIRW_ACCUM_FP32)
+    acc_bad = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, 2)
     cases = [(0, g, ptrs, 1.0, 1, 3, 2, None), (2, None, ptrs, 1.0, 1, 3, 2, None), (2, g, None, 1.0, 1, 3, 2, None),
              (2, g, ptrs, 1.0, 1, 11, 2, None), (2, g, ptrs, 1.0, 4, 3, 2, None), (2, g, ptrs, 1.0, -1, 3, 2, None),
              (2, g, ptrs, -1.0, 1, 3, 2, None), (2, g, ptrs, 1.0, 1, 3, -2, None), (1, huge, ptrs, 1.0, 1, 3, 2, None),
              (2, g, ptrs, 1.0, 1, 3, 2, fp64), (2, g, ptrs, 1.0, 1, 3, 2, parts7), (1, bad_grid, ptrs, 1.0, 1, 3, 2, None),
-             (2, g, ptrs, 1.0, 1, 3, 2, acc32)]
+             (2, g, ptrs, 1.0, 1, 3, 2, acc_bad)]
     for n, grids, dm, dt, rmin, rmax, n_sub, opts in cases:
         ctx = ctypes.c_void_p(1234)
         rc = lib.fdirw_create_batch(n, grids, dm, dt, rmin, rmax, n_sub, ctypes.byref(opts) if opts else None,

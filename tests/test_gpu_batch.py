@@ -213,6 +213,40 @@ def test_zero_radius_sources_and_identity_cases():
         assert np.array_equal(out, c0)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fp32_accum_batch_matches_oracle_and_keeps_every_structure_mass(prec):
+    """FDIRW_ACCUM_FP32 on a batch mixing both cache layouts: fields per structure against the oracle,
+    every structure's total restored to its input's, and chunked execution bit for bit the resident one."""
+    shapes = [(16, 12, 10), (11, 14, 9), (24, 16, 8)]
+    Ds = [synth.random_diffusivity(s, 360 + i, 4.0) for i, s in enumerate(shapes)]
+    n_sub = 20
+    dt = n_sub * min(oracle.stable_dt_sub(s, D) for s, D in zip(shapes, Ds))
+    c0 = np.concatenate([synth.random_field(int(np.prod(s)), 370 + i, 0.0, 2.0) for i, s in enumerate(shapes)])
+    with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, prec, accum="fp32") as b:
+        out = np.empty_like(c0)
+        b.step(c0, out, 3)
+        Rmap = b.radius()
+        info = b.info()
+        offs = b.offsets
+    assert info["accum"] == fdirw.FDIRW_ACCUM_FP32
+    present = set(int(r) for r in np.unique(Rmap))
+    dest = {r for r in present if (info["dest_indexed_radii"] >> r) & 1}
+    assert dest and (present - dest)
+    for i, shape in enumerate(shapes):
+        sl = slice(int(offs[i]), int(offs[i + 1]))
+        ref = c0[sl]
+        for _ in range(3):
+            ref = oracle.superpose_rmap(shape, Ds[i], dt / n_sub, Rmap[sl], n_sub, ref)
+        assert _rel(out[sl], ref) <= FIELD_TOL[prec], (prec, i, _rel(out[sl], ref))
+        assert abs(out[sl].sum() - c0[sl].sum()) <= 1e-13 * c0[sl].sum()
+    limit = info["device_bytes"] - info["cache_bytes"] + info["cache_bytes"] * 2 // 3
+    with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, prec, mem_limit=limit, accum="fp32") as b:
+        out2 = np.empty_like(c0)
+        b.step(c0, out2, 3)
+        assert b.info()["n_chunks"] >= 2
+    assert np.array_equal(out, out2)
+
+
 def test_batch_argument_errors():
     shape = (8, 8, 8)
     D = np.ones(512)
