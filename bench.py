@@ -185,6 +185,12 @@ def march_traffic(args, prec: str, parts: int, R: int, window_cells: float):
     return None
 
 
+# DRAM bytes (read + write) per algorithmic byte of gather_fp32_kernel<bf16> from one ncu capture of the
+# 96^3, R = 6 case (profiles/gather_fp32_R6_96c.md: 3.8927e9 read + 3.33e6 written against 3.8971e9
+# algorithmic); the traffic of a launch grows with its cache bytes.  Valid for that kernel and storage only.
+GATHER_FP32_BF16_DRAM_PER_ALGORITHMIC_BYTE = (3.892684288e9 + 3.326464e6) / (96 ** 3 * (13 ** 3 * 2 + 4 + 8))
+
+
 def gather_roofline(prec: str, accum: str, N: int, R: int, gather_ms: float):
     """HBM roofline of one superposition launch: algorithmic bytes = the kernel cache (N (2R+1)^3 stored
     values, each read once) + the scaled field it multiplies (FP32, or FP32 pairs) + the FP64 output."""
@@ -195,8 +201,12 @@ def gather_roofline(prec: str, accum: str, N: int, R: int, gather_ms: float):
     achieved = nbytes / (gather_ms * 1e-3) / 1e9
     kname = ("gather_f64_kernel<R>" if prec == "fp64" else
              "gather_fp32_kernel<ST,R>" if accum == "fp32" else "gather_ff_kernel<ST,R>")
+    traffic = GATHER_FP32_BF16_DRAM_PER_ALGORITHMIC_BYTE * nbytes if (prec == "bf16" and accum == "fp32") else None
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({peak_src})",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "traffic_source": "ncu capture of the 96^3 R=6 case (profiles/gather_fp32_R6_96c.md), DRAM bytes "
+                              "scaled by algorithmic bytes to this launch" if traffic is not None else None,
+            "peak_source": f"hbm_gbs ({peak_src})",
             "algorithmic": f"cache {N}x{(2 * R + 1) ** 3}x{qb} B + field {chat_b} B + output 8 B per cell "
                            f"= {nbytes / 1e9:.2f} GB per launch"}
 
