@@ -299,8 +299,8 @@ FDIRW_API int fdirw_coupled_step(fdirw_ctx* ctx, const fdirw_coupled_params* par
  * and the march runs mapping 5 (direction-dependent faces); the superposition is unchanged.  A second
  * call replaces the velocity; the kernels are recomputed by the next fdirw_kernels / fdirw_step.  With
  * w = 0 the kernels and steps are bit for bit those without a velocity.  Synchronises the context
- * stream.  Errors: FDIRW_ERR_ARG (NULL or misaligned w, a batch or coarse context, FDIRW_FP64
- * precision), FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
+ * stream.  Errors: FDIRW_ERR_ARG (NULL or misaligned w, NaN or infinite values, a batch or coarse
+ * context, FDIRW_FP64 precision), FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
  * any, stays in place), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
 FDIRW_API int fdirw_set_velocity(fdirw_ctx* ctx, const double* w);
 

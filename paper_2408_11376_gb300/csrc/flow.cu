@@ -124,6 +124,7 @@ int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     cudaFree(AB);
     c->allocated -= 3 * n * 8 + 8 + 6 * n * 4;
     if (e != cudaSuccess) { cudaGetLastError(); return fail(c, FDIRW_ERR_CUDA, cuda_msg("velocity coefficients", e)); }
+    if (!std::isfinite(m)) return fail(c, FDIRW_ERR_ARG, "w holds NaN or infinite values");
     if (!stable) {
         char buf[200];
         std::snprintf(buf, sizeof buf, "unstable with convection: largest outflow coefficient sum %.17g > 1", m);

@@ -142,6 +142,13 @@ def test_velocity_replaced_and_errors():
         c2 = np.empty_like(c0)
         f.step(c0, c2, 1)                                # w2 still in place
         assert np.array_equal(c, c2)
+        bad = w2.reshape(-1).copy()
+        bad[17] = np.nan
+        with pytest.raises(FdirwError) as e:
+            f.set_velocity(bad)
+        assert e.value.code == fdirw.FDIRW_ERR_ARG
+        f.step(c0, c2, 1)                                # w2 still in place
+        assert np.array_equal(c, c2)
         with pytest.raises(ValueError):
             f.set_velocity(np.zeros(N))
     with FDiRW(shape, D, 20 * lam, 3, 20, "fp64") as f:
