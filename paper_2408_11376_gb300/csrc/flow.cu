@@ -30,7 +30,7 @@ __device__ __forceinline__ double harmonic(double a, double b) {
 
 // A and B of the +x, +y, +z face of every cell (FP32, one rounding from FP64), 0 on the last plane; and
 // the largest per-cell sum of outflow coefficients (bits of a non-negative double, for atomicMax) for the
-// stability check.
+// stability check, +inf where a velocity that enters the march is NaN or infinite.
 __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const double* __restrict__ w,
                                  double lam, double lama, float* __restrict__ A,
                                  float* __restrict__ Bc, unsigned long long* __restrict__ max_bits) {
@@ -49,6 +49,7 @@ __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const dou
                 const double wv = w[ax * g.n + i];
                 a = gd + lama * (wv > 0.0 ? wv : 0.0);
                 b = gd + lama * (wv < 0.0 ? -wv : 0.0);
+                if (!isfinite(wv)) out = INFINITY;          // reported as invalid input, never installed
             }
             A[ax * g.n + i] = (float)a;
             Bc[ax * g.n + i] = (float)b;
