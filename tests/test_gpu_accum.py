@@ -83,6 +83,28 @@ def test_fp32_accum_zero_and_mixed_sign_fields():
     assert np.max(np.abs(a - b)) <= 1e-6 * np.abs(b).max()
 
 
+def test_fp32_accum_host_buffers_and_identity_cases():
+    """Host fields give the device result bit for bit; n_steps = 0 and R = 0 copy the field unchanged."""
+    shape, R, n_sub = (16, 12, 10), 3, 25
+    D = _case(shape, 158)
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(D.size, 159)
+    with FDiRW(shape, D, n_sub * lam, R, n_sub, "bf16", accum="fp32") as f:
+        dev_in = torch.from_numpy(c0).to(DEV)
+        dev_out = torch.empty_like(dev_in)
+        f.step(dev_in, dev_out, 2)
+        host = np.empty_like(c0)
+        f.step(c0, host, 2)
+        same = np.empty_like(c0)
+        f.step(c0, same, 0)
+    assert np.array_equal(dev_out.cpu().numpy(), host)
+    assert np.array_equal(same, c0)
+    with FDiRW(shape, D, n_sub * lam, 0, n_sub, "fp32", accum="fp32") as f:
+        out = np.empty_like(c0)
+        f.step(c0, out, 3)
+    assert np.array_equal(out, c0)
+
+
 def test_fp32_accum_deterministic():
     shape, R, n_sub = (24, 16, 16), 5, 40
     D = _case(shape, 156)
