@@ -124,7 +124,8 @@ typedef struct {
     int32_t  march_parts;    /* thread mapping of the last kernel-cache build (see fdirw_opts) */
     int32_t  accum;          /* fdirw_accum in use */
     int32_t  n_structures;   /* batch contexts: number of structures (0 for fdirw_create contexts) */
-    int32_t  n_chunks;       /* batch contexts: structure chunks whose kernels are built one at a time */
+    int32_t  n_chunks;       /* batch contexts: structure chunks whose kernels are built one at a time;
+                                fdirw_create contexts: z-slabs of a streamed cache (1 when resident) */
     int32_t  window_R_min;   /* batch contexts: R_min of the radius rule */
     int32_t  graph_launches; /* batch contexts: CUDA graph launches so far (one per fdirw_step call) */
     int32_t  dest_indexed_radii; /* batch contexts: bit r set when radius r's kernels are stored
@@ -157,8 +158,13 @@ FDIRW_API int fdirw_create(const fdirw_grid* grid, const double* D_map, double d
 
 /* Build (or rebuild) the kernel cache: for every source cell s, march a unit mass over its window for
  * n_sub substeps (Sec. 3.1), store the result in the storage precision and sigma_s = 1 / (FP64 sum of
- * the stored values).  Idempotent; asynchronous on the context stream.
- * Errors: FDIRW_ERR_ARG (NULL ctx), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+ * the stored values).  Idempotent; asynchronous on the context stream.  When the whole cache
+ * (N (2R+1)^3 values) does not fit the device's free memory (less 1 GiB) or mem_limit, the context
+ * streams it instead: the cache holds T destination z-planes (as many as fit next to an N-double
+ * buffer) and every fdirw_step marches, slab by slab, the sources within R planes of the slab before
+ * gathering it (the same results bit for bit, at the cost of a march per step; fdirw_info.n_chunks gives
+ * the number of slabs); fdirw_kernels then builds nothing.
+ * Errors: FDIRW_ERR_ARG (NULL ctx), FDIRW_ERR_NOMEM (not even one z-plane fits), FDIRW_ERR_CUDA. */
 FDIRW_API int fdirw_kernels(fdirw_ctx* ctx);
 
 /* Advance a field n_steps macro steps with the superposition c' = p c (Eq. 8, Eq. 14):
@@ -178,7 +184,7 @@ FDIRW_API int fdirw_mass(fdirw_ctx* ctx, const double* c, double* mass_out);
  * the offset layout o = x - s (o_x fastest, index (ox+R) + (2R+1)*((oy+R) + (2R+1)*(oz+R))), equal to
  * stored value * sigma_s, and 0 where x is outside the domain.  sources: host int64 array; out: host
  * float64 array of n*(2R+1)^3.  Synchronises.  Errors: FDIRW_ERR_ARG (index out of range),
- * FDIRW_ERR_STATE (cache not built), FDIRW_ERR_CUDA, FDIRW_ERR_NOMEM. */
+ * FDIRW_ERR_STATE (cache not built, or streamed by z-slabs), FDIRW_ERR_CUDA, FDIRW_ERR_NOMEM. */
 FDIRW_API int fdirw_read_kernels(fdirw_ctx* ctx, const int64_t* sources, int64_t n, double* out);
 
 /* Snapshot of the context's configuration and last timings.  Synchronises on the timing events. */

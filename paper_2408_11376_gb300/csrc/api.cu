@@ -129,6 +129,7 @@ void release(fdirw_ctx* c) {
     p = c->partials; dfree(p); c->partials = nullptr;
     p = c->dmass; dfree(p); c->dmass = nullptr;
     p = c->dfix; dfree(p); c->dfix = nullptr;
+    p = c->obuf; dfree(p); c->obuf = nullptr;
     p = c->Dd; dfree(p); c->Dd = nullptr;
     p = c->dsrc; dfree(p); c->dsrc = nullptr;
     p = c->dkout; dfree(p); c->dkout = nullptr;
@@ -137,14 +138,104 @@ void release(fdirw_ctx* c) {
 
 }  // namespace
 
+// The kernel cache: all N destinations when they fit the device's free memory (less a reserve) and the
+// context's mem_limit; otherwise slab streaming, a cache of T destination z-planes (as many as fit next
+// to an output field) that every macro step refills slab by slab: the kernels are marched again each
+// step, for the sources within R planes of the slab.
 int fdirw::ensure_cache(fdirw_ctx* c) {
     if (c->Q) return FDIRW_OK;
     const uint64_t W = (uint64_t)(2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
-    c->q_bytes = W * (uint64_t)c->g.n * (uint64_t)fdirw::store_bytes(c->store);
+    const uint64_t plane = W * (uint64_t)c->g.nx * (uint64_t)c->g.ny * (uint64_t)fdirw::store_bytes(c->store);
+    const uint64_t full = plane * (uint64_t)c->g.nz;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    constexpr uint64_t kReserve = 1ull << 30;
+    uint64_t budget = free_b > kReserve ? free_b - kReserve : 0;
+    if (c->mem_limit) budget = std::min<uint64_t>(budget, c->mem_limit > c->allocated ? c->mem_limit - c->allocated : 0);
+    int T = c->g.nz;
+    if (full > budget) {
+        const uint64_t obytes = (uint64_t)c->g.n * 8;
+        const uint64_t rest = budget > obytes ? budget - obytes : 0;
+        T = (int)std::min<uint64_t>(rest / plane, (uint64_t)c->g.nz);
+        if (T < 1)
+            return fail(c, FDIRW_ERR_NOMEM, "the kernel cache does not fit, not even one z-plane of destinations (" +
+                                                std::to_string(plane) + " bytes)");
+        int rc = dalloc(c, reinterpret_cast<void**>(&c->obuf), obytes, "streamed step output");
+        if (rc != FDIRW_OK) return rc;
+        c->slab_T = T < c->g.nz ? T : 0;
+    }
+    c->q_bytes = plane * (uint64_t)T;
     const int rc = dalloc(c, &c->Q, c->q_bytes, "kernel cache");
-    if (rc != FDIRW_OK) { c->q_bytes = 0; return rc; }
+    if (rc != FDIRW_OK) { c->q_bytes = 0; c->slab_T = 0; return rc; }
     // Entries whose source lies outside the domain are never written by the march: zero them once.
     FDIRW_CUDA(c, cudaMemsetAsync(c->Q, 0, c->q_bytes, c->stream));
+    return FDIRW_OK;
+}
+
+// March arguments of a uniform context: every source, the whole cache.
+fdirw::MarchArgs fdirw::march_args(const fdirw_ctx* c) {
+    MarchArgs a{};
+    a.g = c->g;
+    a.R = c->R;
+    a.Rq = c->R;
+    a.q_stride = c->g.n;
+    a.n_sub = c->n_sub;
+    if (c->store == Store::F64) {
+        a.dx = reinterpret_cast<const double*>(c->coef[0]);
+        a.dy = reinterpret_cast<const double*>(c->coef[1]);
+        a.dz = reinterpret_cast<const double*>(c->coef[2]);
+    } else {
+        a.ax = reinterpret_cast<const float*>(c->coef[0]);
+        a.ay = reinterpret_cast<const float*>(c->coef[1]);
+        a.az = reinterpret_cast<const float*>(c->coef[2]);
+    }
+    a.Q = c->Q;
+    a.store = c->store;
+    a.sigma = c->sigma;
+    a.src_begin = 0;
+    a.src_end = c->g.n;
+    a.list = nullptr;
+    if (c->flow) {                                    // convection: direction-dependent faces (mapping 5)
+        a.bx = reinterpret_cast<const float*>(c->coefb[0]);
+        a.by = reinterpret_cast<const float*>(c->coefb[1]);
+        a.bz = reinterpret_cast<const float*>(c->coefb[2]);
+    }
+    return a;
+}
+
+// Macro steps with a streamed cache: per step and slab of T destination planes, the march of the sources
+// within R planes of the slab (only the slab's destinations stored, sigma of every marched source), the
+// scaled field of those sources, and the gather of the slab into a buffer other than the step's input;
+// then the mass restoration (FP32 accumulation).  Results equal the resident cache's bit for bit.
+int fdirw::step_slabs(fdirw_ctx* c, const double* src, double* dst, int n_steps) {
+    const int T = c->slab_T, nz = c->g.nz, R = c->R;
+    const int64_t nxy = (int64_t)c->g.nx * c->g.ny;
+    const bool fp32acc = c->accum == FDIRW_ACCUM_FP32;
+    const int mode = c->store == Store::F64 ? 0 : fp32acc ? 2 : 1;
+    if (fp32acc) FDIRW_CUDA(c, fdirw::launch_mass(src, c->g.n, c->partials, c->dfix, c->stream));
+    MarchArgs a = march_args(c);
+    a.q_stride = (int64_t)T * nxy;
+    const double* cur = src;
+    for (int t = 0; t < n_steps; t++) {
+        // The step writes a buffer other than its input; the last one lands in dst unless dst is the input.
+        double* out = ((n_steps - 1 - t) % 2 == 0) ? dst : c->obuf;
+        if (out == cur) out = (out == dst) ? c->obuf : dst;
+        for (int z0 = 0; z0 < nz; z0 += T) {
+            const int zn = std::min(T, nz - z0);
+            const int zs0 = std::max(z0 - R, 0), zs1 = std::min(z0 + zn + R, nz);
+            a.src_begin = (int64_t)zs0 * nxy;
+            a.src_end = (int64_t)zs1 * nxy;
+            a.dest_lo = (int64_t)z0 * nxy;
+            a.dest_hi = (int64_t)(z0 + zn) * nxy;
+            FDIRW_CUDA(c, launch_march(a, c->num_sms, c->parts_req, c->stream, &c->parts_used));
+            FDIRW_CUDA(c, launch_scale(cur, c->sigma, c->g, R, c->chat, mode, c->stream, zs0, zs1 - zs0));
+            FDIRW_CUDA(c, launch_gather_slab(c->Q, c->store, (int64_t)T * nxy, a.dest_lo, c->chat, c->g, R, mode, z0,
+                                             zn, out, c->stream));
+        }
+        if (fp32acc) FDIRW_CUDA(c, fdirw::launch_restore_mass(out, c->g.n, c->partials, c->dfix, c->stream));
+        cur = out;
+    }
+    if (cur != dst) FDIRW_CUDA(c, cudaMemcpyAsync(dst, cur, (size_t)c->g.n * 8, cudaMemcpyDeviceToDevice, c->stream));
     return FDIRW_OK;
 }
 
@@ -285,32 +376,8 @@ int fdirw_kernels(fdirw_ctx* c) {
     if (c->R == 0) { c->kernels_ready = true; return FDIRW_OK; }
     const int rc = fdirw::ensure_cache(c);
     if (rc != FDIRW_OK) return rc;
-    fdirw::MarchArgs a{};
-    a.g = c->g;
-    a.R = c->R;
-    a.Rq = c->R;
-    a.q_stride = c->g.n;
-    a.n_sub = c->n_sub;
-    if (c->store == Store::F64) {
-        a.dx = reinterpret_cast<const double*>(c->coef[0]);
-        a.dy = reinterpret_cast<const double*>(c->coef[1]);
-        a.dz = reinterpret_cast<const double*>(c->coef[2]);
-    } else {
-        a.ax = reinterpret_cast<const float*>(c->coef[0]);
-        a.ay = reinterpret_cast<const float*>(c->coef[1]);
-        a.az = reinterpret_cast<const float*>(c->coef[2]);
-    }
-    a.Q = c->Q;
-    a.store = c->store;
-    a.sigma = c->sigma;
-    a.src_begin = 0;
-    a.src_end = c->g.n;
-    a.list = nullptr;
-    if (c->flow) {                                    // convection: direction-dependent faces (mapping 5)
-        a.bx = reinterpret_cast<const float*>(c->coefb[0]);
-        a.by = reinterpret_cast<const float*>(c->coefb[1]);
-        a.bz = reinterpret_cast<const float*>(c->coefb[2]);
-    }
+    if (c->slab_T) { c->kernels_ready = true; return FDIRW_OK; }   // streamed: marched by every step
+    fdirw::MarchArgs a = fdirw::march_args(c);
     FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     FDIRW_CUDA(c, fdirw::launch_march(a, c->num_sms, c->parts_req, c->stream, &c->parts_used));
     FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
@@ -349,6 +416,9 @@ int fdirw_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
     const bool identity = c->R == 0 || n_steps == 0;
     if (identity) {
         if (dst != src) FDIRW_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else if (c->slab_T) {
+        const int rc = fdirw::step_slabs(c, src, dst, n_steps);
+        if (rc != FDIRW_OK) return rc;
     } else {
         const bool fp32acc = c->accum == FDIRW_ACCUM_FP32;
         const int mode = c->store == Store::F64 ? 0 : fp32acc ? 2 : 1;
@@ -408,6 +478,7 @@ int fdirw_read_kernels(fdirw_ctx* c, const int64_t* sources, int64_t n, double* 
         if (sources[q] < 0 || sources[q] >= c->g.n) return fail(c, FDIRW_ERR_ARG, "source index out of range");
     if (c->coarse) return fail(c, FDIRW_ERR_ARG, "a coarse-mesh context has no per-source kernels (fdirw_read_coarse)");
     if (!c->kernels_ready) return fail(c, FDIRW_ERR_STATE, "kernel cache not built (call fdirw_kernels)");
+    if (c->slab_T) return fail(c, FDIRW_ERR_STATE, "the kernel cache is streamed by z-slabs: no kernel stays resident");
     if (n == 0) return FDIRW_OK;
     if (c->batch) {
         DeviceGuard dg(c->device);
@@ -469,6 +540,7 @@ int fdirw_get_info(fdirw_ctx* c, fdirw_info* out) {
     }
     if (c->batch) return fdirw::batch_info(c, out);
     if (c->coarse) return fdirw::coarse_info(c, out);
+    out->n_chunks = c->slab_T ? (c->g.nz + c->slab_T - 1) / c->slab_T : 1;   // z-slabs of a streamed cache
     return FDIRW_OK;
 }
 

@@ -36,6 +36,8 @@ struct fdirw_ctx {
     double* partials = nullptr;                     // 2 * kMassBlocks
     double* dmass = nullptr;                        // 1 double
     double* dfix = nullptr;                         // FDIRW_ACCUM_FP32: [M_in, f] of the mass restoration
+    int slab_T = 0;                                 // > 0: the cache holds slab_T destination z-planes (streamed)
+    double* obuf = nullptr;                         // streamed steps: output of the step being computed
     int accum = 0;                                  // fdirw_accum
     double* Dd = nullptr;                           // device copy of D (surrogate features)
     int64_t* dsrc = nullptr;
@@ -99,6 +101,11 @@ int coarse_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps
 int coarse_info(fdirw_ctx* c, fdirw_info* out);
 void coarse_release(fdirw_ctx* c);
 
-// Allocates (once) and zeroes the kernel cache of a context; honours mem_limit.
+// Allocates (once) and zeroes the kernel cache of a context; honours mem_limit, and falls back to a
+// cache of z-slabs of destinations (slab_T) when the whole cache does not fit.
 int ensure_cache(fdirw_ctx* c);
+// March arguments of a uniform context (every source, the whole cache).
+MarchArgs march_args(const fdirw_ctx* c);
+// n_steps macro steps of a uniform context with a streamed cache (slab_T > 0).
+int step_slabs(fdirw_ctx* c, const double* src, double* dst, int n_steps);
 }  // namespace fdirw

@@ -70,6 +70,9 @@ struct MarchArgs {
     // Convection (nullable; mapping 5 only): ax/ay/az then hold the coefficient of the lower cell in the
     // upper cell's update across each +face, bx/by/bz that of the upper cell in the lower cell's update.
     const float* bx; const float* by; const float* bz;
+    // Slab streaming of a uniform context (dest_hi > dest_lo): only destinations in [dest_lo, dest_hi)
+    // are stored, at column dest - dest_lo; the others are rounded (for sigma) but not stored.
+    int64_t dest_lo, dest_hi;
 };
 // Coarse-mesh march of the blocks a.list[src_begin..src_end): window radius R = window_R + (B - 1) / 2
 // (1..10), one source per CTA.
@@ -95,9 +98,10 @@ inline Pad make_pad(const Grid& g, int R) {
     return p;
 }
 // chat = sigma * c into the interior of the padded buffer (zero halo of R cells): mode 0 FP64, mode 1 a
-// float2 (hi, lo) pair with hi = fp32(v), lo = fp32(v - hi), mode 2 fp32(v).
+// float2 (hi, lo) pair with hi = fp32(v), lo = fp32(v - hi), mode 2 fp32(v).  Cells of the z-planes
+// [z0, z0 + zn) only (zn < 0: all planes).
 cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, int mode,
-                         cudaStream_t st);
+                         cudaStream_t st, int z0 = 0, int zn = -1);
 // c_out(x) = sum_o Q[o][x] * chat(x - o).
 cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
                           cudaStream_t st);
@@ -117,6 +121,10 @@ cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Gr
 // field is zero), both sums in a fixed order.  partials: 2 * kMassBlocks doubles; fix: 2 doubles
 // (fix[0] = m_in on entry, fix[1] = f on exit).
 cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* fix, cudaStream_t st);
+// The destinations of the z-planes [z0, z0 + zn) of a uniform context whose cache holds only those
+// destinations (column = cell - qoff, plane stride qs): mode 0 FP64, 1 float-float, 2 FP32 arithmetic.
+cudaError_t launch_gather_slab(const void* Q, Store store, int64_t qs, int64_t qoff, const void* chat, Grid g, int R,
+                               int mode, int z0, int zn, double* c_out, cudaStream_t st);
 // launch_gather_part with the FDIRW_ACCUM_FP32 arithmetic (FP32 chat with a halo of Rp).
 cudaError_t launch_gather_part_fp32(const void* Q, Store store, int64_t qs, const float* chat, int Rp, Grid g, int R,
                                     bool accumulate, double* c_out, cudaStream_t st);

@@ -95,20 +95,30 @@ __device__ __forceinline__ int64_t qcol(const MarchArgs& a, int64_t dest, int64_
 }
 
 // Rounds v to the storage type, writes it to Q[idx] and returns the stored value widened to float
-// (exact for every storage type).
+// (exact for every storage type).  Q == nullptr: round only.
 __device__ __forceinline__ float put(void* Q, Store st, int64_t idx, float v) {
     if (st == Store::F32) {
-        reinterpret_cast<float*>(Q)[idx] = v;
+        if (Q) reinterpret_cast<float*>(Q)[idx] = v;
         return v;
     } else if (st == Store::F16) {
         const __half h = __float2half_rn(v);
-        reinterpret_cast<__half*>(Q)[idx] = h;
+        if (Q) reinterpret_cast<__half*>(Q)[idx] = h;
         return __half2float(h);
     } else {
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        reinterpret_cast<__nv_bfloat16*>(Q)[idx] = b;
+        if (Q) reinterpret_cast<__nv_bfloat16*>(Q)[idx] = b;
         return __bfloat162float(b);
     }
+}
+
+// Stores the march's value for destination `dest` at `plane` (put), or, for a destination outside the
+// streamed slab, only rounds it to the storage type (sigma still sums it).
+__device__ __forceinline__ float store_q(const MarchArgs& a, int64_t plane, int64_t dest, int64_t pos, float v) {
+    if (a.dest_hi > a.dest_lo) {
+        if (dest < a.dest_lo || dest >= a.dest_hi) return put(nullptr, a.store, 0, v);
+        dest -= a.dest_lo;
+    }
+    return put(a.Q, a.store, plane * a.q_stride + qcol(a, dest, pos), v);
 }
 
 // sigma_s = 1 / (sum of the per-column FP64 partials of slot) for every slot of the batch, fixed order:
@@ -246,7 +256,7 @@ __global__ void __launch_bounds__(Map32<R, P>::THREADS, Map32<R, P>::MIN_BLOCKS)
                     float st = 0.f;
                     if (col_ok && z >= 0 && z < nz) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                        st = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.qbase + i, pos), u[j]);
+                        st = store_q(a, qplane(a, R, ci, cj, k), L.qbase + i, pos, u[j]);
                     }
                     sbuf[base + k] = st;
                 }
@@ -362,7 +372,8 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
                 const int z = sz - R + k;
                 if (z >= 0 && z < nz) {
                     const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                    reinterpret_cast<double*>(a.Q)[qplane(a, R, ci, cj, k) * a.g.n + i] = u[k];
+                    if (a.dest_hi <= a.dest_lo || (i >= a.dest_lo && i < a.dest_hi))
+                        reinterpret_cast<double*>(a.Q)[qplane(a, R, ci, cj, k) * a.q_stride + (i - a.dest_lo)] = u[k];
                     colsum += u[k];
                 }
             }
@@ -650,7 +661,7 @@ __global__ void __launch_bounds__(MapTm<R>::THREADS, 1) march_tm_kernel(MarchArg
                 for (int k = 0; k < W1; k++) {
                     float stv = 0.f;
                     if (cell_ok(x, y, k)) {
-                        stv = put(a.Q, a.store, qplane(a, R, x, y, k) * a.q_stride + qcol(a, L.qbase + gidx(x, y, k), pos), u[sc][k]);
+                        stv = store_q(a, qplane(a, R, x, y, k), L.qbase + gidx(x, y, k), pos, u[sc][k]);
                     }
                     sbuf[k * LEVEL + sc * PLANE + t] = stv;
                 }
@@ -962,7 +973,7 @@ __global__ void __launch_bounds__(MapTmc<R>::THREADS, 1) march_tmc_kernel(MarchA
                     float stv = 0.f;
                     if (col_ok && z >= 0 && z < nz) {
                         const int64_t i = (int64_t)x + (int64_t)nx * y + nxy * z;
-                        stv = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, L.qbase + i, pos), u[k]);
+                        stv = store_q(a, qplane(a, R, ci, cj, k), L.qbase + i, pos, u[k]);
                     }
                     sbuf[base + k] = stv;
                 }
@@ -1208,8 +1219,7 @@ __global__ void __launch_bounds__(MapTmp<R>::THREADS, 1) march_tmp_kernel(MarchA
                     stv[h] = 0.f;
                     if (col_ok[h] && z >= 0 && z < nzs[h]) {
                         const int64_t i = (int64_t)xs[h] + (int64_t)nxs[h] * ys[h] + nxy[h] * z;
-                        stv[h] = put(a.Q, a.store, qplane(a, R, ci, cj, k) * a.q_stride + qcol(a, qb[h] + i, pos[h]),
-                                     h == 0 ? f2lo(u[k]) : f2hi(u[k]));
+                        stv[h] = store_q(a, qplane(a, R, ci, cj, k), qb[h] + i, pos[h], h == 0 ? f2lo(u[k]) : f2hi(u[k]));
                     }
                 }
                 sbuf[base + k] = f2pack(stv[0], stv[1]);

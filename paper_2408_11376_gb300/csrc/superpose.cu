@@ -49,18 +49,18 @@ __device__ __forceinline__ void load_q(const ST* p, float (&q)[VX]) {
 template <typename ST, int R>
 __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q, const float2* __restrict__ chat,
                                                         Grid g, Pad p, int64_t qs, bool acc_in,
-                                                        double* __restrict__ out) {
+                                                        double* __restrict__ out, int z0, int zn, int64_t qoff) {
     constexpr int VX = 16 / sizeof(ST);
     constexpr int W1 = 2 * R + 1;
     constexpr int NC = VX + 2 * R;
     const int nxv = g.nx / VX;
-    const int64_t nthreads = (int64_t)nxv * g.ny * g.nz;
+    const int64_t nthreads = (int64_t)nxv * g.ny * zn;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tid >= nthreads) return;
     const int xv = (int)(tid % nxv);
     const int64_t r = tid / nxv;
     const int y = (int)(r % g.ny);
-    const int z = (int)(r / g.ny);
+    const int z = z0 + (int)(r / g.ny);
     const int x0 = xv * VX;
     const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
 
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
             float2 ch[NC];
 #pragma unroll
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
-            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + i0;
+            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + (i0 - qoff);
             // The FP32 pair restarts at zero on every row of 2R+1 terms, so its compensation term stays
             // within a few ulps of the row sum; the row is then added to the destination's pair.
             float s[VX], c[VX];
@@ -101,18 +101,18 @@ __global__ void __launch_bounds__(256) gather_ff_kernel(const ST* __restrict__ Q
 template <typename ST, int R>
 __global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__ Q, const float* __restrict__ chat,
                                                           Grid g, Pad p, int64_t qs, bool acc_in,
-                                                          double* __restrict__ out) {
+                                                          double* __restrict__ out, int z0, int zn, int64_t qoff) {
     constexpr int VX = 16 / sizeof(ST);
     constexpr int W1 = 2 * R + 1;
     constexpr int NC = VX + 2 * R;
     const int nxv = g.nx / VX;
-    const int64_t nthreads = (int64_t)nxv * g.ny * g.nz;
+    const int64_t nthreads = (int64_t)nxv * g.ny * zn;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tid >= nthreads) return;
     const int xv = (int)(tid % nxv);
     const int64_t r = tid / nxv;
     const int y = (int)(r % g.ny);
-    const int z = (int)(r / g.ny);
+    const int z = z0 + (int)(r / g.ny);
     const int x0 = xv * VX;
     const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
 
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__
             float ch[NC];
 #pragma unroll
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
-            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + i0;
+            const ST* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + (i0 - qoff);
             float s[VX];
 #pragma unroll
             for (int j = 0; j < VX; j++) s[j] = 0.f;
@@ -147,18 +147,19 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const ST* __restrict__
 // FP64 path: FP64 storage, FP64 chat, FP64 FMA accumulation, VX = 2.
 template <int R>
 __global__ void __launch_bounds__(256) gather_f64_kernel(const double* __restrict__ Q, const double* __restrict__ chat,
-                                                         Grid g, Pad p, double* __restrict__ out) {
+                                                         Grid g, Pad p, double* __restrict__ out, int64_t qs, int z0,
+                                                         int zn, int64_t qoff) {
     constexpr int VX = 2;
     constexpr int W1 = 2 * R + 1;
     constexpr int NC = VX + 2 * R;
     const int nxv = g.nx / VX;
-    const int64_t nthreads = (int64_t)nxv * g.ny * g.nz;
+    const int64_t nthreads = (int64_t)nxv * g.ny * zn;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tid >= nthreads) return;
     const int xv = (int)(tid % nxv);
     const int64_t r = tid / nxv;
     const int y = (int)(r % g.ny);
-    const int z = (int)(r / g.ny);
+    const int z = z0 + (int)(r / g.ny);
     const int x0 = xv * VX;
     const int64_t i0 = (int64_t)x0 + (int64_t)g.nx * y + (int64_t)g.nx * g.ny * z;
     double acc0 = 0.0, acc1 = 0.0;
@@ -168,10 +169,10 @@ __global__ void __launch_bounds__(256) gather_f64_kernel(const double* __restric
             double ch[NC];
 #pragma unroll
             for (int j = 0; j < NC; j++) ch[j] = __ldg(row + j);
-            const double* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * g.n + i0;
+            const double* qrow = Q + ((int64_t)((oz + R) * W1 + (oy + R)) * W1) * qs + (i0 - qoff);
 #pragma unroll
             for (int ox = -R; ox <= R; ox++) {
-                const double2 q = __ldcs(reinterpret_cast<const double2*>(qrow + (int64_t)(ox + R) * g.n));
+                const double2 q = __ldcs(reinterpret_cast<const double2*>(qrow + (int64_t)(ox + R) * qs));
                 acc0 = fma(q.x, ch[0 - ox + R], acc0);
                 acc1 = fma(q.y, ch[1 - ox + R], acc1);
             }
@@ -185,9 +186,11 @@ __global__ void __launch_bounds__(256) gather_f64_kernel(const double* __restric
 template <typename ST, int MODE>
 __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict__ Q, const void* __restrict__ chat,
                                                             Grid g, Pad p, int R, int64_t qs, bool acc_in,
-                                                            double* __restrict__ out) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+                                                            double* __restrict__ out, int z0, int zn, int64_t qoff) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= nxy * zn) return;
+    const int64_t i = z0 * nxy + tid;
     const int x = (int)(i % g.nx);
     const int64_t r = i / g.nx;
     const int y = (int)(r % g.ny);
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict
             float s = 0.f, c = 0.f;
             for (int ox = -R; ox <= R; ox++, o++) {
                 const int64_t pi = ((int64_t)(z - oz + R) * p.py + (y - oy + R)) * p.px + (x - ox + R);
-                const ST qv = Q[(int64_t)o * qs + i];
+                const ST qv = Q[(int64_t)o * qs + (i - qoff)];
                 if constexpr (MODE == 1) {
                     ff_madd(s, c, widen(qv), reinterpret_cast<const float2*>(chat)[pi]);
                 } else if constexpr (MODE == 2) {
@@ -216,8 +219,8 @@ __global__ void __launch_bounds__(256) gather_scalar_kernel(const ST* __restrict
 }
 
 __global__ void scale_kernel(const double* __restrict__ c, const double* __restrict__ sigma, Grid g, int R, Pad p,
-                             void* __restrict__ chat, int mode) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+                             void* __restrict__ chat, int mode, int64_t i0, int64_t i1) {
+    for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % g.nx);
         const int64_t r = i / g.nx;
         const int y = (int)(r % g.ny);
@@ -442,108 +445,201 @@ int blocks_for(int64_t n, int threads) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// Destination planes [z0, z0 + zn) of the launch and the column offset of its cache (a slab of a
+// streamed uniform cache); {0, nz, 0} for a whole grid.
+struct Slab {
+    int z0, zn;
+    int64_t qoff;
+};
+
 template <typename ST, int R>
 cudaError_t gather_ff_r(const void* Q, const void* chat, Grid g, Pad p, int64_t qs, bool acc_in, double* out,
-                        cudaStream_t st) {
+                        cudaStream_t st, Slab sl) {
     constexpr int VX = 16 / sizeof(ST);
-    const int64_t nt = (int64_t)(g.nx / VX) * g.ny * g.nz;
+    const int64_t nt = (int64_t)(g.nx / VX) * g.ny * sl.zn;
+    if (nt <= 0) return cudaSuccess;
     gather_ff_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q),
                                                                    reinterpret_cast<const float2*>(chat), g, p, qs,
-                                                                   acc_in, out);
+                                                                   acc_in, out, sl.z0, sl.zn, sl.qoff);
     return cudaGetLastError();
 }
 
 template <typename ST>
 cudaError_t gather_ff(const void* Q, const void* chat, Grid g, int R, Pad p, int64_t qs, bool acc_in, double* out,
-                      cudaStream_t st) {
+                      cudaStream_t st, Slab sl) {
     switch (R) {
-        case 1: return gather_ff_r<ST, 1>(Q, chat, g, p, qs, acc_in, out, st);
-        case 2: return gather_ff_r<ST, 2>(Q, chat, g, p, qs, acc_in, out, st);
-        case 3: return gather_ff_r<ST, 3>(Q, chat, g, p, qs, acc_in, out, st);
-        case 4: return gather_ff_r<ST, 4>(Q, chat, g, p, qs, acc_in, out, st);
-        case 5: return gather_ff_r<ST, 5>(Q, chat, g, p, qs, acc_in, out, st);
-        case 6: return gather_ff_r<ST, 6>(Q, chat, g, p, qs, acc_in, out, st);
-        case 7: return gather_ff_r<ST, 7>(Q, chat, g, p, qs, acc_in, out, st);
-        case 8: return gather_ff_r<ST, 8>(Q, chat, g, p, qs, acc_in, out, st);
-        case 9: return gather_ff_r<ST, 9>(Q, chat, g, p, qs, acc_in, out, st);
-        case 10: return gather_ff_r<ST, 10>(Q, chat, g, p, qs, acc_in, out, st);
+        case 1: return gather_ff_r<ST, 1>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 2: return gather_ff_r<ST, 2>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 3: return gather_ff_r<ST, 3>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 4: return gather_ff_r<ST, 4>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 5: return gather_ff_r<ST, 5>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 6: return gather_ff_r<ST, 6>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 7: return gather_ff_r<ST, 7>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 8: return gather_ff_r<ST, 8>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 9: return gather_ff_r<ST, 9>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 10: return gather_ff_r<ST, 10>(Q, chat, g, p, qs, acc_in, out, st, sl);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int R>
-cudaError_t gather_f64_r(const void* Q, const void* chat, Grid g, Pad p, double* out, cudaStream_t st) {
-    const int64_t nt = (int64_t)(g.nx / 2) * g.ny * g.nz;
+cudaError_t gather_f64_r(const void* Q, const void* chat, Grid g, Pad p, int64_t qs, double* out, cudaStream_t st,
+                         Slab sl) {
+    const int64_t nt = (int64_t)(g.nx / 2) * g.ny * sl.zn;
+    if (nt <= 0) return cudaSuccess;
     gather_f64_kernel<R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const double*>(Q),
-                                                               reinterpret_cast<const double*>(chat), g, p, out);
+                                                               reinterpret_cast<const double*>(chat), g, p, out, qs,
+                                                               sl.z0, sl.zn, sl.qoff);
     return cudaGetLastError();
 }
 
-cudaError_t gather_f64(const void* Q, const void* chat, Grid g, int R, Pad p, double* out, cudaStream_t st) {
+cudaError_t gather_f64(const void* Q, const void* chat, Grid g, int R, Pad p, int64_t qs, double* out,
+                       cudaStream_t st, Slab sl) {
     switch (R) {
-        case 1: return gather_f64_r<1>(Q, chat, g, p, out, st);
-        case 2: return gather_f64_r<2>(Q, chat, g, p, out, st);
-        case 3: return gather_f64_r<3>(Q, chat, g, p, out, st);
-        case 4: return gather_f64_r<4>(Q, chat, g, p, out, st);
-        case 5: return gather_f64_r<5>(Q, chat, g, p, out, st);
-        case 6: return gather_f64_r<6>(Q, chat, g, p, out, st);
-        case 7: return gather_f64_r<7>(Q, chat, g, p, out, st);
-        case 8: return gather_f64_r<8>(Q, chat, g, p, out, st);
+        case 1: return gather_f64_r<1>(Q, chat, g, p, qs, out, st, sl);
+        case 2: return gather_f64_r<2>(Q, chat, g, p, qs, out, st, sl);
+        case 3: return gather_f64_r<3>(Q, chat, g, p, qs, out, st, sl);
+        case 4: return gather_f64_r<4>(Q, chat, g, p, qs, out, st, sl);
+        case 5: return gather_f64_r<5>(Q, chat, g, p, qs, out, st, sl);
+        case 6: return gather_f64_r<6>(Q, chat, g, p, qs, out, st, sl);
+        case 7: return gather_f64_r<7>(Q, chat, g, p, qs, out, st, sl);
+        case 8: return gather_f64_r<8>(Q, chat, g, p, qs, out, st, sl);
         default: return cudaErrorInvalidValue;
     }
 }
 
-}  // namespace
-
-cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, int mode,
-                         cudaStream_t st) {
-    const Pad p = make_pad(g, R);
-    int b = blocks_for(g.n, 256);
-    if (b > 152 * 16) b = 152 * 16;
-    scale_kernel<<<b, 256, 0, st>>>(c, sigma, g, R, p, chat, mode);
+template <typename ST, int R>
+cudaError_t gather_fp32_r(const void* Q, const float* chat, Grid g, Pad p, int64_t qs, bool acc_in, double* out,
+                          cudaStream_t st, Slab sl) {
+    constexpr int VX = 16 / sizeof(ST);
+    const int64_t nt = (int64_t)(g.nx / VX) * g.ny * sl.zn;
+    if (nt <= 0) return cudaSuccess;
+    gather_fp32_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q), chat, g, p, qs,
+                                                                     acc_in, out, sl.z0, sl.zn, sl.qoff);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_part(const void* Q, Store store, int64_t qs, const void* chat, int Rp, Grid g, int R,
-                               bool accumulate, double* c_out, cudaStream_t st) {
+template <typename ST>
+cudaError_t gather_fp32_st(const void* Q, const float* chat, Grid g, int R, Pad p, int64_t qs, bool acc_in,
+                           double* out, cudaStream_t st, Slab sl) {
+    switch (R) {
+        case 1: return gather_fp32_r<ST, 1>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 2: return gather_fp32_r<ST, 2>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 3: return gather_fp32_r<ST, 3>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 4: return gather_fp32_r<ST, 4>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 5: return gather_fp32_r<ST, 5>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 6: return gather_fp32_r<ST, 6>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 7: return gather_fp32_r<ST, 7>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 8: return gather_fp32_r<ST, 8>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 9: return gather_fp32_r<ST, 9>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        case 10: return gather_fp32_r<ST, 10>(Q, chat, g, p, qs, acc_in, out, st, sl);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Scalar fallback of both accumulations and the FP64 path (any nx): MODE 0 FP64, 1 float-float, 2 FP32.
+template <int MODE>
+cudaError_t gather_scalar(const void* Q, Store store, const void* ch, Grid g, Pad p, int R, int64_t qs, bool acc,
+                          double* out, cudaStream_t st, Slab sl) {
+    const int64_t n = (int64_t)g.nx * g.ny * sl.zn;
+    if (n <= 0) return cudaSuccess;
+    const int b = blocks_for(n, 256);
+    switch (store) {
+        case Store::F64:
+            if (MODE != 0) return cudaErrorInvalidValue;
+            gather_scalar_kernel<double, MODE><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), ch, g, p, R,
+                                                                  qs, acc, out, sl.z0, sl.zn, sl.qoff);
+            break;
+        case Store::F32:
+            if (MODE == 0) return cudaErrorInvalidValue;
+            gather_scalar_kernel<float, MODE><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
+                                                                 acc, out, sl.z0, sl.zn, sl.qoff);
+            break;
+        case Store::F16:
+            if (MODE == 0) return cudaErrorInvalidValue;
+            gather_scalar_kernel<__half, MODE><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R,
+                                                                  qs, acc, out, sl.z0, sl.zn, sl.qoff);
+            break;
+        case Store::BF16:
+            if (MODE == 0) return cudaErrorInvalidValue;
+            gather_scalar_kernel<__nv_bfloat16, MODE><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q),
+                                                                         ch, g, p, R, qs, acc, out, sl.z0, sl.zn,
+                                                                         sl.qoff);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+// Float-float (FP32 storage types) or FP64 gather of one part (radius R, chat with a halo of Rp).
+cudaError_t gather_part(const void* Q, Store store, int64_t qs, const void* chat, int Rp, Grid g, int R,
+                        bool accumulate, double* c_out, cudaStream_t st, Slab sl) {
     if (R < 1 || R > Rp) return cudaErrorInvalidValue;
     const Pad p = make_pad(g, Rp);
     // The kernels index chat as if its halo were R: move the base by (Rp - R) on every axis.
     const int64_t shift = ((int64_t)(Rp - R) * p.py + (Rp - R)) * p.px + (Rp - R);
     const void* ch = static_cast<const char*>(chat) + shift * 8;   // chat element: double or float2, 8 bytes
     const int vx = 16 / store_bytes(store);
-    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (qs * store_bytes(store)) % 16 == 0;
+    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (qs * store_bytes(store)) % 16 == 0 &&
+                         (sl.qoff * store_bytes(store)) % 16 == 0;
+    if (store == Store::F64 && accumulate) return cudaErrorInvalidValue;   // uniform FP64 contexts only
     if (R <= (store == Store::F64 ? kMaxR64 : kMaxR) && g.nx % vx == 0 && aligned) {
         switch (store) {
-            case Store::F64:
-                if (qs != g.n || accumulate) return cudaErrorInvalidValue;   // uniform FP64 contexts only
-                return gather_f64(Q, ch, g, R, p, c_out, st);
-            case Store::F32: return gather_ff<float>(Q, ch, g, R, p, qs, accumulate, c_out, st);
-            case Store::F16: return gather_ff<__half>(Q, ch, g, R, p, qs, accumulate, c_out, st);
-            case Store::BF16: return gather_ff<__nv_bfloat16>(Q, ch, g, R, p, qs, accumulate, c_out, st);
+            case Store::F64: return gather_f64(Q, ch, g, R, p, qs, c_out, st, sl);
+            case Store::F32: return gather_ff<float>(Q, ch, g, R, p, qs, accumulate, c_out, st, sl);
+            case Store::F16: return gather_ff<__half>(Q, ch, g, R, p, qs, accumulate, c_out, st, sl);
+            case Store::BF16: return gather_ff<__nv_bfloat16>(Q, ch, g, R, p, qs, accumulate, c_out, st, sl);
         }
         return cudaErrorInvalidValue;
     }
-    const int b = blocks_for(g.n, 256);
-    switch (store) {
-        case Store::F64:
-            gather_scalar_kernel<double, 0><<<b, 256, 0, st>>>(reinterpret_cast<const double*>(Q), ch, g, p, R, qs,
-                                                                   accumulate, c_out);
-            break;
-        case Store::F32:
-            gather_scalar_kernel<float, 1><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
-                                                                 accumulate, c_out);
-            break;
-        case Store::F16:
-            gather_scalar_kernel<__half, 1><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R, qs,
-                                                                  accumulate, c_out);
-            break;
-        case Store::BF16:
-            gather_scalar_kernel<__nv_bfloat16, 1><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), ch,
-                                                                         g, p, R, qs, accumulate, c_out);
-            break;
+    return store == Store::F64 ? gather_scalar<0>(Q, store, ch, g, p, R, qs, accumulate, c_out, st, sl)
+                               : gather_scalar<1>(Q, store, ch, g, p, R, qs, accumulate, c_out, st, sl);
+}
+
+// FDIRW_ACCUM_FP32 gather of one part (FP32 chat with a halo of Rp).
+cudaError_t gather_part_fp32(const void* Q, Store store, int64_t qs, const float* chat, int Rp, Grid g, int R,
+                             bool accumulate, double* c_out, cudaStream_t st, Slab sl) {
+    if (R < 1 || R > Rp || R > kMaxR || store == Store::F64) return cudaErrorInvalidValue;
+    const Pad p = make_pad(g, Rp);
+    const float* ch = chat + ((int64_t)(Rp - R) * p.py + (Rp - R)) * p.px + (Rp - R);
+    const int vx = 16 / store_bytes(store);
+    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (qs * store_bytes(store)) % 16 == 0 &&
+                         (sl.qoff * store_bytes(store)) % 16 == 0;
+    if (g.nx % vx == 0 && aligned) {
+        switch (store) {
+            case Store::F32: return gather_fp32_st<float>(Q, ch, g, R, p, qs, accumulate, c_out, st, sl);
+            case Store::F16: return gather_fp32_st<__half>(Q, ch, g, R, p, qs, accumulate, c_out, st, sl);
+            case Store::BF16: return gather_fp32_st<__nv_bfloat16>(Q, ch, g, R, p, qs, accumulate, c_out, st, sl);
+            default: return cudaErrorInvalidValue;
+        }
     }
+    return gather_scalar<2>(Q, store, ch, g, p, R, qs, accumulate, c_out, st, sl);
+}
+
+}  // namespace
+
+cudaError_t launch_scale(const double* c, const double* sigma, Grid g, int R, void* chat, int mode,
+                         cudaStream_t st, int z0, int zn) {
+    const Pad p = make_pad(g, R);
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    const int64_t i0 = (int64_t)z0 * nxy, i1 = zn < 0 ? g.n : (int64_t)(z0 + zn) * nxy;
+    if (i1 <= i0) return cudaSuccess;
+    int b = blocks_for(i1 - i0, 256);
+    if (b > 152 * 16) b = 152 * 16;
+    scale_kernel<<<b, 256, 0, st>>>(c, sigma, g, R, p, chat, mode, i0, i1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gather_part(const void* Q, Store store, int64_t qs, const void* chat, int Rp, Grid g, int R,
+                               bool accumulate, double* c_out, cudaStream_t st) {
+    return gather_part(Q, store, qs, chat, Rp, g, R, accumulate, c_out, st, Slab{0, g.nz, 0});
+}
+
+cudaError_t launch_gather_slab(const void* Q, Store store, int64_t qs, int64_t qoff, const void* chat, Grid g, int R,
+                               int mode, int z0, int zn, double* c_out, cudaStream_t st) {
+    const Slab sl{z0, zn, qoff};
+    if (mode == 2)
+        return gather_part_fp32(Q, store, qs, reinterpret_cast<const float*>(chat), R, g, R, false, c_out, st, sl);
+    return gather_part(Q, store, qs, chat, R, g, R, false, c_out, st, sl);
 }
 
 cudaError_t launch_gather(const void* Q, Store store, const void* chat, Grid g, int R, double* c_out,
@@ -597,67 +693,9 @@ cudaError_t launch_restore_mass(double* c, int64_t n, double* partials, double* 
     return cudaGetLastError();
 }
 
-template <typename ST, int R>
-cudaError_t gather_fp32_r(const void* Q, const float* chat, Grid g, Pad p, int64_t qs, bool acc_in, double* out,
-                          cudaStream_t st) {
-    constexpr int VX = 16 / sizeof(ST);
-    const int64_t nt = (int64_t)(g.nx / VX) * g.ny * g.nz;
-    gather_fp32_kernel<ST, R><<<blocks_for(nt, 256), 256, 0, st>>>(reinterpret_cast<const ST*>(Q), chat, g, p, qs,
-                                                                     acc_in, out);
-    return cudaGetLastError();
-}
-
-template <typename ST>
-cudaError_t gather_fp32_st(const void* Q, const float* chat, Grid g, int R, Pad p, int64_t qs, bool acc_in,
-                           double* out, cudaStream_t st) {
-    switch (R) {
-        case 1: return gather_fp32_r<ST, 1>(Q, chat, g, p, qs, acc_in, out, st);
-        case 2: return gather_fp32_r<ST, 2>(Q, chat, g, p, qs, acc_in, out, st);
-        case 3: return gather_fp32_r<ST, 3>(Q, chat, g, p, qs, acc_in, out, st);
-        case 4: return gather_fp32_r<ST, 4>(Q, chat, g, p, qs, acc_in, out, st);
-        case 5: return gather_fp32_r<ST, 5>(Q, chat, g, p, qs, acc_in, out, st);
-        case 6: return gather_fp32_r<ST, 6>(Q, chat, g, p, qs, acc_in, out, st);
-        case 7: return gather_fp32_r<ST, 7>(Q, chat, g, p, qs, acc_in, out, st);
-        case 8: return gather_fp32_r<ST, 8>(Q, chat, g, p, qs, acc_in, out, st);
-        case 9: return gather_fp32_r<ST, 9>(Q, chat, g, p, qs, acc_in, out, st);
-        case 10: return gather_fp32_r<ST, 10>(Q, chat, g, p, qs, acc_in, out, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 cudaError_t launch_gather_part_fp32(const void* Q, Store store, int64_t qs, const float* chat, int Rp, Grid g, int R,
                                     bool accumulate, double* c_out, cudaStream_t st) {
-    if (R < 1 || R > Rp || R > kMaxR || store == Store::F64) return cudaErrorInvalidValue;
-    const Pad p = make_pad(g, Rp);
-    // The kernels index chat as if its halo were R: move the base by (Rp - R) on every axis.
-    const float* ch = chat + ((int64_t)(Rp - R) * p.py + (Rp - R)) * p.px + (Rp - R);
-    const int vx = 16 / store_bytes(store);
-    const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && (qs * store_bytes(store)) % 16 == 0;
-    if (g.nx % vx == 0 && aligned) {
-        switch (store) {
-            case Store::F32: return gather_fp32_st<float>(Q, ch, g, R, p, qs, accumulate, c_out, st);
-            case Store::F16: return gather_fp32_st<__half>(Q, ch, g, R, p, qs, accumulate, c_out, st);
-            case Store::BF16: return gather_fp32_st<__nv_bfloat16>(Q, ch, g, R, p, qs, accumulate, c_out, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    const int b = blocks_for(g.n, 256);
-    switch (store) {
-        case Store::F32:
-            gather_scalar_kernel<float, 2><<<b, 256, 0, st>>>(reinterpret_cast<const float*>(Q), ch, g, p, R, qs,
-                                                              accumulate, c_out);
-            break;
-        case Store::F16:
-            gather_scalar_kernel<__half, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __half*>(Q), ch, g, p, R, qs,
-                                                               accumulate, c_out);
-            break;
-        case Store::BF16:
-            gather_scalar_kernel<__nv_bfloat16, 2><<<b, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(Q), ch,
-                                                                      g, p, R, qs, accumulate, c_out);
-            break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return gather_part_fp32(Q, store, qs, chat, Rp, g, R, accumulate, c_out, st, Slab{0, g.nz, 0});
 }
 
 cudaError_t launch_gather_fp32(const void* Q, Store store, const float* chat, Grid g, int R, double* c_out,

@@ -669,6 +669,7 @@ FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* c, fdirw_net* net, int64_t* acc
     {
         const int rc = fdirw::ensure_cache(c);
         if (rc != FDIRW_OK) return nfail(net, rc, fdirw_last_error(c));
+        if (c->slab_T) return nfail(net, FDIRW_ERR_STATE, "the surrogate needs a resident kernel cache (this one is streamed)");
     }
     const int64_t N = c->g.n;
     std::vector<int64_t> src(MAX_BATCH), rejected;

@@ -280,10 +280,16 @@ def test_errors_are_reported():
     with pytest.raises(FdirwError) as e:
         FDiRW(shape, torch.from_numpy(bad).to(DEV), 10 * lam, 2, 10)
     assert e.value.code == fdirw.FDIRW_ERR_ARG
-    with FDiRW(shape, D, 10 * lam, 2, 10, mem_limit=100_000) as f:     # create needs ~40 KB, the cache 256 KB
-        with pytest.raises(FdirwError) as e:
+    with FDiRW(shape, D, 10 * lam, 2, 10) as f:
+        base = f.info()["device_bytes"]                                    # everything but the cache
+    plane = 125 * 64 * 4                                                   # one z-plane of FP32 kernels
+    with FDiRW(shape, D, 10 * lam, 2, 10, mem_limit=base + 512 * 8 + plane - 1) as f:
+        with pytest.raises(FdirwError) as e:                               # not even one plane fits
             f.kernels()
         assert e.value.code == fdirw.FDIRW_ERR_NOMEM
+    with FDiRW(shape, D, 10 * lam, 2, 10, mem_limit=base + 512 * 8 + plane) as f:
+        f.kernels()                                                        # one plane: 8 streamed slabs
+        assert f.info()["n_chunks"] == 8
     with FDiRW(shape, D, 10 * lam, 2, 10) as f:
         with pytest.raises(FdirwError) as e:
             f.read_kernels([0])
@@ -362,3 +368,40 @@ def test_workload_192_sampled(prec):
     dests = np.array([0, N - 1, (w.n // 2) * (1 + w.n + w.n * w.n)])
     ref_at = _oracle_at(shape, D, lam, w.R, w.n_sub, c0, dests)
     assert np.max(np.abs(got[dests] - ref_at)) <= FIELD_TOL[prec] * np.abs(ref_at).max()
+
+
+# ------------------------------------------------------------------------- streamed cache (z-slabs)
+
+@pytest.mark.parametrize("prec,accum", [("fp32", "ff"), ("bf16", "fp32"), ("fp64", "ff"), ("fp16", "ff")])
+@pytest.mark.parametrize("n_steps", [1, 2, 3])
+def test_streamed_cache_equals_resident_bitwise(prec, accum, n_steps):
+    """A mem_limit that leaves room for about a third of the cache makes the context stream it by
+    z-slabs (every step re-marches each slab's sources): fields, masses and the in-place call equal the
+    resident cache's bit for bit, and the streamed context reports its slabs and no resident kernels."""
+    shape, R, n_sub = (24, 16, 21), 4, 30
+    D = _case(shape, 160, "per_sphere")
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    c0 = synth.random_field(N, 161)
+    Dd = torch.from_numpy(D).to(DEV)
+    with FDiRW(shape, Dd, n_sub * lam, R, n_sub, prec, accum=accum) as f:
+        f.kernels()
+        info = f.info()
+        cin = torch.from_numpy(c0).to(DEV)
+        ref = torch.empty_like(cin)
+        m_ref = f.step(cin, ref, n_steps, want_mass=True)
+    limit = info["device_bytes"] - info["cache_bytes"] + info["cache_bytes"] // 3 + 8 * N
+    with FDiRW(shape, Dd, n_sub * lam, R, n_sub, prec, mem_limit=limit, accum=accum) as f:
+        out = torch.empty_like(cin)
+        m = f.step(cin, out, n_steps, want_mass=True)
+        sinfo = f.info()
+        with pytest.raises(FdirwError) as e:
+            f.read_kernels([0])
+        assert e.value.code == fdirw.FDIRW_ERR_STATE
+        inplace = cin.clone()
+        f.step(inplace, inplace, n_steps)
+        host = np.empty_like(c0)
+        f.step(c0, host, n_steps)
+    assert sinfo["n_chunks"] >= 3 and sinfo["cache_bytes"] < info["cache_bytes"]
+    assert torch.equal(out, ref) and torch.equal(inplace, ref) and m == m_ref
+    assert np.array_equal(host, ref.cpu().numpy())
