@@ -160,3 +160,26 @@ def test_velocity_replaced_and_errors():
     with FDiRWBatch([shape], [D], 20 * lam, 2, 3, 20) as f:
         with pytest.raises(FdirwError):
             f.set_velocity(w1)
+
+
+def test_flow_kernels_at_the_benchmark_size():
+    """192^3 two-phase packing, R = 8, n_sub = 220 and the bench's flow (mean 0.03 along +x, noise 0.03,
+    zero on solid faces): sampled kernels (corner, face, centre, random) against the oracle's upwind march."""
+    w = synth.WORKLOADS["fdirw-192c-r8"]
+    packing, D, _ = w.make()
+    shape = (w.n,) * 3
+    lam = oracle.stable_dt_sub(shape, D)
+    n_sub = -(-11 * w.n_sub // 10)
+    dt = w.n_sub * lam                                   # the workload's macro step, split into n_sub substeps
+    vel = synth.face_velocity(shape, w.seed + 40, (0.03, 0.0, 0.0), 0.03, packing.solid)
+    N = w.n ** 3
+    rng = np.random.default_rng(162)
+    src = np.concatenate([[0, N - 1, (w.n // 2) * (1 + w.n + w.n * w.n), 7 + w.n * 3], rng.integers(0, N, 4)])
+    with FDiRW(shape, torch.from_numpy(D).to(DEV), dt, w.R, n_sub, "bf16") as f:
+        f.set_velocity(torch.from_numpy(vel.reshape(-1)).to(DEV))
+        f.kernels()
+        ks = f.read_kernels(src).reshape(len(src), -1)
+    lam_sub = dt / n_sub
+    ref = _oracle_kernels(shape, D, vel, lam_sub, w.R, n_sub, src).reshape(len(src), -1)
+    err = np.linalg.norm(ks - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= KERNEL_TOL["bf16"], err.max()
