@@ -96,6 +96,17 @@ def _load():
             lib.fo_coarse_pbc.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [_U8, ctypes.c_int, ctypes.c_double,
                                                                          ctypes.c_int, _D]
             lib.fo_coarse_pbc.restype = ctypes.c_int
+            lib.fo_coarse_kernels_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, _U8, ctypes.c_int,
+                                                                                 ctypes.c_double, ctypes.c_int,
+                                                                                 ctypes.c_int, _D]
+            lib.fo_coarse_kernels_adv.restype = ctypes.c_int
+            lib.fo_coarse_kernels_open_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, _D, _U8,
+                                                                                      ctypes.c_int, ctypes.c_double,
+                                                                                      ctypes.c_int, ctypes.c_int, _D]
+            lib.fo_coarse_kernels_open_adv.restype = ctypes.c_int
+            lib.fo_coarse_pbc_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, _D, _U8, ctypes.c_int,
+                                                                             ctypes.c_double, ctypes.c_int, _D]
+            lib.fo_coarse_pbc_adv.restype = ctypes.c_int
             lib.fo_coarse_step_far.argtypes = [ctypes.c_int] * 3 + [_U8, ctypes.c_int, ctypes.c_int, _D, _D,
                                                                    ctypes.c_double, ctypes.c_double, _D, _D, _D]
             lib.fo_coarse_step_far.restype = ctypes.c_int
@@ -254,15 +265,32 @@ def coarse_counts(shape, liquid, B: int) -> np.ndarray:
     return out
 
 
-def coarse_kernels(shape, D, liquid, B: int, lam: float, R: int, n_sub: int) -> np.ndarray:
+def _liquid_velocity(shape, w, liquid):
+    """Copies of the face velocities (wx, wy, wz) with the faces that touch a non-liquid cell zeroed (the
+    liquid path's reading of Sec. 5: no flux of either kind there)."""
+    nx, ny, nz = shape
+    out = [np.array(_f64(a).reshape(-1)) for a in w]
+    lq = _u8(liquid, out[0].size)
+    _load().fo_mask_faces(nx, ny, nz, _pu8(lq), _p(out[0]), _p(out[1]), _p(out[2]))
+    return out
+
+
+def coarse_kernels(shape, D, liquid, B: int, lam: float, R: int, n_sub: int, w=None, lama=None) -> np.ndarray:
     """Coarse matrix P of Eq. 10 in its band layout [n_blocks, Wc, Wc, Wc] (source block J, offsets
-    [dz+Rc, dy+Rc, dx+Rc] to the destination block), Wc = 2 ceil(R/B) + 1."""
+    [dz+Rc, dy+Rc, dx+Rc] to the destination block), Wc = 2 ceil(R/B) + 1.  With face velocities w (and
+    lama = dt_sub / h, default lam) the block-source march carries the upwind faces (Sec. 5)."""
     nx, ny, nz = shape
     g = Conductance(shape, D, liquid)
     Wc = 2 * coarse_radius(R, B) + 1
     nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
     out = np.empty((nc, Wc, Wc, Wc), dtype=np.float64)
-    if _load().fo_coarse_kernels(*g.args, _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub), _p(out)) != 0:
+    if w is None:
+        rc = _load().fo_coarse_kernels(*g.args, _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub), _p(out))
+    else:
+        wx, wy, wz = _liquid_velocity(shape, w, g.liquid)
+        rc = _load().fo_coarse_kernels_adv(*g.args, _p(wx), _p(wy), _p(wz), float(lam if lama is None else lama),
+                                           _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub), _p(out))
+    if rc != 0:
         raise ValueError("fo_coarse_kernels rejected its arguments")
     return out
 
@@ -289,28 +317,43 @@ def boundary_conductance(shape, D, liquid) -> np.ndarray:
     return out
 
 
-def coarse_kernels_open(shape, D, liquid, B: int, lam: float, R: int, n_sub: int) -> np.ndarray:
-    """Coarse matrix with the grid's outer faces open to the far field (no renormalisation)."""
+def coarse_kernels_open(shape, D, liquid, B: int, lam: float, R: int, n_sub: int, w=None, lama=None) -> np.ndarray:
+    """Coarse matrix with the grid's outer faces open to the far field (no renormalisation); face
+    velocities w add the upwind faces inside the grid (the open faces stay diffusive)."""
     nx, ny, nz = shape
     g = Conductance(shape, D, liquid)
     gb = boundary_conductance(shape, D, liquid)
     Wc = 2 * coarse_radius(R, B) + 1
     nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
     out = np.empty((nc, Wc, Wc, Wc), dtype=np.float64)
-    if _load().fo_coarse_kernels_open(*g.args, _p(gb), _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub),
-                                      _p(out)) != 0:
+    if w is None:
+        rc = _load().fo_coarse_kernels_open(*g.args, _p(gb), _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub),
+                                            _p(out))
+    else:
+        wx, wy, wz = _liquid_velocity(shape, w, g.liquid)
+        rc = _load().fo_coarse_kernels_open_adv(*g.args, _p(wx), _p(wy), _p(wz), float(lam if lama is None else lama),
+                                                _p(gb), _pu8(g.liquid), int(B), float(lam), int(R), int(n_sub),
+                                                _p(out))
+    if rc != 0:
         raise ValueError("fo_coarse_kernels_open rejected its arguments")
     return out
 
 
-def coarse_pbc(shape, D, liquid, B: int, lam: float, n_sub: int) -> np.ndarray:
-    """P_BC of Eq. 10 on the blocks: the liquid marched from 0 with every far-field ghost at 1, mapped."""
+def coarse_pbc(shape, D, liquid, B: int, lam: float, n_sub: int, w=None, lama=None) -> np.ndarray:
+    """P_BC of Eq. 10 on the blocks: the liquid marched from 0 with every far-field ghost at 1, mapped;
+    face velocities w add the upwind faces inside the grid."""
     nx, ny, nz = shape
     g = Conductance(shape, D, liquid)
     gb = boundary_conductance(shape, D, liquid)
     nc = ((nx + B - 1) // B) * ((ny + B - 1) // B) * ((nz + B - 1) // B)
     out = np.empty(nc, dtype=np.float64)
-    if _load().fo_coarse_pbc(*g.args, _p(gb), _pu8(g.liquid), int(B), float(lam), int(n_sub), _p(out)) != 0:
+    if w is None:
+        rc = _load().fo_coarse_pbc(*g.args, _p(gb), _pu8(g.liquid), int(B), float(lam), int(n_sub), _p(out))
+    else:
+        wx, wy, wz = _liquid_velocity(shape, w, g.liquid)
+        rc = _load().fo_coarse_pbc_adv(*g.args, _p(wx), _p(wy), _p(wz), float(lam if lama is None else lama), _p(gb),
+                                       _pu8(g.liquid), int(B), float(lam), int(n_sub), _p(out))
+    if rc != 0:
         raise ValueError("fo_coarse_pbc failed")
     return out
 

@@ -89,6 +89,19 @@ static void box_substep(int nx, int ny, const double* gx, const double* gy, cons
             }
 }
 
+static void box_substep_adv(int nx, int ny, const double* gx, const double* gy, const double* gz,
+                            const double* wx, const double* wy, const double* wz, double lam, double lama,
+                            int x0, int y0, int z0, int bx, int by, int bz, const double* u, double* un);
+
+/* box_substep, or box_substep_adv when face velocities are given (wx != NULL; Sec. 5 convection). */
+static void box_step(int nx, int ny, const double* gx, const double* gy, const double* gz, const double* wx,
+                     const double* wy, const double* wz, double lam, double lama, int x0, int y0, int z0, int bx,
+                     int by, int bz, const double* u, double* un)
+{
+    if (wx) box_substep_adv(nx, ny, gx, gy, gz, wx, wy, wz, lam, lama, x0, y0, z0, bx, by, bz, u, un);
+    else box_substep(nx, ny, gx, gy, gz, lam, x0, y0, z0, bx, by, bz, u, un);
+}
+
 /* Spreading kernel of source s (Sec. 3.1: point-source explicit FD march, column s of p in Eq. 8),
  * on the window of radius R clipped to the domain, n_sub substeps.
  * k_out: (2R+1)^3 doubles on the offset layout, the marched field divided by its total.
@@ -270,8 +283,9 @@ void fo_coarse_counts(int nx, int ny, int nz, const uint8_t* liquid, int B, int6
  * marched mass on the liquid cells of block I and m the total (N_J in exact arithmetic, so each column
  * conserves mass).  Stored source-major: P_band[J][d], d = I - J over [-Rc, Rc]^3, Rc = ceil(R / B),
  * offset layout d_x fastest; 0 where block I is outside the grid or has no liquid.  OpenMP over J. */
-int fo_coarse_kernels(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                      const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
+static int coarse_kernels_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                               const double* wxv, const double* wyv, const double* wzv, double lama,
+                               const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
 {
     if (B < 1 || R < 0 || n_sub < 0) return -1;
     int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
@@ -304,7 +318,7 @@ int fo_coarse_kernels(int nx, int ny, int nz, const double* gx, const double* gy
                         u[i + (int64_t)wx * (j + (int64_t)wy * l)] = 1.0;
                 }
         for (int k = 0; k < n_sub; k++) {
-            box_substep(nx, ny, gx, gy, gz, lam, x0, y0, z0, wx, wy, wz, u, un);
+            box_step(nx, ny, gx, gy, gz, wxv, wyv, wzv, lam, lama, x0, y0, z0, wx, wy, wz, u, un);
             double* t = u; u = un; un = t;
         }
         double m = 0.0;
@@ -332,6 +346,21 @@ int fo_coarse_kernels(int nx, int ny, int nz, const double* gx, const double* gy
     }
     free(cnt);
     return err ? -1 : 0;
+}
+
+int fo_coarse_kernels(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                      const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
+{
+    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, liquid, B, lam, R, n_sub, P_band);
+}
+
+/* fo_coarse_kernels with the block-source march carrying the upwind faces of face velocities w (Sec. 5),
+ * lama = dt_sub / h.  The caller zeroes w on faces that touch a non-liquid cell (no flux there). */
+int fo_coarse_kernels_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                          const double* wx, const double* wy, const double* wz, double lama, const uint8_t* liquid,
+                          int B, double lam, int R, int n_sub, double* P_band)
+{
+    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, liquid, B, lam, R, n_sub, P_band);
 }
 
 /* One coarse FDiRW step, Eqs. 13-15 without the boundary term: 'mapping' C_I = mean of c over the
@@ -396,10 +425,11 @@ void fo_boundary_conductance(int nx, int ny, int nz, const double* D, const uint
 
 /* One flux-form substep as box_substep plus the open faces: u_i += lam gb_i (ghost - u_i). */
 static void box_substep_open(int nx, int ny, const double* gx, const double* gy, const double* gz,
+                             const double* wxv, const double* wyv, const double* wzv, double lama,
                              const double* gb, double ghost, double lam, int x0, int y0, int z0, int bx, int by,
                              int bz, const double* u, double* un)
 {
-    box_substep(nx, ny, gx, gy, gz, lam, x0, y0, z0, bx, by, bz, u, un);
+    box_step(nx, ny, gx, gy, gz, wxv, wyv, wzv, lam, lama, x0, y0, z0, bx, by, bz, u, un);
     for (int l = 0; l < bz; l++)
         for (int j = 0; j < by; j++)
             for (int i = 0; i < bx; i++) {
@@ -411,9 +441,10 @@ static void box_substep_open(int nx, int ny, const double* gx, const double* gy,
 
 /* Coarse matrix with open faces: as fo_coarse_kernels, the march also losing mass through the open
  * faces (ghost 0), and no renormalisation: P[I][J] = S_I / N_I (the column carries the mass that stays). */
-int fo_coarse_kernels_open(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                           const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
-                           double* P_band)
+static int coarse_kernels_open_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                                    const double* wxv, const double* wyv, const double* wzv, double lama,
+                                    const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
+                                    double* P_band)
 {
     if (B < 1 || R < 0 || n_sub < 0) return -1;
     int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
@@ -446,7 +477,7 @@ int fo_coarse_kernels_open(int nx, int ny, int nz, const double* gx, const doubl
                         u[i + (int64_t)wx * (j + (int64_t)wy * l)] = 1.0;
                 }
         for (int k = 0; k < n_sub; k++) {
-            box_substep_open(nx, ny, gx, gy, gz, gb, 0.0, lam, x0, y0, z0, wx, wy, wz, u, un);
+            box_substep_open(nx, ny, gx, gy, gz, wxv, wyv, wzv, lama, gb, 0.0, lam, x0, y0, z0, wx, wy, wz, u, un);
             double* t = u; u = un; un = t;
         }
         for (int l = 0; l < wz; l++)
@@ -474,10 +505,29 @@ int fo_coarse_kernels_open(int nx, int ny, int nz, const double* gx, const doubl
     return err ? -1 : 0;
 }
 
+int fo_coarse_kernels_open(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                           const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
+                           double* P_band)
+{
+    return coarse_kernels_open_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, gb, liquid, B, lam, R, n_sub,
+                                    P_band);
+}
+
+/* fo_coarse_kernels_open with upwind faces (Sec. 5); the open faces stay diffusive (no flow leaves the
+ * grid), and the caller zeroes w on faces that touch a non-liquid cell. */
+int fo_coarse_kernels_open_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                               const double* wx, const double* wy, const double* wz, double lama, const double* gb,
+                               const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
+{
+    return coarse_kernels_open_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, gb, liquid, B, lam, R, n_sub, P_band);
+}
+
 /* P_BC of Eq. 10: the liquid phase marched n_sub substeps over the whole grid from 0 with every ghost at
- * c_far = 1, then mapped to the blocks (Eq. 11): PBC[I] = mean over the liquid cells of block I. */
-int fo_coarse_pbc(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz, const double* gb,
-                  const uint8_t* liquid, int B, double lam, int n_sub, double* PBC)
+ * c_far = 1, then mapped to the blocks (Eq. 11): PBC[I] = mean over the liquid cells of block I.  With face
+ * velocities (wx != NULL) the interior faces carry the upwind advective flux too. */
+static int coarse_pbc_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                           const double* wxv, const double* wyv, const double* wzv, double lama, const double* gb,
+                           const uint8_t* liquid, int B, double lam, int n_sub, double* PBC)
 {
     int64_t N = (int64_t)nx * ny * nz;
     int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
@@ -487,7 +537,7 @@ int fo_coarse_pbc(int nx, int ny, int nz, const double* gx, const double* gy, co
     int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
     if (!u || !un || !cnt) { free(u); free(un); free(cnt); return -1; }
     for (int k = 0; k < n_sub; k++) {
-        box_substep_open(nx, ny, gx, gy, gz, gb, 1.0, lam, 0, 0, 0, nx, ny, nz, u, un);
+        box_substep_open(nx, ny, gx, gy, gz, wxv, wyv, wzv, lama, gb, 1.0, lam, 0, 0, 0, nx, ny, nz, u, un);
         double* t = u; u = un; un = t;
     }
     fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
@@ -501,6 +551,19 @@ int fo_coarse_pbc(int nx, int ny, int nz, const double* gx, const double* gy, co
     for (int64_t I = 0; I < NC; I++) if (cnt[I] > 0) PBC[I] /= (double)cnt[I];
     free(u); free(un); free(cnt);
     return 0;
+}
+
+int fo_coarse_pbc(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz, const double* gb,
+                  const uint8_t* liquid, int B, double lam, int n_sub, double* PBC)
+{
+    return coarse_pbc_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, gb, liquid, B, lam, n_sub, PBC);
+}
+
+int fo_coarse_pbc_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                      const double* wx, const double* wy, const double* wz, double lama, const double* gb,
+                      const uint8_t* liquid, int B, double lam, int n_sub, double* PBC)
+{
+    return coarse_pbc_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, gb, liquid, B, lam, n_sub, PBC);
 }
 
 /* One coarse step with the far field (Eqs. 13-15 with the P_BC c_far term of Eq. 14, then Eq. 7):

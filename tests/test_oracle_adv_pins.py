@@ -63,3 +63,67 @@ def test_superpose_adv_conserves_mass():
     c = synth.random_field(720, 113)
     out = oracle.superpose_adv(shape, D, w, lam, 0.5, 3, 9, c)
     assert out.sum() == pytest.approx(c.sum(), rel=1e-13) and out.min() >= 0.0
+
+
+# ---------------------------------------------------------------- convection on the coarse (liquid) path
+
+def _packing(shape, seed):
+    p = synth.sphere_packing(shape, 0.45, seed, r_range=(1.5, 3.0))
+    return synth.diffusivity_per_sphere(p), (~p.solid).astype(np.uint8)
+
+
+def test_coarse_no_flow_is_the_diffusion_matrix():
+    shape = (12, 11, 10)
+    D, liquid = _packing(shape, 112)
+    lam = 0.5 * oracle.stable_dt_sub(shape, D)
+    w0 = _w(D.size)
+    assert np.array_equal(oracle.coarse_kernels(shape, D, liquid, 3, lam, 2, 12, w=w0),
+                          oracle.coarse_kernels(shape, D, liquid, 3, lam, 2, 12))
+    assert np.array_equal(oracle.coarse_kernels_open(shape, D, liquid, 3, lam, 2, 12, w=w0),
+                          oracle.coarse_kernels_open(shape, D, liquid, 3, lam, 2, 12))
+    assert np.array_equal(oracle.coarse_pbc(shape, D, liquid, 3, lam, 12, w=w0),
+                          oracle.coarse_pbc(shape, D, liquid, 3, lam, 12))
+
+
+def test_coarse_unit_blocks_are_the_fine_upwind_kernels():
+    """B = 1 on an all-liquid grid: column J of P is the fine kernel of source J with the same flow."""
+    shape = (9, 8, 7)
+    N = 504
+    D = synth.random_diffusivity(shape, 113, 2.0)
+    lam = 0.5 * oracle.stable_dt_sub(shape, D)
+    w = synth.face_velocity(shape, 114, (0.3, -0.2, 0.1), 0.3)
+    P = oracle.coarse_kernels(shape, D, np.ones(N, np.uint8), 1, lam, 2, 15, w=w)
+    for J in (0, 77, 250, 503):
+        k, _ = oracle.source_kernel_adv(shape, D, w, lam, lam, 2, 15, J)
+        assert np.array_equal(P[J], k), J
+
+
+def test_coarse_flow_columns_conserve_and_stay_positive():
+    """Closed windows: every column carries its block's liquid cells exactly (sum_I P[I][J] N_I = N_J),
+    the flow moves mass downstream (the +x neighbour block gains against the no-flow matrix), and with
+    the outer faces open the columns only lose mass."""
+    shape = (15, 9, 9)
+    D, liquid = _packing(shape, 115)
+    lam = 0.5 * oracle.stable_dt_sub(shape, D)
+    B, R, n_sub = 3, 3, 20
+    w = synth.face_velocity(shape, 116, (0.6, 0.0, 0.0), 0.0)
+    P = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub, w=w)
+    P0 = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub)
+    Po = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub, w=w)
+    cnt = oracle.coarse_counts(shape, liquid, B)
+    ncx, ncy, ncz = 5, 3, 3
+    Rc = 1
+    for J in np.flatnonzero(cnt):
+        bx, by, bz = J % ncx, (J // ncx) % ncy, J // (ncx * ncy)
+        tot = 0.0
+        for dz in range(-Rc, Rc + 1):
+            for dy in range(-Rc, Rc + 1):
+                for dx in range(-Rc, Rc + 1):
+                    cx, cy, cz = bx + dx, by + dy, bz + dz
+                    if 0 <= cx < ncx and 0 <= cy < ncy and 0 <= cz < ncz:
+                        tot += P[J, dz + Rc, dy + Rc, dx + Rc] * cnt[cx + ncx * (cy + ncy * cz)]
+        assert tot == pytest.approx(cnt[J], rel=1e-12)
+    assert P.min() >= 0.0 and Po.min() >= 0.0
+    assert np.all(Po.reshape(len(cnt), -1).sum(1) <= P.reshape(len(cnt), -1).sum(1) * (1 + 1e-12) + 1e-15)
+    downstream = P[:, Rc, Rc, Rc + 1] - P0[:, Rc, Rc, Rc + 1]
+    assert downstream[np.flatnonzero(cnt)].sum() > 0.0
