@@ -256,7 +256,8 @@ FDIRW_API int fdirw_read_coarse(fdirw_ctx* ctx, const int64_t* blocks, int64_t n
  * is conserved.  Calling it again only resets c_far.
  *   V_far : far-field volume in cell volumes (> 0, finite); c_far: its current concentration (finite)
  * Errors: FDIRW_ERR_ARG (not a coarse context, bad values), FDIRW_ERR_UNSTABLE (the open faces push
- * dt_sub * max(sum g) / h^2 above 1), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
+ * dt_sub * max(sum g) / h^2 above 1), FDIRW_ERR_STATE (the first call after fdirw_set_velocity: open the
+ * far field before setting a velocity), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
 FDIRW_API int fdirw_coarse_far_field(fdirw_ctx* ctx, double V_far, double c_far);
 
 /* Current far-field concentration (after the last fdirw_step).  Synchronises the context stream.
@@ -302,11 +303,14 @@ FDIRW_API int fdirw_coupled_step(fdirw_ctx* ctx, const fdirw_coupled_params* par
  * then carries, across each interior face, the diffusive flux lam g (u_lower - u_upper) plus the upwind
  * advective flux lam_a (w+ u_lower - w- u_upper), lam = dt_sub / h^2, lam_a = dt_sub / h, w+ = max(w, 0),
  * w- = max(-w, 0); window and domain edges stay closed.  The face coefficients are rounded once to FP32
- * and the march runs mapping 5 (direction-dependent faces); the superposition is unchanged.  A second
- * call replaces the velocity; the kernels are recomputed by the next fdirw_kernels / fdirw_step.  With
- * w = 0 the kernels and steps are bit for bit those without a velocity.  Synchronises the context
- * stream.  Errors: FDIRW_ERR_ARG (NULL or misaligned w, NaN or infinite values, a batch or coarse
- * context, FDIRW_FP64 precision), FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
+ * and the march runs mapping 5 (direction-dependent faces); the superposition is unchanged.  On a
+ * coarse-mesh context faces touching a non-liquid cell carry neither flux, the block-source march and
+ * the P_BC march use the same faces, and the far field's open faces stay diffusive (open the far field
+ * first: its stability check then includes the flow).  A second call replaces the velocity; the kernels
+ * (or P and P_BC) are recomputed by the next fdirw_kernels / fdirw_step.  With w = 0 the kernels and
+ * steps are bit for bit those without a velocity.  Synchronises the context stream.
+ * Errors: FDIRW_ERR_ARG (NULL or misaligned w, NaN or infinite values, a batch context, FDIRW_FP64
+ * precision), FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
  * any, stays in place), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
 FDIRW_API int fdirw_set_velocity(fdirw_ctx* ctx, const double* w);
 

@@ -138,18 +138,29 @@ __global__ void open_faces_kernel(Grid g, const double* __restrict__ D, const ui
 // One explicit substep of the liquid phase over the whole grid with every far-field ghost at 1 (the
 // P_BC march): u' = u + (am u + sum c u_nb + abnd), am = -(sum of the cell's coefficients + abnd), in the
 // FP32 increment form and association of the windowed kernels.
+// With convection (bx != NULL) the inflow from the upper neighbour uses B and the diagonal sums the cell's
+// outflows (A of its +faces, B of its -faces), as the block-source march.
 __global__ void pbc_substep_kernel(Grid g, const float* __restrict__ ax, const float* __restrict__ ay,
-                                   const float* __restrict__ az, const float* __restrict__ abnd,
-                                   const float* __restrict__ u, float* __restrict__ un) {
+                                   const float* __restrict__ az, const float* __restrict__ bx,
+                                   const float* __restrict__ by, const float* __restrict__ bz,
+                                   const float* __restrict__ abnd, const float* __restrict__ u,
+                                   float* __restrict__ un) {
     const int64_t nxy = (int64_t)g.nx * g.ny;
+    const float* ux = bx ? bx : ax;                   // coefficient of the upper neighbour in this cell
+    const float* uy = bx ? by : ay;
+    const float* uz = bx ? bz : az;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / nxy);
-        const float cxm = x > 0 ? ax[i - 1] : 0.f, cxp = x + 1 < g.nx ? ax[i] : 0.f;
-        const float cym = y > 0 ? ay[i - g.nx] : 0.f, cyp = y + 1 < g.ny ? ay[i] : 0.f;
-        const float czm = z > 0 ? az[i - nxy] : 0.f, czp = z + 1 < g.nz ? az[i] : 0.f;
+        const float cxm = x > 0 ? ax[i - 1] : 0.f, cxp = x + 1 < g.nx ? ux[i] : 0.f;
+        const float cym = y > 0 ? ay[i - g.nx] : 0.f, cyp = y + 1 < g.ny ? uy[i] : 0.f;
+        const float czm = z > 0 ? az[i - nxy] : 0.f, czp = z + 1 < g.nz ? uz[i] : 0.f;
+        // outflows: the cell's own +faces (A) and the lower neighbours' B; equal to the inflows without flow
+        const float oxm = x > 0 ? ux[i - 1] : 0.f, oxp = x + 1 < g.nx ? ax[i] : 0.f;
+        const float oym = y > 0 ? uy[i - g.nx] : 0.f, oyp = y + 1 < g.ny ? ay[i] : 0.f;
+        const float ozm = z > 0 ? uz[i - nxy] : 0.f, ozp = z + 1 < g.nz ? az[i] : 0.f;
         const float vb = abnd[i];
         const float cur = u[i];
-        const float am = -((((cxm + cxp) + (cym + cyp)) + (czm + czp)) + vb);
+        const float am = -((((oxm + oxp) + (oym + oyp)) + (ozm + ozp)) + vb);
         float v = am * cur;
         v = fmaf(cxm, x > 0 ? u[i - 1] : 0.f, v);
         v = fmaf(cxp, x + 1 < g.nx ? u[i + 1] : 0.f, v);
@@ -352,6 +363,11 @@ int coarse_kernels(fdirw_ctx* c) {
     a.ccount = k.count;
     a.Qc = k.Qc;
     a.abnd = k.open ? k.abnd : nullptr;
+    if (c->flow) {                                     // convection: direction-dependent faces
+        a.bx = reinterpret_cast<const float*>(c->coefb[0]);
+        a.by = reinterpret_cast<const float*>(c->coefb[1]);
+        a.bz = reinterpret_cast<const float*>(c->coefb[2]);
+    }
     FDIRW_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     if (k.nodes > 0 && c->n_sub >= 0) FDIRW_CUDA(c, launch_march_coarse(a, k.Rw, c->num_sms, c->stream));
     FDIRW_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
@@ -362,7 +378,7 @@ int coarse_kernels(fdirw_ctx* c) {
         FDIRW_CUDA(c, cudaMemsetAsync(u0, 0, (size_t)c->g.n * 4, c->stream));
         for (int t = 0; t < c->n_sub; t++) {
             pbc_substep_kernel<<<grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(
-                c->g, a.ax, a.ay, a.az, k.abnd, u0, u1);
+                c->g, a.ax, a.ay, a.az, a.bx, a.by, a.bz, k.abnd, u0, u1);
             FDIRW_CUDA(c, cudaGetLastError());
             std::swap(u0, u1);
         }
@@ -439,6 +455,14 @@ int coarse_info(fdirw_ctx* c, fdirw_info* out) {
     out->cache_bytes = (uint64_t)(2 * c->coarse->Rc + 1) * (2 * c->coarse->Rc + 1) * (2 * c->coarse->Rc + 1) *
                        (uint64_t)c->coarse->nc * 8;
     return FDIRW_OK;
+}
+
+const uint8_t* coarse_liquid(fdirw_ctx* c) { return c->coarse ? c->coarse->liquid : nullptr; }
+
+const float* coarse_open_faces(fdirw_ctx* c) { return (c->coarse && c->coarse->open) ? c->coarse->abnd : nullptr; }
+
+void coarse_invalidate(fdirw_ctx* c) {
+    if (c->coarse) c->coarse->built = false;
 }
 
 void coarse_release(fdirw_ctx* c) {
@@ -565,6 +589,8 @@ int fdirw_coarse_far_field(fdirw_ctx* c, double V_far, double c_far) {
         return fail(c, FDIRW_ERR_ARG, "V_far must be finite and > 0, c_far finite");
     DeviceGuard dg(c->device);
     fdirw::Coarse& k = *c->coarse;
+    if (c->flow && !k.abnd)
+        return fail(c, FDIRW_ERR_STATE, "open the far field before setting a velocity (its stability check includes the flow)");
     const uint64_t n = (uint64_t)c->g.n;
     int rc;
     if (!k.abnd) {

@@ -100,6 +100,9 @@ int coarse_kernels(fdirw_ctx* c);
 int coarse_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps, double* mass_out);
 int coarse_info(fdirw_ctx* c, fdirw_info* out);
 void coarse_release(fdirw_ctx* c);
+const uint8_t* coarse_liquid(fdirw_ctx* c);    // the coarse context's liquid mask (device)
+const float* coarse_open_faces(fdirw_ctx* c);  // lam * open-face conductance per cell, or NULL (no far field)
+void coarse_invalidate(fdirw_ctx* c);          // the coarse matrix and P_BC must be rebuilt
 
 // Allocates (once) and zeroes the kernel cache of a context; honours mem_limit, and falls back to a
 // cache of z-slabs of destinations (slab_T) when the whole cache does not fit.

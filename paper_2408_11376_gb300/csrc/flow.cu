@@ -4,6 +4,8 @@
 // upper cell's, with lam = dt_sub / h^2 and lam_a = dt_sub / h.  The two coefficients replace the
 // symmetric lam g of the diffusion-only march: A (lower into upper) in the context's coefficient arrays,
 // B (upper into lower) in a second set, and the march runs mapping 5 with direction-dependent faces.
+// On a coarse-mesh context the liquid mask closes faces touching non-liquid cells for both fluxes, and
+// the block-source march and the P_BC march use the same coefficients; open faces stay diffusive.
 #include "fdirw.h"
 #include "fdirw_internal.h"
 #include "ctx.h"
@@ -28,12 +30,14 @@ __device__ __forceinline__ double harmonic(double a, double b) {
     return (a + b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
 }
 
-// A and B of the +x, +y, +z face of every cell (FP32, one rounding from FP64), 0 on the last plane; and
-// the largest per-cell sum of outflow coefficients (bits of a non-negative double, for atomicMax) for the
-// stability check, +inf where a velocity that enters the march is NaN or infinite.
+// A and B of the +x, +y, +z face of every cell (FP32, one rounding from FP64), 0 on the last plane and,
+// with a liquid mask, on faces touching a non-liquid cell; and the largest per-cell sum of outflow
+// coefficients, open faces included (bits of a non-negative double, for atomicMax) for the stability
+// check, +inf where a velocity that enters the march is NaN or infinite.
 __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const double* __restrict__ w,
-                                 double lam, double lama, float* __restrict__ A,
-                                 float* __restrict__ Bc, unsigned long long* __restrict__ max_bits) {
+                                 const uint8_t* __restrict__ liquid, bool open, double lam, double lama,
+                                 float* __restrict__ A, float* __restrict__ Bc,
+                                 unsigned long long* __restrict__ max_bits) {
     const int64_t nxy = (int64_t)g.nx * g.ny;
     const int64_t stride[3] = {1, g.nx, nxy};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -45,10 +49,12 @@ __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const dou
             double a = 0.0, b = 0.0;
             if (c3[ax] + 1 < n3[ax]) {
                 const int64_t j = i + stride[ax];
-                const double gd = lam * harmonic(D[i], D[j]);
                 const double wv = w[ax * g.n + i];
-                a = gd + lama * (wv > 0.0 ? wv : 0.0);
-                b = gd + lama * (wv < 0.0 ? -wv : 0.0);
+                if (!liquid || (liquid[i] && liquid[j])) {
+                    const double gd = lam * harmonic(D[i], D[j]);
+                    a = gd + lama * (wv > 0.0 ? wv : 0.0);
+                    b = gd + lama * (wv < 0.0 ? -wv : 0.0);
+                }
                 if (!isfinite(wv)) out = INFINITY;          // reported as invalid input, never installed
             }
             A[ax * g.n + i] = (float)a;
@@ -57,10 +63,17 @@ __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const dou
             // -face of cell i: outflow is the lower neighbour's B
             if (c3[ax] > 0) {
                 const int64_t j = i - stride[ax];
-                const double gd = lam * harmonic(D[j], D[i]);
-                const double wv = w[ax * g.n + j];
-                out += gd + lama * (wv < 0.0 ? -wv : 0.0);
+                if (!liquid || (liquid[i] && liquid[j])) {
+                    const double gd = lam * harmonic(D[j], D[i]);
+                    const double wv = w[ax * g.n + j];
+                    out += gd + lama * (wv < 0.0 ? -wv : 0.0);
+                }
             }
+        }
+        if (open && liquid && liquid[i]) {                // open faces (far field): diffusive outflow D_i per face
+            const int faces = (c3[0] == 0) + (c3[0] == g.nx - 1) + (c3[1] == 0) + (c3[1] == g.ny - 1) +
+                              (c3[2] == 0) + (c3[2] == g.nz - 1);
+            out += lam * (D[i] * (double)faces);
         }
         atomicMax(max_bits, (unsigned long long)__double_as_longlong(out));
     }
@@ -73,7 +86,7 @@ extern "C" {
 
 int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
-    if (c->batch || c->coarse) return fail(c, FDIRW_ERR_ARG, "convection serves fdirw_create contexts only");
+    if (c->batch) return fail(c, FDIRW_ERR_ARG, "convection is not available for batch contexts");
     if (c->store == fdirw::Store::F64) return fail(c, FDIRW_ERR_ARG, "convection needs an FP32-march precision");
     if (!w) return fail(c, FDIRW_ERR_ARG, "NULL velocity field");
     if ((reinterpret_cast<uintptr_t>(w) & 7u) != 0) return fail(c, FDIRW_ERR_ARG, "w must be 8-byte aligned");
@@ -105,8 +118,10 @@ int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     cudaError_t e = cudaMemcpyAsync(dw, w, 3 * n * 8, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, 8, c->stream);
     if (e == cudaSuccess) {
+        const uint8_t* liquid = c->coarse ? fdirw::coarse_liquid(c) : nullptr;
+        const bool open = c->coarse && fdirw::coarse_open_faces(c) != nullptr;
         fdirw::flow_coef_kernel<<<fdirw::grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(
-            c->g, c->Dd, dw, c->lam, c->lam * c->h, AB, AB + 3 * n, mx);
+            c->g, c->Dd, dw, liquid, open, c->lam, c->lam * c->h, AB, AB + 3 * n, mx);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, mx, 8, cudaMemcpyDeviceToHost, c->stream);
@@ -133,6 +148,7 @@ int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     }
     c->kernels_ready = false;
     c->flow = true;
+    if (c->coarse) fdirw::coarse_invalidate(c);        // P and P_BC are rebuilt with the flow
     return FDIRW_OK;
 }
 

@@ -1413,16 +1413,16 @@ cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStrea
 
 cudaError_t launch_march_coarse(const MarchArgs& a, int R, int num_sms, cudaStream_t st) {
     switch (R) {
-        case 1: return launch_tmc<1, true>(a, num_sms, st);
-        case 2: return launch_tmc<2, true>(a, num_sms, st);
-        case 3: return launch_tmc<3, true>(a, num_sms, st);
-        case 4: return launch_tmc<4, true>(a, num_sms, st);
-        case 5: return launch_tmc<5, true>(a, num_sms, st);
-        case 6: return launch_tmc<6, true>(a, num_sms, st);
-        case 7: return launch_tmc<7, true>(a, num_sms, st);
-        case 8: return launch_tmc<8, true>(a, num_sms, st);
-        case 9: return launch_tmc<9, true>(a, num_sms, st);
-        case 10: return launch_tmc<10, true>(a, num_sms, st);
+        case 1: return a.bx ? launch_tmc<1, true, true>(a, num_sms, st) : launch_tmc<1, true>(a, num_sms, st);
+        case 2: return a.bx ? launch_tmc<2, true, true>(a, num_sms, st) : launch_tmc<2, true>(a, num_sms, st);
+        case 3: return a.bx ? launch_tmc<3, true, true>(a, num_sms, st) : launch_tmc<3, true>(a, num_sms, st);
+        case 4: return a.bx ? launch_tmc<4, true, true>(a, num_sms, st) : launch_tmc<4, true>(a, num_sms, st);
+        case 5: return a.bx ? launch_tmc<5, true, true>(a, num_sms, st) : launch_tmc<5, true>(a, num_sms, st);
+        case 6: return a.bx ? launch_tmc<6, true, true>(a, num_sms, st) : launch_tmc<6, true>(a, num_sms, st);
+        case 7: return a.bx ? launch_tmc<7, true, true>(a, num_sms, st) : launch_tmc<7, true>(a, num_sms, st);
+        case 8: return a.bx ? launch_tmc<8, true, true>(a, num_sms, st) : launch_tmc<8, true>(a, num_sms, st);
+        case 9: return a.bx ? launch_tmc<9, true, true>(a, num_sms, st) : launch_tmc<9, true>(a, num_sms, st);
+        case 10: return a.bx ? launch_tmc<10, true, true>(a, num_sms, st) : launch_tmc<10, true>(a, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -220,3 +220,94 @@ def test_coupled_exchange_and_solid_march_are_exact():
         field = c0.copy()
         f.coupled_step(field, 1, 0.02, 1.0, 1e-5, dt, 2)
     assert np.array_equal(field, ref)
+
+
+# ------------------------------------------------------------------ convection on the coarse path (Sec. 5)
+
+def _flow(shape, seed, liquid, mean=(0.25, -0.1, 0.05), amp=0.2):
+    return synth.face_velocity(shape, seed, mean, amp, liquid == 0)
+
+
+def test_coarse_flow_matrix_and_steps_match_oracle():
+    shape, B, R, n_sub = (23, 21, 19), 5, 3, 24
+    D, liquid = _case(shape, 170)
+    lam = 0.5 * oracle.stable_dt_sub(shape, D)
+    w = _flow(shape, 171, liquid)
+    P = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub, w=w)
+    c0 = synth.random_field(D.size, 172, 0.0, 2.0)
+    ref = c0
+    for _ in range(3):
+        ref = oracle.coarse_step(shape, liquid, B, R, P, ref)
+    with FDiRWCoarse(shape, D, liquid, B, n_sub * lam, R, n_sub) as f:
+        f.set_velocity(w)
+        f.kernels()
+        got = f.read_coarse(np.arange(P.shape[0]))
+        out = np.empty_like(c0)
+        m = f.step(c0, out, 3, want_mass=True)
+    cnt = oracle.coarse_counts(shape, liquid, B)
+    for J in np.flatnonzero(cnt):
+        assert _rel(got[J], P[J]) <= P_TOL, (J, _rel(got[J], P[J]))
+    assert _rel(out, ref) <= FIELD_TOL
+    assert abs(m - c0.sum()) <= 1e-12 * c0.sum()
+    assert np.array_equal(out[liquid == 0], c0[liquid == 0])
+
+
+def test_coarse_no_flow_is_bitwise_the_diffusion_path():
+    shape, B, R, n_sub = (17, 16, 15), 3, 4, 20
+    D, liquid = _case(shape, 173)
+    lam = oracle.stable_dt_sub(shape, D)
+    c0 = synth.random_field(D.size, 174)
+    outs = []
+    for flow in (False, True):
+        with FDiRWCoarse(shape, D, liquid, B, n_sub * lam, R, n_sub) as f:
+            f.far_field(1000.0, 0.3)
+            if flow:
+                f.set_velocity(np.zeros(3 * D.size))
+            o = np.empty_like(c0)
+            f.step(c0, o, 2)
+            outs.append((o, f.read_coarse(np.arange(10)), f.read_pbc(), f.c_far()))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_coarse_flow_far_field_matches_oracle():
+    shape, B, R, n_sub, V_far, cf0 = (22, 19, 17), 5, 4, 24, 3000.0, 0.4
+    D, liquid = _case(shape, 175)
+    lam = 0.4 * oracle.stable_dt_sub(shape, D)
+    w = _flow(shape, 176, liquid)
+    P = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub, w=w)
+    pbc = oracle.coarse_pbc(shape, D, liquid, B, lam, n_sub, w=w)
+    c0 = synth.random_field(D.size, 177, 0.0, 1.0)
+    ref, cf = c0, cf0
+    for _ in range(3):
+        ref, cf = oracle.coarse_step_far(shape, liquid, B, R, P, pbc, V_far, cf, ref)
+    with FDiRWCoarse(shape, D, liquid, B, n_sub * lam, R, n_sub) as f:
+        f.far_field(V_far, cf0)
+        f.set_velocity(w)
+        f.kernels()
+        gotP = f.read_coarse(np.arange(P.shape[0]))
+        gotpbc = f.read_pbc()
+        out = np.empty_like(c0)
+        f.step(c0, out, 3)
+        cfar = f.c_far()
+    for J in np.flatnonzero(oracle.coarse_counts(shape, liquid, B)):
+        assert _rel(gotP[J], P[J]) <= P_TOL
+    assert _rel(gotpbc, pbc) <= P_TOL
+    assert _rel(out, ref) <= FIELD_TOL
+    assert abs(cfar - cf) <= FIELD_TOL * np.abs(ref).sum() / V_far
+    assert out.sum() + V_far * cfar == pytest.approx(c0.sum() + V_far * cf0, rel=1e-12)
+
+
+def test_coarse_flow_ordering_and_stability_errors():
+    shape = (10, 10, 10)
+    D = np.ones(1000)
+    with FDiRWCoarse(shape, D, None, 5, 0.05, 2, 1) as f:
+        f.set_velocity(np.zeros(3000))
+        with pytest.raises(FdirwError) as e:
+            f.far_field(100.0, 0.0)                     # the far field must come first
+        assert e.value.code == fdirw.FDIRW_ERR_STATE
+    with FDiRWCoarse(shape, D, None, 5, 0.1, 2, 1) as f:
+        f.far_field(100.0, 0.0)                         # lam sum = 0.1 * (6 + open faces) <= 0.9
+        with pytest.raises(FdirwError) as e:
+            f.set_velocity(np.full(3000, 2.0))          # the flow pushes a boundary cell's outflow over 1
+        assert e.value.code == fdirw.FDIRW_ERR_UNSTABLE
