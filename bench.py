@@ -706,7 +706,34 @@ def coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, liquid, dt_macro):
     far_leg = {"V_far_cells": V_far, "c_far0": 0.0, "c_far_after": c_far,
                "near_field_mass_after": float(far.sum().item()),
                "total_rel_err": abs(far_total - mass0) / mass0, "matrix_pbc_and_steps_ms": fe[0].elapsed_time(fe[1])}
+    # Convection on the coarse path (Sec. 5): the far field above plus the --flow leg's face velocities
+    # (mean 0.03 along +x, noise 0.03, zero on faces touching non-liquid cells) and, as there, n_sub raised
+    # by a tenth so that the diffusive part leaves room for the advective outflow.
+    from paper_2408_11376_gb300 import synth
+    vel = torch.from_numpy(synth.face_velocity(shape, w.seed + 40, (0.03, 0.0, 0.0), 0.03, ~liquid).reshape(-1)).to(dev)
+    flow_out = torch.empty_like(c_liq)
+    ff = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    n_sub_flow = -(-11 * w.n_sub // 10)
+    with torch.cuda.stream(stream):
+        f = fdirw.FDiRWCoarse(shape, D, lq, B, dt_macro, w.R, n_sub_flow, args.prec, device=dev.index, stream=stream)
+        f.far_field(V_far, 0.0)
+        try:
+            f.set_velocity(vel)
+            ff[0].record(stream)
+            f.kernels()
+            ff[1].record(stream)
+            f.step(c_liq, flow_out, w.steps)
+            ff[2].record(stream)
+            flow_cfar = f.c_far()
+            stream.synchronize()
+            flow_leg = {"velocity": "mean 0.03 along +x, noise 0.03, 0 on non-liquid faces", "n_sub": n_sub_flow,
+                        "matrix_and_pbc_ms": ff[0].elapsed_time(ff[1]), "steps_ms": ff[1].elapsed_time(ff[2]),
+                        "total_rel_err": abs(float(flow_out.sum().item()) + V_far * flow_cfar - mass0) / mass0}
+        except fdirw.FdirwError as e:       # reported, not fatal: the other legs stand
+            flow_leg = {"error": str(e)}
+        f.close()
     return {"block": B, "nodes": info["coarse_nodes"], "liquid_cells": int(liquid.sum()), "far_field": far_leg,
+            "convection": flow_leg,
             "macro_steps_per_s": 1000.0 * w.steps / job_ms, "job_ms": job_ms, "matrix_build_ms": build_ms,
             "march_kernel_ms": info["kernels_ms"], "steps_ms": steps_ms,
             "march_cell_substeps_per_s": w.n_sub * info["window_cells"] / (info["kernels_ms"] * 1e-3),
