@@ -148,28 +148,42 @@ int fdirw::ensure_cache(fdirw_ctx* c) {
     const uint64_t plane = W * (uint64_t)c->g.nx * (uint64_t)c->g.ny * (uint64_t)fdirw::store_bytes(c->store);
     const uint64_t full = plane * (uint64_t)c->g.nz;
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    uint64_t budget = ~0ull;
     constexpr uint64_t kReserve = 1ull << 30;
-    uint64_t budget = free_b > kReserve ? free_b - kReserve : 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = free_b > kReserve ? free_b - kReserve : 0;
+    else cudaGetLastError();                                   // unknown: let the allocation decide
     if (c->mem_limit) budget = std::min<uint64_t>(budget, c->mem_limit > c->allocated ? c->mem_limit - c->allocated : 0);
+    const uint64_t obytes = (uint64_t)c->g.n * 8;
     int T = c->g.nz;
     if (full > budget) {
-        const uint64_t obytes = (uint64_t)c->g.n * 8;
         const uint64_t rest = budget > obytes ? budget - obytes : 0;
         T = (int)std::min<uint64_t>(rest / plane, (uint64_t)c->g.nz);
-        if (T < 1)
-            return fail(c, FDIRW_ERR_NOMEM, "the kernel cache does not fit, not even one z-plane of destinations (" +
-                                                std::to_string(plane) + " bytes)");
-        int rc = dalloc(c, reinterpret_cast<void**>(&c->obuf), obytes, "streamed step output");
-        if (rc != FDIRW_OK) return rc;
-        c->slab_T = T < c->g.nz ? T : 0;
     }
-    c->q_bytes = plane * (uint64_t)T;
-    const int rc = dalloc(c, &c->Q, c->q_bytes, "kernel cache");
-    if (rc != FDIRW_OK) { c->q_bytes = 0; c->slab_T = 0; return rc; }
-    // Entries whose source lies outside the domain are never written by the march: zero them once.
-    FDIRW_CUDA(c, cudaMemsetAsync(c->Q, 0, c->q_bytes, c->stream));
-    return FDIRW_OK;
+    // Largest slab that allocates: the whole grid when it fits, else halving after a failed allocation
+    // (free memory can be fragmented or taken meanwhile).
+    while (T >= 1) {
+        const bool streamed = T < c->g.nz;
+        if (streamed && !c->obuf) {
+            const int rc = dalloc(c, reinterpret_cast<void**>(&c->obuf), obytes, "streamed step output");
+            if (rc != FDIRW_OK) return rc;
+        }
+        const int rc = dalloc(c, &c->Q, plane * (uint64_t)T, "kernel cache");
+        if (rc == FDIRW_OK) {
+            c->q_bytes = plane * (uint64_t)T;
+            c->slab_T = streamed ? T : 0;
+            if (!streamed && c->obuf) {
+                void* p = c->obuf; dfree(p); c->obuf = nullptr;
+                c->allocated -= obytes;
+            }
+            // Entries whose source lies outside the domain are never written by the march: zero them once.
+            FDIRW_CUDA(c, cudaMemsetAsync(c->Q, 0, c->q_bytes, c->stream));
+            return FDIRW_OK;
+        }
+        if (rc != FDIRW_ERR_NOMEM) return rc;
+        T = streamed ? T / 2 : std::min(T - 1, std::max(c->g.nz / 2, 1));
+    }
+    return fail(c, FDIRW_ERR_NOMEM, "the kernel cache does not fit, not even one z-plane of destinations (" +
+                                        std::to_string(plane) + " bytes)");
 }
 
 // March arguments of a uniform context: every source, the whole cache.
