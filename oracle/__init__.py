@@ -96,6 +96,9 @@ def _load():
             lib.fo_coarse_pbc.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [_U8, ctypes.c_int, ctypes.c_double,
                                                                          ctypes.c_int, _D]
             lib.fo_coarse_pbc.restype = ctypes.c_int
+            lib.fo_superpose_rmap_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, ctypes.c_double,
+                                                                                 _I32, ctypes.c_int, _D, _D]
+            lib.fo_superpose_rmap_adv.restype = ctypes.c_int
             lib.fo_coarse_kernels_adv.argtypes = [ctypes.c_int] * 3 + [_D] * 6 + [ctypes.c_double, _U8, ctypes.c_int,
                                                                                  ctypes.c_double, ctypes.c_int,
                                                                                  ctypes.c_int, _D]
@@ -236,6 +239,21 @@ def superpose_rmap(shape, D, lam: float, Rmap, n_sub: int, c, cond: Conductance 
     out = np.empty_like(c)
     if _load().fo_superpose_rmap(*g.args, float(lam), Rm.ctypes.data_as(_I32), int(n_sub), _p(c), _p(out)) != 0:
         raise ValueError("fo_superpose_rmap failed")
+    return out
+
+
+def superpose_rmap_adv(shape, D, w, lam: float, lama: float, Rmap, n_sub: int, c) -> np.ndarray:
+    """superpose_rmap whose kernels include the upwind convection of face velocities w (Sec. 5)."""
+    g = Conductance(shape, D)
+    wx, wy, wz = (_f64(a).reshape(-1) for a in w)
+    c = _f64(c).reshape(-1)
+    Rm = np.ascontiguousarray(Rmap, dtype=np.int32).reshape(-1)
+    if Rm.size != c.size:
+        raise ValueError("Rmap has the wrong size")
+    out = np.empty_like(c)
+    if _load().fo_superpose_rmap_adv(*g.args, _p(wx), _p(wy), _p(wz), float(lam), float(lama),
+                                     Rm.ctypes.data_as(_I32), int(n_sub), _p(c), _p(out)) != 0:
+        raise ValueError("fo_superpose_rmap_adv failed")
     return out
 
 

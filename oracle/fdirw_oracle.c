@@ -207,8 +207,15 @@ void fo_radius_map(int64_t N, const double* D, double dt_macro, double h, int R_
 
 /* Eq. 8 with a radius per source: c_out(x) = sum_s c_in(s) k_s(x), k_s the kernel of s on its own
  * window of radius Rmap[s] (scatter over sources, as fo_superpose). */
-int fo_superpose_rmap(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                      double lam, const int32_t* Rmap, int n_sub, const double* c_in, double* c_out)
+int fo_source_kernel_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                         const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
+                         int n_sub, int64_t s, double* k_out, double* mass_before);
+
+/* Eq. 8 with a per-source window radius; with face velocities (wx != NULL) the kernels carry the Sec. 5
+ * upwind faces. */
+static int superpose_rmap_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                               const double* wx, const double* wy, const double* wz, double lama, double lam,
+                               const int32_t* Rmap, int n_sub, const double* c_in, double* c_out)
 {
     enum { CHUNK = 256 };
     int64_t N = (int64_t)nx * ny * nz;
@@ -227,7 +234,10 @@ int fo_superpose_rmap(int nx, int ny, int nz, const double* gx, const double* gy
         /* kernels of a chunk of sources in parallel (independent), then the scatter in source order */
         #pragma omp parallel for schedule(dynamic, 1) reduction(|:bad)
         for (int64_t s = s0; s < s1; s++)
-            if (fo_source_kernel(nx, ny, nz, gx, gy, gz, lam, Rmap[s], n_sub, s, k + (s - s0) * Wm, NULL) != 0) bad = 1;
+            if ((wx ? fo_source_kernel_adv(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, Rmap[s], n_sub, s,
+                                           k + (s - s0) * Wm, NULL)
+                    : fo_source_kernel(nx, ny, nz, gx, gy, gz, lam, Rmap[s], n_sub, s, k + (s - s0) * Wm, NULL)) != 0)
+                bad = 1;
         if (bad) break;
         for (int64_t s = s0; s < s1; s++) {
             const double* ks = k + (s - s0) * Wm;
@@ -244,6 +254,19 @@ int fo_superpose_rmap(int nx, int ny, int nz, const double* gx, const double* gy
     }
     free(k);
     return bad ? -1 : 0;
+}
+
+int fo_superpose_rmap(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                      double lam, const int32_t* Rmap, int n_sub, const double* c_in, double* c_out)
+{
+    return superpose_rmap_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, lam, Rmap, n_sub, c_in, c_out);
+}
+
+int fo_superpose_rmap_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                          const double* wx, const double* wy, const double* wz, double lam, double lama,
+                          const int32_t* Rmap, int n_sub, const double* c_in, double* c_out)
+{
+    return superpose_rmap_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, lam, Rmap, n_sub, c_in, c_out);
 }
 
 /* ---- Coarse mesh (Sec. 3.1, Eqs. 10-15).  The coarsening rule is a reading (the paper takes it from its

@@ -127,3 +127,19 @@ def test_coarse_flow_columns_conserve_and_stay_positive():
     assert np.all(Po.reshape(len(cnt), -1).sum(1) <= P.reshape(len(cnt), -1).sum(1) * (1 + 1e-12) + 1e-15)
     downstream = P[:, Rc, Rc, Rc + 1] - P0[:, Rc, Rc, Rc + 1]
     assert downstream[np.flatnonzero(cnt)].sum() > 0.0
+
+
+def test_radius_map_superposition_with_flow():
+    """The per-source-radius superposition with flow: w = 0 gives superpose_rmap bit for bit, and a
+    constant radius map gives superpose_adv bit for bit (both follow from the definitions)."""
+    shape = (10, 9, 8)
+    N = 720
+    D = synth.random_diffusivity(shape, 117, 3.0)
+    lam = 0.5 * oracle.stable_dt_sub(shape, D)
+    c = synth.random_field(N, 118)
+    Rmap = (np.arange(N) % 3 + 1).astype(np.int32)
+    assert np.array_equal(oracle.superpose_rmap_adv(shape, D, _w(N), lam, lam, Rmap, 9, c),
+                          oracle.superpose_rmap(shape, D, lam, Rmap, 9, c))
+    w = synth.face_velocity(shape, 119, (0.2, 0.1, -0.1), 0.2)
+    assert np.array_equal(oracle.superpose_rmap_adv(shape, D, w, lam, lam, np.full(N, 2, np.int32), 9, c),
+                          oracle.superpose_adv(shape, D, w, lam, lam, 2, 9, c))
