@@ -306,11 +306,13 @@ FDIRW_API int fdirw_coupled_step(fdirw_ctx* ctx, const fdirw_coupled_params* par
  * and the march runs mapping 5 (direction-dependent faces); the superposition is unchanged.  On a
  * coarse-mesh context faces touching a non-liquid cell carry neither flux, the block-source march and
  * the P_BC march use the same faces, and the far field's open faces stay diffusive (open the far field
- * first: its stability check then includes the flow).  A second call replaces the velocity; the kernels
+ * first: its stability check then includes the flow).  On a batch context w spans the concatenated cells
+ * (structure i at its first global cell) and each structure uses its own lam, h and radius.  A second
+ * call replaces the velocity; the kernels
  * (or P and P_BC) are recomputed by the next fdirw_kernels / fdirw_step.  With w = 0 the kernels and
  * steps are bit for bit those without a velocity.  Synchronises the context stream.
- * Errors: FDIRW_ERR_ARG (NULL or misaligned w, NaN or infinite values, a batch context, FDIRW_FP64
- * precision), FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
+ * Errors: FDIRW_ERR_ARG (NULL or misaligned w, NaN or infinite values, FDIRW_FP64 precision),
+ * FDIRW_ERR_UNSTABLE (some cell's outflow coefficients sum above 1; the previous velocity, if
  * any, stays in place), FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA. */
 FDIRW_API int fdirw_set_velocity(fdirw_ctx* ctx, const double* w);
 

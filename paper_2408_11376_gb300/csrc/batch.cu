@@ -309,6 +309,11 @@ MarchArgs march_args(const fdirw_ctx* c, const Chunk& ch, int r) {
     a.Q = static_cast<char*>(b.arena) + ch.k_off[r];
     a.store = c->store;
     a.sigma = c->sigma;
+    if (c->flow) {                                    // convection: direction-dependent faces (mapping 5)
+        a.bx = reinterpret_cast<const float*>(c->coefb[0]);
+        a.by = reinterpret_cast<const float*>(c->coefb[1]);
+        a.bz = reinterpret_cast<const float*>(c->coefb[2]);
+    }
     a.src_begin = ch.seg_begin[r];
     a.src_end = ch.seg_end[r];
     a.list = b.d_list[r];
@@ -678,6 +683,23 @@ int batch_info(fdirw_ctx* c, fdirw_info* out) {
 }
 
 void batch_release(fdirw_ctx* c) { release_batch(c); }
+
+void batch_structures(const fdirw_ctx* c, std::vector<Grid>& grids, std::vector<int64_t>& base,
+                      std::vector<double>& lams, std::vector<double>& hs) {
+    const Batch& b = *c->batch;
+    grids = b.grids;
+    base.assign(b.base.begin(), b.base.end() - 1);
+    lams = b.lams;
+    hs = b.hs;
+}
+
+void batch_invalidate(fdirw_ctx* c) {
+    Batch& b = *c->batch;
+    drop_graph(b);                                    // its launches carry the old march arguments
+    b.resident = -1;                                  // no chunk's kernels are current
+    for (auto& v : b.built) v = 0;
+    c->kernels_ready = false;
+}
 
 }  // namespace fdirw
 

@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -94,6 +95,10 @@ int batch_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
 int batch_read_kernels(fdirw_ctx* c, const int64_t* sources, int64_t n, double* out);
 int batch_info(fdirw_ctx* c, fdirw_info* out);
 void batch_release(fdirw_ctx* c);
+// Structures of a batch context: grid, first global cell, lam and h of each.
+void batch_structures(const fdirw_ctx* c, std::vector<Grid>& grids, std::vector<int64_t>& base,
+                      std::vector<double>& lams, std::vector<double>& hs);
+void batch_invalidate(fdirw_ctx* c);           // the kernels must be rebuilt (new coefficients)
 
 // Coarse-mesh contexts (coarse.cu).
 int coarse_kernels(fdirw_ctx* c);

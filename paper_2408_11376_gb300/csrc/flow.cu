@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 using namespace fdirw::host;
 
@@ -34,9 +35,9 @@ __device__ __forceinline__ double harmonic(double a, double b) {
 // with a liquid mask, on faces touching a non-liquid cell; and the largest per-cell sum of outflow
 // coefficients, open faces included (bits of a non-negative double, for atomicMax) for the stability
 // check, +inf where a velocity that enters the march is NaN or infinite.
-__global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const double* __restrict__ w,
+__global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const double* __restrict__ w, int64_t ws,
                                  const uint8_t* __restrict__ liquid, bool open, double lam, double lama,
-                                 float* __restrict__ A, float* __restrict__ Bc,
+                                 float* __restrict__ A, float* __restrict__ Bc, int64_t os,
                                  unsigned long long* __restrict__ max_bits) {
     const int64_t nxy = (int64_t)g.nx * g.ny;
     const int64_t stride[3] = {1, g.nx, nxy};
@@ -49,7 +50,7 @@ __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const dou
             double a = 0.0, b = 0.0;
             if (c3[ax] + 1 < n3[ax]) {
                 const int64_t j = i + stride[ax];
-                const double wv = w[ax * g.n + i];
+                const double wv = w[ax * ws + i];
                 if (!liquid || (liquid[i] && liquid[j])) {
                     const double gd = lam * harmonic(D[i], D[j]);
                     a = gd + lama * (wv > 0.0 ? wv : 0.0);
@@ -57,15 +58,15 @@ __global__ void flow_coef_kernel(Grid g, const double* __restrict__ D, const dou
                 }
                 if (!isfinite(wv)) out = INFINITY;          // reported as invalid input, never installed
             }
-            A[ax * g.n + i] = (float)a;
-            Bc[ax * g.n + i] = (float)b;
+            A[ax * os + i] = (float)a;
+            Bc[ax * os + i] = (float)b;
             out += a;                                   // outflow from i through its +face
             // -face of cell i: outflow is the lower neighbour's B
             if (c3[ax] > 0) {
                 const int64_t j = i - stride[ax];
                 if (!liquid || (liquid[i] && liquid[j])) {
                     const double gd = lam * harmonic(D[j], D[i]);
-                    const double wv = w[ax * g.n + j];
+                    const double wv = w[ax * ws + j];
                     out += gd + lama * (wv < 0.0 ? -wv : 0.0);
                 }
             }
@@ -86,7 +87,6 @@ extern "C" {
 
 int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     if (!c) return fail(nullptr, FDIRW_ERR_ARG, "NULL context");
-    if (c->batch) return fail(c, FDIRW_ERR_ARG, "convection is not available for batch contexts");
     if (c->store == fdirw::Store::F64) return fail(c, FDIRW_ERR_ARG, "convection needs an FP32-march precision");
     if (!w) return fail(c, FDIRW_ERR_ARG, "NULL velocity field");
     if ((reinterpret_cast<uintptr_t>(w) & 7u) != 0) return fail(c, FDIRW_ERR_ARG, "w must be 8-byte aligned");
@@ -118,11 +118,25 @@ int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     cudaError_t e = cudaMemcpyAsync(dw, w, 3 * n * 8, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, 8, c->stream);
     if (e == cudaSuccess) {
-        const uint8_t* liquid = c->coarse ? fdirw::coarse_liquid(c) : nullptr;
-        const bool open = c->coarse && fdirw::coarse_open_faces(c) != nullptr;
-        fdirw::flow_coef_kernel<<<fdirw::grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(
-            c->g, c->Dd, dw, liquid, open, c->lam, c->lam * c->h, AB, AB + 3 * n, mx);
-        e = cudaGetLastError();
+        if (c->batch) {
+            // Every structure with its own grid, lam and h; w, A and B span the concatenated cells.
+            std::vector<fdirw::Grid> grids;
+            std::vector<int64_t> base;
+            std::vector<double> lams, hs;
+            fdirw::batch_structures(c, grids, base, lams, hs);
+            for (size_t i = 0; i < grids.size() && e == cudaSuccess; i++) {
+                fdirw::flow_coef_kernel<<<fdirw::grid_blocks(grids[i].n, 256), 256, 0, c->stream>>>(
+                    grids[i], c->Dd + base[i], dw + base[i], (int64_t)n, nullptr, false, lams[i], lams[i] * hs[i],
+                    AB + base[i], AB + 3 * n + base[i], (int64_t)n, mx);
+                e = cudaGetLastError();
+            }
+        } else {
+            const uint8_t* liquid = c->coarse ? fdirw::coarse_liquid(c) : nullptr;
+            const bool open = c->coarse && fdirw::coarse_open_faces(c) != nullptr;
+            fdirw::flow_coef_kernel<<<fdirw::grid_blocks(c->g.n, 256), 256, 0, c->stream>>>(
+                c->g, c->Dd, dw, (int64_t)n, liquid, open, c->lam, c->lam * c->h, AB, AB + 3 * n, (int64_t)n, mx);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, mx, 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -149,6 +163,7 @@ int fdirw_set_velocity(fdirw_ctx* c, const double* w) {
     c->kernels_ready = false;
     c->flow = true;
     if (c->coarse) fdirw::coarse_invalidate(c);        // P and P_BC are rebuilt with the flow
+    if (c->batch) fdirw::batch_invalidate(c);          // every chunk's kernels, and the captured graph
     return FDIRW_OK;
 }
 

@@ -247,6 +247,52 @@ def test_fp32_accum_batch_matches_oracle_and_keeps_every_structure_mass(prec):
     assert np.array_equal(out, out2)
 
 
+@pytest.mark.parametrize("accum", ["ff", "fp32"])
+def test_batch_flow_matches_oracle(accum):
+    """Convection on a batch mixing both cache layouts: each structure's field after two macro steps
+    against the oracle's per-source-radius upwind superposition, chunked execution bit for bit the
+    resident one, and w = 0 bit for bit the diffusion-only batch."""
+    shapes = [(16, 12, 10), (11, 14, 9), (24, 16, 8)]
+    Ds = [synth.random_diffusivity(s, 380 + i, 4.0) for i, s in enumerate(shapes)]
+    n_sub = 30
+    dt = n_sub * 0.6 * min(oracle.stable_dt_sub(s, D) for s, D in zip(shapes, Ds))
+    ws = [synth.face_velocity(s, 390 + i, (0.2, -0.1, 0.05), 0.15) for i, s in enumerate(shapes)]
+    w_all = np.concatenate([w for w in ws], axis=1)          # (3, total): structure i at its offset
+    c0 = np.concatenate([synth.random_field(int(np.prod(s)), 400 + i) for i, s in enumerate(shapes)])
+    with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, "fp32", accum=accum) as b:
+        b.set_velocity(w_all)
+        out = np.empty_like(c0)
+        b.step(c0, out, 2)
+        Rmap = b.radius()
+        info = b.info()
+        offs = b.offsets
+    for i, shape in enumerate(shapes):
+        sl = slice(int(offs[i]), int(offs[i + 1]))
+        lam = dt / n_sub
+        ref = c0[sl]
+        for _ in range(2):
+            ref = oracle.superpose_rmap_adv(shape, Ds[i], ws[i], lam, lam, Rmap[sl], n_sub, ref)
+        assert _rel(out[sl], ref) <= FIELD_TOL["fp32"], (i, _rel(out[sl], ref))
+        assert abs(out[sl].sum() - c0[sl].sum()) <= 1e-12 * c0[sl].sum()
+    limit = info["device_bytes"] - info["cache_bytes"] + info["cache_bytes"] * 2 // 3
+    with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, "fp32", mem_limit=limit, accum=accum) as b:
+        b.set_velocity(w_all)
+        out2 = np.empty_like(c0)
+        b.step(c0, out2, 2)
+        assert b.info()["n_chunks"] >= 2
+    assert np.array_equal(out, out2)
+    outs = []
+    for flow in (False, True):
+        with FDiRWBatch(shapes, Ds, dt, 1, 6, n_sub, "bf16", accum=accum) as b:
+            o = np.empty_like(c0)
+            b.step(c0, o, 1)                                  # builds and captures without a velocity
+            if flow:
+                b.set_velocity(np.zeros_like(w_all))          # drops the graph; the kernels are rebuilt
+                b.step(c0, o, 1)
+            outs.append(o)
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_batch_argument_errors():
     shape = (8, 8, 8)
     D = np.ones(512)

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2408_11376_gb300 import FDiRW, FDiRWBatch, FdirwError, fdirw, synth
+from paper_2408_11376_gb300 import FDiRW, FdirwError, fdirw, synth
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -152,9 +152,6 @@ def test_velocity_replaced_and_errors():
         with pytest.raises(ValueError):
             f.set_velocity(np.zeros(N))
     with FDiRW(shape, D, 20 * lam, 3, 20, "fp64") as f:
-        with pytest.raises(FdirwError):
-            f.set_velocity(w1)
-    with FDiRWBatch([shape], [D], 20 * lam, 2, 3, 20) as f:
         with pytest.raises(FdirwError):
             f.set_velocity(w1)
 
