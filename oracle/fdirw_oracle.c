@@ -299,16 +299,32 @@ void fo_coarse_counts(int nx, int ny, int nz, const uint8_t* liquid, int B, int6
                 if (liquid[IDX(x, y, z, nx, ny)]) cnt[(x / B) + (int64_t)ncx * ((y / B) + (int64_t)ncy * (z / B))]++;
 }
 
-/* Column J of the coarse matrix P (Eq. 10) for every block J with liquid cells: the remapped unit
- * C_J = 1 (Eq. 12: 1 on each liquid cell of J) marched n_sub explicit substeps on the window of block J
- * widened by R cells (clipped to the domain; zero flux through its faces and through non-liquid
- * faces, which gx/gy/gz already carry), then mapped (Eq. 11): P[I][J] = N_J S_I / (m N_I), with S_I the
- * marched mass on the liquid cells of block I and m the total (N_J in exact arithmetic, so each column
- * conserves mass).  Stored source-major: P_band[J][d], d = I - J over [-Rc, Rc]^3, Rc = ceil(R / B),
- * offset layout d_x fastest; 0 where block I is outside the grid or has no liquid.  OpenMP over J. */
+/* One flux-form substep as box_substep plus the open faces: u_i += lam gb_i (ghost - u_i). */
+static void box_substep_open(int nx, int ny, const double* gx, const double* gy, const double* gz,
+                             const double* wxv, const double* wyv, const double* wzv, double lama,
+                             const double* gb, double ghost, double lam, int x0, int y0, int z0, int bx, int by,
+                             int bz, const double* u, double* un)
+{
+    box_step(nx, ny, gx, gy, gz, wxv, wyv, wzv, lam, lama, x0, y0, z0, bx, by, bz, u, un);
+    for (int l = 0; l < bz; l++)
+        for (int j = 0; j < by; j++)
+            for (int i = 0; i < bx; i++) {
+                int64_t li = i + (int64_t)bx * (j + (int64_t)by * l);
+                int64_t gi = IDX(x0 + i, y0 + j, z0 + l, nx, ny);
+                un[li] += lam * (gb[gi] * (ghost - u[li]));
+            }
+}
+
+/* Column J of the coarse matrix for every block J with liquid (Sec. 3.1 for the march, Eqs. 11-12 for
+ * the block means): march 1 on J's liquid cells over J's block widened by R cells (box faces closed;
+ * with open = 1 the grid's outer faces also exchange with a ghost at 0 through gb), sum the marched
+ * field over the liquid cells of every block of the window, and write P[I][J] = N_J S_I / (m N_I)
+ * (closed: m the marched total, so each column carries N_J) or S_I / N_I (open: the mass that stays).
+ * Face velocities (wxv != NULL) add the Sec. 5 upwind faces to the march. */
 static int coarse_kernels_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                               const double* wxv, const double* wyv, const double* wzv, double lama,
-                               const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
+                               const double* wxv, const double* wyv, const double* wzv, double lama, int open,
+                               const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
+                               double* P_band)
 {
     if (B < 1 || R < 0 || n_sub < 0) return -1;
     int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
@@ -341,11 +357,13 @@ static int coarse_kernels_impl(int nx, int ny, int nz, const double* gx, const d
                         u[i + (int64_t)wx * (j + (int64_t)wy * l)] = 1.0;
                 }
         for (int k = 0; k < n_sub; k++) {
-            box_step(nx, ny, gx, gy, gz, wxv, wyv, wzv, lam, lama, x0, y0, z0, wx, wy, wz, u, un);
+            if (open) box_substep_open(nx, ny, gx, gy, gz, wxv, wyv, wzv, lama, gb, 0.0, lam, x0, y0, z0, wx, wy, wz, u, un);
+            else box_step(nx, ny, gx, gy, gz, wxv, wyv, wzv, lam, lama, x0, y0, z0, wx, wy, wz, u, un);
             double* t = u; u = un; un = t;
         }
         double m = 0.0;
-        for (int64_t q = 0; q < nb; q++) m += u[q];
+        if (!open)
+            for (int64_t q = 0; q < nb; q++) m += u[q];
         for (int l = 0; l < wz; l++)
             for (int j = 0; j < wy; j++)
                 for (int i = 0; i < wx; i++) {
@@ -363,7 +381,7 @@ static int coarse_kernels_impl(int nx, int ny, int nz, const double* gx, const d
                     int64_t I = cx + (int64_t)ncx * (cy + (int64_t)ncy * cz);
                     if (cnt[I] == 0) continue;
                     int64_t o = (dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc));
-                    P_band[J * Wc3 + o] = ((double)cnt[J] * S[o]) / (m * (double)cnt[I]);
+                    P_band[J * Wc3 + o] = open ? S[o] / (double)cnt[I] : ((double)cnt[J] * S[o]) / (m * (double)cnt[I]);
                 }
         free(u); free(un); free(S);
     }
@@ -371,10 +389,18 @@ static int coarse_kernels_impl(int nx, int ny, int nz, const double* gx, const d
     return err ? -1 : 0;
 }
 
+/* Column J of the coarse matrix P (Eq. 10) for every block J with liquid cells: the remapped unit
+ * C_J = 1 (Eq. 12: 1 on each liquid cell of J) marched n_sub explicit substeps on the window of block J
+ * widened by R cells (clipped to the domain; zero flux through its faces and through non-liquid
+ * faces, which gx/gy/gz already carry), then mapped (Eq. 11): P[I][J] = N_J S_I / (m N_I), with S_I the
+ * marched mass on the liquid cells of block I and m the total (N_J in exact arithmetic, so each column
+ * conserves mass).  Stored source-major: P_band[J][d], d = I - J over [-Rc, Rc]^3, Rc = ceil(R / B),
+ * offset layout d_x fastest; 0 where block I is outside the grid or has no liquid.  OpenMP over J. */
 int fo_coarse_kernels(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                       const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
 {
-    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, liquid, B, lam, R, n_sub, P_band);
+    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, 0, NULL, liquid, B, lam, R, n_sub,
+                               P_band);
 }
 
 /* fo_coarse_kernels with the block-source march carrying the upwind faces of face velocities w (Sec. 5),
@@ -383,7 +409,7 @@ int fo_coarse_kernels_adv(int nx, int ny, int nz, const double* gx, const double
                           const double* wx, const double* wy, const double* wz, double lama, const uint8_t* liquid,
                           int B, double lam, int R, int n_sub, double* P_band)
 {
-    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, liquid, B, lam, R, n_sub, P_band);
+    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, 0, NULL, liquid, B, lam, R, n_sub, P_band);
 }
 
 /* One coarse FDiRW step, Eqs. 13-15 without the boundary term: 'mapping' C_I = mean of c over the
@@ -446,94 +472,14 @@ void fo_boundary_conductance(int nx, int ny, int nz, const double* D, const uint
             }
 }
 
-/* One flux-form substep as box_substep plus the open faces: u_i += lam gb_i (ghost - u_i). */
-static void box_substep_open(int nx, int ny, const double* gx, const double* gy, const double* gz,
-                             const double* wxv, const double* wyv, const double* wzv, double lama,
-                             const double* gb, double ghost, double lam, int x0, int y0, int z0, int bx, int by,
-                             int bz, const double* u, double* un)
-{
-    box_step(nx, ny, gx, gy, gz, wxv, wyv, wzv, lam, lama, x0, y0, z0, bx, by, bz, u, un);
-    for (int l = 0; l < bz; l++)
-        for (int j = 0; j < by; j++)
-            for (int i = 0; i < bx; i++) {
-                int64_t li = i + (int64_t)bx * (j + (int64_t)by * l);
-                int64_t gi = IDX(x0 + i, y0 + j, z0 + l, nx, ny);
-                un[li] += lam * (gb[gi] * (ghost - u[li]));
-            }
-}
-
 /* Coarse matrix with open faces: as fo_coarse_kernels, the march also losing mass through the open
  * faces (ghost 0), and no renormalisation: P[I][J] = S_I / N_I (the column carries the mass that stays). */
-static int coarse_kernels_open_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                                    const double* wxv, const double* wyv, const double* wzv, double lama,
-                                    const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
-                                    double* P_band)
-{
-    if (B < 1 || R < 0 || n_sub < 0) return -1;
-    int ncx = (nx + B - 1) / B, ncy = (ny + B - 1) / B, ncz = (nz + B - 1) / B;
-    int64_t NC = (int64_t)ncx * ncy * ncz;
-    int Rc = (R + B - 1) / B, Wc = 2 * Rc + 1;
-    int64_t Wc3 = (int64_t)Wc * Wc * Wc;
-    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)NC);
-    if (!cnt) return -1;
-    fo_coarse_counts(nx, ny, nz, liquid, B, cnt);
-    memset(P_band, 0, sizeof(double) * (size_t)(NC * Wc3));
-    int err = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
-    for (int64_t J = 0; J < NC; J++) {
-        if (cnt[J] == 0 || err) continue;
-        int bx = (int)(J % ncx), by = (int)((J / ncx) % ncy), bz = (int)(J / ((int64_t)ncx * ncy));
-        int x0 = bx * B - R < 0 ? 0 : bx * B - R, x1 = bx * B + B - 1 + R > nx - 1 ? nx - 1 : bx * B + B - 1 + R;
-        int y0 = by * B - R < 0 ? 0 : by * B - R, y1 = by * B + B - 1 + R > ny - 1 ? ny - 1 : by * B + B - 1 + R;
-        int z0 = bz * B - R < 0 ? 0 : bz * B - R, z1 = bz * B + B - 1 + R > nz - 1 ? nz - 1 : bz * B + B - 1 + R;
-        int wx = x1 - x0 + 1, wy = y1 - y0 + 1, wz = z1 - z0 + 1;
-        int64_t nb = (int64_t)wx * wy * wz;
-        double* u = (double*)calloc((size_t)nb, sizeof(double));
-        double* un = (double*)calloc((size_t)nb, sizeof(double));
-        double* S = (double*)calloc((size_t)Wc3, sizeof(double));
-        if (!u || !un || !S) { free(u); free(un); free(S); err = 1; continue; }
-        for (int l = 0; l < wz; l++)
-            for (int j = 0; j < wy; j++)
-                for (int i = 0; i < wx; i++) {
-                    int x = x0 + i, y = y0 + j, z = z0 + l;
-                    if (x / B == bx && y / B == by && z / B == bz && liquid[IDX(x, y, z, nx, ny)])
-                        u[i + (int64_t)wx * (j + (int64_t)wy * l)] = 1.0;
-                }
-        for (int k = 0; k < n_sub; k++) {
-            box_substep_open(nx, ny, gx, gy, gz, wxv, wyv, wzv, lama, gb, 0.0, lam, x0, y0, z0, wx, wy, wz, u, un);
-            double* t = u; u = un; un = t;
-        }
-        for (int l = 0; l < wz; l++)
-            for (int j = 0; j < wy; j++)
-                for (int i = 0; i < wx; i++) {
-                    int x = x0 + i, y = y0 + j, z = z0 + l;
-                    if (!liquid[IDX(x, y, z, nx, ny)]) continue;
-                    int dx = x / B - bx, dy = y / B - by, dz = z / B - bz;
-                    S[(dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc))] +=
-                        u[i + (int64_t)wx * (j + (int64_t)wy * l)];
-                }
-        for (int dz = -Rc; dz <= Rc; dz++)
-            for (int dy = -Rc; dy <= Rc; dy++)
-                for (int dx = -Rc; dx <= Rc; dx++) {
-                    int cx = bx + dx, cy = by + dy, cz = bz + dz;
-                    if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy || cz < 0 || cz >= ncz) continue;
-                    int64_t I = cx + (int64_t)ncx * (cy + (int64_t)ncy * cz);
-                    if (cnt[I] == 0) continue;
-                    int64_t o = (dx + Rc) + (int64_t)Wc * ((dy + Rc) + (int64_t)Wc * (dz + Rc));
-                    P_band[J * Wc3 + o] = S[o] / (double)cnt[I];
-                }
-        free(u); free(un); free(S);
-    }
-    free(cnt);
-    return err ? -1 : 0;
-}
-
 int fo_coarse_kernels_open(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                            const double* gb, const uint8_t* liquid, int B, double lam, int R, int n_sub,
                            double* P_band)
 {
-    return coarse_kernels_open_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, gb, liquid, B, lam, R, n_sub,
-                                    P_band);
+    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, 0.0, 1, gb, liquid, B, lam, R, n_sub,
+                               P_band);
 }
 
 /* fo_coarse_kernels_open with upwind faces (Sec. 5); the open faces stay diffusive (no flow leaves the
@@ -542,7 +488,7 @@ int fo_coarse_kernels_open_adv(int nx, int ny, int nz, const double* gx, const d
                                const double* wx, const double* wy, const double* wz, double lama, const double* gb,
                                const uint8_t* liquid, int B, double lam, int R, int n_sub, double* P_band)
 {
-    return coarse_kernels_open_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, gb, liquid, B, lam, R, n_sub, P_band);
+    return coarse_kernels_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lama, 1, gb, liquid, B, lam, R, n_sub, P_band);
 }
 
 /* P_BC of Eq. 10: the liquid phase marched n_sub substeps over the whole grid from 0 with every ghost at
