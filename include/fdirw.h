@@ -53,7 +53,7 @@ extern "C" {
 #define FDIRW_ERR_UNSTABLE -2   /* lam * max face-conductance sum > 1 (explicit march would not be stable) */
 #define FDIRW_ERR_NOMEM    -3   /* device allocation failed or would exceed opts.mem_limit */
 #define FDIRW_ERR_CUDA     -4   /* a CUDA runtime call failed (message has the CUDA error string) */
-#define FDIRW_ERR_TIMEOUT  -5   /* a bounded device-side wait gave up (reserved; no current kernel waits) */
+#define FDIRW_ERR_TIMEOUT  -5   /* a bounded device-side wait gave up (the surrogate's MMA-completion waits) */
 #define FDIRW_ERR_STATE    -6   /* call not valid in the context's current state */
 
 /* Arithmetic of the path (Sec. 3.3: lower precision for the stored proportions, higher precision for
