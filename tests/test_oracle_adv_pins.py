@@ -65,6 +65,23 @@ def test_superpose_adv_conserves_mass():
     assert out.sum() == pytest.approx(c.sum(), rel=1e-13) and out.min() >= 0.0
 
 
+def test_superpose_adv_moves_the_mean_by_lam_a_w():
+    """Eq. 8 with convection on a field that is a point mass a: the step gives a times that source's
+    kernel, so the mass stays a and the first moment moves by a n_sub lam_a w exactly (n_sub <= R: no
+    walker reaches a window face), with lam != lam_a."""
+    shape, a = (25, 9, 9), 3.0
+    N = 25 * 9 * 9
+    lam, lama, wx, wy, n_sub, R = 0.05, 0.5, 0.4, -0.2, 4, 4
+    s = 12 + 25 * (4 + 9 * 4)
+    c = np.zeros(N)
+    c[s] = a
+    out = oracle.superpose_adv(shape, np.ones(N), _w(N, wx, wy), lam, lama, R, n_sub, c).reshape(9, 9, 25)
+    x, y = np.arange(25) - 12, np.arange(9) - 4
+    assert out.sum() == pytest.approx(a, rel=1e-14) and out.min() >= 0.0
+    assert (out.sum(axis=(0, 1)) * x).sum() == pytest.approx(a * n_sub * lama * wx, abs=1e-12)
+    assert (out.sum(axis=(0, 2)) * y).sum() == pytest.approx(a * n_sub * lama * wy, abs=1e-12)
+
+
 # ---------------------------------------------------------------- convection on the coarse (liquid) path
 
 def _packing(shape, seed):

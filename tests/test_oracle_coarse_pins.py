@@ -184,6 +184,27 @@ def test_absorption_counts_every_interface_face_and_conserves():
     assert oracle.absorb(shape, liquid, k, cS, cL, dt, c).sum() == pytest.approx(c.sum(), rel=1e-14)
 
 
+def test_absorption_only_across_interface_faces_in_every_direction():
+    """The reaction of Eqs. 4-6 acts on the solid/liquid interface only: a grid of one phase is left as it
+    is whatever its values.  A liquid cell whose six face neighbours are solid (3^3 grid, liquid centre)
+    loses m to each of them, m = k f_L f_S dt with f_L = (4e-3 - 1e-3) / 1e-3 = 3 and f_S = (1 - 0.2) / 1
+    = 0.8; the edge and corner cells touch no liquid and keep their values."""
+    k, cS, cL, dt = 0.01, 1.0, 1e-3, 0.1
+    shape = (3, 3, 3)
+    c = np.full(27, 0.2)
+    c[13] = 4e-3
+    for liquid in (np.ones(27), np.zeros(27)):
+        assert np.array_equal(oracle.absorb(shape, liquid, k, cS, cL, dt, c), c)
+    liquid = np.zeros(27)
+    liquid[13] = 1
+    got = oracle.absorb(shape, liquid, k, cS, cL, dt, c)
+    m = 0.01 * 3.0 * 0.8 * 0.1
+    want = np.full(27, 0.2)
+    want[[4, 10, 12, 14, 16, 22]] = 0.2 + m         # the six face neighbours of cell 13
+    want[13] = 4e-3 - 6 * m
+    assert got == pytest.approx(want, abs=1e-17)
+
+
 def test_solid_march_is_the_full_march_of_the_solid():
     shape = (7, 6, 5)
     D = synth.random_diffusivity(shape, 99, 3.0)
@@ -194,6 +215,22 @@ def test_solid_march_is_the_full_march_of_the_solid():
                        rtol=1e-14, atol=0)
     all_liquid = np.ones(D.size)
     assert np.array_equal(oracle.solid_march(shape, D, all_liquid, lam, 9, c), c)   # no solid face: unchanged
+
+
+def test_coupled_step_by_hand():
+    """Chain solid, solid, liquid (cells of 1, B = 1, closed: P_BC = 0).  The reading's order within the
+    macro step: the Eq. 4-6 exchange on the pre-step values first, f_L = (1 - 0.5) / 0.5 = 1,
+    f_S = (1 - 0) / 1 = 1, m = k f_L f_S dt = 0.5 * 0.2 = 0.1; then one solid substep of lam_s = 0.25
+    across the solid-solid face (conductance 1) moves 0.25 * 0.1 to the first cell; then the coarse step
+    of the lone liquid node (P = 1) keeps 0.9, and Eq. 7 leaves c_far unchanged (the near-field total is
+    unchanged).  Marching the solid before the exchange would leave the first cell at 0."""
+    shape, liquid, D = (3, 1, 1), np.array([0, 0, 1], np.uint8), np.ones(3)
+    P = oracle.coarse_kernels(shape, D, liquid, 1, 0.1, 1, 4)
+    assert P[2, 1, 1, 1] == 1.0 and np.count_nonzero(P) == 1
+    c, cf = oracle.coupled_step(shape, D, liquid, 1, 1, P, np.zeros(3), 10.0, 0.3, 0.5, 1.0, 0.5, 0.2, 0.25, 1,
+                                np.array([0.0, 0.0, 1.0]))
+    assert c == pytest.approx([0.025, 0.075, 0.9], abs=1e-16)
+    assert cf == pytest.approx(0.3, abs=1e-16)
 
 
 def test_coupled_step_conserves_the_total():

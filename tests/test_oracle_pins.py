@@ -161,30 +161,62 @@ def test_two_cell_closed_form():
     assert np.allclose(got, [(1 + mu ** n) / 2, (1 - mu ** n) / 2], rtol=0, atol=1e-15)
 
 
-def test_harmonic_face_rule_reproduces_layered_medium_homogenisation():
-    # A 1D chain of cells with period-3 diffusivities.  Homogenisation of a layered medium in series
-    # gives D_eff with 1/D_eff = mean(1/D).  The long-time variance of the point-source solution grows
-    # as 2 D_eff t, so its slope pins the face rule (an arithmetic-mean face rule gives ~0.36 here,
-    # against 0.123).
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_harmonic_face_rule_reproduces_layered_medium_homogenisation(axis):
+    # Cells with period-3 diffusivities along one axis; the two other axes are 2 cells wide, so the face
+    # rule must pair each cell with its neighbour along that axis and not along another.  Homogenisation
+    # of a layered medium in series gives D_eff with 1/D_eff = mean(1/D).  The long-time variance of the
+    # point-source solution along the layered axis grows as 2 D_eff t, so its slope pins the face rule
+    # (an arithmetic-mean face rule gives ~0.36 here, against 0.123).  The marginal along that axis is a
+    # 1D chain exactly (the faces across the other axes only move mass within a layer); the full-domain
+    # march stands for a window covering the domain, which the solution does not reach in 3000 substeps.
     period = np.array([1.0, 0.3, 0.05])
-    nx = 801
-    D = np.tile(period, nx // 3 + 1)[:nx]
-    shape = (nx, 1, 1)
+    n = 801
+    layer = np.tile(period, n // 3 + 1)[:n]
+    dims = [2, 2, 2]
+    dims[axis] = n
+    shape = tuple(dims)
+    coord = np.meshgrid(np.arange(dims[0]), np.arange(dims[1]), np.arange(dims[2]), indexing="ij")[axis]
+    D = layer[coord].transpose(2, 1, 0).reshape(-1)          # x fastest
     lam = oracle.stable_dt_sub(shape, D)
-    R = 400
     cond = oracle.Conductance(shape, D)
-    x = np.arange(-R, R + 1, dtype=np.float64)
+    x = np.arange(n, dtype=np.float64)
     slopes = []
     for s in (399, 400, 401):                   # three phases of the period
+        c0 = np.zeros(D.size)
+        at = [0, 0, 0]
+        at[axis] = s
+        c0[at[0] + dims[0] * (at[1] + dims[1] * at[2])] = 1.0
+        c1 = oracle.full_march(shape, D, lam, 1500, c0, cond)
+        c2 = oracle.full_march(shape, D, lam, 1500, c1, cond)
         var = []
-        for n_sub in (1500, 3000):
-            k, _ = oracle.source_kernel(shape, D, lam, R, n_sub, s, cond)
-            kk = k[R, R, :]
+        for c in (c1, c2):
+            kk = c.reshape(dims[2], dims[1], dims[0]).sum(axis=tuple(a for a in (0, 1, 2) if a != 2 - axis))
             mean = (kk * x).sum()
             var.append((kk * (x - mean) ** 2).sum())
         slopes.append((var[1] - var[0]) / (2.0 * lam * 1500))
     d_eff = 1.0 / np.mean(1.0 / period)
     assert abs(np.mean(slopes) - d_eff) <= 0.01 * d_eff
+
+
+def test_grid_spacing_scales_out():
+    # The diffusion equation is unchanged by x -> x / h, t -> t / h^2: with lam = (dt_macro / n_sub) / h^2
+    # the lazy walk's exact variance 2 lam n_sub (cells^2), times h^2, is the continuum 2 D dt_macro for
+    # every h (window never reached: R >= n_sub).  The largest stable dt_sub turns back into 1 / (max face
+    # sum) through the same lam.
+    D, n_sub, R = 1.0, 8, 8
+    W1 = 2 * R + 1
+    shape = (W1, W1, W1)
+    Dm = np.full(W1 ** 3, D)
+    o = np.arange(-R, R + 1, dtype=np.float64)
+    for h, dt_macro in ((0.5, 0.2), (2.0, 3.2), (1.0, 0.8)):
+        lam = oracle.lam_of(dt_macro, n_sub, h)
+        assert lam == pytest.approx(0.1, rel=1e-15)
+        k, _ = oracle.source_kernel(shape, Dm, lam, R, n_sub, R + W1 * (R + W1 * R))
+        var_x = float((k.sum(axis=(0, 1)) * o * o).sum())
+        assert var_x * h * h == pytest.approx(2.0 * D * dt_macro, rel=1e-13)
+        dts = oracle.stable_dt_sub(shape, Dm, h)
+        assert oracle.lam_of(dts * n_sub, n_sub, h) == pytest.approx(1.0 / 6.0, rel=1e-15)
 
 
 def test_stability_limit_closed_form():

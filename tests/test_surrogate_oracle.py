@@ -10,7 +10,10 @@ from paper_2408_11376_gb300 import synth
 
 def test_bf16_round_matches_torch():
     rng = np.random.default_rng(0)
-    x = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e-30, 100), [0.0, -0.0, 1.0, 65504.0, 3e38]])
+    # exact ties between two BF16 values (low 16 bits 0x8000), with an even and an odd upper half
+    ties = np.array([0x3F808000, 0x3F818000, 0xBF808000, 0xBF818000, 0x00018000], dtype=np.uint32).view(np.float32)
+    x = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e-30, 100), [0.0, -0.0, 1.0, 65504.0, 3e38],
+                        ties.astype(np.float64)])
     ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(so.bf16_round(x), ref)
 
@@ -90,3 +93,24 @@ def test_features_and_gate():
     assert f[1].sum() == 9 * 9 * 8                # in-domain cells of the clipped patch (x, y, z)
     assert f[0, 8, 8, 8] == 0.0 and f[0, 8, 8, 9] == -0.5 and f[0, 8, 8, 10] == 1.0
     assert so.gate(1.0009) and not so.gate(1.0011) and not so.gate(0.998)
+
+
+def test_delta_prior_forward_closed_form():
+    """With no noise the prior carries the source marker through the relu layers unchanged (centre taps
+    1), and layer 4 gives z = bf16(L) a0 - fp32(L), L = -ln(eps): in closed form the head is
+    exp(bf16(L) - fp32(L)) at the source, exp(-fp32(L)) on the other in-domain cells and 0 outside the
+    domain.  An edge source puts part of the patch outside."""
+    shape = (12, 11, 10)
+    s = 0 + 12 * (5 + 11 * 9)                    # x = 0, y = 5, z = 9: patch outside in -x and +z
+    feat = so.features(np.ones(12 * 11 * 10), shape, s)
+    Ws, bs = so.init_params(0, noise=0.0)
+    y, m, _ = so.forward(feat, Ws, bs)
+    L = -np.log(so.EPS)
+    Lb = float(so.bf16_round(np.array([L]))[0])
+    Lf = float(np.float32(L))
+    inside = feat[1] > 0.5
+    want = np.where(inside, np.exp(-Lf), 0.0)
+    want[so.HALF, so.HALF, so.HALF] = np.exp(Lb - Lf)
+    assert np.allclose(y, want, rtol=1e-14, atol=0)
+    assert inside.sum() == 9 * 11 * 9               # x in [0, 8], y in [0, 10], z in [1, 9]
+    assert m == pytest.approx(np.exp(Lb - Lf) + (inside.sum() - 1) * np.exp(-Lf), rel=1e-14)
