@@ -9,16 +9,26 @@ with gcc on first use and marshals numpy arrays.  Section/equation citations ref
 
 * ``face_conductance``  -- Eq. 1 discretised by finite differences (harmonic-mean face rule: a reading;
   the paper does not state the face rule).
-* ``stable_dt_sub``     -- largest substep keeping every explicit coefficient non-negative.
+* ``stable_dt_sub``, ``lam_of`` -- largest substep keeping every explicit coefficient non-negative;
+  lam = dt_sub / h^2.
 * ``source_kernel`` / ``kernels`` -- Sec. 3.1: column s of p is an explicit FD march from a unit point
   source at s; here on the window of radius R, zero flux at window and domain faces, renormalised to
   unit mass in FP64.
 * ``superpose``         -- Eq. 8 / Eq. 14: c' = p c.
 * ``full_march``        -- the fine-mesh FD solver of Sec. 4.1 over the whole domain (linearity pin).
 * ``mass``              -- Eq. 7: total mass.
+* ``radius_map`` / ``superpose_rmap`` -- Eq. 8 with a window radius per source (the batched variant's
+  radius rule is a reading).
+* ``coarse_counts``, ``coarse_kernels``, ``coarse_step`` -- the coarse mesh, Eqs. 10-15.
+* ``boundary_conductance``, ``coarse_kernels_open``, ``coarse_pbc``, ``coarse_step_far`` -- the far-field
+  boundary: the P_BC c_far term of Eqs. 10 and 14 and the Eq. 7 update of c_far.
+* ``absorb``, ``solid_march``, ``coupled_step`` -- the coupled macro step of Sec. 2 (Eqs. 1-7).
+* ``source_kernel_adv``, ``superpose_adv``, ``superpose_rmap_adv`` and the ``w=`` forms of the coarse
+  functions -- convection (Sec. 5) as upwind faces in the march.
 
-Parity status: every function above is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``
-(closed forms, invariants, brute force).
+Parity status: every function above is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``
+(closed forms, hand-worked cases, invariants, brute force); ``tests/test_oracle_mutants.py`` checks that
+those pins fail on plausible mistakes planted in a copy of this package.
 """
 from __future__ import annotations
 

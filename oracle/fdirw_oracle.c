@@ -184,9 +184,6 @@ int fo_superpose(int nx, int ny, int nz, const double* gx, const double* gy, con
     return 0;
 }
 
-/* Brute-force explicit FD march of a whole field over the full domain (no window), n_sub substeps:
- * the fine-mesh FD solver the paper compares against (Sec. 4.1).  By linearity (Eq. 8) it equals one
- * superposition step whenever every window covers the whole domain. */
 /* Per-source window radius from the local diffusivity (not in the paper, which has no window; reading
  * of the batched variant): twice the diffusion length sqrt(2 D dt_macro) of the macro step, in cells,
  * rounded up and clamped:  R(s) = clamp(ceil(2 sqrt(2 D(s) dt_macro) / h), R_min, R_max).
@@ -205,14 +202,13 @@ void fo_radius_map(int64_t N, const double* D, double dt_macro, double h, int R_
     }
 }
 
-/* Eq. 8 with a radius per source: c_out(x) = sum_s c_in(s) k_s(x), k_s the kernel of s on its own
- * window of radius Rmap[s] (scatter over sources, as fo_superpose). */
 int fo_source_kernel_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                          const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
                          int n_sub, int64_t s, double* k_out, double* mass_before);
 
-/* Eq. 8 with a per-source window radius; with face velocities (wx != NULL) the kernels carry the Sec. 5
- * upwind faces. */
+/* Eq. 8 with a radius per source: c_out(x) = sum_s c_in(s) k_s(x), k_s the kernel of s on its own
+ * window of radius Rmap[s] (scatter over sources, as fo_superpose); with face velocities (wx != NULL) the
+ * kernels carry the Sec. 5 upwind faces. */
 static int superpose_rmap_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                                const double* wx, const double* wy, const double* wz, double lama, double lam,
                                const int32_t* Rmap, int n_sub, const double* c_in, double* c_out)
@@ -742,6 +738,9 @@ int fo_superpose_adv(int nx, int ny, int nz, const double* gx, const double* gy,
     return 0;
 }
 
+/* Brute-force explicit FD march of a whole field over the full domain (no window), n_sub substeps:
+ * the fine-mesh FD solver the paper compares against (Sec. 4.1).  By linearity (Eq. 8) it equals one
+ * superposition step whenever every window covers the whole domain. */
 int fo_full_march(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
                   double lam, int n_sub, const double* c_in, double* c_out)
 {
