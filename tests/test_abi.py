@@ -128,3 +128,44 @@ def test_product_path_never_imports_the_oracle():
                         assert (node.module or "").split(".")[0] != "oracle", f
             if f.endswith((".cu", ".h", ".cpp", ".c")):
                 assert "fdirw_oracle" not in open(os.path.join(dirpath, f)).read(), f
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """The ctypes structures and constants of the binding against the C header, compiled with gcc: every
+    field at the same offset with the same size, the same struct sizes, the same constant values."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = (fdirw.fdirw_grid, fdirw.fdirw_opts, fdirw.fdirw_coupled_params, fdirw.fdirw_info)
+    consts = ("FDIRW_OK", "FDIRW_ERR_ARG", "FDIRW_ERR_UNSTABLE", "FDIRW_ERR_NOMEM", "FDIRW_ERR_CUDA",
+              "FDIRW_ERR_TIMEOUT", "FDIRW_ERR_STATE", "FDIRW_FP64", "FDIRW_FP32", "FDIRW_FP32_STORE_FP16",
+              "FDIRW_FP32_STORE_BF16", "FDIRW_ACCUM_FF", "FDIRW_ACCUM_FP32")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fdirw.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'    printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'    printf("{n}.{f} %zu %zu\\n", offsetof({n}, {f}), sizeof((({n}*)0)->{f}));')
+    for c in consts:
+        lines.append(f'    printf("{c} %d\\n", (int)({c}));')
+    lines.append('    printf("FDIRW_NET_NPARAM %d\\n", (int)(FDIRW_NET_NPARAM));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        k, *v = l.split()
+        got[k] = tuple(int(x) for x in v)
+    for st in structs:
+        n = st.__name__
+        assert got[n] == (ctypes.sizeof(st),), n
+        for f, t in st._fields_:
+            assert got[f"{n}.{f}"] == (getattr(st, f).offset, ctypes.sizeof(t)), (n, f)
+    for c in consts:
+        assert got[c] == (getattr(fdirw, c),), c
+    assert got["FDIRW_NET_NPARAM"] == (fdirw.NET_NPARAM,)
