@@ -169,3 +169,55 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     for c in consts:
         assert got[c] == (getattr(fdirw, c),), c
     assert got["FDIRW_NET_NPARAM"] == (fdirw.NET_NPARAM,)
+
+
+_SCALARS = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double, "float": ctypes.c_float,
+            "int": ctypes.c_int}
+_POINTEES = {"double": ctypes.c_double, "int64_t": ctypes.c_int64, "fdirw_grid": fdirw.fdirw_grid,
+             "fdirw_opts": fdirw.fdirw_opts, "fdirw_info": fdirw.fdirw_info,
+             "fdirw_coupled_params": fdirw.fdirw_coupled_params}
+
+
+def _prototypes():
+    """(return type, name, [parameter types]) of every FDIRW_API declaration in the header."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "fdirw.h")).read(), flags=re.S)
+    out = []
+    for ret, name, params in re.findall(r"FDIRW_API\s+([\w\s\*]+?)\s*\b(fdirw_\w+)\s*\(([^)]*)\)\s*;", src):
+        types = []
+        for p in params.split(","):
+            p = " ".join(p.split())
+            if p == "void":
+                continue
+            m = re.match(r"^(.*?)(\w+)$", p)
+            types.append(m.group(1).replace("const", "").replace(" ", ""))
+        out.append((ret.replace("const", "").replace(" ", ""), name, types))
+    return out
+
+
+def test_binding_argtypes_match_the_header_prototypes(lib):
+    """Every entry point's ctypes signature against its C prototype: the same arity, the same scalar types
+    (an int64 passed where the C side reads an int32 would shift every later argument), and pointers
+    declared as pointers (of the same pointee where the binding names one)."""
+    protos = _prototypes()
+    assert {n for _, n, _ in protos} == set(fdirw.EXPORTED)
+    for ret, name, types in protos:
+        f = getattr(lib, name)
+        assert len(f.argtypes) == len(types), name
+        for i, (ct, at) in enumerate(zip(types, f.argtypes)):
+            if "*" in ct:
+                base = ct.rstrip("*")
+                if at is ctypes.c_void_p:
+                    continue
+                assert hasattr(at, "_type_") and ct.count("*") >= 1, (name, i, ct, at)
+                if ct.count("*") == 2 or base in ("void", "fdirw_ctx", "fdirw_net"):
+                    assert at._type_ is ctypes.c_void_p, (name, i, ct, at)      # pointer to a handle
+                else:
+                    assert at._type_ is _POINTEES[base], (name, i, ct, at)
+            else:
+                assert at is _SCALARS[ct], (name, i, ct, at)
+        if ret == "int":
+            assert f.restype is ctypes.c_int, name
+        elif ret == "void":
+            assert f.restype is None, name
+        else:
+            assert ret == "char*" and f.restype is ctypes.c_char_p, name
