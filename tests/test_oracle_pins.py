@@ -89,6 +89,50 @@ def test_kernel_symmetry_when_window_is_domain():
     assert np.max(np.abs(P - P.T)) <= 1e-14
 
 
+def _box_propagator(shape, D, lam, n_sub, lo, hi):
+    """(I + lam A_B)^n_sub for the box [lo, hi] (inclusive, x fastest): A_B is the graph Laplacian of the
+    faces with both cells in the box, each of conductance 2 D_a D_b / (D_a + D_b), assembled densely here
+    and raised to the power with numpy's matrix_power."""
+    nx, ny, _ = shape
+    Dg = np.asarray(D).reshape(shape[2], ny, nx)
+    cells = [(x, y, z) for z in range(lo[2], hi[2] + 1) for y in range(lo[1], hi[1] + 1) for x in range(lo[0], hi[0] + 1)]
+    at = {c: i for i, c in enumerate(cells)}
+    A = np.zeros((len(cells), len(cells)))
+    for (x, y, z), i in at.items():
+        for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+            j = at.get((x + d[0], y + d[1], z + d[2]))
+            if j is None:
+                continue
+            a, b = Dg[z, y, x], Dg[z + d[2], y + d[1], x + d[0]]
+            g = 2.0 * a * b / (a + b) if a + b > 0 else 0.0
+            A[i, j] += g
+            A[j, i] += g
+            A[i, i] -= g
+            A[j, j] -= g
+    return np.linalg.matrix_power(np.eye(len(cells)) + lam * A, n_sub), cells
+
+
+@pytest.mark.parametrize("s", [(4, 4, 3), (0, 7, 6), (8, 0, 3)])
+def test_windowed_kernel_is_a_column_of_the_box_propagator(s):
+    """Sec. 3.1 with a window smaller than the domain and a rough D: the kernel of s is column s of the
+    box propagator (I + lam A_B)^n_sub of its clipped window B_s, divided by that column's sum, and the box
+    propagator is symmetric (symmetric faces, equal cell volumes).  An interior window, a corner and an
+    edge."""
+    shape, R, n_sub = (9, 8, 7), 2, 13
+    D = _rough_D(shape, 5)
+    lam = 0.8 * oracle.stable_dt_sub(shape, D)
+    lo = [max(v - R, 0) for v in s]
+    hi = [min(v + R, n - 1) for v, n in zip(s, shape)]
+    M, cells = _box_propagator(shape, D, lam, n_sub, lo, hi)
+    assert np.max(np.abs(M - M.T)) <= 1e-15
+    col = M[:, cells.index(tuple(s))]
+    k, m = oracle.source_kernel(shape, D, lam, R, n_sub, s[0] + shape[0] * (s[1] + shape[1] * s[2]))
+    got = np.array([k[z - s[2] + R, y - s[1] + R, x - s[0] + R] for x, y, z in cells])
+    assert m == pytest.approx(col.sum(), abs=1e-14)
+    assert np.max(np.abs(got - col / col.sum())) <= 1e-15
+    assert k.sum() == pytest.approx(got.sum(), abs=1e-15)          # nothing outside the clipped window
+
+
 # ---------------------------------------------------------------- closed forms
 
 @pytest.mark.parametrize("shape,R,s", [
