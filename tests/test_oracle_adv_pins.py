@@ -65,6 +65,56 @@ def test_superpose_adv_conserves_mass():
     assert out.sum() == pytest.approx(c.sum(), rel=1e-13) and out.min() >= 0.0
 
 
+def test_kernel_is_a_column_of_the_upwind_box_propagator():
+    """Sec. 5 with a rough D and a non-uniform flow: the kernel of s is column s of (I + lam A_B + lam_a V_B)^n_sub
+    for its clipped window B_s, divided by the column's sum.  A_B is the diffusive graph Laplacian of the
+    faces inside the box (harmonic-mean conductances); V_B is the upwind operator: through the face from
+    a lower cell l to the upper cell u with velocity w, u gains w+ u_l - w- u_u and l loses it.  Both are
+    assembled densely here and raised with numpy's matrix_power."""
+    shape, R, n_sub, lama = (8, 7, 6), 2, 9, 0.3
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    D = synth.random_diffusivity(shape, 117, 4.0)
+    rng = np.random.default_rng(118)
+    w = tuple(rng.uniform(-0.3, 0.3, N) for _ in range(3))
+    lam = 0.3 * oracle.stable_dt_sub(shape, D)         # diffusion 0.3 + outflow at most 6 * 0.3 * 0.3: below 1
+    Dg = D.reshape(nz, ny, nx)
+    for s in ((4, 3, 3), (0, 6, 5), (7, 0, 2)):
+        lo = [max(v - R, 0) for v in s]
+        hi = [min(v + R, n - 1) for v, n in zip(s, shape)]
+        cells = [(x, y, z) for z in range(lo[2], hi[2] + 1) for y in range(lo[1], hi[1] + 1)
+                 for x in range(lo[0], hi[0] + 1)]
+        at = {c: i for i, c in enumerate(cells)}
+        A = np.zeros((len(cells), len(cells)))
+        V = np.zeros_like(A)
+        for (x, y, z), l in at.items():
+            for axis, d in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+                u = at.get((x + d[0], y + d[1], z + d[2]))
+                if u is None:
+                    continue
+                a, b = Dg[z, y, x], Dg[z + d[2], y + d[1], x + d[0]]
+                g = 2.0 * a * b / (a + b) if a + b > 0 else 0.0
+                A[l, u] += g
+                A[u, l] += g
+                A[l, l] -= g
+                A[u, u] -= g
+                wf = w[axis][x + nx * (y + ny * z)]
+                wp, wm = max(wf, 0.0), max(-wf, 0.0)
+                V[u, l] += wp
+                V[l, l] -= wp
+                V[l, u] += wm
+                V[u, u] -= wm
+        step = np.eye(len(cells)) + lam * A + lama * V
+        assert np.diag(step).min() >= 0.0                  # every explicit coefficient non-negative
+        M = np.linalg.matrix_power(step, n_sub)
+        col = M[:, at[s]]
+        k, m = oracle.source_kernel_adv(shape, D, w, lam, lama, R, n_sub, s[0] + nx * (s[1] + ny * s[2]))
+        got = np.array([k[z - s[2] + R, y - s[1] + R, x - s[0] + R] for x, y, z in cells])
+        assert m == pytest.approx(col.sum(), abs=1e-14)
+        assert np.max(np.abs(got - col / col.sum())) <= 1e-15
+        assert k.min() >= 0.0 and k.sum() == pytest.approx(1.0, abs=1e-14)
+
+
 def test_superpose_adv_moves_the_mean_by_lam_a_w():
     """Eq. 8 with convection on a field that is a point mass a: the step gives a times that source's
     kernel, so the mass stays a and the first moment moves by a n_sub lam_a w exactly (n_sub <= R: no
