@@ -250,3 +250,95 @@ def test_coupled_step_conserves_the_total():
                                     lam, 2, c)
         assert c.sum() + V_far * cf == pytest.approx(total, rel=1e-13)
     assert c[liquid == 0].sum() > 1e-6 * (liquid == 0).sum()       # the solid absorbed
+
+
+def _liquid_operator(shape, D, liquid, lo, hi, gb=None):
+    """Dense graph Laplacian of the box [lo, hi] (x fastest) over the faces whose two cells are both inside
+    the box and both liquid (harmonic-mean conductances), minus gb_i on the diagonal when the open faces
+    lose to a ghost (gb: conductance to the far field per cell)."""
+    nx, ny, nz = shape
+    Dg = np.asarray(D).reshape(nz, ny, nx)
+    Lg = np.asarray(liquid).reshape(nz, ny, nx)
+    cells = [(x, y, z) for z in range(lo[2], hi[2] + 1) for y in range(lo[1], hi[1] + 1) for x in range(lo[0], hi[0] + 1)]
+    at = {c: i for i, c in enumerate(cells)}
+    A = np.zeros((len(cells), len(cells)))
+    for (x, y, z), i in at.items():
+        for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+            j = at.get((x + d[0], y + d[1], z + d[2]))
+            if j is None or not (Lg[z, y, x] and Lg[z + d[2], y + d[1], x + d[0]]):
+                continue
+            a, b = Dg[z, y, x], Dg[z + d[2], y + d[1], x + d[0]]
+            g = 2.0 * a * b / (a + b)
+            A[i, j] += g
+            A[j, i] += g
+            A[i, i] -= g
+            A[j, j] -= g
+        if gb is not None:
+            A[i, i] -= gb[x + nx * (y + ny * z)]
+    return A, cells
+
+
+def test_coarse_columns_from_the_block_window_propagator():
+    """Eqs. 10-12 on a rough D with a liquid mask, blocks of B = 2 (the last ones clipped) and R = 2: column J
+    is the unit on J's liquid cells pushed through (I + lam A_W)^n_sub on J's window W (the block widened
+    by R, clipped; liquid-liquid faces only), summed over the liquid cells of each block I and mapped to
+    N_J S_I / (m N_I).  With the outer faces open to a ghost at 0 (each open face of conductance D_i) the
+    column is S_I / N_I; and P_BC is the whole grid marched from 0 with the ghost at 1, mean per block.
+    The propagators are assembled densely here and raised with numpy's matrix_power."""
+    shape, B, R, n_sub = (7, 5, 4), 2, 2, 6
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    D = synth.random_diffusivity(shape, 131, 3.0)
+    liquid = (np.random.default_rng(132).random(N) < 0.75).astype(np.uint8)
+    lam = 0.8 * oracle.stable_dt_sub(shape, D)
+    ncx, ncy, ncz = (nx + B - 1) // B, (ny + B - 1) // B, (nz + B - 1) // B
+    Rc = oracle.coarse_radius(R, B)
+    cnt = oracle.coarse_counts(shape, liquid, B)
+    gb = oracle.boundary_conductance(shape, D, liquid)
+    closed = oracle.coarse_kernels(shape, D, liquid, B, lam, R, n_sub)
+    opened = oracle.coarse_kernels_open(shape, D, liquid, B, lam, R, n_sub)
+    Lg = liquid.reshape(nz, ny, nx)
+    checked = 0
+    for J in range(ncx * ncy * ncz):
+        if cnt[J] == 0:
+            assert not closed[J].any() and not opened[J].any()
+            continue
+        bx, by, bz = J % ncx, (J // ncx) % ncy, J // (ncx * ncy)
+        lo = [max(b * B - R, 0) for b in (bx, by, bz)]
+        hi = [min(b * B + B - 1 + R, n - 1) for b, n in zip((bx, by, bz), shape)]
+        for open_, P in ((False, closed), (True, opened)):
+            A, cells = _liquid_operator(shape, D, liquid, lo, hi, gb if open_ else None)
+            u0 = np.array([1.0 if (x // B, y // B, z // B) == (bx, by, bz) and Lg[z, y, x] else 0.0
+                           for x, y, z in cells])
+            u = np.linalg.matrix_power(np.eye(len(cells)) + lam * A, n_sub) @ u0
+            m = u.sum()
+            want = np.zeros((2 * Rc + 1,) * 3)
+            for (x, y, z), v in zip(cells, u):
+                if Lg[z, y, x]:
+                    want[z // B - bz + Rc, y // B - by + Rc, x // B - bx + Rc] += v
+            for dz in range(-Rc, Rc + 1):
+                for dy in range(-Rc, Rc + 1):
+                    for dx in range(-Rc, Rc + 1):
+                        cx, cy, cz = bx + dx, by + dy, bz + dz
+                        inside = 0 <= cx < ncx and 0 <= cy < ncy and 0 <= cz < ncz
+                        I = cx + ncx * (cy + ncy * cz) if inside else -1
+                        o = (dz + Rc, dy + Rc, dx + Rc)
+                        if not inside or cnt[I] == 0:
+                            want[o] = 0.0
+                        else:
+                            want[o] = want[o] / cnt[I] if open_ else cnt[J] * want[o] / (m * cnt[I])
+            assert np.max(np.abs(P[J] - want)) <= 1e-14, (J, open_)
+        checked += 1
+    assert checked >= 20
+    A, cells = _liquid_operator(shape, D, liquid, (0, 0, 0), (nx - 1, ny - 1, nz - 1), gb)
+    step = np.eye(N) + lam * A
+    u = np.zeros(N)
+    for _ in range(n_sub):
+        u = step @ u + lam * gb                       # cells in x-fastest order, as the field
+    want = np.zeros(ncx * ncy * ncz)
+    for i in range(N):
+        if liquid[i]:
+            x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+            want[x // B + ncx * (y // B + ncy * (z // B))] += u[i]
+    want = np.where(cnt > 0, want / np.maximum(cnt, 1), 0.0)
+    assert np.max(np.abs(oracle.coarse_pbc(shape, D, liquid, B, lam, n_sub) - want)) <= 1e-14
