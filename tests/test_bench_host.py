@@ -73,3 +73,15 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     assert bench.main(["--impl", "reference", "--workload", "fdirw-32c-r3", "--steps", "1", "--warmup", "0",
                        "--ref-sample", "8"]) == 0
     assert capsys.readouterr().out.strip() == ""
+
+
+def test_batch_reference_arm_line(capsys, monkeypatch):
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    assert bench.main(["--impl", "reference", "--workload", "fdirw-batch2x48c-r3to10", "--steps", "1", "--warmup",
+                       "0", "--ref-sample", "8"]) == 0
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["config"]["workload"] == "fdirw-batch2x48c-r3to10"
+    assert d["config"]["structures"] == 2 and d["config"]["cells"] == 2 * 48 ** 3
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
+    assert "32 seeded random sources" in d["cpu_baseline"]["sample"]
