@@ -233,6 +233,26 @@ def test_thread_mappings_agree_bitwise(R):
     assert err.max() <= KERNEL_TOL["fp32"]
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 40), (1, 37, 1), (33, 1, 1), (4, 1, 23), (1, 6, 19)])
+def test_thin_domains_every_mapping(shape):
+    """Grids one cell thick in one or two axes, so every window is clipped to a single column or row of
+    columns (R = 3, and R = 8 beyond the thin extents): each FP32 thread mapping gives the same bits, the
+    kernels of every source match the oracle, and so do two macro steps."""
+    D = _case(shape, 91, "rough")
+    lam = oracle.stable_dt_sub(shape, D)
+    N = int(np.prod(shape))
+    c0 = synth.random_field(N, 92)
+    src = np.arange(N)
+    for R in (3, 8):
+        runs = [_gpu_run(shape, D, lam, R, 21, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5, 6)]
+        for got, m, ks, info in runs[1:]:
+            assert np.array_equal(got, runs[0][0]) and np.array_equal(ks, runs[0][2]) and m == runs[0][1]
+        ref, _ = oracle.kernels(shape, D, lam, R, 21, src)
+        err = np.linalg.norm((runs[0][2] - ref).reshape(N, -1), axis=1) / np.linalg.norm(ref.reshape(N, -1), axis=1)
+        assert err.max() <= KERNEL_TOL["fp32"], (R, err.max())
+        assert _rel(runs[0][0], _oracle_steps(shape, D, lam, R, 21, c0, 2)) <= FIELD_TOL["fp32"]
+
+
 def test_deterministic_bitwise():
     shape = (24, 16, 12)
     D = _case(shape, 51)
