@@ -103,12 +103,14 @@ static void box_step(int nx, int ny, const double* gx, const double* gy, const d
 }
 
 /* Spreading kernel of source s (Sec. 3.1: point-source explicit FD march, column s of p in Eq. 8),
- * on the window of radius R clipped to the domain, n_sub substeps.
+ * on the window of radius R clipped to the domain, n_sub substeps; with face velocities (wx != NULL)
+ * every substep also carries the Sec. 5 upwind faces (box_substep_adv).
  * k_out: (2R+1)^3 doubles on the offset layout, the marched field divided by its total.
  * mass_before (nullable): the total before that division (1 up to rounding: the flux form conserves).
  * Returns 0, or -1 on a bad argument or allocation failure. */
-int fo_source_kernel(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                     double lam, int R, int n_sub, int64_t s, double* k_out, double* mass_before)
+static int source_kernel_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                              const double* wx, const double* wy, const double* wz, double lam, double lama,
+                              int R, int n_sub, int64_t s, double* k_out, double* mass_before)
 {
     if (R < 0 || n_sub < 0 || s < 0 || s >= (int64_t)nx * ny * nz) return -1;
     int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
@@ -122,7 +124,7 @@ int fo_source_kernel(int nx, int ny, int nz, const double* gx, const double* gy,
     if (!u || !un) { free(u); free(un); return -1; }
     u[(sx - x0) + (int64_t)bx * ((sy - y0) + (int64_t)by * (sz - z0))] = 1.0;
     for (int k = 0; k < n_sub; k++) {
-        box_substep(nx, ny, gx, gy, gz, lam, x0, y0, z0, bx, by, bz, u, un);
+        box_step(nx, ny, gx, gy, gz, wx, wy, wz, lam, lama, x0, y0, z0, bx, by, bz, u, un);
         double* t = u; u = un; un = t;
     }
     double m = 0.0;
@@ -139,6 +141,20 @@ int fo_source_kernel(int nx, int ny, int nz, const double* gx, const double* gy,
             }
     free(u); free(un);
     return 0;
+}
+
+int fo_source_kernel(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                     double lam, int R, int n_sub, int64_t s, double* k_out, double* mass_before)
+{
+    return source_kernel_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, lam, 0.0, R, n_sub, s, k_out, mass_before);
+}
+
+/* Spreading kernel with convection (Sec. 5): face velocities w, lama = dt_sub / h. */
+int fo_source_kernel_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                         const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
+                         int n_sub, int64_t s, double* k_out, double* mass_before)
+{
+    return source_kernel_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, R, n_sub, s, k_out, mass_before);
 }
 
 /* Kernels of a list of sources (the precomputed coefficient matrix of Sec. 3.1, one column per
@@ -160,9 +176,11 @@ int fo_kernels(int nx, int ny, int nz, const double* gx, const double* gy, const
 }
 
 /* One superposition step, Eq. 8 (and Eq. 14 on the full mesh): c_out(x) = sum_s c_in(s) k_s(x).
- * Written as a scatter over sources in index order, each kernel recomputed by its march. */
-int fo_superpose(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                 double lam, int R, int n_sub, const double* c_in, double* c_out)
+ * Written as a scatter over sources in index order, each kernel recomputed by its march (with the Sec. 5
+ * upwind faces when wx != NULL). */
+static int superpose_impl(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                          const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
+                          int n_sub, const double* c_in, double* c_out)
 {
     int64_t N = (int64_t)nx * ny * nz;
     int W1 = 2 * R + 1;
@@ -170,7 +188,10 @@ int fo_superpose(int nx, int ny, int nz, const double* gx, const double* gy, con
     if (!k) return -1;
     memset(c_out, 0, sizeof(double) * (size_t)N);
     for (int64_t s = 0; s < N; s++) {
-        if (fo_source_kernel(nx, ny, nz, gx, gy, gz, lam, R, n_sub, s, k, NULL) != 0) { free(k); return -1; }
+        if (source_kernel_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, R, n_sub, s, k, NULL) != 0) {
+            free(k);
+            return -1;
+        }
         int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
         for (int oz = -R; oz <= R; oz++)
             for (int oy = -R; oy <= R; oy++)
@@ -182,6 +203,20 @@ int fo_superpose(int nx, int ny, int nz, const double* gx, const double* gy, con
     }
     free(k);
     return 0;
+}
+
+int fo_superpose(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                 double lam, int R, int n_sub, const double* c_in, double* c_out)
+{
+    return superpose_impl(nx, ny, nz, gx, gy, gz, NULL, NULL, NULL, lam, 0.0, R, n_sub, c_in, c_out);
+}
+
+/* Eq. 8 with convection (Sec. 5): the kernels carry the upwind faces of face velocities w. */
+int fo_superpose_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
+                     const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
+                     int n_sub, const double* c_in, double* c_out)
+{
+    return superpose_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, R, n_sub, c_in, c_out);
 }
 
 /* Per-source window radius from the local diffusivity (not in the paper, which has no window; reading
@@ -201,10 +236,6 @@ void fo_radius_map(int64_t N, const double* D, double dt_macro, double h, int R_
         Rmap[s] = R < R_min ? R_min : R;
     }
 }
-
-int fo_source_kernel_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                         const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
-                         int n_sub, int64_t s, double* k_out, double* mass_before);
 
 /* Eq. 8 with a radius per source: c_out(x) = sum_s c_in(s) k_s(x), k_s the kernel of s on its own
  * window of radius Rmap[s] (scatter over sources, as fo_superpose); with face velocities (wx != NULL) the
@@ -230,9 +261,8 @@ static int superpose_rmap_impl(int nx, int ny, int nz, const double* gx, const d
         /* kernels of a chunk of sources in parallel (independent), then the scatter in source order */
         #pragma omp parallel for schedule(dynamic, 1) reduction(|:bad)
         for (int64_t s = s0; s < s1; s++)
-            if ((wx ? fo_source_kernel_adv(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, Rmap[s], n_sub, s,
-                                           k + (s - s0) * Wm, NULL)
-                    : fo_source_kernel(nx, ny, nz, gx, gy, gz, lam, Rmap[s], n_sub, s, k + (s - s0) * Wm, NULL)) != 0)
+            if (source_kernel_impl(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, Rmap[s], n_sub, s,
+                                   k + (s - s0) * Wm, NULL) != 0)
                 bad = 1;
         if (bad) break;
         for (int64_t s = s0; s < s1; s++) {
@@ -672,70 +702,6 @@ static void box_substep_adv(int nx, int ny, const double* gx, const double* gy, 
                 }
                 un[li] = ui + lam * acc + lama * adv;
             }
-}
-
-/* Spreading kernel with convection: fo_source_kernel with box_substep_adv (renormalised the same way). */
-int fo_source_kernel_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                         const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
-                         int n_sub, int64_t s, double* k_out, double* mass_before)
-{
-    if (R < 0 || n_sub < 0 || s < 0 || s >= (int64_t)nx * ny * nz) return -1;
-    int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
-    int x0 = sx - R < 0 ? 0 : sx - R, x1 = sx + R > nx - 1 ? nx - 1 : sx + R;
-    int y0 = sy - R < 0 ? 0 : sy - R, y1 = sy + R > ny - 1 ? ny - 1 : sy + R;
-    int z0 = sz - R < 0 ? 0 : sz - R, z1 = sz + R > nz - 1 ? nz - 1 : sz + R;
-    int bx = x1 - x0 + 1, by = y1 - y0 + 1, bz = z1 - z0 + 1;
-    int64_t nb = (int64_t)bx * by * bz;
-    double* u = (double*)calloc((size_t)nb, sizeof(double));
-    double* un = (double*)calloc((size_t)nb, sizeof(double));
-    if (!u || !un) { free(u); free(un); return -1; }
-    u[(sx - x0) + (int64_t)bx * ((sy - y0) + (int64_t)by * (sz - z0))] = 1.0;
-    for (int k = 0; k < n_sub; k++) {
-        box_substep_adv(nx, ny, gx, gy, gz, wx, wy, wz, lam, lama, x0, y0, z0, bx, by, bz, u, un);
-        double* t = u; u = un; un = t;
-    }
-    double m = 0.0;
-    for (int64_t q = 0; q < nb; q++) m += u[q];
-    if (mass_before) *mass_before = m;
-    int W1 = 2 * R + 1;
-    memset(k_out, 0, sizeof(double) * (size_t)W1 * W1 * W1);
-    for (int l = 0; l < bz; l++)
-        for (int j = 0; j < by; j++)
-            for (int i = 0; i < bx; i++) {
-                int ox = x0 + i - sx, oy = y0 + j - sy, oz = z0 + l - sz;
-                k_out[(ox + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (oz + R))] =
-                    u[i + (int64_t)bx * (j + (int64_t)by * l)] / m;
-            }
-    free(u); free(un);
-    return 0;
-}
-
-/* Eq. 8 with convection: c_out = sum_s c_in(s) k_s (scatter), kernels from fo_source_kernel_adv. */
-int fo_superpose_adv(int nx, int ny, int nz, const double* gx, const double* gy, const double* gz,
-                     const double* wx, const double* wy, const double* wz, double lam, double lama, int R,
-                     int n_sub, const double* c_in, double* c_out)
-{
-    int64_t N = (int64_t)nx * ny * nz;
-    int W1 = 2 * R + 1;
-    double* k = (double*)malloc(sizeof(double) * (size_t)W1 * W1 * W1);
-    if (!k) return -1;
-    memset(c_out, 0, sizeof(double) * (size_t)N);
-    for (int64_t s = 0; s < N; s++) {
-        if (fo_source_kernel_adv(nx, ny, nz, gx, gy, gz, wx, wy, wz, lam, lama, R, n_sub, s, k, NULL) != 0) {
-            free(k);
-            return -1;
-        }
-        int sx = (int)(s % nx), sy = (int)((s / nx) % ny), sz = (int)(s / ((int64_t)nx * ny));
-        for (int oz = -R; oz <= R; oz++)
-            for (int oy = -R; oy <= R; oy++)
-                for (int ox = -R; ox <= R; ox++) {
-                    int x = sx + ox, y = sy + oy, z = sz + oz;
-                    if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) continue;
-                    c_out[IDX(x, y, z, nx, ny)] += c_in[s] * k[(ox + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (oz + R))];
-                }
-    }
-    free(k);
-    return 0;
 }
 
 /* Brute-force explicit FD march of a whole field over the full domain (no window), n_sub substeps:

@@ -51,8 +51,8 @@ MUTANTS = [
     ("kernel_offsets_x_z_transposed", C,
      "k_out[(ox + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (oz + R))] =",
      "k_out[(oz + R) + (int64_t)W1 * ((oy + R) + (int64_t)W1 * (ox + R))] =", 0, "pins"),
-    ("march_one_substep_short", C, "    for (int k = 0; k < n_sub; k++) {\n        box_substep(nx, ny, gx, gy, gz, lam, x0",
-     "    for (int k = 1; k < n_sub; k++) {\n        box_substep(nx, ny, gx, gy, gz, lam, x0", 0, "pins"),
+    ("march_one_substep_short", C, "    for (int k = 0; k < n_sub; k++) {\n        box_step(nx, ny, gx, gy, gz, wx, wy, wz, lam, lama, x0",
+     "    for (int k = 1; k < n_sub; k++) {\n        box_step(nx, ny, gx, gy, gz, wx, wy, wz, lam, lama, x0", 0, "pins"),
     # Eq. 8: c' = p c, not p^T c
     ("superpose_transposed", C, "c_out[IDX(x, y, z, nx, ny)] += c_in[s] * k[",
      "c_out[IDX(x, y, z, nx, ny)] += c_in[IDX(x, y, z, nx, ny)] * k[", 0, "pins"),
@@ -123,8 +123,6 @@ MUTANTS = [
     ("upwind_lower_y_face_velocity_index", C, "double w = wy[gi - sy];", "double w = wy[gi];", 0, "adv"),
     ("upwind_scaled_by_lam", C, "un[li] = ui + lam * acc + lama * adv;", "un[li] = ui + lam * acc + lam * adv;", 0,
      "adv"),
-    ("superpose_adv_transposed", C, "c_out[IDX(x, y, z, nx, ny)] += c_in[s] * k[",
-     "c_out[IDX(x, y, z, nx, ny)] += c_in[IDX(x, y, z, nx, ny)] * k[", 1, "adv"),
     ("upwind_upper_x_outflow_sign", C, "adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + 1] : 0.0);",
      "adv += (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + 1] : 0.0);", 0, "adv"),
     ("superpose_adv_lam_lama_swapped", PY,
