@@ -150,9 +150,9 @@ MUTANTS = [
     ("feature_zero_D_channel", SU, "1.5) if d > 0 else -0.5", "1.5) if d > 0 else 0.0", 0, "surrogate"),
 ]
 
-# The driver puts the copy first on the path, checks that the copy is what `import oracle` loads, then
+# The launcher script puts the copy first on the path, checks that the copy is what `import oracle` loads, then
 # runs pytest; tests imported afterwards find the copy in sys.modules.
-_DRIVER = ("import sys; sys.path.insert(0, sys.argv[1]); import oracle; "
+_LAUNCHER = ("import sys; sys.path.insert(0, sys.argv[1]); import oracle; "
            "assert oracle.__file__.startswith(sys.argv[1]), oracle.__file__; "
            "import pytest; sys.exit(pytest.main(sys.argv[2:]))")
 
@@ -184,7 +184,7 @@ def _run_pins(dst_root, first, threads):
     order = [first] + [k for k in PIN_FILES if k != first]
     files = [os.path.join(TESTS, PIN_FILES[k]) for k in order]
     env = dict(os.environ, OMP_NUM_THREADS=str(threads), PYTHONDONTWRITEBYTECODE="1")
-    cmd = [sys.executable, "-c", _DRIVER, dst_root, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu", *files]
+    cmd = [sys.executable, "-c", _LAUNCHER, dst_root, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu", *files]
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
