@@ -89,9 +89,55 @@ static void box_substep(int nx, int ny, const double* gx, const double* gy, cons
             }
 }
 
+/* One substep with convection (Sec. 5: a steady flow folded into the computation of p).  Reading:
+ * w[a][i] is the velocity through the +a face of cell i (toward +a when positive), the advective flux
+ * through a face is upwind, lam_a (w+ u_lower - w- u_upper) from the lower cell to the upper one with
+ * lam_a = dt_sub / h, and it adds to the diffusive flux of box_substep.  Faces on a window's or the
+ * domain's edge carry neither. */
 static void box_substep_adv(int nx, int ny, const double* gx, const double* gy, const double* gz,
                             const double* wx, const double* wy, const double* wz, double lam, double lama,
-                            int x0, int y0, int z0, int bx, int by, int bz, const double* u, double* un);
+                            int x0, int y0, int z0, int bx, int by, int bz, const double* u, double* un)
+{
+    for (int l = 0; l < bz; l++)
+        for (int j = 0; j < by; j++)
+            for (int i = 0; i < bx; i++) {
+                int64_t li = i + (int64_t)bx * (j + (int64_t)by * l);
+                int64_t gi = IDX(x0 + i, y0 + j, z0 + l, nx, ny);
+                int64_t sy = nx, sz = (int64_t)nx * ny, ly = bx, lz = (int64_t)bx * by;
+                double ui = u[li], acc = 0.0, adv = 0.0;
+                if (i > 0) {
+                    acc += gx[gi - 1] * (u[li - 1] - ui);
+                    double w = wx[gi - 1];
+                    adv += (w > 0.0 ? w * u[li - 1] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
+                }
+                if (i + 1 < bx) {
+                    acc += gx[gi] * (u[li + 1] - ui);
+                    double w = wx[gi];
+                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + 1] : 0.0);
+                }
+                if (j > 0) {
+                    acc += gy[gi - sy] * (u[li - ly] - ui);
+                    double w = wy[gi - sy];
+                    adv += (w > 0.0 ? w * u[li - ly] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
+                }
+                if (j + 1 < by) {
+                    acc += gy[gi] * (u[li + ly] - ui);
+                    double w = wy[gi];
+                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + ly] : 0.0);
+                }
+                if (l > 0) {
+                    acc += gz[gi - sz] * (u[li - lz] - ui);
+                    double w = wz[gi - sz];
+                    adv += (w > 0.0 ? w * u[li - lz] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
+                }
+                if (l + 1 < bz) {
+                    acc += gz[gi] * (u[li + lz] - ui);
+                    double w = wz[gi];
+                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + lz] : 0.0);
+                }
+                un[li] = ui + lam * acc + lama * adv;
+            }
+}
 
 /* box_substep, or box_substep_adv when face velocities are given (wx != NULL; Sec. 5 convection). */
 static void box_step(int nx, int ny, const double* gx, const double* gy, const double* gz, const double* wx,
@@ -652,56 +698,6 @@ int fo_solid_march(int nx, int ny, int nz, const double* D, const uint8_t* liqui
     memcpy(c_out, u, sizeof(double) * (size_t)N);
     free(gx); free(gy); free(gz); free(u); free(un); free(solid);
     return 0;
-}
-
-/* ---- Convection (Sec. 5: a steady flow folded into the computation of p).  Reading: w[a][i] is the
- * velocity through the +a face of cell i (toward +a when positive), the advective flux through a face is
- * upwind, lam_a (w+ u_lower - w- u_upper) from the lower cell to the upper one with lam_a = dt_sub / h,
- * and it adds to the diffusive flux of box_substep.  Faces on a window's or the domain's edge carry
- * neither. */
-static void box_substep_adv(int nx, int ny, const double* gx, const double* gy, const double* gz,
-                            const double* wx, const double* wy, const double* wz, double lam, double lama,
-                            int x0, int y0, int z0, int bx, int by, int bz, const double* u, double* un)
-{
-    for (int l = 0; l < bz; l++)
-        for (int j = 0; j < by; j++)
-            for (int i = 0; i < bx; i++) {
-                int64_t li = i + (int64_t)bx * (j + (int64_t)by * l);
-                int64_t gi = IDX(x0 + i, y0 + j, z0 + l, nx, ny);
-                int64_t sy = nx, sz = (int64_t)nx * ny, ly = bx, lz = (int64_t)bx * by;
-                double ui = u[li], acc = 0.0, adv = 0.0;
-                if (i > 0) {
-                    acc += gx[gi - 1] * (u[li - 1] - ui);
-                    double w = wx[gi - 1];
-                    adv += (w > 0.0 ? w * u[li - 1] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
-                }
-                if (i + 1 < bx) {
-                    acc += gx[gi] * (u[li + 1] - ui);
-                    double w = wx[gi];
-                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + 1] : 0.0);
-                }
-                if (j > 0) {
-                    acc += gy[gi - sy] * (u[li - ly] - ui);
-                    double w = wy[gi - sy];
-                    adv += (w > 0.0 ? w * u[li - ly] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
-                }
-                if (j + 1 < by) {
-                    acc += gy[gi] * (u[li + ly] - ui);
-                    double w = wy[gi];
-                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + ly] : 0.0);
-                }
-                if (l > 0) {
-                    acc += gz[gi - sz] * (u[li - lz] - ui);
-                    double w = wz[gi - sz];
-                    adv += (w > 0.0 ? w * u[li - lz] : 0.0) - (w < 0.0 ? -w * ui : 0.0);
-                }
-                if (l + 1 < bz) {
-                    acc += gz[gi] * (u[li + lz] - ui);
-                    double w = wz[gi];
-                    adv -= (w > 0.0 ? w * ui : 0.0) - (w < 0.0 ? -w * u[li + lz] : 0.0);
-                }
-                un[li] = ui + lam * acc + lama * adv;
-            }
 }
 
 /* Brute-force explicit FD march of a whole field over the full domain (no window), n_sub substeps:
