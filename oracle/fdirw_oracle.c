@@ -5,11 +5,13 @@
  * load this library.  It shares no code, header, table or helper with the CUDA path.
  *
  * Method (paper: Mao, Hu, Li, "A GPU accelerated mixed-precision FDiRW solver", Sec. 3.1):
- *   Eq. 8:  c(t + dt) = p(dt) c(t)        (the boundary term p_BC c_far is not part of this path)
+ *   Eq. 8:  c(t + dt) = p(dt) c(t)        (the boundary term p_BC c_far: the far-field functions below)
  *   Column s of p is the result of an explicit finite-difference march of the diffusion equation
  *   (Eq. 1, pure-diffusion part) from a unit point source at cell s (Sec. 3.1, text after Eq. 9).
  *   Here each source's march runs on its own window: the cube of cells within L-infinity distance R
  *   of s, clipped to the domain, with zero flux through the window faces and the domain faces.
+ *   Further down: a window radius per source, the coarse mesh of Eqs. 10-15, the far-field boundary
+ *   (Eqs. 7, 10, 14), the coupled macro step (Sec. 2, Eqs. 1-7) and convection (Sec. 5).
  *
  * Conventions (readings of points the paper leaves open):
  *   - grid nx*ny*nz, cell size h, index i = x + nx*(y + ny*z);
