@@ -85,3 +85,13 @@ def test_batch_reference_arm_line(capsys, monkeypatch):
     assert d["config"]["structures"] == 2 and d["config"]["cells"] == 2 * 48 ** 3
     assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
     assert "32 seeded random sources" in d["cpu_baseline"]["sample"]
+
+
+def test_our_arm_fails_loudly_without_a_gpu():
+    """No CPU fallback: without CUDA the CUDA arm stops with an error instead of timing anything else."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(SystemExit) as e:
+        bench.main(["--steps", "1", "--warmup", "3"])
+    assert "needs a CUDA GPU" in str(e.value.code)
