@@ -18,8 +18,11 @@ the prediction fails a mass/positivity gate.  Definition followed here (and by t
   on y itself has dL/dz proportional to y, which vanishes wherever the prediction starts small).  Its
   gradient flows back through the relu layers (hand-derived below).
 
-Pins (tests/test_surrogate_oracle.py): conv3d against scipy.ndimage.correlate; the backward pass against
-central finite differences of the forward pass; BF16 rounding against torch's bfloat16 cast.
+Pins (tests/test_surrogate_oracle.py): conv3d against scipy.ndimage.correlate; every weight and bias
+gradient of the hand-derived backward against float64 autograd through torch's conv3d (1e-12 relative on
+every entry, interior and edge patches); the BF16-emulating forward against the same chain in torch with
+torch's BF16 cast at the same points; central finite differences off the relu kinks; BF16 rounding
+against torch's bfloat16 cast.
 """
 from __future__ import annotations
 

@@ -139,6 +139,10 @@ MUTANTS = [
     ("conv_grad_weight_transposed", SU, 'np.einsum("czyx,ozyx->oc", sl, g)', 'np.einsum("czyx,ozyx->co", sl, g)', 0,
      "surrogate"),
     ("backward_ignores_relu", SU, "g = ga * (zs[l - 1] > 0.0)", "g = ga", 0, "surrogate"),
+    ("conv_grad_input_drops_edge_tap", SU, "for dx in (-1, 0, 1):", "for dx in (-1, 0):", 1, "surrogate"),
+    ("relu_mask_skipped_below_the_head", SU, "g = ga * (zs[l - 1] > 0.0)",
+     "g = ga * (zs[l - 1] > 0.0) if l < LAYERS - 1 else ga", 0, "surrogate"),
+    ("relu_mask_of_the_layer_above", SU, "g = ga * (zs[l - 1] > 0.0)", "g = ga * (zs[l] > 0.0)", 0, "surrogate"),
     ("loss_gradient_half", SU, "return float((w * d * d).sum()), 2.0 * w * d", "return float((w * d * d).sum()), w * d", 0,
      "surrogate"),
     ("head_without_exp", SU, "y = np.where(mask, np.exp(zs[-1][0]), 0.0)", "y = np.where(mask, zs[-1][0], 0.0)", 0,
