@@ -117,22 +117,48 @@ def _dist():
 
 # ----------------------------------------------------------------------------- oracle (CPU) timing
 
-def oracle_sample(w, D, n_sources: int, seed: int = 7):
-    """Times the FP64 CPU oracle's kernel marches on a seeded sample of sources (all host threads).
-    The oracle recomputes every source's kernel for each superposition step, so one of its macro steps
-    costs N kernel marches; the sample gives seconds per source."""
+def oracle_sample(w, D, n_sources: int, seed: int = 7, threads: int = 0):
+    """Times the FP64 CPU oracle's kernel marches on a seeded sample of sources (all host threads unless
+    `threads` is given).  The oracle recomputes every source's kernel for each superposition step, so one
+    of its macro steps costs N kernel marches; the sample gives seconds per source."""
     import oracle
     shape = (w.n,) * 3
     lam = oracle.stable_dt_sub(shape, D)
     cond = oracle.Conductance(shape, D)
     rng = np.random.default_rng(seed)
     src = rng.integers(0, w.n ** 3, n_sources)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     t0 = time.perf_counter()
     oracle.kernels(shape, D, lam, w.R, w.n_sub, src, cond)
     dt = time.perf_counter() - t0
     return dt / n_sources, threads, dt
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.strip().lower().startswith("model name"):
+                return l.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith("model name"):
+                return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_single_thread(w, D, n_sources: int, seed: int = 11):
+    """Seconds per source of the FP64 oracle on ONE host thread (seeded sample), for the single-core figure."""
+    import oracle
+    t_src, _, dt = oracle_sample(w, D, n_sources, seed, threads=1)
+    oracle.set_threads(os.cpu_count() or 1)
+    return t_src, dt
 
 
 def run_reference(args, w):
@@ -148,14 +174,21 @@ def run_reference(args, w):
             per_step.append(t_src)
     t_src = statistics.mean(per_step)
     value = 1.0 / (N * t_src)
+    t1, dt1 = oracle_single_thread(w, D, args.ref_sample_1t)
     sample = (f"{args.ref_sample} seeded random sources of {w.name} per step (FP64 windowed marches); "
               f"macro-steps/s = 1/(N * seconds per source), the oracle recomputing every kernel each step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * N * t_src, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "grid": f"{w.n}^3", "R": w.R, "n_sub": w.n_sub,
-                       "macro_steps": w.steps},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+                       "macro_steps": w.steps, "prec": "fp64", "accum": "fp64"},
+            "timing": {"kind": "sample-extrapolated", "sources_per_step": args.ref_sample,
+                       "timed_ms_per_step": 1000.0 * args.ref_sample * t_src,
+                       "note": "each step times the sample; ms_per_step and value extrapolate it to all N sources"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(),
+                             "single_thread": {"value": 1.0 / (N * t1), "cores": 1,
+                                               "sample": f"{args.ref_sample_1t} seeded random sources ({dt1:.1f} s)"}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -171,9 +204,10 @@ def march_kernel_name(prec: str, parts: int) -> str:
 
 
 # DRAM bytes (read + write) per clipped window cell of march_tm_kernel<8> with BF16 storage, from one ncu
-# capture of the 64^3 case with the same recipe (profiles/march_tm_R8_64c.md: 1.262 GB read + 3.117 GB
-# written over 1.049e9 window cells); the traffic of a full launch scales with its window cells (the
-# stored kernel values dominate it).  Valid for that kernel, radius and storage only.
+# capture of the 64^3 case with the same recipe (`--set full` on the first march launch of
+# `bench.py --workload fdirw-64c-r8 --prec bf16 --march-parts 4`: 1.262 GB read + 3.117 GB written over
+# 1.049e9 window cells); the traffic of a full launch scales with its window cells (the stored kernel values
+# dominate it).  Valid for that kernel, radius and storage only.
 TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL = (1.261629e9 + 3.116823e9) / 1.049e9
 
 
@@ -186,12 +220,13 @@ def march_traffic(args, prec: str, parts: int, R: int, window_cells: float):
 
 
 # DRAM bytes (read + write) per algorithmic byte of gather_fp32_kernel<bf16> from one ncu capture of the
-# 96^3, R = 6 case (profiles/gather_fp32_R6_96c.md: 3.8927e9 read + 3.33e6 written against 3.8971e9
-# algorithmic); the traffic of a launch grows with its cache bytes.  Valid for that kernel and storage only.
+# 96^3, R = 6 case (`bench.py --workload fdirw-96c-r6`: 3.8927e9 read + 3.33e6 written against
+# 3.8971e9 algorithmic); the traffic of a launch grows with its cache bytes.  Valid for that kernel and
+# storage only.
 GATHER_FP32_BF16_DRAM_PER_ALGORITHMIC_BYTE = (3.892684288e9 + 3.326464e6) / (96 ** 3 * (13 ** 3 * 2 + 4 + 8))
 
 
-def gather_roofline(prec: str, accum: str, N: int, R: int, gather_ms: float):
+def gather_roofline(prec: str, accum: str, N: int, R: int, gather_ms: float, probe=None):
     """HBM roofline of one superposition launch: algorithmic bytes = the kernel cache (N (2R+1)^3 stored
     values, each read once) + the scaled field it multiplies (FP32, or FP32 pairs) + the FP64 output."""
     peaks, peak_src = _peaks()
@@ -204,30 +239,65 @@ def gather_roofline(prec: str, accum: str, N: int, R: int, gather_ms: float):
     traffic = GATHER_FP32_BF16_DRAM_PER_ALGORITHMIC_BYTE * nbytes if (prec == "bf16" and accum == "fp32") else None
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "traffic_source": "ncu capture of the 96^3 R=6 case (profiles/gather_fp32_R6_96c.md), DRAM bytes "
+            "traffic_source": "ncu capture of the 96^3 R=6 case of the same kernel and storage, DRAM bytes "
                               "scaled by algorithmic bytes to this launch" if traffic is not None else None,
-            "peak_source": f"hbm_gbs ({peak_src})",
+            "peak_source": f"hbm_gbs ({peak_src}, a read + write copy)",
             "algorithmic": f"cache {N}x{(2 * R + 1) ** 3}x{qb} B + field {chat_b} B + output 8 B per cell "
-                           f"= {nbytes / 1e9:.2f} GB per launch"}
+                           f"= {nbytes / 1e9:.2f} GB per launch",
+            **({"read_peak_measured": probe["read_bytes_per_s"] / 1e9,
+                "frac_of_read_peak": achieved / (probe["read_bytes_per_s"] / 1e9),
+                "read_peak_source": "measured in this run: streaming read of a 4 GiB buffer (fdirw_probe_peaks); the "
+                                    "gather reads almost only, so this is its tighter ceiling"} if probe else {})}
 
 
-def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: float, traffic, clocks, kname: str):
+def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: float, traffic, clocks, kname: str,
+                      probe=None):
     """Achieved FP32 flop rate of the march (13 flop per cell-substep over the clipped windows) against the
-    FP32 pipe peak at the measured maximum SM clock."""
+    FP32 FMA rate measured on this GPU in this run (fdirw_probe_peaks), beside the FP32 pipe's unit-count
+    peak at the measured maximum SM clock."""
     peaks, peak_src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    derived = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_CELL_SUBSTEP * n_sub * window_cells / (march_ms * 1e-3) / 1e12
+    measured = probe["fp32_flops"] / 1e12 if probe else None
+    peak = measured if measured else derived
     out = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak, "traffic": traffic,
-           "peak_source": f"FP32 pipe: {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz "
-                          f"(sm_max_mhz, {peak_src})",
+           "peak_source": ("measured in this run: FP32 FMA loop of fdirw_probe_peaks (register-only, 4 x 512 "
+                           "threads per SM)" if measured else
+                           f"derived: FP32 pipe, {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz"),
+           "peak_derived": derived, "frac_of_derived": achieved / derived,
+           "peak_derived_source": f"FP32 pipe: {num_sms} SMs x {FP32_LANES_PER_SM} FMA/clk x 2 flop x {sm_max:.0f} MHz "
+                                  f"(sm_max_mhz, {peak_src})",
            "algorithmic": f"{FLOP_PER_CELL_SUBSTEP} flop per cell-substep x n_sub x sum of clipped window cells "
                           f"({window_cells:.4g})"}
     if clocks.get("sm_mhz"):
-        out["frac_at_sampled_clock"] = achieved / (num_sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+        out["frac_of_derived_at_sampled_clock"] = achieved / (num_sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     return out
+
+
+# Shared-memory wavefronts of march_tm_kernel<8> per COMPUTED thread-cell-substep (every CTA batch marches 256
+# threads x 68 cells whatever the windows' clipping), from the 64^3 capture of that kernel with the 192^3
+# recipe (`--set full` on the first march launch of `bench.py --workload fdirw-64c-r8 --prec bf16
+# --march-parts 4`: 3.23e10 wavefronts over 87,382 batches x 256 x 68 x 200).  A launch's wavefronts scale
+# with its computed cells; the shared-memory peak is one 128-byte wavefront per SM-cycle (32 banks x 4 B).
+TM_R8_SMEM_WAVEFRONTS_PER_COMPUTED_CELL = 3.23e10 / (87382 * 256 * 68 * 200)
+
+
+def march_smem(n_src: int, n_sub: int, R: int, parts: int, march_ms: float, sm_mhz: float, num_sms: int):
+    """Shared-memory throughput of the march launch as a fraction of one wavefront per SM-cycle (mapping 4
+    at R = 8 only, the kernel the capture covers)."""
+    if parts != 4 or R != 8:
+        return None
+    spb = 256 // (R + 1) ** 2
+    computed = -(-n_src // spb) * 256 * 4 * (2 * R + 1) * n_sub
+    wavefronts = TM_R8_SMEM_WAVEFRONTS_PER_COMPUTED_CELL * computed
+    per_cycle = wavefronts / (march_ms * 1e-3 * sm_mhz * 1e6 * num_sms)
+    return {"wavefronts_per_launch": wavefronts, "achieved_per_sm_cycle": per_cycle, "peak_per_sm_cycle": 1.0,
+            "frac": per_cycle, "clock_mhz": sm_mhz,
+            "source": "64^3 ncu capture of the same kernel (wavefronts per computed cell-substep), scaled to this "
+                      "launch's computed cells; divided by its CUDA-event time at the sampled SM clock"}
 
 
 def run_batch(args, bw):
@@ -460,6 +530,8 @@ def run_ours(args, w):
     dt_macro = w.n_sub * dt_sub
     prec = args.prec
 
+    probe = None if args.no_probe else fdirw.fdirw_probe_peaks(local)
+
     def one_pass(times=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         with torch.cuda.stream(stream):
@@ -541,18 +613,25 @@ def run_ours(args, w):
     clocks = clk.summary()
     roofline = fp32_alu_roofline(torch, dev, w.n_sub, info["window_cells"], march_ms,
                                  march_traffic(args, prec, info["march_parts"], w.R, info["window_cells"]), clocks,
-                                 march_kernel_name(prec, info["march_parts"]))
+                                 march_kernel_name(prec, info["march_parts"]), probe)
+    roofline["smem"] = march_smem(N, w.n_sub, w.R, info["march_parts"], march_ms,
+                                  clocks.get("sm_mhz") or _peaks()[0].get("sm_max_mhz", 2070.0),
+                                  torch.cuda.get_device_properties(dev).multi_processor_count)
     if roofline["traffic"] is not None and args.traffic is None:
-        roofline["traffic_source"] = ("ncu capture of the 64^3 case (profiles/march_tm_R8_64c.md), DRAM bytes "
-                                      "scaled by window cells to this launch")
+        roofline["traffic_source"] = ("ncu capture of the 64^3 case of the same kernel, radius and storage, DRAM "
+                                      "bytes scaled by window cells to this launch")
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         t_src, threads, dt = oracle_sample(w, D_host, args.ref_sample)
+        t1, dt1 = oracle_single_thread(w, D_host, args.ref_sample_1t)
         cpu = {"value": 1.0 / (N * t_src), "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.ref_sample} seeded random sources of {w.name} ({dt:.1f} s of FP64 windowed marches "
                          f"on {threads} host threads); macro-steps/s = 1/(N * seconds per source), the oracle "
-                         "recomputing every kernel each step"}
+                         "recomputing every kernel each step",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": 1.0 / (N * t1), "cores": 1,
+                                 "sample": f"{args.ref_sample_1t} seeded random sources ({dt1:.1f} s)"}}
 
     n_launch = 4 + 1 + 2 + 2 * w.steps + 2      # conductance + 3 coef, march, mass(in), scale+gather per step, mass(out)
     if args.accum == "fp32":
@@ -564,6 +643,8 @@ def run_ours(args, w):
         "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": w.name, "grid": f"{w.n}^3", "R": w.R, "n_sub": w.n_sub, "macro_steps": w.steps,
                    "prec": prec, "accum": args.accum, "porosity": w.porosity,
+                   "mass": ("FP64 total restored to the input's after every macro step (FP32 row sums are not "
+                            "mass-neutral)" if args.accum == "fp32" else "float-float row sums; no restoration"),
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "march_threads_per_column": info["march_parts"],
                    "l2": f"inputs larger than L2 (kernel cache {info['cache_bytes'] / 1e9:.1f} GB, read every step)"},
@@ -572,7 +653,12 @@ def run_ours(args, w):
         "phase_ms": {"create": statistics.mean(t[0] for t in times), "kernels": statistics.mean(t[1] for t in times),
                      "march_kernel": march_ms, "steps": steps_ms, "gather_kernel": gather_ms},
         "mass_rel_err": abs(times[-1][6] - mass0) / mass0,
-        "roofline": roofline, "gather_roofline": gather_roofline(prec, args.accum, N, w.R, gather_ms),
+        "mass_restoration": ({"enforced_every_step": True, "pre_restoration_drift_max": info["last_restore_drift"],
+                              "note": "mass_rel_err is 0 by construction here; the drift is |M_in - S| / M_in of "
+                                      "the FP32-accumulated field before each step's restoration"}
+                             if args.accum == "fp32" else None),
+        "roofline": roofline, "gather_roofline": gather_roofline(prec, args.accum, N, w.R, gather_ms, probe),
+        "measured_peaks": probe,
         "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu_baseline": fp64,
         "gpu_launches": n_launch * args.steps, "clocks": clocks,
     }
@@ -897,9 +983,11 @@ def main(argv=None):
     ap.add_argument("--flow", action="store_true",
                     help="also time the convection path (steady face velocities folded into the march)")
     ap.add_argument("--ref-sample", type=int, default=32768, help="sources per oracle timing sample")
+    ap.add_argument("--ref-sample-1t", type=int, default=2048, help="sources of the single-thread oracle sample")
     ap.add_argument("--march-parts", type=int, default=0,
                     help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "
                          "lateral faces, 6 = source pairs in f32x2); 0 = autotune")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FP32 FMA and HBM read peak probes")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per march launch from an ncu capture of the current kernel")
     args = ap.parse_args(argv)

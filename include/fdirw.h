@@ -53,7 +53,7 @@ extern "C" {
 #define FDIRW_ERR_UNSTABLE -2   /* lam * max face-conductance sum > 1 (explicit march would not be stable) */
 #define FDIRW_ERR_NOMEM    -3   /* device allocation failed or would exceed opts.mem_limit */
 #define FDIRW_ERR_CUDA     -4   /* a CUDA runtime call failed (message has the CUDA error string) */
-#define FDIRW_ERR_TIMEOUT  -5   /* a bounded device-side wait gave up (the surrogate's MMA-completion waits) */
+#define FDIRW_ERR_TIMEOUT  -5   /* a bounded device-side wait gave up (the surrogate's MMA-completion waits, 2 s each) */
 #define FDIRW_ERR_STATE    -6   /* call not valid in the context's current state */
 
 /* Arithmetic of the path (Sec. 3.3: lower precision for the stored proportions, higher precision for
@@ -132,6 +132,9 @@ typedef struct {
                                     destination-indexed (radii on >= 20% of the cells), else source-indexed */
     int32_t  coarse_block;   /* coarse-mesh contexts: block side B (0 otherwise) */
     int64_t  coarse_nodes;   /* coarse-mesh contexts: representative nodes (blocks with liquid cells) */
+    double   last_restore_drift; /* FDIRW_ACCUM_FP32 on fdirw_create contexts: the largest |M_in - S| / |M_in|
+                                    over the macro steps of the last fdirw_step call, S the FP64 total of a
+                                    step's FP32-accumulated field before its mass restoration (0 otherwise) */
 } fdirw_info;
 
 typedef struct fdirw_ctx fdirw_ctx;
@@ -366,6 +369,33 @@ FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t
  * nullable) receives the number of accepted sources.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_NOMEM,
  * FDIRW_ERR_CUDA, FDIRW_ERR_TIMEOUT (a convolution's bounded wait on its MMAs gave up). */
 FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* ctx, fdirw_net* net, int64_t* accepted_out);
+/* Intermediate values of the network for n sources (1..1024), for checking it element by element
+ * against a reference implementation.  Volumes are [n][16 channels][17^3] with voxel v = i + 17 (j + 17 k)
+ * of the patch (offset (i-8, j-8, k-8)); BF16 values are returned as their 16-bit patterns.  All outputs
+ * are nullable and may be host or device memory.
+ *   acts_out  : [4][n][16][17^3] BF16: the input of each layer (layer 0's is the feature volume, layers
+ *               1..3 the relu outputs of the layer below), as the convolutions read them
+ *   z_out     : [n][17^3] float: the head's pre-exponential output z (channel 0 plus its bias)
+ *   targets   : nullable; with targets (n * 17^3 float64, host or device) the backward pass runs too:
+ *   grads_out : [4][n][16][17^3] BF16: entry l is the gradient of the loss of fdirw_net_gradients with
+ *               respect to layer l's output (for l < 3 after the relu mask), as the weight gradient reads it
+ *   grads_param_out : FDIRW_NET_NPARAM floats, the parameter gradients summed over the batch
+ *   loss_out  : the mean loss over the batch
+ * Synchronises the context stream; allocates one staging volume for the BF16 outputs.  Errors:
+ * FDIRW_ERR_ARG, FDIRW_ERR_STATE (the network gave up on running MMAs earlier), FDIRW_ERR_NOMEM,
+ * FDIRW_ERR_CUDA, FDIRW_ERR_TIMEOUT. */
+FDIRW_API int fdirw_net_trace(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                              const double* targets, uint16_t* acts_out, float* z_out, uint16_t* grads_out,
+                              float* grads_param_out, double* loss_out);
+/* Failure-injection hook for tests of the bounded wait.  Every convolution waits for its MMAs on an
+ * mbarrier for at most wait_ns nanoseconds of the GPU's global timer (0 restores the default, 2 s).  With
+ * withhold_mma != 0 the convolutions issue neither their MMAs nor the commit that completes the wait,
+ * so the first wait runs out with nothing in flight: the call returns FDIRW_ERR_TIMEOUT, the kernel has
+ * freed its tensor memory, and the network stays usable once the hook is cleared.  A wait that runs out
+ * while MMAs were issued is waited once more; if they still have not completed, the call returns
+ * FDIRW_ERR_TIMEOUT and every later call on this network returns FDIRW_ERR_STATE (the tensor memory it
+ * released may still be written).  Errors: FDIRW_ERR_ARG (NULL net). */
+FDIRW_API int fdirw_net_test_wait(fdirw_net* net, uint64_t wait_ns, int32_t withhold_mma);
 
 /* FP64 total of a device field without allocating any memory.  The paper has no counterpart: this is a
  * library service for callers that may not call cudaMalloc when they need the mass budget -- a host
@@ -373,7 +403,8 @@ FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* ctx, fdirw_net* net, int64_t* a
  * the synchronisation it can imply) is not allowed, or a caller that holds no fdirw context (creating one
  * allocates).  The reduction scratch is a fixed array compiled into the library: 2^14 FP64 partial sums
  * (128 KiB per GPU, held from the library's load until the process exits), one per chunk of 2^16 cells.
- *   c        : n float64 values in device memory of the current device (x fastest; any layout works)
+ *   c        : n float64 values in device memory of the current device (x fastest; any layout works);
+ *              may be NULL when n = 0 (the total written is then 0)
  *   n        : 0 <= n <= 2^30 (larger fields are rejected with FDIRW_ERR_ARG: they need more partials
  *              than the fixed scratch holds)
  *   mass_out : one float64 in device memory of the current device; receives the total
@@ -386,6 +417,16 @@ FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* ctx, fdirw_net* net, int64_t* a
  * Errors: FDIRW_ERR_ARG (n out of range, NULL, misaligned or non-device pointers), FDIRW_ERR_CUDA; the
  * message is available from fdirw_last_error(NULL). */
 FDIRW_API int fdirw_mass_noalloc(const double* c, int64_t n, double* mass_out, void* stream);
+
+/* Peaks of a GPU for roofline reports (no counterpart in the paper; a measuring service beside the method).
+ *   device           : CUDA device (-1 = current); the current device is restored afterwards
+ *   fp32_flops       : host, nullable: FP32 flop/s of a register-only loop of independent FMAs (2 flop
+ *                      each) over 4 blocks of 512 threads per SM, best of three timed runs after one warm-up
+ *   read_bytes_per_s : host, nullable: bytes/s of a streaming read (16-byte loads, four in flight per
+ *                      thread) of a 4 GiB device buffer, larger than L2, best of three after one warm-up
+ * Allocates and frees the 4 GiB buffer; synchronises the device.  Errors: FDIRW_ERR_NOMEM, FDIRW_ERR_CUDA;
+ * the message is available from fdirw_last_error(NULL). */
+FDIRW_API int fdirw_probe_peaks(int32_t device, double* fp32_flops, double* read_bytes_per_s);
 
 #ifdef __cplusplus
 }

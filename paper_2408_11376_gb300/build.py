@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfdirw.so")
-SOURCES = ["api.cu", "setup.cu", "march.cu", "superpose.cu", "surrogate.cu", "noalloc.cu", "batch.cu", "coarse.cu", "flow.cu"]
+SOURCES = ["api.cu", "setup.cu", "march.cu", "superpose.cu", "surrogate.cu", "noalloc.cu", "batch.cu", "coarse.cu", "flow.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

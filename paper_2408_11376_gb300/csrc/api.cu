@@ -226,7 +226,10 @@ int fdirw::step_slabs(fdirw_ctx* c, const double* src, double* dst, int n_steps)
     const int64_t nxy = (int64_t)c->g.nx * c->g.ny;
     const bool fp32acc = c->accum == FDIRW_ACCUM_FP32;
     const int mode = c->store == Store::F64 ? 0 : fp32acc ? 2 : 1;
-    if (fp32acc) FDIRW_CUDA(c, fdirw::launch_mass(src, c->g.n, c->partials, c->dfix, c->stream));
+    if (fp32acc) {
+        FDIRW_CUDA(c, fdirw::launch_mass(src, c->g.n, c->partials, c->dfix, c->stream));
+        FDIRW_CUDA(c, cudaMemsetAsync(c->dfix + 2, 0, 8, c->stream));
+    }
     MarchArgs a = march_args(c);
     a.q_stride = (int64_t)T * nxy;
     const double* cur = src;
@@ -372,7 +375,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->cbuf), n * 8, "field staging")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->partials), 2 * fdirw::kMassBlocks * 8, "mass partials")) != FDIRW_OK) return bail(rc);
     if ((rc = dalloc(c, reinterpret_cast<void**>(&c->dmass), 8, "mass")) != FDIRW_OK) return bail(rc);
-    if ((rc = dalloc(c, reinterpret_cast<void**>(&c->dfix), 16, "mass restoration")) != FDIRW_OK) return bail(rc);
+    if ((rc = dalloc(c, reinterpret_cast<void**>(&c->dfix), 24, "mass restoration")) != FDIRW_OK) return bail(rc);
     cudaError_t e = cudaMemsetAsync(c->chat, 0, (size_t)pad.n * 8, c->stream);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&c->ev[i]);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -437,7 +440,10 @@ int fdirw_step(fdirw_ctx* c, const double* c_in, double* c_out, int32_t n_steps,
         const bool fp32acc = c->accum == FDIRW_ACCUM_FP32;
         const int mode = c->store == Store::F64 ? 0 : fp32acc ? 2 : 1;
         // FDIRW_ACCUM_FP32: the FP64 total of the call's input, the target of every step's restoration.
-        if (fp32acc) FDIRW_CUDA(c, fdirw::launch_mass(src, c->g.n, c->partials, c->dfix, c->stream));
+        if (fp32acc) {
+            FDIRW_CUDA(c, fdirw::launch_mass(src, c->g.n, c->partials, c->dfix, c->stream));
+            FDIRW_CUDA(c, cudaMemsetAsync(c->dfix + 2, 0, 8, c->stream));
+        }
         const double* cur = src;
         for (int t = 0; t < n_steps; t++) {
             FDIRW_CUDA(c, fdirw::launch_scale(cur, c->sigma, c->g, c->R, c->chat, mode, c->stream));
@@ -554,6 +560,10 @@ int fdirw_get_info(fdirw_ctx* c, fdirw_info* out) {
     }
     if (c->batch) return fdirw::batch_info(c, out);
     if (c->coarse) return fdirw::coarse_info(c, out);
+    if (c->accum == FDIRW_ACCUM_FP32 && c->dfix) {
+        FDIRW_CUDA(c, cudaMemcpyAsync(&out->last_restore_drift, c->dfix + 2, 8, cudaMemcpyDeviceToHost, c->stream));
+        FDIRW_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     out->n_chunks = c->slab_T ? (c->g.nz + c->slab_T - 1) / c->slab_T : 1;   // z-slabs of a streamed cache
     return FDIRW_OK;
 }

@@ -36,7 +36,7 @@ struct fdirw_ctx {
     double* cbuf = nullptr;                         // staging for host fields
     double* partials = nullptr;                     // 2 * kMassBlocks
     double* dmass = nullptr;                        // 1 double
-    double* dfix = nullptr;                         // FDIRW_ACCUM_FP32: [M_in, f] of the mass restoration
+    double* dfix = nullptr;                         // FDIRW_ACCUM_FP32: [M_in, f, max drift] of the mass restoration
     int slab_T = 0;                                 // > 0: the cache holds slab_T destination z-planes (streamed)
     double* obuf = nullptr;                         // streamed steps: output of the step being computed
     int accum = 0;                                  // fdirw_accum

@@ -79,7 +79,8 @@ extern "C" FDIRW_API int fdirw_mass_noalloc(const double* c, int64_t n, double* 
     if (n < 0 || n > (int64_t)kMaxChunks * kChunk)
         return fdirw::set_thread_error(FDIRW_ERR_ARG, "fdirw_mass_noalloc: n = " + std::to_string(n) +
                                                           " is outside [0, 2^30], the capacity of its fixed scratch");
-    if (!c || !mass_out) return fdirw::set_thread_error(FDIRW_ERR_ARG, "fdirw_mass_noalloc: NULL c or mass_out");
+    if ((!c && n > 0) || !mass_out)
+        return fdirw::set_thread_error(FDIRW_ERR_ARG, "fdirw_mass_noalloc: NULL c or mass_out");
     if (((reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(mass_out)) & 7u) != 0)
         return fdirw::set_thread_error(FDIRW_ERR_ARG, "fdirw_mass_noalloc: c and mass_out must be 8-byte aligned");
     int dev = 0;
@@ -107,8 +108,13 @@ extern "C" FDIRW_API int fdirw_mass_noalloc(const double* c, int64_t n, double* 
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int nb = (int)((n + kChunk - 1) / kChunk);
-    if (nb > 0) chunk_sum_kernel<<<nb, 256, 0, st>>>(c, n, scratch);
-    e = cudaGetLastError();
+    // The launch status is read right after each launch that was issued (an empty field launches only the
+    // final kernel, which writes 0), so an earlier call's error left on this thread is not reported here.
+    e = cudaSuccess;
+    if (nb > 0) {
+        chunk_sum_kernel<<<nb, 256, 0, st>>>(c, n, scratch);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         partials_sum_kernel<<<1, kFinalThreads, 0, st>>>(scratch, nb, mass_out);
         e = cudaGetLastError();

@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(256) mass_abs_partial_kernel(const double* __r
     }
 }
 
-// Pass 2: one block sums both partial sets and writes f = (m_in - S) / A into fix[1] (0 when A = 0).
+// Pass 2: one block sums both partial sets and writes f = (m_in - S) / A into fix[1] (0 when A = 0) and
+// the running maximum of |m_in - S| / |m_in| into fix[2].
 __global__ void __launch_bounds__(kMassBlocks) mass_fix_kernel(const double* __restrict__ partials,
                                                                double* __restrict__ fix) {
     __shared__ double sh[2][kMassBlocks / 32];
@@ -320,7 +321,11 @@ __global__ void __launch_bounds__(kMassBlocks) mass_fix_kernel(const double* __r
             S += __shfl_xor_sync(0xffffffffu, S, off);
             A += __shfl_xor_sync(0xffffffffu, A, off);
         }
-        if (threadIdx.x == 0) fix[1] = A > 0.0 ? (fix[0] - S) / A : 0.0;
+        if (threadIdx.x == 0) {
+            fix[1] = A > 0.0 ? (fix[0] - S) / A : 0.0;
+            // largest relative drift of the FP32-accumulated totals before restoration since fix[2] was reset
+            if (fix[0] != 0.0) fix[2] = fmax(fix[2], fabs(fix[0] - S) / fabs(fix[0]));
+        }
     }
 }
 

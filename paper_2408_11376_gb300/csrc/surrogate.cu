@@ -20,7 +20,9 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -40,7 +42,7 @@ constexpr int NPARAM = NW + NL * C;                                // + biases [
 constexpr int WCAN = TAPS * C * C;                                 // bf16 per layer, canonical layout
 constexpr int MAX_BATCH = 1024;
 constexpr size_t CONV_SMEM = (size_t)2 * RROWS * 16 + (size_t)TAPS * 512 + 16;
-constexpr uint32_t WAIT_LIMIT = 1u << 26;                          // mbarrier polls before giving up
+constexpr uint64_t WAIT_NS = 2000000000ull;                        // default MMA-wait budget: 2 s
 constexpr double GATE_TOL = 1e-3;
 
 enum Mode { FWD_RELU = 0, FWD_HEAD = 1, DGRAD = 2 };
@@ -54,7 +56,9 @@ struct ConvArgs {
     const float* bias;              // [C]
     int batch;
     int mode;
-    int* err;
+    int* err;                       // 1: a wait gave up with nothing left in flight; 2: MMAs may still run
+    uint64_t wait_ns;               // budget of each wait on the MMAs
+    int hold;                       // test hook: issue no MMA and no commit, so the first wait runs out
 };
 
 __device__ __forceinline__ uint4 pack8(const float* v) {
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
             load_plane(z + 1);
             tc::fence_async_smem();
             __syncthreads();
-            if (t == 0) {
+            if (t == 0 && !a.hold) {
                 tc::fence_after_sync();
 #pragma unroll 1
                 for (int tile = 0; tile < NTILE; tile++) {
@@ -131,13 +135,18 @@ __global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
                 }
                 tc::mma_commit(mb);
             }
-            bool done = tc::mbar_wait(mb, phase, WAIT_LIMIT);
-            phase ^= 1u;
+            const bool done = tc::mbar_wait(mb, phase, a.wait_ns);
             ok = __syncthreads_and(done ? 1 : 0) != 0;
             if (!ok) {
-                if (t == 0) atomicExch(a.err, 1);
+                // MMAs issued for this plane may still be writing the accumulator: wait for them once
+                // more (bounded) before the TMEM is freed.  If they still have not completed, the TMEM
+                // freed below may be overwritten after its release, which the host reports as err 2.
+                bool drained = a.hold != 0;
+                if (!drained) drained = __syncthreads_and(tc::mbar_wait(mb, phase, a.wait_ns) ? 1 : 0) != 0;
+                if (t == 0) atomicMax(a.err, drained ? 1 : 2);
                 break;
             }
+            phase ^= 1u;
             tc::fence_after_sync();
 #pragma unroll 1
             for (int tile = 0; tile < NTILE; tile++) {
@@ -408,6 +417,18 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float*
     p[e] -= lr * (mm / (1.f - b1t)) / (sqrtf(vv / (1.f - b2t)) + 1e-8f);
 }
 
+// Unpacks a batch of activation or gradient volumes ([n][2 halves][ROWS][8] BF16, zero halo) into
+// [n][C][KV] BF16 bit patterns, voxel v = i + 17 (j + 17 k) of the patch.
+__global__ void unpack_kernel(const __nv_bfloat16* __restrict__ src, int n, uint16_t* __restrict__ dst) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * C * KV;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / (C * KV)), c = (int)((idx / KV) % C), v = (int)(idx % KV);
+        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
+        const int64_t half = c < 8 ? 0 : ROWS;
+        dst[idx] = __bfloat16_as_ushort(src[(int64_t)b * PATCH + (half + prow(i, j, k)) * 8 + (c & 7)]);
+    }
+}
+
 }  // namespace net
 }  // namespace fdirw
 
@@ -435,6 +456,9 @@ struct fdirw_net {
     float* partial = nullptr;
     float* grads = nullptr;
     int* derr = nullptr;
+    uint64_t wait_ns = WAIT_NS;    // budget of each MMA wait (fdirw_net_test_wait)
+    int hold = 0;                  // test hook: convolutions withhold their MMAs (fdirw_net_test_wait)
+    bool failed = false;           // a wait gave up while MMAs may still have been running
     std::string err;
 };
 
@@ -479,7 +503,7 @@ int ensure_capacity(fdirw_net* net, int n) {
 
 int launch_conv(fdirw_net* net, cudaStream_t st, int num_sms, const __nv_bfloat16* in, __nv_bfloat16* out,
                 float* zhead, const __nv_bfloat16* mask, const __nv_bfloat16* w, const float* bias, int n, int mode) {
-    ConvArgs a{in, out, zhead, mask, w, bias, n, mode, net->derr};
+    ConvArgs a{in, out, zhead, mask, w, bias, n, mode, net->derr, net->wait_ns, net->hold};
     NET_CUDA(net, cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CONV_SMEM));
     const int grid = n < num_sms * 3 ? n : num_sms * 3;
     conv_kernel<<<grid, 128, CONV_SMEM, st>>>(a);
@@ -512,8 +536,22 @@ int check_err(fdirw_net* net, cudaStream_t st) {
     NET_CUDA(net, cudaStreamSynchronize(st));
     if (h) {
         cudaMemsetAsync(net->derr, 0, 4, st);
+        if (h >= 2) {
+            net->failed = true;
+            return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core convolution gave up on MMAs that had not completed "
+                                                 "after two waits; the network refuses further calls");
+        }
         return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
     }
+    return FDIRW_OK;
+}
+
+// Calls on a network whose convolution gave up on running MMAs are refused: the tensor memory it
+// released may still be written by them.
+int usable(fdirw_net* net) {
+    if (net && net->failed)
+        return nfail(net, FDIRW_ERR_STATE, "this network's convolution gave up on MMAs that may still be running; "
+                                           "destroy it (and, to be safe, the CUDA context)");
     return FDIRW_OK;
 }
 
@@ -527,11 +565,19 @@ int upload_sources(fdirw_ctx* c, fdirw_net* net, const int64_t* sources, int64_t
     return FDIRW_OK;
 }
 
+// Receives the gradient with respect to layer l's output (its pre-activation; masked by the relu) before
+// layer l's weight gradient is formed.
+using GradHook = std::function<int(int, const __nv_bfloat16*)>;
+
 // Backward through the 4 layers into net->grads (sum over the batch); the head gradient is in gbuf[0].
-int backward(fdirw_ctx* c, fdirw_net* net, int n) {
+int backward(fdirw_ctx* c, fdirw_net* net, int n, const GradHook* hook = nullptr) {
     cudaStream_t st = c->stream;
     int cur = 0;
     for (int l = NL - 1; l >= 0; l--) {
+        if (hook) {
+            const int rc = (*hook)(l, net->gbuf[cur]);
+            if (rc != FDIRW_OK) return rc;
+        }
         wgrad_partial_kernel<<<dim3(TAPS, WG_BLOCKS), 256, 0, st>>>(net->act[l], net->gbuf[cur], n, net->partial);
         NET_CUDA(net, cudaGetLastError());
         wgrad_reduce_kernel<<<(TAPS * C * C + 255) / 256, 256, 0, st>>>(net->partial, net->grads + (size_t)l * TAPS * C * C);
@@ -549,7 +595,7 @@ int backward(fdirw_ctx* c, fdirw_net* net, int n) {
 }
 
 int gradients(fdirw_ctx* c, fdirw_net* net, const int64_t* sources, int64_t n, const double* targets,
-              double* loss_out) {
+              double* loss_out, const GradHook* hook = nullptr) {
     int rc = upload_sources(c, net, sources, n);
     if (rc != FDIRW_OK) return rc;
     NET_CUDA(net, cudaMemcpyAsync(net->dtgt, targets, (size_t)n * KV * 8, cudaMemcpyDefault, c->stream));
@@ -557,7 +603,7 @@ int gradients(fdirw_ctx* c, fdirw_net* net, const int64_t* sources, int64_t n, c
     NET_CUDA(net, cudaMemsetAsync(net->gbuf[0], 0, (size_t)n * PATCH * 2, c->stream));
     head_train_kernel<<<(int)n, 256, 0, c->stream>>>(net->zhead, c->g, net->dsrc, net->dtgt, net->gbuf[0], net->dloss);
     NET_CUDA(net, cudaGetLastError());
-    if ((rc = backward(c, net, (int)n)) != FDIRW_OK) return rc;
+    if ((rc = backward(c, net, (int)n, hook)) != FDIRW_OK) return rc;
     std::vector<double> lv((size_t)n);
     NET_CUDA(net, cudaMemcpyAsync(lv.data(), net->dloss, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
     if ((rc = check_err(net, c->stream)) != FDIRW_OK) return rc;
@@ -623,6 +669,7 @@ FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* s
                                 double* kernels_out, double* mass_out, int32_t* accept_out) {
     if (!ctx || !net || (n > 0 && !sources)) return nfail(net, FDIRW_ERR_ARG, "NULL ctx, net or sources");
     if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (const int u = usable(net); u != FDIRW_OK) return u;
     if (n == 0) return FDIRW_OK;
     int rc = upload_sources(ctx, net, sources, n);
     if (rc != FDIRW_OK) return rc;
@@ -639,6 +686,7 @@ FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t*
                                   const double* targets, float* grads_out, double* loss_out) {
     if (!ctx || !net || n <= 0 || !sources || !targets) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
     if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (const int u = usable(net); u != FDIRW_OK) return u;
     int rc = gradients(ctx, net, sources, n, targets, loss_out);
     if (rc != FDIRW_OK) return rc;
     if (grads_out) NET_CUDA(net, cudaMemcpy(grads_out, net->grads, NPARAM * 4, cudaMemcpyDeviceToHost));
@@ -649,6 +697,7 @@ FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t
                                    const double* targets, float lr, double* loss_out) {
     if (!ctx || !net || n <= 0 || !sources || !targets || !(lr > 0.f)) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
     if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (const int u = usable(net); u != FDIRW_OK) return u;
     int rc = gradients(ctx, net, sources, n, targets, loss_out);
     if (rc != FDIRW_OK) return rc;
     net->step++;
@@ -661,9 +710,64 @@ FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t
     return FDIRW_OK;
 }
 
+FDIRW_API int fdirw_net_test_wait(fdirw_net* net, uint64_t wait_ns, int32_t withhold_mma) {
+    if (!net) return nfail(net, FDIRW_ERR_ARG, "NULL net");
+    net->wait_ns = wait_ns ? wait_ns : WAIT_NS;
+    net->hold = withhold_mma ? 1 : 0;
+    return FDIRW_OK;
+}
+
+FDIRW_API int fdirw_net_trace(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
+                              const double* targets, uint16_t* acts_out, float* z_out, uint16_t* grads_out,
+                              float* grads_param_out, double* loss_out) {
+    if (!ctx || !net || n <= 0 || !sources) return nfail(net, FDIRW_ERR_ARG, "bad arguments");
+    if (grads_out && !targets) return nfail(net, FDIRW_ERR_ARG, "gradient buffers need targets");
+    if (ctx->batch || ctx->coarse) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves fdirw_create contexts only");
+    if (const int u = usable(net); u != FDIRW_OK) return u;
+    cudaStream_t st = ctx->stream;
+    const size_t vol = (size_t)n * C * KV;      // BF16 values of one traced volume set
+    uint16_t* stage = nullptr;
+    if (acts_out || grads_out) NET_CUDA(net, cudaMalloc(&stage, vol * 2));
+    const int ub = (int)std::min<int64_t>(((int64_t)vol + 255) / 256, 152 * 16);
+    auto dump = [&](const __nv_bfloat16* src, uint16_t* dst) -> int {
+        unpack_kernel<<<ub, 256, 0, st>>>(src, (int)n, stage);
+        NET_CUDA(net, cudaGetLastError());
+        NET_CUDA(net, cudaMemcpyAsync(dst, stage, vol * 2, cudaMemcpyDefault, st));
+        return FDIRW_OK;
+    };
+    int rc = FDIRW_OK;
+    if (targets) {
+        GradHook hook = [&](int l, const __nv_bfloat16* g) -> int {
+            if (l == NL - 1) {          // the forward pass is complete here
+                if (acts_out)
+                    for (int a = 0; a < NL; a++)
+                        if (const int r = dump(net->act[a], acts_out + (size_t)a * vol); r != FDIRW_OK) return r;
+                if (z_out) NET_CUDA(net, cudaMemcpyAsync(z_out, net->zhead, (size_t)n * KV * 4, cudaMemcpyDefault, st));
+            }
+            return grads_out ? dump(g, grads_out + (size_t)l * vol) : FDIRW_OK;
+        };
+        rc = gradients(ctx, net, sources, n, targets, loss_out, &hook);
+        if (rc == FDIRW_OK && grads_param_out)
+            rc = cudaMemcpy(grads_param_out, net->grads, NPARAM * 4, cudaMemcpyDefault) == cudaSuccess
+                     ? FDIRW_OK : nfail(net, FDIRW_ERR_CUDA, "copying the parameter gradients");
+    } else {
+        rc = upload_sources(ctx, net, sources, n);
+        if (rc == FDIRW_OK) rc = forward(ctx, net, (int)n);
+        if (rc == FDIRW_OK && acts_out)
+            for (int a = 0; a < NL && rc == FDIRW_OK; a++) rc = dump(net->act[a], acts_out + (size_t)a * vol);
+        if (rc == FDIRW_OK && z_out && cudaMemcpyAsync(z_out, net->zhead, (size_t)n * KV * 4, cudaMemcpyDefault, st) != cudaSuccess)
+            rc = nfail(net, FDIRW_ERR_CUDA, "copying the head");
+        if (rc == FDIRW_OK) rc = check_err(net, st);
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(stage);
+    return rc;
+}
+
 FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* c, fdirw_net* net, int64_t* accepted_out) {
     if (!c || !net) return nfail(net, FDIRW_ERR_ARG, "NULL ctx or net");
     if (c->batch || c->coarse || c->flow) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves diffusion-only fdirw_create contexts");
+    if (const int u = usable(net); u != FDIRW_OK) return u;
     if (c->R != SH) return nfail(net, FDIRW_ERR_ARG, "the surrogate predicts 17^3 kernels: window_R must be 8");
     if (c->store == Store::F64) return nfail(net, FDIRW_ERR_ARG, "the surrogate serves the FP32-march precisions only");
     {

@@ -41,17 +41,26 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar_saddr, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar_saddr), "r"(count) : "memory");
 }
 
-// Bounded wait on an mbarrier phase: returns false if it did not complete within max_iters polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint32_t max_iters) {
-    for (uint32_t i = 0; i < max_iters; i++) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: returns false if it did not complete within budget_ns nanoseconds
+// of the GPU's global timer (each try_wait may itself suspend the thread for a short, system-defined
+// time, so the budget is checked between polls).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint64_t budget_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         uint32_t done = 0;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done) : "r"(mbar_saddr), "r"(parity) : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > budget_ns) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

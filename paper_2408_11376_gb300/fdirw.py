@@ -36,7 +36,8 @@ EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "f
             "fdirw_net_params", "fdirw_net_destroy", "fdirw_net_predict", "fdirw_net_gradients", "fdirw_net_train_step",
             "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius", "fdirw_create_coarse",
             "fdirw_read_coarse", "fdirw_coarse_far_field", "fdirw_coarse_get_far_field", "fdirw_read_coarse_pbc",
-            "fdirw_coupled_step", "fdirw_set_velocity")
+            "fdirw_coupled_step", "fdirw_set_velocity", "fdirw_net_trace", "fdirw_net_test_wait",
+            "fdirw_probe_peaks")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -74,7 +75,8 @@ class fdirw_info(ctypes.Structure):
                 ("march_parts", ctypes.c_int32), ("accum", ctypes.c_int32),
                 ("n_structures", ctypes.c_int32), ("n_chunks", ctypes.c_int32), ("window_R_min", ctypes.c_int32),
                 ("graph_launches", ctypes.c_int32), ("dest_indexed_radii", ctypes.c_int32),
-                ("coarse_block", ctypes.c_int32), ("coarse_nodes", ctypes.c_int64)]
+                ("coarse_block", ctypes.c_int32), ("coarse_nodes", ctypes.c_int64),
+                ("last_restore_drift", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -117,6 +119,9 @@ def load(path: str | None = None):
         lib.fdirw_net_gradients.argtypes = [vp, vp, vp, i64, vp, vp, dp]
         lib.fdirw_net_train_step.argtypes = [vp, vp, vp, i64, vp, ctypes.c_float, dp]
         lib.fdirw_kernels_surrogate.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        lib.fdirw_net_trace.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, dp]
+        lib.fdirw_net_test_wait.argtypes = [vp, ctypes.c_uint64, i32]
+        lib.fdirw_probe_peaks.argtypes = [i32, dp, dp]
         lib.fdirw_create_batch.argtypes = [i32, ctypes.POINTER(fdirw_grid), ctypes.POINTER(vp), ctypes.c_double, i32,
                                            i32, i32, ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
         lib.fdirw_read_radius.argtypes = [vp, vp]
@@ -301,6 +306,13 @@ def fdirw_get_info(ctx: int) -> dict:
 def fdirw_destroy(ctx: int) -> None:
     if ctx:
         load().fdirw_destroy(ctypes.c_void_p(ctx))
+
+
+def fdirw_probe_peaks(device: int = -1) -> dict:
+    """Measured FP32 FMA rate (flop/s) and streaming HBM read bandwidth (bytes/s) of a GPU."""
+    f, r = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().fdirw_probe_peaks(int(device), ctypes.byref(f), ctypes.byref(r)))
+    return {"fp32_flops": f.value, "read_bytes_per_s": r.value}
 
 
 def fdirw_mass_noalloc(c, mass_out, stream=None) -> None:
@@ -501,6 +513,31 @@ class Net:
                                            src.size, ctypes.c_void_p(_ptr(t)), float(lr), ctypes.byref(loss)),
                ctypes.c_void_p(ctx))
         return loss.value
+
+    def trace(self, ctx: int, sources, targets=None):
+        """fdirw_net_trace: (acts [4, n, 16, 17^3] uint16 BF16 patterns, z [n, 17^3] float32, grads
+        [4, n, 16, 17^3] uint16 or None, parameter gradients [NET_NPARAM] float32 or None, mean loss or None)."""
+        src = self._src(sources)
+        n = src.size
+        acts = np.empty((4, n, 16, 17 ** 3), dtype=np.uint16)
+        z = np.empty((n, 17 ** 3), dtype=np.float32)
+        grads = pg = t = None
+        loss = ctypes.c_double(0.0)
+        if targets is not None:
+            t = np.ascontiguousarray(targets, dtype=np.float64)
+            grads = np.empty((4, n, 16, 17 ** 3), dtype=np.uint16)
+            pg = np.empty(NET_NPARAM, dtype=np.float32)
+        _check(load().fdirw_net_trace(ctypes.c_void_p(ctx), ctypes.c_void_p(self.h), ctypes.c_void_p(src.ctypes.data), n,
+                                      ctypes.c_void_p(t.ctypes.data if t is not None else 0),
+                                      ctypes.c_void_p(acts.ctypes.data), ctypes.c_void_p(z.ctypes.data),
+                                      ctypes.c_void_p(grads.ctypes.data if grads is not None else 0),
+                                      ctypes.c_void_p(pg.ctypes.data if pg is not None else 0),
+                                      ctypes.byref(loss) if t is not None else None), ctypes.c_void_p(ctx))
+        return acts, z, grads, pg, (loss.value if t is not None else None)
+
+    def test_wait(self, wait_ns: int = 0, withhold_mma: bool = False) -> None:
+        """fdirw_net_test_wait: the MMA-wait budget (0 = default) and the withhold-MMA test hook."""
+        _check(load().fdirw_net_test_wait(ctypes.c_void_p(self.h), int(wait_ns), 1 if withhold_mma else 0))
 
     def build_kernels(self, ctx: int) -> int:
         """fdirw_kernels_surrogate: returns the number of accepted sources."""

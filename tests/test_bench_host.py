@@ -50,7 +50,7 @@ def test_reference_arm_prints_one_contract_line(capsys, monkeypatch):
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
     assert bench.main(["--impl", "reference", "--workload", "fdirw-32c-r3", "--steps", "2", "--warmup", "1",
-                       "--ref-sample", "64"]) == 0
+                       "--ref-sample", "64", "--ref-sample-1t", "16"]) == 0
     lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -64,6 +64,12 @@ def test_reference_arm_prints_one_contract_line(capsys, monkeypatch):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and "64 seeded random sources" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the line says that it extrapolates a timed sample, and gives the single-thread rate and the CPU model
+    assert d["timing"]["kind"] == "sample-extrapolated" and d["timing"]["sources_per_step"] == 64
+    assert d["timing"]["timed_ms_per_step"] == pytest.approx(d["ms_per_step"] * 64 / 32 ** 3, rel=1e-9)
+    st = d["cpu_baseline"]["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and "16 seeded random sources" in st["sample"]
+    assert isinstance(d["cpu_baseline"]["cpu_model"], str) and d["cpu_baseline"]["cpu_model"]
 
 
 def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):

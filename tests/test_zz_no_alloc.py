@@ -40,6 +40,10 @@ def test_mass_noalloc_matches_fdirw_mass_on_consecutive_calls():
     fdirw.fdirw_mass_noalloc(small, out)
     torch.cuda.synchronize()
     assert abs(float(out.item()) - float(small.sum().item())) <= 1e-12 * float(small.sum().item())
+    # an empty field: only the final kernel runs, and it writes 0
+    fdirw.fdirw_mass_noalloc(fields[0][:0], out)
+    torch.cuda.synchronize()
+    assert float(out.item()) == 0.0
 
 
 def test_mass_noalloc_rejects_what_it_cannot_serve():
