@@ -606,9 +606,9 @@ def run_ours(args, w):
             pg.destroy_process_group()
         return 0
 
-    fp64 = None
+    fp64, ref64 = None, None
     if not args.no_fp64 and ws == 1:
-        fp64 = fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec=prec)
+        fp64, ref64 = fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec=prec)
 
     clocks = clk.summary()
     roofline = fp32_alu_roofline(torch, dev, w.n_sub, info["window_cells"], march_ms,
@@ -665,7 +665,7 @@ def run_ours(args, w):
     if fp64:
         line["speedup_vs_fp64_gpu"] = value / fp64["macro_steps_per_s"]
     if args.surrogate:
-        line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec)
+        line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec, ref64)
     if args.coarse:
         line["coarse_mesh"] = coarse_leg(args, fdirw, torch, dev, stream, w, shape, D, ~packing.solid, dt_macro)
     if args.flow:
@@ -678,10 +678,13 @@ def run_ours(args, w):
     return 0
 
 
-def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec):
+def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec, ref64=None):
     """Learned surrogate: trains on FD kernels of seeded packings (porosity U[0.3,0.5], per-sphere log10
     ratio U[3,8]; 200k kernels by default), then builds the workload's kernel cache with the gate and FD
-    fallback and compares it with the FD-only build (time, acceptance, kernel and field error)."""
+    fallback and compares it with the FD-only build: build times, the network's convolution time and
+    tensor-core rate, per-source costs and the acceptance that would make the gated build break even,
+    acceptance of solid and pore sources, the error of accepted kernels against FD, and the field after
+    the workload's macro steps against the FD-only field and the plain FP64 field."""
     from paper_2408_11376_gb300 import surrogate as sg
     t0 = time.perf_counter()
     data = sg.training_set(args.surrogate_structures, args.surrogate_per_structure, 20240825, n_sub=w.n_sub)
@@ -698,6 +701,7 @@ def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, pr
     del data
     torch.cuda.empty_cache()
     N = c0.numel()
+    solid = (D < 0.5).cpu().numpy()
     rng = np.random.default_rng(5)
     probe = np.sort(rng.integers(0, N, 4096))
     res = {}
@@ -712,26 +716,56 @@ def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, pr
             acc = f.kernels() if mode == "fd" else net.build_kernels(f.ctx)
             e1.record(stream)
             stream.synchronize()
+            info = fdirw.fdirw_get_info(f.ctx)
             out = torch.empty_like(c0)
             mass = f.step(c0, out, w.steps, want_mass=True)
             k = f.read_kernels(probe)
+            if mode == "surrogate":
+                # the network's own rate: forward passes of 1024 sources, convolutions timed on the device
+                src = rng.integers(0, N, 1024)
+                net.predict(f.ctx, src)
+                net.predict(f.ctx, src)
+                conv_ms = net.conv_ms()
+                # acceptance by phase on 16 batches of random sources
+                samp = rng.integers(0, N, 16 * 1024)
+                accs = np.concatenate([net.predict(f.ctx, samp[i:i + 1024])[2] for i in range(0, samp.size, 1024)])
             f.close()
         res[mode] = {"build_ms": e0.elapsed_time(e1), "accepted": acc if mode == "surrogate" else None,
-                     "field": out, "mass": mass, "kernels": k}
+                     "field": out, "mass": mass, "kernels": k, "march_ms": info["kernels_ms"]}
     sgm, fd = res["surrogate"], res["fd"]
     kd = np.linalg.norm((sgm["kernels"] - fd["kernels"]).reshape(len(probe), -1), axis=1)
     kn = np.linalg.norm(fd["kernels"].reshape(len(probe), -1), axis=1)
     changed = kd > 0
     mass0 = float(c0.sum().item())
+    peaks, peak_src = _peaks()
+    mma_flops = 1024 * 4 * 17 * 81 * 2 * 128 * 16 * 16      # 4 layers x 17 planes x 81 MMAs of 128 x 16 x 16
+    useful = 27 * 2 * (7 * 16 + 16 * 16 + 16 * 16 + 16 * 1) * 17 ** 3
+    net_us = conv_ms * 1e3 / 1024
+    fd_us = fd["march_ms"] * 1e3 / N
+    sa = solid[samp]
     out = {"training_kernels": n_train, "epochs": args.surrogate_epochs, "loss_per_epoch": hist,
            "data_gen_s": t_data, "train_s": t_train, "train_samples_per_s": n_train * len(hist) / t_train,
            "fd_build_ms": fd["build_ms"], "surrogate_build_ms": sgm["build_ms"],
            "gain_build": fd["build_ms"] / sgm["build_ms"],
            "accepted_fraction": sgm["accepted"] / N,
-           "probe_accepted_kernel_rel_l2_max": float((kd / kn)[changed].max()) if changed.any() else 0.0,
+           "accepted_fraction_sample": {"solid": float(accs[sa].mean()) if sa.any() else None,
+                                        "pore": float(accs[~sa].mean()) if (~sa).any() else None,
+                                        "sources": int(samp.size)},
+           "tensor": {"conv_ms_per_1024_sources": conv_ms, "mma_flops": mma_flops,
+                      "achieved_tflops": mma_flops / (conv_ms * 1e-3) / 1e12,
+                      "peak": peaks["bf16_tflops"], "frac": mma_flops / (conv_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                      "peak_source": f"bf16_tflops ({peak_src})",
+                      "useful_flops_per_source": useful},
+           "per_source_us": {"fd_march": fd_us, "net_convolutions": net_us},
+           "break_even_acceptance": net_us / fd_us,
+           "probe_accepted_kernel_rel_l2": ({"max": float((kd / kn)[changed].max()), "median": float(np.median((kd / kn)[changed])),
+                                             "n": int(changed.sum())} if changed.any() else None),
            "field_rel_l2_vs_fd_after_steps": float((torch.linalg.vector_norm(sgm["field"] - fd["field"]) /
                                                      torch.linalg.vector_norm(fd["field"])).item()),
            "mass_rel_err": abs(sgm["mass"] - mass0) / mass0}
+    if ref64 is not None:
+        out["field_rel_l2_vs_fp64_after_steps"] = float((torch.linalg.vector_norm(sgm["field"] - ref64) /
+                                                          torch.linalg.vector_norm(ref64)).item())
     net.close()
     return out
 
@@ -951,9 +985,10 @@ def fp64_leg(fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, value_prec):
             fdirw.fdirw_destroy(ctx)
         out["rel_l2_vs_fp64"][p if acc == "ff" else p + "_fp32acc"] = {
             "max_over_steps": max(errs), "last": errs[-1], "mass_rel_err": abs(m - mass0) / mass0}
+    last = ref[-1].clone()
     del ref
     torch.cuda.empty_cache()
-    return out
+    return out, last
 
 
 def main(argv=None):

@@ -333,7 +333,8 @@ FDIRW_API const char* fdirw_last_error(const fdirw_ctx* ctx);
  * Sec. 3.1 that the FD march computes, and the march stays its fallback).
  *
  * Network: features of source s on the 17^3 patch centred on s -- clamp(log10 D / 8 + 1, -0.5, 1.5) and a
- * domain mask in the domain (0 outside), and a source marker at the centre -- then 4 convolutions (3^3
+ * domain mask in the domain (0 outside), a source marker at the centre, and on every voxel its offset o
+ * from the source as o_x / 8, o_y / 8, o_z / 8 and |o|^2 / 256 (channels 0-6; 7-15 are 0) -- then 4 convolutions (3^3
  * taps, 16 -> 16 channels, zero padding, bias) with ReLU after the first three, BF16 weights and
  * activations, FP32 accumulation on the tensor cores; head y = exp(z[channel 0]) on in-domain cells.
  * Gate: a prediction is accepted when |sum y - 1| <= 1e-3 (FP64 sum).
@@ -355,8 +356,9 @@ FDIRW_API void fdirw_net_destroy(fdirw_net* net);
  * decisions (host int32, nullable) for n sources of ctx's domain. */
 FDIRW_API int fdirw_net_predict(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                                 double* kernels_out, double* mass_out, int32_t* accept_out);
-/* Gradients of the training loss sum_i sum_v (k_iv + 1e-9)(z_iv - ln(k_iv + 1e-9))^2 (k = targets, z = the
- * head's pre-exponential output, in-domain cells only) with respect to the parameters (host,
+/* Gradients of the training loss sum_i sum_v (y_iv - k_iv z_iv + k_iv ln k_iv - k_iv) (the generalised
+ * Kullback-Leibler divergence; k = targets, z = the head's pre-exponential output, y = exp(z), in-domain
+ * cells only, 0 ln 0 = 0; its gradient with respect to z is y - k) with respect to the parameters (host,
  * FDIRW_NET_NPARAM floats, nullable) and the mean loss over the batch (host, nullable). */
 FDIRW_API int fdirw_net_gradients(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                                   const double* targets, float* grads_out, double* loss_out);
@@ -387,6 +389,10 @@ FDIRW_API int fdirw_kernels_surrogate(fdirw_ctx* ctx, fdirw_net* net, int64_t* a
 FDIRW_API int fdirw_net_trace(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sources, int64_t n,
                               const double* targets, uint16_t* acts_out, float* z_out, uint16_t* grads_out,
                               float* grads_param_out, double* loss_out);
+/* Device time (ms, host float) of the four tensor-core convolutions of the network's last forward pass
+ * (prediction, training step, gradients, trace or gated build batch), from CUDA events recorded on the
+ * context stream around them; 0 before the first forward pass.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_CUDA. */
+FDIRW_API int fdirw_net_timing(fdirw_net* net, float* conv_ms);
 /* Failure-injection hook for tests of the bounded wait.  Every convolution waits for its MMAs on an
  * mbarrier for at most wait_ns nanoseconds of the GPU's global timer (0 restores the default, 2 s).  With
  * withhold_mma != 0 the convolutions issue neither their MMAs nor the commit that completes the wait,

@@ -4,19 +4,23 @@ The paper has no learned part: the surrogate is a network that predicts a source
 column of p, Sec. 3.1) from its local diffusivity patch, with the explicit FD march as the fallback when
 the prediction fails a mass/positivity gate.  Definition followed here (and by the CUDA path):
 
-* features of source s: a 17^3 patch centred on s (offsets -8..8), 16 channels, of which three are used:
+* features of source s: a 17^3 patch centred on s (offsets o = -8..8 per axis), 16 channels, of which
+  seven are used:
   ch0 = clamp(log10(D)/8 + 1, -0.5, 1.5) in the domain (D = 0 -> -0.5), 0 outside;
-  ch1 = 1 in the domain, 0 outside;  ch2 = 1 at the source cell, 0 elsewhere (a translation-equivariant
-  net with a 9^3 receptive field could not otherwise tell where the source is).
+  ch1 = 1 in the domain, 0 outside;  ch2 = 1 at the source cell, 0 elsewhere;
+  ch3, ch4, ch5 = o_x / 8, o_y / 8, o_z / 8 and ch6 = |o|^2 / 256 on every voxel of the patch (the
+  network is translation-equivariant with a 9^3 receptive field, so without these a voxel more than 4
+  cells from the source could not tell where the source is; all four are exact in BF16).
 * 4 layers z_l = conv3d_same(a_{l-1}, W_l) + b_l, 3^3 taps, 16 -> 16 channels, zero padding;
   a_l = relu(z_l) for l = 1..3, stored in BF16 (the GPU keeps activations in BF16); the features and
   the weights are BF16 too; sums are exact here (FP64) and FP32 on the GPU.
 * head: y = exp(z_4[channel 0]) on in-domain cells, 0 outside; mass m = sum y (FP64).
 * gate: accept when |m - 1| <= 1e-3 (y >= 0 holds by construction); the stored kernel is then y / m.
-* training loss per sample: sum_v (k_v + eps) (z_v - ln(k_v + eps))^2 over in-domain cells (z = z_4
-  channel 0, k the FD kernel, eps = 1e-9): a squared error on ln y weighted by the kernel's mass (a loss
-  on y itself has dL/dz proportional to y, which vanishes wherever the prediction starts small).  Its
-  gradient flows back through the relu layers (hand-derived below).
+* training loss per sample: the generalised Kullback-Leibler divergence of the prediction from the FD
+  kernel k over in-domain cells, sum_v (y_v - k_v z_v + k_v ln k_v - k_v) with y = exp(z), z = z_4
+  channel 0 (0 ln 0 = 0).  It is >= 0 with equality at y = k, and its gradient with respect to z is y - k:
+  mass predicted where the kernel has none is penalised directly, which is what the mass gate checks.
+  The gradient flows back through the relu layers (hand-derived below).
 
 Pins (tests/test_surrogate_oracle.py): conv3d against scipy.ndimage.correlate; every weight and bias
 gradient of the hand-derived backward against float64 autograd through torch's conv3d (1e-12 relative on
@@ -66,6 +70,11 @@ def features(D, shape, s) -> np.ndarray:
                 f[0, k, j, i] = min(max(np.log10(d) / 8.0 + 1.0, -0.5), 1.5) if d > 0 else -0.5
                 f[1, k, j, i] = 1.0
     f[2, HALF, HALF, HALF] = 1.0
+    o = np.arange(P) - HALF
+    f[3] = (o / 8.0)[None, None, :]
+    f[4] = (o / 8.0)[None, :, None]
+    f[5] = (o / 8.0)[:, None, None]
+    f[6] = (o[:, None, None] ** 2 + o[None, :, None] ** 2 + o[None, None, :] ** 2) / 256.0
     return bf16_round(f)
 
 
@@ -148,11 +157,14 @@ EPS = 1e-9
 
 
 def loss_grad(cache, k):
-    """Loss sum_v (k + eps)(z - ln(k + eps))^2 over in-domain cells and its gradient with respect to z."""
+    """Loss sum_v (y - k z + k ln k - k) over in-domain cells, y = exp(z), and its gradient y - k with
+    respect to z (0 outside the domain)."""
     _, zs, mask = cache
-    w = np.asarray(k, dtype=np.float64) + EPS
-    d = np.where(mask, zs[-1][0] - np.log(w), 0.0)
-    return float((w * d * d).sum()), 2.0 * w * d
+    kk = np.asarray(k, dtype=np.float64)
+    z = zs[-1][0]
+    y = np.exp(z)
+    klnk = np.where(kk > 0.0, kk * np.log(np.where(kk > 0.0, kk, 1.0)), 0.0)
+    return float(np.where(mask, y - kk * z + klnk - kk, 0.0).sum()), np.where(mask, y - kk, 0.0)
 
 
 def gate(m: float) -> bool:

@@ -2,7 +2,8 @@
 // paper; what it predicts is the column of p of Sec. 3.1, and the explicit FD march stays its fallback).
 //
 // Network (per source s, a 17^3 patch centred on s): features [log10 D / 8 + 1, domain mask, source
-// marker] (16 channels, 13 zero) -> 4 x { conv3d 3^3, 16 -> 16 channels, zero padding, + bias } with
+// marker, o_x / 8, o_y / 8, o_z / 8, |o|^2 / 256 with o the offset from the source] (16 channels, 9 zero)
+// -> 4 x { conv3d 3^3, 16 -> 16 channels, zero padding, + bias } with
 // ReLU after layers 1-3 -> head y = exp(z_4[channel 0]) on in-domain cells.  Gate: accept the prediction
 // when |sum y - 1| <= 1e-3 (FP64); the stored kernel is then renormalised like the FD kernels.
 //
@@ -34,15 +35,27 @@ namespace net {
 constexpr int SP = 17, SH = 8, PP = 19, PLANE = PP * PP, VOL = PP * PLANE, KV = SP * SP * SP;
 constexpr int GUARD = 64, ROWS = GUARD + VOL + GUARD;            // rows per 8-channel half of a patch
 constexpr int64_t PATCH = 2 * (int64_t)ROWS * 8;                   // bf16 elements per patch activation
-constexpr int RSLOT = 4, RROWS = GUARD + RSLOT * PLANE + GUARD;    // plane ring in shared memory
-constexpr int NTILE = 3;                                           // 128-row tiles per plane (384 >= 361)
 constexpr int NL = 4, C = 16, TAPS = 27;
 constexpr int NW = NL * TAPS * C * C;                              // weights [layer][tap][co][ci]
 constexpr int NPARAM = NW + NL * C;                                // + biases [layer][co]
 constexpr int WCAN = TAPS * C * C;                                 // bf16 per layer, canonical layout
 constexpr int MAX_BATCH = 1024;
-constexpr size_t CONV_SMEM = (size_t)2 * RROWS * 16 + (size_t)TAPS * 512 + 16;
 constexpr uint64_t WAIT_NS = 2000000000ull;                        // default MMA-wait budget: 2 s
+constexpr int NTILE = 3;                                           // 128-row tiles per plane (384 >= 361)
+constexpr int HALO_ROWS = PP + 1;                                  // rows a tap can reach beyond a tile (dy, dx)
+constexpr int TROWS = 128 + 2 * HALO_ROWS;                         // plane rows one tile reads: 168
+constexpr int NSLOT = 16;                                          // plane slots of the shared-memory ring
+constexpr int RROWS = NSLOT * TROWS;                               // ring rows per 8-channel half
+constexpr int NZ = 3;                                              // z taps stacked into one MMA's N
+constexpr int N48 = NZ * C;                                        // MMA N: 3 output planes x 16 channels
+constexpr int TAPS_XY = 9;                                         // (dy, dx) taps: MMAs per input plane
+constexpr int ACC_PLANES = PP;                                     // accumulators of padded planes 0..18
+constexpr int EPI_SETS = 2;                                        // epilogue warp sets (alternate output planes)
+constexpr int CONV_THREADS = 64 + EPI_SETS * 128;                  // producer, MMA and the epilogue warps
+constexpr int NBAR = 2 * NSLOT + 2 * SP + 1;                       // ring full/empty, plane acc full/empty, drain
+constexpr size_t CONV_SMEM_USED = (size_t)2 * RROWS * 16 + (size_t)WCAN * 2 + NBAR * 8 + 16;
+// One CTA per SM (it allocates all 512 TMEM columns): the shared-memory request keeps a second one off.
+constexpr size_t CONV_SMEM = CONV_SMEM_USED > 120 * 1024 ? CONV_SMEM_USED : 120 * 1024;
 constexpr double GATE_TOL = 1e-3;
 
 enum Mode { FWD_RELU = 0, FWD_HEAD = 1, DGRAD = 2 };
@@ -70,92 +83,165 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
     return r;
 }
 
-__global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
+// Warp-specialised convolution, one work unit = one 128-row tile of one patch (every plane's rows
+// 128 t .. 128 t + 127 of the 19 x 19 padded plane).  An input plane q feeds output planes q + 1, q and
+// q - 1 through the z taps dz = -1, 0, +1, so each (dy, dx) tap is ONE MMA with N = 48 = 3 x 16: its A
+// operand (the plane's rows shifted by dx + 19 dy) is read once for all three z taps, and its D columns
+// are the accumulators of output planes q + 1, q, q - 1, which TMEM holds side by side (plane z at column
+// 16 (18 - z); planes 0 and 18 only collect halo terms and are never read).  The first MMA that reaches an
+// accumulator in a unit overwrites it: at input plane 1 the first tap's N = 48 MMA (planes 2, 1, 0), at
+// input plane q >= 2 the first tap split into an N = 16 MMA that overwrites plane q + 1 and an N = 32 MMA
+// that accumulates into planes q and q - 1; every other MMA accumulates.
+//   warp 0 (one thread): streams input planes 1..17 of the unit (the 168 rows the tile reaches, both
+//     8-channel halves) into a ring of NSLOT slots with cp.async.bulk ("full" mbarrier per slot), refilling
+//     a slot once its "empty" barrier says the 9 MMAs that read it have completed;
+//   warp 1 (one thread): per input plane, the 9 MMAs into accumulators q + 1, q, q - 1 (after the
+//     epilogue has released plane q + 1 of the previous unit), then commits to the slot's "empty" barrier
+//     and, for the output plane now complete (q - 1; plane 17 too after plane 17), to its "acc full";
+//   warps 2..: EPI_SETS sets of 4 warps, set s taking the output planes z with z mod EPI_SETS = s: drain
+//     the plane's 16 columns with tcgen05.ld (warp w reads TMEM lanes 32 (w mod 4)..), arrive on its
+//     "acc empty", apply bias / relu / mask and write the rows.
+// Every wait is bounded by a.wait_ns.  A role whose wait runs out stops; the others then run out too.
+// Before the TMEM is freed, the MMA thread waits (bounded) for every MMA it issued and the producer for
+// every copy it issued; if either is still outstanding the kernel reports err 2.
+__global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* ring0 = sm;
     uint8_t* ring1 = sm + (size_t)RROWS * 16;
     uint8_t* wsm = ring1 + (size_t)RROWS * 16;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(wsm + TAPS * 512);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + (size_t)WCAN * 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // barriers: FULL + slot, EMPTY + slot, AFULL + z - 1, AEMPTY + z - 1 (output planes z = 1..17), DRAIN
+    constexpr int FULL = 0, EMPTY = NSLOT, AFULL = 2 * NSLOT, AEMPTY = 2 * NSLOT + SP, DRAIN = 2 * NSLOT + 2 * SP;
+    const uint32_t bar0 = tc::smem_u32(bars);
+    auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    const int units = a.batch * NTILE;
 
-    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    if (warp == 1) tc::tmem_alloc(tslot, 512);
     if (t == 0) {
-        tc::mbar_init(tc::smem_u32(mbar), 1);
+        for (int i = 0; i < NSLOT; i++) {
+            tc::mbar_init(bar(FULL + i), 1);
+            tc::mbar_init(bar(EMPTY + i), 1);
+        }
+        for (int i = 0; i < SP; i++) {
+            tc::mbar_init(bar(AFULL + i), 1);
+            tc::mbar_init(bar(AEMPTY + i), 4);
+        }
+        tc::mbar_init(bar(DRAIN), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     const uint4* wsrc = reinterpret_cast<const uint4*>(a.w);
-    for (int i = t; i < TAPS * 512 / 16; i += 128) reinterpret_cast<uint4*>(wsm)[i] = wsrc[i];
+    for (int i = t; i < WCAN * 2 / 16; i += CONV_THREADS) reinterpret_cast<uint4*>(wsm)[i] = wsrc[i];
     const uint4 z4 = make_uint4(0, 0, 0, 0);
-    for (int i = t; i < GUARD; i += 128) {     // guard rows (read only by halo outputs, which are dropped)
-        reinterpret_cast<uint4*>(ring0)[i] = z4;
-        reinterpret_cast<uint4*>(ring1)[i] = z4;
-        reinterpret_cast<uint4*>(ring0)[RROWS - GUARD + i] = z4;
-        reinterpret_cast<uint4*>(ring1)[RROWS - GUARD + i] = z4;
-    }
+    for (int i = t; i < 2 * RROWS; i += CONV_THREADS) reinterpret_cast<uint4*>(ring0)[i] = z4;   // both halves
+    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t mb = tc::smem_u32(mbar);
-    const uint32_t r0 = tc::smem_u32(ring0), wsa = tc::smem_u32(wsm);
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 16);
-    uint32_t phase = 0;
-    bool ok = true;
+    int err = 0;
 
-    for (int p = blockIdx.x; p < a.batch && ok; p += gridDim.x) {
-        const uint4* in0 = reinterpret_cast<const uint4*>(a.in + (int64_t)p * PATCH);
-        const uint4* in1 = in0 + ROWS;
-        auto load_plane = [&](int zz) {
-            const int slot = zz & 3;
-            for (int i = t; i < 2 * PLANE; i += 128) {
-                const int h = i >= PLANE, r = i - h * PLANE;
-                const uint4 v = (h ? in1 : in0)[GUARD + zz * PLANE + r];
-                reinterpret_cast<uint4*>(h ? ring1 : ring0)[GUARD + slot * PLANE + r] = v;
+    if (warp == 0) {
+        if (lane == 0) {                                  // producer
+            uint32_t q = 0;
+            bool alive = true;
+            for (int u = blockIdx.x; u < units && alive; u += gridDim.x) {
+                const int p = u / NTILE, tile = u % NTILE;
+                const int r_lo = tile * 128 - HALO_ROWS;                      // plane row of slot row 0
+                const int r0 = r_lo > 0 ? r_lo : 0, r1 = r_lo + TROWS < PLANE ? r_lo + TROWS : PLANE;
+                const uint32_t bytes = (uint32_t)(r1 - r0) * 16;
+                const uint8_t* h0 = reinterpret_cast<const uint8_t*>(a.in + (int64_t)p * PATCH);
+                const uint8_t* h1 = h0 + (size_t)ROWS * 16;
+                for (int zz = 1; zz <= SP; zz++, q++) {
+                    const uint32_t slot = q % NSLOT, use = q / NSLOT;
+                    if (use > 0 && !tc::mbar_wait(bar(EMPTY + (int)slot), (use - 1) & 1u, a.wait_ns)) { alive = false; break; }
+                    const size_t off = (size_t)(GUARD + zz * PLANE + r0) * 16;
+                    const uint32_t dst = (uint32_t)(slot * TROWS + (r0 - r_lo)) * 16;
+                    tc::mbar_arrive_expect_tx(bar(FULL + (int)slot), 2 * bytes);
+                    tc::bulk_g2s(tc::smem_u32(ring0) + dst, h0 + off, bytes, bar(FULL + (int)slot));
+                    tc::bulk_g2s(tc::smem_u32(ring1) + dst, h1 + off, bytes, bar(FULL + (int)slot));
+                }
             }
-        };
-        load_plane(0);
-        load_plane(1);
-        for (int z = 1; z <= SP && ok; z++) {
-            load_plane(z + 1);
-            tc::fence_async_smem();
-            __syncthreads();
-            if (t == 0 && !a.hold) {
-                tc::fence_after_sync();
-#pragma unroll 1
-                for (int tile = 0; tile < NTILE; tile++) {
-#pragma unroll 1
-                    for (int tap = 0; tap < TAPS; tap++) {
-                        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                        const int row = GUARD + ((z + dz) & 3) * PLANE + tile * 128 + dx + PP * dy;
-                        const uint64_t ad = tc::smem_desc(r0 + (uint32_t)row * 16, RROWS * 16, 128);
-                        const uint64_t bd = tc::smem_desc(wsa + (uint32_t)tap * 512, 256, 128);
-                        tc::mma_bf16(tmem + (uint32_t)(tile * 16), ad, bd, IDESC, tap > 0 ? 1u : 0u);
+            for (uint32_t sl = 0; sl < NSLOT && sl < q; sl++) {     // the last copy into every used slot has landed
+                const uint32_t last = (q - 1 - sl) / NSLOT;
+                if (!tc::mbar_wait(bar(FULL + (int)sl), last & 1u, a.wait_ns)) err = 2;
+            }
+            if (!alive && err == 0) err = 1;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                  // MMA issuer
+            constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, N48);
+            constexpr uint32_t IDESC16 = tc::idesc_bf16_f32(128, C), IDESC32 = tc::idesc_bf16_f32(128, 2 * C);
+            // K-major no-swizzle operands; a descriptor's start-address field counts 16-byte rows, so row and
+            // tap offsets are added to the base descriptors directly.  B per (dy, dx) tap: [2 K chunks]
+            // [6 groups of 8 N rows][8 x 8], 1536 B.
+            const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(ring0), RROWS * 16, 128);
+            const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(wsm), (N48 / 8) * 128, 128);
+            uint32_t q = 0, unit = 0;
+            bool alive = true, issued = false;
+            for (int u = blockIdx.x; u < units && alive; u += gridDim.x, unit++) {
+                for (int zz = 1; zz <= SP; zz++, q++) {
+                    const uint32_t slot = q % NSLOT;
+                    alive = tc::mbar_wait(bar(FULL + (int)slot), (q / NSLOT) & 1u, a.wait_ns);
+                    // accumulators first written at this plane: zz + 1 (and plane 1 at zz = 1)
+                    if (alive && unit > 0 && zz + 1 <= SP)
+                        alive = tc::mbar_wait(bar(AEMPTY + zz), (unit - 1) & 1u, a.wait_ns);
+                    if (alive && unit > 0 && zz == 1)
+                        alive = tc::mbar_wait(bar(AEMPTY + 0), (unit - 1) & 1u, a.wait_ns);
+                    if (!alive) break;
+                    tc::fence_after_sync();
+                    if (!a.hold) {
+                        const uint32_t dst = tmem + (uint32_t)(16 * (SP - zz));     // planes zz + 1, zz, zz - 1
+                        const uint32_t base = slot * TROWS + HALO_ROWS;
+#pragma unroll
+                        for (int txy = 0; txy < TAPS_XY; txy++) {
+                            const int dy = txy / 3 - 1, dx = txy % 3 - 1;
+                            const uint64_t ad = adesc0 + (base + (uint32_t)(dx + PP * dy));
+                            const uint64_t bd = bdesc0 + (uint64_t)(txy * (N48 * C * 2 / 16));
+                            if (txy > 0) {
+                                tc::mma_bf16(dst, ad, bd, IDESC, 1u);
+                            } else if (zz == 1) {
+                                tc::mma_bf16(dst, ad, bd, IDESC, 0u);                          // planes 2, 1, 0 fresh
+                            } else {
+                                tc::mma_bf16(dst, ad, bd, IDESC16, 0u);                        // plane zz + 1 fresh
+                                tc::mma_bf16(dst + 16, ad, bd + (2 * 128 / 16), IDESC32, 1u);  // planes zz, zz - 1
+                            }
+                        }
+                        issued = true;
+                        tc::mma_commit(bar(EMPTY + (int)slot));                       // input plane zz is done
+                        if (zz >= 2) tc::mma_commit(bar(AFULL + (zz - 2)));          // output plane zz - 1
+                        if (zz == SP) tc::mma_commit(bar(AFULL + (SP - 1)));         // output plane 17
                     }
                 }
-                tc::mma_commit(mb);
             }
-            const bool done = tc::mbar_wait(mb, phase, a.wait_ns);
-            ok = __syncthreads_and(done ? 1 : 0) != 0;
-            if (!ok) {
-                // MMAs issued for this plane may still be writing the accumulator: wait for them once
-                // more (bounded) before the TMEM is freed.  If they still have not completed, the TMEM
-                // freed below may be overwritten after its release, which the host reports as err 2.
-                bool drained = a.hold != 0;
-                if (!drained) drained = __syncthreads_and(tc::mbar_wait(mb, phase, a.wait_ns) ? 1 : 0) != 0;
-                if (t == 0) atomicMax(a.err, drained ? 1 : 2);
-                break;
+            if (issued) {                                 // every MMA issued has completed
+                tc::mma_commit(bar(DRAIN));
+                if (!tc::mbar_wait(bar(DRAIN), 0, a.wait_ns)) err = 2;
             }
-            phase ^= 1u;
-            tc::fence_after_sync();
-#pragma unroll 1
-            for (int tile = 0; tile < NTILE; tile++) {
+            if (!alive && err == 0) err = 1;
+        }
+    } else {                                              // epilogue warp sets
+        const int quarter = warp & 3, set = (warp - 2) / 4;
+        const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
+        uint32_t unit = 0;
+        bool alive = true;
+        for (int u = blockIdx.x; u < units && alive; u += gridDim.x, unit++) {
+            const int p = u / NTILE, tile = u % NTILE;
+            const int r = tile * 128 + 32 * quarter + lane;
+            const int x = r % PP, y = r / PP;
+            const bool interior = r < PLANE && x >= 1 && x <= SP && y >= 1 && y <= SP;
+            for (int z = 1 + set; z <= SP; z += EPI_SETS) {
+                alive = __all_sync(0xffffffffu, tc::mbar_wait(bar(AFULL + z - 1), unit & 1u, a.wait_ns) ? 1 : 0) != 0;
+                if (!alive) break;
+                tc::fence_after_sync();
+                const uint32_t col = tmem + lanes + (uint32_t)(16 * (ACC_PLANES - 1 - z));
                 float v[16];
-                tc::tmem_ld16_wait(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(tile * 16), v);
-                const int r = tile * 128 + 32 * warp + lane;
+                tc::tmem_ld16_wait(col, v);
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(bar(AEMPTY + z - 1));
                 if (r >= PLANE) continue;
-                const int x = r % PP, y = r / PP;
-                const bool interior = x >= 1 && x <= SP && y >= 1 && y <= SP;
                 const int64_t row = GUARD + (int64_t)z * PLANE + r;
                 if (a.mode == FWD_HEAD) {
                     if (interior) a.zhead[(int64_t)p * KV + ((z - 1) * SP + (y - 1)) * SP + (x - 1)] = v[0] + a.bias[0];
@@ -176,14 +262,14 @@ __global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
                 dst[row] = pack8(o);
                 dst[ROWS + row] = pack8(o + 8);
             }
-            tc::fence_before_sync();
-            __syncthreads();
         }
+        if (!alive && lane == 0) err = 1;
     }
+    if (err) atomicMax(a.err, err);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
 // Row of padded voxel (i, j, k) of the 17^3 patch (0-based interior coordinates).
@@ -225,6 +311,11 @@ __global__ void features_kernel(const double* __restrict__ D, Grid g, const int6
             rowp[1] = __float2bfloat16_rn(1.f);
         }
         if (i == SH && j == SH && k == SH) rowp[2] = __float2bfloat16_rn(1.f);
+        const int ox = i - SH, oy = j - SH, oz = k - SH;     // offsets from the source: exact in BF16
+        rowp[3] = __float2bfloat16_rn((float)ox * 0.125f);
+        rowp[4] = __float2bfloat16_rn((float)oy * 0.125f);
+        rowp[5] = __float2bfloat16_rn((float)oz * 0.125f);
+        rowp[6] = __float2bfloat16_rn((float)(ox * ox + oy * oy + oz * oz) * (1.f / 256.f));
     }
 }
 
@@ -256,10 +347,9 @@ __global__ void __launch_bounds__(256) head_predict_kernel(const float* __restri
     }
 }
 
-// Head for training: loss sum_v (k + eps)(z - ln(k + eps))^2 over in-domain cells (a squared error on
-// ln y weighted by the target kernel's mass; a loss on y itself has dL/dz proportional to y, which
-// vanishes where the prediction is small) and its gradient 2 (k + eps)(z - ln(k + eps)) (channel 0).
-constexpr double LOSS_EPS = 1e-9;
+// Head for training: the generalised Kullback-Leibler divergence sum_v (y - k z + k ln k - k), y = exp(z),
+// over in-domain cells (0 ln 0 = 0) and its gradient y - k with respect to z (channel 0); the gradient
+// penalises predicted mass wherever the target kernel has less, which is what the mass gate checks.
 __global__ void __launch_bounds__(256) head_train_kernel(const float* __restrict__ zhead, Grid g,
                                                          const int64_t* __restrict__ src, const double* __restrict__ tgt,
                                                          __nv_bfloat16* __restrict__ grad, double* __restrict__ loss) {
@@ -271,10 +361,15 @@ __global__ void __launch_bounds__(256) head_train_kernel(const float* __restrict
         const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
         int64_t gi;
         const bool ind = in_domain(q, i, j, k, g, &gi);
-        const double w = tgt[(int64_t)b * KV + v] + LOSS_EPS;
-        const double d = ind ? (double)zhead[(int64_t)b * KV + v] - log(w) : 0.0;
-        acc += w * d * d;
-        grad[(int64_t)b * PATCH + (int64_t)prow(i, j, k) * 8] = __float2bfloat16_rn((float)(2.0 * w * d));
+        double gz = 0.0;
+        if (ind) {
+            const double kk = tgt[(int64_t)b * KV + v];
+            const double z = (double)zhead[(int64_t)b * KV + v];
+            const double y = exp(z);
+            acc += y - kk * z + (kk > 0.0 ? kk * log(kk) : 0.0) - kk;
+            gz = y - kk;
+        }
+        grad[(int64_t)b * PATCH + (int64_t)prow(i, j, k) * 8] = __float2bfloat16_rn((float)gz);
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -386,7 +481,9 @@ __global__ void __launch_bounds__(256) bgrad_kernel(const __nv_bfloat16* __restr
     if (threadIdx.x == 0) db[c] = sh[0];
 }
 
-// Canonical UMMA layouts of the BF16 weights: per tap [kchunk 2][ngroup 2][8 n][8 k] (512 B).
+// Canonical UMMA layouts of the BF16 weights for the N = 48 convolution: per (dy, dx) tap txy = (dx+1) +
+// 3 (dy+1), a K-major [2 K chunks][6 groups of 8 N rows][8 n][8 k] block (1536 B) whose N row
+// n48 = 16 (dz + 1) + n holds z tap dz (so D columns 16 (dz + 1).. belong to output plane q - dz).
 // Forward: n = co, k = ci.  Input gradient: tap -> 26 - tap (flip), n = ci, k = co (transpose).
 __global__ void canon_kernel(const float* __restrict__ params, __nv_bfloat16* __restrict__ wf,
                              __nv_bfloat16* __restrict__ wd) {
@@ -395,7 +492,10 @@ __global__ void canon_kernel(const float* __restrict__ params, __nv_bfloat16* __
     const int l = e / (TAPS * C * C), rem = e % (TAPS * C * C);
     const int tap = rem / (C * C), co = (rem / C) % C, ci = rem % C;
     const __nv_bfloat16 w = __float2bfloat16_rn(params[e]);
-    auto cidx = [](int tp, int n, int k) { return tp * 256 + (k >> 3) * 128 + (n >> 3) * 64 + (n & 7) * 8 + (k & 7); };
+    auto cidx = [](int tp, int n, int k) {
+        const int txy = tp % 9, dzi = tp / 9, n48 = C * dzi + n;
+        return txy * (N48 * C) + (k >> 3) * (N48 * 8) + (n48 >> 3) * 64 + (n48 & 7) * 8 + (k & 7);
+    };
     wf[(int64_t)l * WCAN + cidx(tap, co, ci)] = w;
     wd[(int64_t)l * WCAN + cidx(TAPS - 1 - tap, ci, co)] = w;
 }
@@ -456,6 +556,8 @@ struct fdirw_net {
     float* partial = nullptr;
     float* grads = nullptr;
     int* derr = nullptr;
+    cudaEvent_t ev[2] = {};        // around the four convolutions of the last forward pass
+    bool timed = false;
     uint64_t wait_ns = WAIT_NS;    // budget of each MMA wait (fdirw_net_test_wait)
     int hold = 0;                  // test hook: convolutions withhold their MMAs (fdirw_net_test_wait)
     bool failed = false;           // a wait gave up while MMAs may still have been running
@@ -505,8 +607,12 @@ int launch_conv(fdirw_net* net, cudaStream_t st, int num_sms, const __nv_bfloat1
                 float* zhead, const __nv_bfloat16* mask, const __nv_bfloat16* w, const float* bias, int n, int mode) {
     ConvArgs a{in, out, zhead, mask, w, bias, n, mode, net->derr, net->wait_ns, net->hold};
     NET_CUDA(net, cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CONV_SMEM));
-    const int grid = n < num_sms * 3 ? n : num_sms * 3;
-    conv_kernel<<<grid, 128, CONV_SMEM, st>>>(a);
+    int per_sm = 0;
+    NET_CUDA(net, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel, CONV_THREADS, CONV_SMEM));
+    if (per_sm != 1) return nfail(net, FDIRW_ERR_CUDA, "the convolution needs exactly one CTA per SM (TMEM)");
+    const int units = n * NTILE;
+    const int grid = units < num_sms ? units : num_sms;
+    conv_kernel<<<grid, CONV_THREADS, CONV_SMEM, st>>>(a);
     NET_CUDA(net, cudaGetLastError());
     return FDIRW_OK;
 }
@@ -520,6 +626,7 @@ int forward(fdirw_ctx* c, fdirw_net* net, int n) {
     const int fb = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
     features_kernel<<<fb, 256, 0, st>>>(c->Dd, c->g, net->dsrc, n, net->act[0]);
     NET_CUDA(net, cudaGetLastError());
+    NET_CUDA(net, cudaEventRecord(net->ev[0], st));
     for (int l = 0; l < NL; l++) {
         const bool head = l == NL - 1;
         const int rc = launch_conv(net, st, c->num_sms, net->act[l], head ? nullptr : net->act[l + 1],
@@ -527,6 +634,8 @@ int forward(fdirw_ctx* c, fdirw_net* net, int n) {
                                    net->params + NW + l * C, n, head ? FWD_HEAD : FWD_RELU);
         if (rc != FDIRW_OK) return rc;
     }
+    NET_CUDA(net, cudaEventRecord(net->ev[1], st));
+    net->timed = true;
     return FDIRW_OK;
 }
 
@@ -635,7 +744,8 @@ FDIRW_API int fdirw_net_create(const float* params, int32_t device, fdirw_net** 
         cudaMalloc(&net->v, NPARAM * 4) != cudaSuccess || cudaMalloc(&net->grads, NPARAM * 4) != cudaSuccess ||
         cudaMalloc(&net->wf, (size_t)NL * WCAN * 2) != cudaSuccess || cudaMalloc(&net->wd, (size_t)NL * WCAN * 2) != cudaSuccess ||
         cudaMalloc(&net->partial, (size_t)TAPS * WG_BLOCKS * C * C * 4) != cudaSuccess ||
-        cudaMalloc(&net->derr, 4) != cudaSuccess)
+        cudaMalloc(&net->derr, 4) != cudaSuccess || cudaEventCreate(&net->ev[0]) != cudaSuccess ||
+        cudaEventCreate(&net->ev[1]) != cudaSuccess)
         return bail("allocating the network");
     if (cudaMemcpy(net->params, params, NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(net->m, 0, NPARAM * 4) != cudaSuccess || cudaMemset(net->v, 0, NPARAM * 4) != cudaSuccess ||
@@ -662,6 +772,7 @@ FDIRW_API void fdirw_net_destroy(fdirw_net* net) {
     cudaFree(net->params); cudaFree(net->m); cudaFree(net->v); cudaFree(net->wf); cudaFree(net->wd);
     cudaFree(net->zhead); cudaFree(net->dsrc); cudaFree(net->dtgt); cudaFree(net->dkout); cudaFree(net->dmass);
     cudaFree(net->dacc); cudaFree(net->dloss); cudaFree(net->partial); cudaFree(net->grads); cudaFree(net->derr);
+    for (auto e : net->ev) if (e) cudaEventDestroy(e);
     delete net;
 }
 
@@ -707,6 +818,15 @@ FDIRW_API int fdirw_net_train_step(fdirw_ctx* ctx, fdirw_net* net, const int64_t
     NET_CUDA(net, cudaGetLastError());
     canon_kernel<<<(NW + 255) / 256, 256, 0, ctx->stream>>>(net->params, net->wf, net->wd);
     NET_CUDA(net, cudaGetLastError());
+    return FDIRW_OK;
+}
+
+FDIRW_API int fdirw_net_timing(fdirw_net* net, float* conv_ms) {
+    if (!net || !conv_ms) return nfail(net, FDIRW_ERR_ARG, "NULL net or conv_ms");
+    *conv_ms = 0.f;
+    if (!net->timed) return FDIRW_OK;
+    NET_CUDA(net, cudaEventSynchronize(net->ev[1]));
+    NET_CUDA(net, cudaEventElapsedTime(conv_ms, net->ev[0], net->ev[1]));
     return FDIRW_OK;
 }
 

@@ -50,17 +50,37 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // Bounded wait on an mbarrier phase: returns false if it did not complete within budget_ns nanoseconds
 // of the GPU's global timer (each try_wait may itself suspend the thread for a short, system-defined
 // time, so the budget is checked between polls).
+__device__ __forceinline__ bool mbar_try(uint32_t mbar_saddr, uint32_t parity) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done) : "r"(mbar_saddr), "r"(parity) : "memory");
+    return done != 0;
+}
+// The timer is read only once the first poll has failed, so a phase that is already complete costs one poll.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint64_t budget_ns) {
+    if (mbar_try(mbar_saddr, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (;;) {
-        uint32_t done = 0;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done) : "r"(mbar_saddr), "r"(parity) : "memory");
-        if (done) return true;
+        if (mbar_try(mbar_saddr, parity)) return true;
         if (globaltimer_ns() - t0 > budget_ns) return false;
     }
+}
+
+// Arrives on the mbarrier and adds tx_bytes to the transaction count its current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar_saddr, uint32_t tx_bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar_saddr), "r"(tx_bytes) : "memory");
+}
+// Plain arrival (count 1) on the mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar_saddr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar_saddr) : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global memory into this
+// CTA's shared memory, completing `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void* src, uint32_t bytes, uint32_t mbar_saddr) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst_saddr), "l"(src), "r"(bytes), "r"(mbar_saddr) : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -90,6 +110,14 @@ __device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, float (&v)[16]) {
                  :: "memory");
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Writes 0 into 16 consecutive 32-bit columns of this thread's TMEM lane, and waits for the stores.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                 :: "r"(taddr), "r"(z) : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 }  // namespace tc

@@ -37,7 +37,7 @@ EXPORTED = ("fdirw_stable_dt", "fdirw_create", "fdirw_kernels", "fdirw_step", "f
             "fdirw_kernels_surrogate", "fdirw_create_batch", "fdirw_read_radius", "fdirw_create_coarse",
             "fdirw_read_coarse", "fdirw_coarse_far_field", "fdirw_coarse_get_far_field", "fdirw_read_coarse_pbc",
             "fdirw_coupled_step", "fdirw_set_velocity", "fdirw_net_trace", "fdirw_net_test_wait",
-            "fdirw_probe_peaks")
+            "fdirw_probe_peaks", "fdirw_net_timing")
 NET_NPARAM = 4 * 27 * 16 * 16 + 4 * 16
 NET_KV = 17 ** 3
 
@@ -122,6 +122,7 @@ def load(path: str | None = None):
         lib.fdirw_net_trace.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, dp]
         lib.fdirw_net_test_wait.argtypes = [vp, ctypes.c_uint64, i32]
         lib.fdirw_probe_peaks.argtypes = [i32, dp, dp]
+        lib.fdirw_net_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.fdirw_create_batch.argtypes = [i32, ctypes.POINTER(fdirw_grid), ctypes.POINTER(vp), ctypes.c_double, i32,
                                            i32, i32, ctypes.POINTER(fdirw_opts), ctypes.POINTER(vp)]
         lib.fdirw_read_radius.argtypes = [vp, vp]
@@ -534,6 +535,12 @@ class Net:
                                       ctypes.c_void_p(pg.ctypes.data if pg is not None else 0),
                                       ctypes.byref(loss) if t is not None else None), ctypes.c_void_p(ctx))
         return acts, z, grads, pg, (loss.value if t is not None else None)
+
+    def conv_ms(self) -> float:
+        """fdirw_net_timing: device time of the last forward pass's four convolutions (ms)."""
+        v = ctypes.c_float(0.0)
+        _check(load().fdirw_net_timing(ctypes.c_void_p(self.h), ctypes.byref(v)))
+        return float(v.value)
 
     def test_wait(self, wait_ns: int = 0, withhold_mma: bool = False) -> None:
         """fdirw_net_test_wait: the MMA-wait budget (0 = default) and the withhold-MMA test hook."""

@@ -6,7 +6,8 @@ Recipe: training structures are seeded sphere packings (porosity U[0.3, 0.5], pe
 diffusivity ratio U[3, 8]); their FD kernels (window R = 8, n_sub substeps at the stability limit) are
 the targets; the network starts from a delta-kernel prior (the source marker routed to the head so that
 z = 0 at the source and ln(1e-9) elsewhere) plus N(0, 0.02) noise, and is trained with Adam on the
-mass-weighted log-space loss sum (k + 1e-9)(z - ln(k + 1e-9))^2.
+generalised Kullback-Leibler divergence sum (y - k ln y + k ln k - k), y = exp(z), whose gradient y - k
+penalises predicted mass wherever the FD kernel has less (the gate checks the total mass).
 """
 from __future__ import annotations
 

@@ -173,7 +173,7 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
 
 _SCALARS = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64, "double": ctypes.c_double, "float": ctypes.c_float,
             "int": ctypes.c_int}
-_POINTEES = {"double": ctypes.c_double, "int64_t": ctypes.c_int64, "fdirw_grid": fdirw.fdirw_grid,
+_POINTEES = {"double": ctypes.c_double, "int64_t": ctypes.c_int64, "float": ctypes.c_float, "fdirw_grid": fdirw.fdirw_grid,
              "fdirw_opts": fdirw.fdirw_opts, "fdirw_info": fdirw.fdirw_info,
              "fdirw_coupled_params": fdirw.fdirw_coupled_params}
 

@@ -139,11 +139,11 @@ def test_backward_layers_match_oracle_element_by_element():
         g = [_bits(grads[l, q]).reshape(16, 17, 17, 17) for l in range(4)]
         zq = z[q].astype(np.float64).reshape(17, 17, 17)
         inside = a[0][1] > 0.5
-        w = tg[q] + so.EPS
-        d = np.where(inside, zq - np.log(w), 0.0)
-        lo += float((w * d * d).sum())
+        kq = tg[q]
+        yq = np.exp(zq)
+        lo += float(np.where(inside, yq - kq * zq + kq * np.log(kq) - kq, 0.0).sum())
         head = np.zeros((16, 17, 17, 17))
-        head[0] = so.bf16_round(2.0 * w * d)
+        head[0] = so.bf16_round(np.where(inside, yq - kq, 0.0))
         _layer_check(g[3], head, np.zeros_like(head), 0, True, ("head gradient", q), max_mismatch=1e-3)
         for l in (2, 1, 0):
             ref = so.bf16_round(so.conv3d_same_grad_input(g[l + 1], Wb[l + 1]) * (a[l + 1] > 0.0))

@@ -143,8 +143,9 @@ MUTANTS = [
     ("relu_mask_skipped_below_the_head", SU, "g = ga * (zs[l - 1] > 0.0)",
      "g = ga * (zs[l - 1] > 0.0) if l < LAYERS - 1 else ga", 0, "surrogate"),
     ("relu_mask_of_the_layer_above", SU, "g = ga * (zs[l - 1] > 0.0)", "g = ga * (zs[l] > 0.0)", 0, "surrogate"),
-    ("loss_gradient_half", SU, "return float((w * d * d).sum()), 2.0 * w * d", "return float((w * d * d).sum()), w * d", 0,
-     "surrogate"),
+    ("loss_gradient_target_sign", SU, "np.where(mask, y - kk, 0.0)", "np.where(mask, y + kk, 0.0)", 0, "surrogate"),
+    ("loss_without_predicted_mass", SU, "np.where(mask, y - kk * z + klnk - kk, 0.0)", "np.where(mask, -kk * z + klnk - kk, 0.0)",
+     0, "surrogate"),
     ("head_without_exp", SU, "y = np.where(mask, np.exp(zs[-1][0]), 0.0)", "y = np.where(mask, zs[-1][0], 0.0)", 0,
      "surrogate"),
     ("head_not_masked", SU, "y = np.where(mask, np.exp(zs[-1][0]), 0.0)", "y = np.exp(zs[-1][0])", 0, "surrogate"),
@@ -152,6 +153,9 @@ MUTANTS = [
      "surrogate"),
     ("feature_log_scale", SU, "np.log10(d) / 8.0 + 1.0", "np.log10(d) / 4.0 + 1.0", 0, "surrogate"),
     ("feature_zero_D_channel", SU, "1.5) if d > 0 else -0.5", "1.5) if d > 0 else 0.0", 0, "surrogate"),
+    ("offset_x_channel_along_y", SU, "f[3] = (o / 8.0)[None, None, :]", "f[3] = (o / 8.0)[None, :, None]", 0,
+     "surrogate"),
+    ("offset_square_scale", SU, "o[None, None, :] ** 2) / 256.0", "o[None, None, :] ** 2) / 192.0", 0, "surrogate"),
 ]
 
 # The launcher script puts the copy first on the path, checks that the copy is what `import oracle` loads, then

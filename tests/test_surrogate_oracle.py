@@ -66,9 +66,10 @@ def _autograd(feat, Ws, bs, k):
         z = torch.nn.functional.conv3d(h, Wt[l], bt[l], padding=1)
         h = torch.relu(z) if l + 1 < so.LAYERS else z
     mask = torch.tensor(feat[1] > 0.5)
-    w = torch.tensor(np.asarray(k, dtype=np.float64) + so.EPS)
-    d = torch.where(mask, h[0, 0] - torch.log(w), torch.zeros_like(w))
-    loss = (w * d * d).sum()
+    kk = torch.tensor(np.asarray(k, dtype=np.float64))
+    z = h[0, 0]
+    klnk = torch.where(kk > 0, kk * torch.log(torch.where(kk > 0, kk, torch.ones_like(kk))), torch.zeros_like(kk))
+    loss = torch.where(mask, torch.exp(z) - kk * z + klnk - kk, torch.zeros_like(kk)).sum()
     loss.backward()
     dWs = [W.grad.numpy().transpose(2, 3, 4, 0, 1).reshape(27, so.C, so.C) for W in Wt]
     return float(loss.item()), dWs, [b.grad.numpy() for b in bt]
@@ -179,6 +180,30 @@ def test_features_and_gate():
     assert f[1].sum() == 9 * 9 * 8                # in-domain cells of the clipped patch (x, y, z)
     assert f[0, 8, 8, 8] == 0.0 and f[0, 8, 8, 9] == -0.5 and f[0, 8, 8, 10] == 1.0
     assert so.gate(1.0009) and not so.gate(1.0011) and not so.gate(0.998)
+
+
+def test_offset_channels():
+    """Channels 3-6 encode each voxel's offset o from the source: channel 3 grows by exactly 1/8 per cell
+    along x and not at all along y or z (4 along y, 5 along z), all three vanish at the source and are odd
+    about it, channel 6 equals (c3^2 + c4^2 + c5^2) / 4 = |o|^2 / 256, every value is a BF16 number, and none
+    depends on the domain or on where the source sits in it."""
+    shape = (10, 9, 8)
+    D = np.ones(720)
+    corner = so.features(D, shape, 0)
+    inner = so.features(synth.random_diffusivity(shape, 3, 6.0), shape, 4 + 10 * (4 + 9 * 4))
+    assert np.array_equal(corner[3:7], inner[3:7])
+    f = inner
+    for ch, axis in ((3, 3), (4, 2), (5, 1)):              # f is [channel, z, y, x]
+        d = np.diff(f[ch], axis=axis - 1)
+        assert np.all(d == 0.125), ch
+        for other in {1, 2, 3} - {axis}:
+            assert np.all(np.diff(f[ch], axis=other - 1) == 0.0), (ch, other)
+        assert f[ch, 8, 8, 8] == 0.0
+        assert np.array_equal(f[ch], -np.flip(f[ch], axis=axis - 1))
+    assert np.array_equal(f[6], (f[3] ** 2 + f[4] ** 2 + f[5] ** 2) / 4.0)
+    assert f[6].max() == 192.0 / 256.0 and f[6, 8, 8, 8] == 0.0
+    assert np.array_equal(so.bf16_round(f), f)
+    assert not f[7:].any()
 
 
 def test_delta_prior_forward_closed_form():
