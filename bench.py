@@ -199,7 +199,7 @@ def run_reference(args, w):
 def march_kernel_name(prec: str, parts: int) -> str:
     if prec == "fp64":
         return "march_f64_kernel<R>"
-    return {4: "march_tm_kernel<R>", 5: "march_tmc_kernel<R>", 6: "march_tmp_kernel<R>"}.get(
+    return {4: "march_tm_kernel<R>", 5: "march_tmc_kernel<R>", 6: "march_tmp_kernel<R>", 7: "march_tmx_kernel<R>"}.get(
         parts, f"march_f32_kernel<R,{parts}>")
 
 
@@ -1004,7 +1004,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU baseline and accuracy leg")
-    ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and compare its gated build")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="train the learned surrogate and compare its gated build (on by default for R = 8 single grids)")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--surrogate-structures", type=int, default=20)
     ap.add_argument("--surrogate-per-structure", type=int, default=10000)
     ap.add_argument("--surrogate-epochs", type=int, default=4)
@@ -1021,7 +1023,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample-1t", type=int, default=2048, help="sources of the single-thread oracle sample")
     ap.add_argument("--march-parts", type=int, default=0,
                     help="force a march thread mapping (1-3 threads per column, 4 = 2x2 TMEM blocks, 5 = TMEM "
-                         "lateral faces, 6 = source pairs in f32x2); 0 = autotune")
+                         "lateral faces, 6 = source pairs in f32x2, 7 = column pairs with TMEM faces); 0 = autotune")
     ap.add_argument("--no-probe", action="store_true", help="skip the FP32 FMA and HBM read peak probes")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per march launch from an ncu capture of the current kernel")
@@ -1037,6 +1039,8 @@ def main(argv=None):
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if w.R == 8 and args.prec != "fp64" and not args.no_surrogate and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        args.surrogate = True
     return run_ours(args, w)
 
 

@@ -97,8 +97,10 @@ typedef struct {
                              5 = one thread per window column with its lateral face coefficients in
                              Tensor Memory; 6 = one thread per window column for a pair of sources,
                              packed f32x2 arithmetic, lateral faces of both in Tensor Memory (R <= 8);
-                             window_R 9 and 10 take 4 or 5 only (another request is autotuned between
-                             those two); 0 = autotune (each candidate timed once on the first build for a device, R
+                             7 = one thread per pair of x-adjacent window columns with their lateral faces
+                             and diagonals in Tensor Memory;
+                             window_R 9 and 10 take 4, 5 or 7 only (another request is autotuned between
+                             those three); 0 = autotune (each candidate timed once on the first build for a device, R
                              and storage type, result cached for the process; that build synchronises the
                              stream) */
     int32_t  accum;       /* fdirw_accum; FDIRW_ACCUM_FP32 needs an FP32-march precision and an fdirw_create

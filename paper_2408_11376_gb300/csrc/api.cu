@@ -297,7 +297,7 @@ int fdirw_create(const fdirw_grid* grid, const double* D_map, double dt_macro, i
     fdirw_opts o{FDIRW_FP32, -1, nullptr, 0, 0, 0};
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP64 || o.prec > FDIRW_FP32_STORE_BF16) return fail(nullptr, FDIRW_ERR_ARG, "unknown prec");
-    if (o.march_parts < 0 || o.march_parts > 6) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 6]");
+    if (o.march_parts < 0 || o.march_parts > 7) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 7]");
     if (o.accum != FDIRW_ACCUM_FF && o.accum != FDIRW_ACCUM_FP32) return fail(nullptr, FDIRW_ERR_ARG, "unknown accum");
     if (o.accum == FDIRW_ACCUM_FP32 && o.prec == FDIRW_FP64)
         return fail(nullptr, FDIRW_ERR_ARG, "FDIRW_ACCUM_FP32 needs an FP32-march precision");

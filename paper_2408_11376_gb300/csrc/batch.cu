@@ -731,7 +731,7 @@ int fdirw_create_batch(int32_t n, const fdirw_grid* grids, const double* const* 
     if (opts) o = *opts;
     if (o.prec < FDIRW_FP32 || o.prec > FDIRW_FP32_STORE_BF16)
         return fail(nullptr, FDIRW_ERR_ARG, "a batch needs an FP32-march precision (FP32, FP16 or BF16 storage)");
-    if (o.march_parts < 0 || o.march_parts > 6) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 6]");
+    if (o.march_parts < 0 || o.march_parts > 7) return fail(nullptr, FDIRW_ERR_ARG, "march_parts must be in [0, 7]");
     if (o.accum != FDIRW_ACCUM_FF && o.accum != FDIRW_ACCUM_FP32) return fail(nullptr, FDIRW_ERR_ARG, "unknown accum");
 
     DeviceGuard dg(o.device);

@@ -399,6 +399,13 @@ __global__ void __launch_bounds__(Shape<R>::THREADS64, 1) march_f64_kernel(March
 // One CTA of 256 threads per SM (two threads per TMEM lane, 256 columns each; the CTA allocates all 512
 // columns once and frees them before it exits, and its shared-memory request keeps a second CTA off the
 // SM so an allocation never waits).
+// Where the stored values of one source of a CTA batch go (written by the source's first thread, read by
+// every thread of the CTA in the epilogue).
+struct SlotInfo {
+    int64_t qbase, pos, nxy;
+    int sx, sy, sz, nx, ny, nz, ok, pad;
+};
+
 template <int R>
 struct MapTm {
     static constexpr int W1 = 2 * R + 1;
@@ -415,7 +422,7 @@ struct MapTm {
     static constexpr int LA0 = (TCOLS - 12 * W1) / 4;
     static constexpr int LA = LA0 < W1 ? LA0 : W1;        // levels whose diagonals live in TMEM
     static constexpr int NR = W1 - LA;                    // levels whose diagonals live in registers
-    static constexpr size_t SMEM_USED = (size_t)2 * BUF * 4 + (size_t)SPB * COLS * 8;
+    static constexpr size_t SMEM_USED = (size_t)2 * BUF * 4 + (size_t)SPB * COLS * 8 + (size_t)SPB * sizeof(SlotInfo);
     static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
 };
 
@@ -481,6 +488,7 @@ __global__ void __launch_bounds__(MapTm<R>::THREADS, 1) march_tm_kernel(MarchArg
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* xbuf = reinterpret_cast<float*>(smem_raw);                         // [2][W1][4][256]
     double* red = reinterpret_cast<double*>(smem_raw + (size_t)2 * BUF * 4);  // [SPB*COLS]
+    SlotInfo* sinfo = reinterpret_cast<SlotInfo*>(red + SPB * COLS);           // [SPB]
     __shared__ uint32_t s_taddr;
 
     const int t = threadIdx.x;
@@ -544,6 +552,8 @@ __global__ void __launch_bounds__(MapTm<R>::THREADS, 1) march_tm_kernel(MarchArg
         auto zface = [&](int x, int y, int k) -> float {
             return (k + 1 < W1 && cell_ok(x, y, k) && sz - R + k + 1 < nz) ? __ldg(az + gidx(x, y, k)) : 0.f;
         };
+        if (active && b == 0)
+            sinfo[slot] = SlotInfo{L.qbase, pos, nxy, sx, sy, sz, nx, ny, nz, src_ok ? 1 : 0, 0};
 
         // Registers: state u[sub][k], z faces cz[sub][k] (+z face of the cell), diagonals of the levels
         // whose TMEM slot has no room for them.  Sub-column sc = sxb + 2*syb at window (2bi+sxb, 2bj+syb).
@@ -651,23 +661,30 @@ __global__ void __launch_bounds__(MapTm<R>::THREADS, 1) march_tm_kernel(MarchArg
             }
         }
 
-        // Epilogue: store, then per-column FP64 sums in k order (same order as march_f32_kernel).
+        // Epilogue: round to the storage type, then per-column FP64 sums in k order (same order as
+        // march_f32_kernel) and the cache stores.
         float* sbuf = xbuf + (a.n_sub & 1) * BUF;
         if (active) {
 #pragma unroll
             for (int sc = 0; sc < 4; sc++) {
                 const int x = 2 * bi + (sc & 1), y = 2 * bj + (sc >> 1);
 #pragma unroll
-                for (int k = 0; k < W1; k++) {
-                    float stv = 0.f;
-                    if (cell_ok(x, y, k)) {
-                        stv = store_q(a, qplane(a, R, x, y, k), L.qbase + gidx(x, y, k), pos, u[sc][k]);
-                    }
-                    sbuf[k * LEVEL + sc * PLANE + t] = stv;
-                }
+                for (int k = 0; k < W1; k++) sbuf[k * LEVEL + sc * PLANE + t] = cell_ok(x, y, k) ? put(nullptr, a.store, 0, u[sc][k]) : 0.f;
             }
         }
         __syncthreads();
+        // Stores with the batch's sources fastest: a cell's SPB sources have adjacent destinations in the
+        // same plane, so one warp store covers about 32 / SPB cells instead of 32 planes.  The values are
+        // already rounded, so storing rounds nothing further.
+        for (int w = t; w < SPB * W1 * W1 * W1; w += blockDim.x) {
+            const int sl = w % SPB, c3 = w / SPB;
+            const int x = c3 % W1, y = (c3 / W1) % W1, k = c3 / (W1 * W1);
+            const SlotInfo& si = sinfo[sl];
+            const int gx = si.sx - R + x, gy = si.sy - R + y, gz = si.sz - R + k;
+            if (!si.ok || gx < 0 || gx >= si.nx || gy < 0 || gy >= si.ny || gz < 0 || gz >= si.nz) continue;
+            const float v = sbuf[k * LEVEL + ((x & 1) + 2 * (y & 1)) * PLANE + sl * TPS + (x >> 1) + NB * (y >> 1)];
+            store_q(a, qplane(a, R, x, y, k), si.qbase + gx + (int64_t)si.nx * gy + si.nxy * gz, si.pos, v);
+        }
         for (int c = t; c < SPB * COLS; c += blockDim.x) {
             const int sl = c / COLS, cc = c - sl * COLS;
             const int x = cc % W1, y = cc / W1;
@@ -704,6 +721,255 @@ cudaError_t launch_tm(const MarchArgs& a, int num_sms, cudaStream_t st) {
     const int64_t nbatch = (nsrc + M::SPB - 1) / M::SPB;
     const int64_t grid = nbatch < (int64_t)num_sms ? nbatch : (int64_t)num_sms;
     march_tm_kernel<R><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Column pairs with TMEM-resident faces and diagonals (mapping id 7; any R <= 10, made for R = 9, 10).
+//
+// Each thread owns two x-adjacent window columns (2 (2R+1) cells; the last pair of a window row is half
+// padding), so the halo it exchanges through shared memory per substep is 4 words per cell (its two new
+// values, the outer x neighbours and the y neighbours of both columns) instead of 5.  The 7 lateral faces
+// of a pair's level (3 x, 4 y) and its 2 diagonals live in the thread's TMEM lane (8 + 1 words, loaded one
+// level ahead); u and the z faces stay in registers, which leaves room below the register cap of a
+// 256-thread CTA at R = 10 (mapping 5 runs 448 threads there and spills under a 128-register cap).  One
+// CTA of 256 threads per SM, two threads per TMEM lane; the FP32 operations and their order are those of
+// march_f32_kernel, so the results are bitwise those of every other mapping.
+template <int R>
+struct MapTmx {
+    static constexpr int W1 = 2 * R + 1;
+    static constexpr int COLS = W1 * W1;
+    static constexpr int NBX = R + 1;                     // column pairs per window row
+    static constexpr int TPS = NBX * W1;                  // threads per source
+    static constexpr int THREADS = 256;
+    static constexpr int SPB = THREADS / TPS;
+    static constexpr int LEVEL = 2 * THREADS;             // floats per level: [sub-column][thread]
+    static constexpr int BUF = W1 * LEVEL;
+    static constexpr size_t SMEM_USED = (size_t)2 * BUF * 4 + (size_t)SPB * COLS * 8;
+    static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+    static_assert(SPB >= 1 && 9 * W1 <= 256, "a source must fit a CTA and its coefficients 256 TMEM columns");
+};
+
+__device__ __forceinline__ void tm_st1(uint32_t a, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" :: "r"(a), "r"(v) : "memory");
+}
+// The 9 words of a pair's level: 8 at a8, 1 at a1.
+__device__ __forceinline__ void tm_ld9(uint32_t a8, uint32_t a1, uint32_t (&r)[9]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(a8));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[8]) : "r"(a1));
+}
+__device__ __forceinline__ void tm_wait_ld9(uint32_t (&r)[9]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]) :: "memory");
+}
+
+template <int R>
+__global__ void __launch_bounds__(MapTmx<R>::THREADS, 1) march_tmx_kernel(MarchArgs a) {
+    using M = MapTmx<R>;
+    constexpr int W1 = M::W1, COLS = M::COLS, NBX = M::NBX, TPS = M::TPS, SPB = M::SPB;
+    constexpr int LEVEL = M::LEVEL, PLANE = M::THREADS, BUF = M::BUF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* xbuf = reinterpret_cast<float*>(smem_raw);                         // [2][W1][2][256]
+    double* red = reinterpret_cast<double*>(smem_raw + (size_t)2 * BUF * 4);  // [SPB*COLS]
+    __shared__ uint32_t s_taddr;
+
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(dst) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const uint32_t tbase = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * (warp >> 2));
+    const uint32_t regA = tbase, regB = tbase + (uint32_t)(8 * W1);      // level k: 8 words at 8k, 1 at 8 W1 + k
+
+    const bool active = t < SPB * TPS;
+    const int slot = active ? t / TPS : 0;
+    const int b = active ? t - slot * TPS : 0;
+    const int bi = b % NBX, bj = b / NBX;
+    const int tl = (active && bi > 0) ? t - 1 : t;
+    const int tr = (active && bi < NBX - 1) ? t + 1 : t;
+    const int tb = (active && bj > 0) ? t - NBX : t;
+    const int tt = (active && bj < W1 - 1) ? t + NBX : t;
+    const int64_t nbatch = (a.src_end - a.src_begin + SPB - 1) / SPB;
+
+    for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+        const int64_t first = a.src_begin + bt * SPB;
+        int64_t s = first + slot;
+        const bool src_ok = active && s < a.src_end;
+        if (src_ok && a.list) s = a.list[s];
+        const int64_t pos = first + slot;
+        const SrcLoc L = locate(a, src_ok, s);
+        const int nx = L.nx, ny = L.ny, nz = L.nz;
+        const int64_t nxy = (int64_t)nx * ny;
+        const float* ax = a.ax + L.base;
+        const float* ay = a.ay + L.base;
+        const float* az = a.az + L.base;
+        int sx = 0, sy = 0, sz = 0;
+        if (src_ok) {
+            sx = (int)(s % nx);
+            const int64_t r = s / nx;
+            sy = (int)(r % ny);
+            sz = (int)(r / ny);
+        }
+        auto cell_ok = [&](int x, int y, int k) -> bool {
+            const int gx = sx - R + x, gy = sy - R + y, gz = sz - R + k;
+            return src_ok && x >= 0 && x < W1 && y >= 0 && y < W1 && k >= 0 && k < W1 &&
+                   gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+        };
+        auto gidx = [&](int x, int y, int k) -> int64_t {
+            return (int64_t)(sx - R + x) + (int64_t)nx * (sy - R + y) + nxy * (sz - R + k);
+        };
+        auto xface = [&](int x, int y, int k) -> float {
+            return (x + 1 < W1 && cell_ok(x, y, k) && sx - R + x + 1 < nx) ? __ldg(ax + gidx(x, y, k)) : 0.f;
+        };
+        auto yface = [&](int x, int y, int k) -> float {
+            return (y + 1 < W1 && cell_ok(x, y, k) && sy - R + y + 1 < ny) ? __ldg(ay + gidx(x, y, k)) : 0.f;
+        };
+        auto zface = [&](int x, int y, int k) -> float {
+            return (k + 1 < W1 && cell_ok(x, y, k) && sz - R + k + 1 < nz) ? __ldg(az + gidx(x, y, k)) : 0.f;
+        };
+
+        // Sub-column sc at window (2 bi + sc, bj): state u[sc][k] and +z faces cz[sc][k] in registers.
+        float u[2][W1], cz[2][W1];
+#pragma unroll
+        for (int sc = 0; sc < 2; sc++) {
+            const int x = 2 * bi + sc, y = bj;
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                cz[sc][k] = zface(x, y, k);
+                u[sc][k] = (src_ok && x == R && y == R && k == R) ? 1.f : 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < W1; k++) {
+            const int x0 = 2 * bi, y = bj;
+            float f[9];
+            f[0] = bi > 0 ? xface(x0 - 1, y, k) : 0.f;        // -x face of sub-column 0
+            f[1] = xface(x0, y, k);                            // between the two sub-columns
+            f[2] = xface(x0 + 1, y, k);                        // +x face of sub-column 1
+            f[3] = bj > 0 ? yface(x0, y - 1, k) : 0.f;        // -y face of sub-column 0
+            f[4] = yface(x0, y, k);                            // +y face of sub-column 0
+            f[5] = bj > 0 ? yface(x0 + 1, y - 1, k) : 0.f;    // -y face of sub-column 1
+            f[6] = yface(x0 + 1, y, k);                        // +y face of sub-column 1
+            // diagonals, same association as march_f32_kernel: -(((cxm+cxp)+(cym+cyp))+(czm+czp))
+            f[7] = -(((f[0] + f[1]) + (f[3] + f[4])) + ((k > 0 ? cz[0][k > 0 ? k - 1 : 0] : 0.f) + cz[0][k]));
+            f[8] = -(((f[1] + f[2]) + (f[5] + f[6])) + ((k > 0 ? cz[1][k > 0 ? k - 1 : 0] : 0.f) + cz[1][k]));
+            uint32_t w[9];
+#pragma unroll
+            for (int q = 0; q < 9; q++) w[q] = __float_as_uint(f[q]);
+            tm_st8(regA + (uint32_t)(8 * k), w);
+            tm_st1(regB + (uint32_t)k, w[8]);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+        #pragma unroll(2)   // two substeps per iteration: no register copies at the back edge
+        for (int it = 0; it < a.n_sub; it++) {
+            float* buf = xbuf + (it & 1) * BUF;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < W1; k++)
+#pragma unroll
+                    for (int sc = 0; sc < 2; sc++) buf[k * LEVEL + sc * PLANE + t] = u[sc][k];
+            }
+            __syncthreads();
+            uint32_t cb[2][9];
+            tm_ld9(regA, regB, cb[0]);
+            tm_wait_ld9(cb[0]);
+            float prev[2] = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < W1; k++) {
+                uint32_t (&cc)[9] = cb[k & 1];
+                uint32_t (&cn)[9] = cb[(k + 1) & 1];
+                if (k + 1 < W1) tm_ld9(regA + (uint32_t)(8 * (k + 1)), regB + (uint32_t)(k + 1), cn);
+                const float* lv = buf + k * LEVEL;
+                const float l = lv[1 * PLANE + tl], r = lv[0 * PLANE + tr];
+                const float b0 = lv[0 * PLANE + tb], b1 = lv[1 * PLANE + tb];
+                const float t0 = lv[0 * PLANE + tt], t1 = lv[1 * PLANE + tt];
+                float c[9];
+#pragma unroll
+                for (int q = 0; q < 9; q++) c[q] = __uint_as_float(cc[q]);
+                const float cxm[2] = {c[0], c[1]}, cxp[2] = {c[1], c[2]};
+                const float cym[2] = {c[3], c[5]}, cyp[2] = {c[4], c[6]};
+                const float amv[2] = {c[7], c[8]};
+                const float uxm[2] = {l, u[0][k]}, uxp[2] = {u[1][k], r};
+                const float uym[2] = {b0, b1}, uyp[2] = {t0, t1};
+                float nu[2];
+#pragma unroll
+                for (int sc = 0; sc < 2; sc++) {
+                    const float cur = u[sc][k];
+                    float v = amv[sc] * cur;
+                    v = fmaf(cxm[sc], uxm[sc], v);
+                    v = fmaf(cxp[sc], uxp[sc], v);
+                    v = fmaf(cym[sc], uym[sc], v);
+                    v = fmaf(cyp[sc], uyp[sc], v);
+                    v = fmaf(k > 0 ? cz[sc][k > 0 ? k - 1 : 0] : 0.f, prev[sc], v);
+                    v = fmaf(cz[sc][k], k + 1 < W1 ? u[sc][k + 1 < W1 ? k + 1 : k] : 0.f, v);
+                    nu[sc] = __fadd_rn(cur, v);
+                }
+#pragma unroll
+                for (int sc = 0; sc < 2; sc++) { prev[sc] = u[sc][k]; u[sc][k] = nu[sc]; }
+                if (k + 1 < W1) tm_wait_ld9(cn);
+            }
+        }
+
+        // Epilogue: store, then per-column FP64 sums in k order (same order as march_f32_kernel).
+        float* sbuf = xbuf + (a.n_sub & 1) * BUF;
+        if (active) {
+#pragma unroll
+            for (int sc = 0; sc < 2; sc++) {
+                const int x = 2 * bi + sc, y = bj;
+#pragma unroll
+                for (int k = 0; k < W1; k++) {
+                    float stv = 0.f;
+                    if (cell_ok(x, y, k)) stv = store_q(a, qplane(a, R, x, y, k), L.qbase + gidx(x, y, k), pos, u[sc][k]);
+                    sbuf[k * LEVEL + sc * PLANE + t] = stv;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < SPB * COLS; c += blockDim.x) {
+            const int sl = c / COLS, cc = c - sl * COLS;
+            const int x = cc % W1, y = cc / W1;
+            const int tt2 = sl * TPS + (x >> 1) + NBX * y;
+            const int sc = x & 1;
+            double colsum = 0.0;
+#pragma unroll
+            for (int k = 0; k < W1; k++) colsum += (double)sbuf[k * LEVEL + sc * PLANE + tt2];
+            red[c] = colsum;
+        }
+        __syncthreads();
+        finish_sigma<COLS, SPB>(red, first, a.src_end, a.list, a.sigma);
+        __syncthreads();
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr) : "memory");
+}
+
+template <int R>
+cudaError_t launch_tmx(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    using M = MapTmx<R>;
+    const int64_t nsrc = a.src_end - a.src_begin;
+    if (nsrc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(march_tmx_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_tmx_kernel<R>, M::THREADS, M::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm != 1) return cudaErrorInvalidConfiguration;   // TMEM allocation assumes one CTA per SM
+    const int64_t nbatch = (nsrc + M::SPB - 1) / M::SPB;
+    const int64_t grid = nbatch < (int64_t)num_sms ? nbatch : (int64_t)num_sms;
+    march_tmx_kernel<R><<<(unsigned)grid, M::THREADS, M::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1292,6 +1558,7 @@ cudaError_t launch_f32_p(const MarchArgs& a, int P, int num_sms, cudaStream_t st
         case 4: return launch_tm<R>(a, num_sms, st);
         case 5: return a.bx ? launch_tmc<R, false, true>(a, num_sms, st) : launch_tmc<R>(a, num_sms, st);
         case 6: return launch_tmp<R>(a, num_sms, st);
+        case 7: return launch_tmx<R>(a, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1338,9 +1605,11 @@ cudaError_t dispatch(const MarchArgs& a, int P, int num_sms, cudaStream_t st) {
         case 7: return launch_f32_p<7>(a, P, num_sms, st);
         case 8: return launch_f32_p<8>(a, P, num_sms, st);
         case 9: return P == 5 ? (a.bx ? launch_tmc<9, false, true>(a, num_sms, st) : launch_tmc<9>(a, num_sms, st))
-                       : P == 4 ? launch_tm<9>(a, num_sms, st) : cudaErrorInvalidValue;
+                       : P == 4 ? launch_tm<9>(a, num_sms, st) : P == 7 ? launch_tmx<9>(a, num_sms, st)
+                       : cudaErrorInvalidValue;
         case 10: return P == 5 ? (a.bx ? launch_tmc<10, false, true>(a, num_sms, st) : launch_tmc<10>(a, num_sms, st))
-                        : P == 4 ? launch_tm<10>(a, num_sms, st) : cudaErrorInvalidValue;
+                        : P == 4 ? launch_tm<10>(a, num_sms, st) : P == 7 ? launch_tmx<10>(a, num_sms, st)
+                        : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1367,9 +1636,9 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     float best_ms = 1e30f;
     *best = default_parts(a.R);
-    for (int P = 1; P <= 6 && e == cudaSuccess; P++) {
+    for (int P = 1; P <= 7 && e == cudaSuccess; P++) {
         if (P <= 3 && P > W1) continue;
-        if (a.R > 8 && (P < 4 || P > 5)) continue; // only mappings 4 and 5 cover R = 9, 10
+        if (a.R > 8 && (P < 4 || P == 6)) continue; // mappings 4, 5 and 7 cover R = 9, 10
         if (P == 5 && a.R < 6) continue;          // one CTA of < 6 warps per SM: never the fastest there
         e = dispatch(warm, P, num_sms, st);
         float ms = 1e30f;
@@ -1393,7 +1662,10 @@ cudaError_t tune_parts(const MarchArgs& a, int num_sms, cudaStream_t st, int* be
 
 cudaError_t tune_march(const MarchArgs& a, int num_sms, int parts_req, cudaStream_t st, int* parts) {
     if (a.store == Store::F64) { *parts = 1; return cudaSuccess; }
-    if (parts_req >= 1 && parts_req <= 6 && (a.R <= 8 || parts_req == 4 || parts_req == 5)) { *parts = parts_req; return cudaSuccess; }
+    if (parts_req >= 1 && parts_req <= 7 && (a.R <= 8 || parts_req == 4 || parts_req == 5 || parts_req == 7)) {
+        *parts = parts_req;
+        return cudaSuccess;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     const auto key = std::make_tuple(dev, a.R, (int)a.store);
@@ -1434,7 +1706,7 @@ cudaError_t launch_march(const MarchArgs& a, int num_sms, int parts_req, cudaStr
         return dispatch(a, 5, num_sms, st);
     }
     if (a.store != Store::F64) {
-        if (parts_req >= 1 && parts_req <= 6 && (a.R <= 8 || parts_req == 4 || parts_req == 5)) {
+        if (parts_req >= 1 && parts_req <= 7 && (a.R <= 8 || parts_req == 4 || parts_req == 5 || parts_req == 7)) {
             P = parts_req;
         } else {
             int dev = 0;

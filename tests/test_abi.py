@@ -47,7 +47,7 @@ def test_host_side_argument_checks(lib):
         assert fdirw.fdirw_last_error()
     g = fdirw.fdirw_grid(4, 4, 4, 1.0)
     assert lib.fdirw_create(ctypes.byref(g), None, 1.0, 2, 3, None, ctypes.byref(ctypes.c_void_p())) == fdirw.FDIRW_ERR_ARG
-    for R, bad_opts in ((2, fdirw.fdirw_opts(7, -1, None, 0, 0, 0)), (2, fdirw.fdirw_opts(1, -1, None, 0, 7, 0)),
+    for R, bad_opts in ((2, fdirw.fdirw_opts(7, -1, None, 0, 0, 0)), (2, fdirw.fdirw_opts(1, -1, None, 0, 8, 0)),
                         (9, fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)),
                         (2, fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, 2)),                  # unknown accum
                         (2, fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, fdirw.FDIRW_ACCUM_FP32))):
@@ -65,13 +65,13 @@ def test_batch_host_side_argument_checks(lib):
     ptrs = (ctypes.c_void_p * 2)(D.ctypes.data, D.ctypes.data)
     huge = (fdirw.fdirw_grid * 1)(fdirw.fdirw_grid(1024, 1024, 256, 1.0))     # 2^28 cells
     fp64 = fdirw.fdirw_opts(fdirw.FDIRW_FP64, -1, None, 0, 0, 0)
-    parts7 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 7, 0)
+    parts8 = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 8, 0)
     bad_grid = (fdirw.fdirw_grid * 1)(fdirw.fdirw_grid(4, 0, 4, 1.0))
     acc_bad = fdirw.fdirw_opts(fdirw.FDIRW_FP32, -1, None, 0, 0, 2)
     cases = [(0, g, ptrs, 1.0, 1, 3, 2, None), (2, None, ptrs, 1.0, 1, 3, 2, None), (2, g, None, 1.0, 1, 3, 2, None),
              (2, g, ptrs, 1.0, 1, 11, 2, None), (2, g, ptrs, 1.0, 4, 3, 2, None), (2, g, ptrs, 1.0, -1, 3, 2, None),
              (2, g, ptrs, -1.0, 1, 3, 2, None), (2, g, ptrs, 1.0, 1, 3, -2, None), (1, huge, ptrs, 1.0, 1, 3, 2, None),
-             (2, g, ptrs, 1.0, 1, 3, 2, fp64), (2, g, ptrs, 1.0, 1, 3, 2, parts7), (1, bad_grid, ptrs, 1.0, 1, 3, 2, None),
+             (2, g, ptrs, 1.0, 1, 3, 2, fp64), (2, g, ptrs, 1.0, 1, 3, 2, parts8), (1, bad_grid, ptrs, 1.0, 1, 3, 2, None),
              (2, g, ptrs, 1.0, 1, 3, 2, acc_bad)]
     for n, grids, dm, dt, rmin, rmax, n_sub, opts in cases:
         ctx = ctypes.c_void_p(1234)

@@ -93,17 +93,18 @@ def test_kernels_match_oracle(prec, shape, R, n_sub):
 
 @pytest.mark.parametrize("R", [9, 10])
 def test_large_radius_mappings_agree_bitwise(R):
-    """R = 9, 10 run on mapping 4 (2x2 blocks, one source per CTA) and mapping 5 (one column per thread):
-    same bits."""
+    """R = 9, 10 run on mapping 4 (2x2 blocks, one source per CTA), mapping 5 (one column per thread) and
+    mapping 7 (column pairs): same bits."""
     shape = (23, 22, 21)
     D = _case(shape, 83, "per_sphere")
     lam = oracle.stable_dt_sub(shape, D)
     N = int(np.prod(shape))
     c0 = synth.random_field(N, 84)
     src = np.arange(1, N, 29)
-    runs = [_gpu_run(shape, D, lam, R, 31, c0, 2, "fp32", src, parts=P) for P in (4, 5)]
-    assert [r[3]["march_parts"] for r in runs] == [4, 5]
-    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][2], runs[1][2])
+    runs = [_gpu_run(shape, D, lam, R, 31, c0, 2, "fp32", src, parts=P) for P in (4, 5, 7)]
+    assert [r[3]["march_parts"] for r in runs] == [4, 5, 7]
+    for got, m, ks, info in runs[1:]:
+        assert np.array_equal(runs[0][0], got) and np.array_equal(runs[0][2], ks)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -216,18 +217,19 @@ def test_one_dimensional_chain():
 @pytest.mark.parametrize("R", [2, 5, 8])
 def test_thread_mappings_agree_bitwise(R):
     """Every thread mapping of the FP32 march (1, 2 or 3 threads per window column, 2x2 column blocks
-    with TMEM-resident coefficients, one column per thread with TMEM-resident lateral faces, or one
-    column of a source pair per thread in packed f32x2 arithmetic) gives the same bits."""
+    with TMEM-resident coefficients, one column per thread with TMEM-resident lateral faces, one column
+    of a source pair per thread in packed f32x2 arithmetic, or column pairs with TMEM-resident faces and
+    diagonals) gives the same bits."""
     shape = (19, 17, 13)
     D = _case(shape, 81, "per_sphere")
     lam = oracle.stable_dt_sub(shape, D)
     N = int(np.prod(shape))
     c0 = synth.random_field(N, 82)
     src = np.arange(0, N, 7)
-    runs = [_gpu_run(shape, D, lam, R, 37, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5, 6)]
+    runs = [_gpu_run(shape, D, lam, R, 37, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5, 6, 7)]
     for got, m, ks, info in runs[1:]:
         assert np.array_equal(got, runs[0][0]) and np.array_equal(ks, runs[0][2]) and m == runs[0][1]
-    assert [r[3]["march_parts"] for r in runs] == [1, 2, 3, 4, 5, 6]
+    assert [r[3]["march_parts"] for r in runs] == [1, 2, 3, 4, 5, 6, 7]
     ref, _ = oracle.kernels(shape, D, lam, R, 37, src)
     err = np.linalg.norm((runs[0][2] - ref).reshape(len(src), -1), axis=1) / np.linalg.norm(ref.reshape(len(src), -1), axis=1)
     assert err.max() <= KERNEL_TOL["fp32"]
@@ -244,7 +246,7 @@ def test_thin_domains_every_mapping(shape):
     c0 = synth.random_field(N, 92)
     src = np.arange(N)
     for R in (3, 8):
-        runs = [_gpu_run(shape, D, lam, R, 21, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5, 6)]
+        runs = [_gpu_run(shape, D, lam, R, 21, c0, 2, "fp32", src, parts=P) for P in (1, 2, 3, 4, 5, 6, 7)]
         for got, m, ks, info in runs[1:]:
             assert np.array_equal(got, runs[0][0]) and np.array_equal(ks, runs[0][2]) and m == runs[0][1]
         ref, _ = oracle.kernels(shape, D, lam, R, 21, src)
