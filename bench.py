@@ -204,11 +204,11 @@ def march_kernel_name(prec: str, parts: int) -> str:
 
 
 # DRAM bytes (read + write) per clipped window cell of march_tm_kernel<8> with BF16 storage, from one ncu
-# capture of the 64^3 case with the same recipe (`--set full` on the first march launch of
-# `bench.py --workload fdirw-64c-r8 --prec bf16 --march-parts 4`: 1.262 GB read + 3.117 GB written over
-# 1.049e9 window cells); the traffic of a full launch scales with its window cells (the stored kernel values
-# dominate it).  Valid for that kernel, radius and storage only.
-TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL = (1.261629e9 + 3.116823e9) / 1.049e9
+# capture of the 64^3 case with the same recipe (`--set full` on the first march launch of `bench.py
+# --workload fdirw-64c-r8 --prec bf16 --march-parts 4 --no-surrogate --no-probe`: 0.641 GB read + 2.307 GB
+# written over 1.0488e9 window cells); the traffic of a full launch scales with its window cells (the
+# stored kernel values dominate it).  Valid for that kernel, radius and storage only.
+TM_R8_BF16_DRAM_BYTES_PER_WINDOW_CELL = (0.641067008e9 + 2.306592e9) / 1048772096
 
 
 def march_traffic(args, prec: str, parts: int, R: int, window_cells: float):
@@ -278,11 +278,10 @@ def fp32_alu_roofline(torch, dev, n_sub: int, window_cells: float, march_ms: flo
 
 
 # Shared-memory wavefronts of march_tm_kernel<8> per COMPUTED thread-cell-substep (every CTA batch marches 256
-# threads x 68 cells whatever the windows' clipping), from the 64^3 capture of that kernel with the 192^3
-# recipe (`--set full` on the first march launch of `bench.py --workload fdirw-64c-r8 --prec bf16
-# --march-parts 4`: 3.23e10 wavefronts over 87,382 batches x 256 x 68 x 200).  A launch's wavefronts scale
-# with its computed cells; the shared-memory peak is one 128-byte wavefront per SM-cycle (32 banks x 4 B).
-TM_R8_SMEM_WAVEFRONTS_PER_COMPUTED_CELL = 3.23e10 / (87382 * 256 * 68 * 200)
+# threads x 68 cells whatever the windows' clipping), from the same 64^3 capture: 3.298e10 wavefronts over
+# 87,382 batches x 256 x 68 x 200.  A launch's wavefronts scale with its computed cells; the shared-memory
+# peak is one 128-byte wavefront per SM-cycle (32 banks x 4 B).
+TM_R8_SMEM_WAVEFRONTS_PER_COMPUTED_CELL = 3.2981171846e10 / (87382 * 256 * 68 * 200)
 
 
 def march_smem(n_src: int, n_sub: int, R: int, parts: int, march_ms: float, sm_mhz: float, num_sms: int):
@@ -664,6 +663,9 @@ def run_ours(args, w):
     }
     if fp64:
         line["speedup_vs_fp64_gpu"] = value / fp64["macro_steps_per_s"]
+    if args.oracle_full_step:
+        line["oracle_full_step"] = oracle_full_step_leg(fdirw, torch, stream, w, shape, D, D_host, c0, c_host, dt_macro,
+                                                        prec, args.accum)
     if args.surrogate:
         line["surrogate"] = surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec, ref64)
     if args.coarse:
@@ -676,6 +678,33 @@ def run_ours(args, w):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def oracle_full_step_leg(fdirw, torch, stream, w, shape, D, D_host, c0, c_host, dt_macro, prec, accum):
+    """One complete macro step of the workload by the FP64 oracle on all host cores (every source's kernel
+    marched on the CPU; the per-source-radius superposition with every radius = R, which the oracle's pins
+    tie to the uniform one bit for bit), against the plain FP64 GPU path and the bench's precision."""
+    import oracle
+    N = c0.numel()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    ref = oracle.superpose_rmap(shape, D_host, dt_macro / w.n_sub, np.full(N, w.R, dtype=np.int32), w.n_sub, c_host)
+    t_oracle = time.perf_counter() - t0
+    refd = torch.from_numpy(ref).to(c0.device)
+    out = {"oracle_s": t_oracle, "cores": threads, "cpu_model": cpu_model()}
+    for p, acc in (("fp64", "ff"), (prec, accum)):
+        with torch.cuda.stream(stream):
+            ctx = fdirw.fdirw_create(shape, D, dt_macro, w.R, w.n_sub, p, stream=stream, accum=acc)
+            got = torch.empty_like(c0)
+            fdirw.fdirw_step(ctx, c0, got, 1)
+            fdirw.fdirw_destroy(ctx)
+        stream.synchronize()
+        out[f"rel_l2_{p}_{acc}_vs_oracle"] = float((torch.linalg.vector_norm(got - refd) /
+                                                    torch.linalg.vector_norm(refd)).item())
+        del got
+        torch.cuda.empty_cache()
+    return out
 
 
 def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, prec, ref64=None):
@@ -1007,6 +1036,9 @@ def main(argv=None):
     ap.add_argument("--surrogate", action="store_true",
                     help="train the learned surrogate and compare its gated build (on by default for R = 8 single grids)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--oracle-full-step", action="store_true",
+                    help="also run one complete macro step with the FP64 oracle on all host cores (about 15 min at "
+                         "192^3) and compare the GPU's FP64 and default-precision steps with it")
     ap.add_argument("--surrogate-structures", type=int, default=20)
     ap.add_argument("--surrogate-per-structure", type=int, default=10000)
     ap.add_argument("--surrogate-epochs", type=int, default=4)
