@@ -792,6 +792,8 @@ def surrogate_leg(args, fdirw, torch, dev, stream, w, shape, D, c0, dt_macro, pr
            "field_rel_l2_vs_fd_after_steps": float((torch.linalg.vector_norm(sgm["field"] - fd["field"]) /
                                                      torch.linalg.vector_norm(fd["field"])).item()),
            "mass_rel_err": abs(sgm["mass"] - mass0) / mass0}
+    # one training step (forward, loss, tensor-core input and weight gradients, Adam) of 256 sources
+    out["train_step"] = sg.train_rate(20, device=dev.index if dev.index is not None else 0)
     if ref64 is not None:
         out["field_rel_l2_vs_fp64_after_steps"] = float((torch.linalg.vector_norm(sgm["field"] - ref64) /
                                                           torch.linalg.vector_norm(ref64)).item())

@@ -14,11 +14,13 @@
 // no-swizzle operand (LBO = distance between the halves, SBO = 8 rows) -- no im2col copy.  One thread
 // issues the MMAs, tcgen05.commit signals an mbarrier, and 4 warps drain the accumulators with
 // tcgen05.ld.  The same kernel runs the input gradient (flipped, transposed taps, ReLU mask in the
-// epilogue).  The weight gradient (a reduction over voxels with M = 16 channels, too thin for UMMA)
-// runs on the FP32 pipe with a fixed-order two-stage reduction.
+// epilogue).  The weight and bias gradients (wgrad_kernel) reduce over voxel rows on the tensor cores too:
+// the dz-shifted activation rows and a ones group stacked into M, the (dx, dy)-shifted gradient rows into
+// N = 144, both MN-major, gathered by tensor copies through overlapping tensor-map views.
 #include "ctx.h"
 #include "tc.cuh"
 
+#include <cuda.h>   // CUtensorMap and its encoding enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -414,71 +416,193 @@ __global__ void __launch_bounds__(256) head_store_kernel(const float* __restrict
     }
 }
 
-// Weight gradient of one layer: partial[tap][blk][co][ci] = sum over this block's voxels of
-// act[v + tap][ci] * grad[v][co]; the voxels of the batch (interior only) are split into fixed chunks.
-constexpr int WG_BLOCKS = 64, WG_CHUNK = 64;
-__global__ void __launch_bounds__(256) wgrad_partial_kernel(const __nv_bfloat16* __restrict__ act,
-                                                            const __nv_bfloat16* __restrict__ grad, int n,
-                                                            float* __restrict__ partial) {
-    __shared__ float As[WG_CHUNK][C + 1], Gs[WG_CHUNK][C + 1];
-    const int tap = blockIdx.x, blk = blockIdx.y;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int co = threadIdx.x / C, ci = threadIdx.x % C;
-    const int64_t total = (int64_t)n * KV;
-    const int64_t per = (total + WG_BLOCKS - 1) / WG_BLOCKS;
-    const int64_t lo = blk * per, hi = lo + per < total ? lo + per : total;
-    float acc = 0.f;
-    for (int64_t base = lo; base < hi; base += WG_CHUNK) {
-        for (int e = threadIdx.x; e < WG_CHUNK * C; e += blockDim.x) {
-            const int qv = e / C, c = e % C;
-            const int64_t u = base + qv;
-            float av = 0.f, gv = 0.f;
-            if (u < hi) {
-                const int b = (int)(u / KV), v = (int)(u % KV);
-                const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
-                const int64_t half = c < 8 ? 0 : ROWS;
-                const __nv_bfloat16* pa = act + (int64_t)b * PATCH + (half + prow(i + dx, j + dy, k + dz)) * 8 + (c & 7);
-                const __nv_bfloat16* pg = grad + (int64_t)b * PATCH + (half + prow(i, j, k)) * 8 + (c & 7);
-                av = __bfloat162float(*pa);
-                gv = __bfloat162float(*pg);
-            }
-            As[qv][c] = av;
-            Gs[qv][c] = gv;
+// Weight and bias gradients of one layer on the tensor cores.  dW[tap][co][ci] = sum over rows r' of
+// act[r' + off(tap)][ci] grad[r'][co] and db[co] = sum over r' of grad[r'][co], r' over the interior rows
+// (grad is zero on halo rows), off(tap) = dx + 19 dy + 361 dz.  The reduction runs over rows, so both
+// operands are MN-major (channels contiguous within a 16-byte row), and the taps are split between them:
+// with r = r' - dx - 19 dy, the term is act[r + 361 dz][ci] grad[r + dx' + 19 dy'][co], dx' = -dx, dy' = -dy.
+// Per 32-row unit (rows r of padded planes 1..17, which the +-20-row in-plane shifts cannot push past the
+// plane halo):
+//   A (M = 128): groups g = 3 h + dz_i (g < 6) hold channels 8h.. of act rows r + 361 (dz_i - 1); group 6
+//     holds ones (its D rows are db); groups 7..15 are never read back;
+//   B (N = 144): groups 9 h + 3 dy_i + dx_i hold channels 8h.. of grad rows r + (dx_i - 1) + 19 (dy_i - 1);
+// so ONE MMA (K = 16 rows) yields every (tap, ci, co) pair: the MMA's cost does not depend on N, so one
+// N = 144 MMA replaces four N = 16 ones.  In the no-swizzle MN-major layout a core matrix is 8 rows x 16
+// bytes; a group of a unit is 512 contiguous bytes, core matrices of consecutive rows 128 B apart (the K
+// stride), groups 512 B apart (the M / N stride).
+//   Both operands arrive as one tiled tensor copy each: the activation buffer is described to the TMA unit
+//   as an overlapping 3-D view (rows x channels flattened: the unit's 256 elements, dz: 361 rows, half), the
+//   gradient buffer as a 4-D one (elements, dx: 16 B, dy: 19 rows, half); each box lands in shared memory in
+//   the group order above.
+//   warp 0 (one thread): copies WG_SUB units per stage into a ring of WG_NST stages (full / empty mbarriers);
+//   warp 1 (one thread): 2 MMAs (M = 128, N = 144, K = 16) per unit, accumulating in TMEM over the CTA's
+//     contiguous range of units, then commits to the done barrier;
+//   warps 0..3: read the accumulator (warp w: TMEM lanes 32 w..) into partial[part][slot][co][ci].
+// Fixed partition into WG_PARTS ranges and a fixed-order sum over them (wgrad_reduce_kernel): the result
+// depends on the batch only.  Waits are bounded like the convolution's (err 1, or 2 if MMAs or copies may
+// still be in flight).
+constexpr int WG_ROWS = 32;                                        // rows (the K extent) per unit
+constexpr int WG_UNITS = (SP * PLANE + WG_ROWS - 1) / WG_ROWS;    // units per patch: 192
+constexpr int WG_SLOTS = 32;                                       // partial slots: 27 taps, the bias, 4 unused
+constexpr int WG_GROUP = WG_ROWS * 16;                             // bytes per 8-channel group of a unit: 512
+constexpr int WG_NA = 6, WG_NB = 18;                               // copied groups of A and of B
+constexpr int WG_ONES = WG_NA * WG_GROUP;                          // A group 6
+constexpr int WG_B = 8 * WG_GROUP;                                 // B (A's unread groups 8..15 overlay it)
+constexpr int WG_UNIT = WG_B + WG_NB * WG_GROUP;                   // shared bytes per unit: 13312
+constexpr int WG_N = WG_NB * 8;                                    // MMA N: 144
+constexpr int WG_SUB = 4;                                          // units per ring stage
+constexpr int WG_NST = 3;                                          // ring stages
+constexpr int WG_PARTS = 152;                                      // CTAs, each a contiguous range of units
+constexpr int WG_THREADS = 128;
+constexpr uint32_t WG_TX = (WG_NA + WG_NB) * WG_GROUP;            // bytes copied per unit
+constexpr size_t WG_SMEM = (size_t)WG_NST * WG_SUB * WG_UNIT + (2 * WG_NST + 1) * 8 + 16;
+static_assert(WG_ROWS * 8 == 256, "one box row is 256 BF16 elements");
+static_assert(16 * WG_GROUP <= WG_UNIT, "A's 16 groups stay inside the unit's shared bytes");
+// The first unit's rows start at plane 1; the last unit ends 7 rows into plane 18.  A reaches one plane
+// either way, B 20 rows either way: inside the guard rows of the patch's half, and B inside the volume.
+static_assert(GUARD + PLANE - PLANE >= 0, "A rows below the first unit leave the patch");
+static_assert(GUARD + PLANE + WG_UNITS * WG_ROWS + PLANE <= ROWS, "A rows past the last unit leave the patch");
+static_assert(PLANE + WG_UNITS * WG_ROWS + PP + 1 <= VOL, "B rows past the last unit leave the volume");
+
+struct WgradArgs {
+    float* partial;                 // [WG_PARTS][WG_SLOTS][C co][C ci]
+    int batch;
+    int* err;
+    uint64_t wait_ns;
+};
+
+// tm_act: the layer's input [batch][PATCH] as the view (elements, dz, half), box (256, 3, 2); tm_grad: the
+// gradient of its output as (elements, dx, dy, half), box (256, 3, 3, 2).
+__global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(const __grid_constant__ CUtensorMap tm_act,
+                                                           const __grid_constant__ CUtensorMap tm_grad, WgradArgs a) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)WG_NST * WG_SUB * WG_UNIT);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * WG_NST + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    constexpr int FULL = 0, EMPTY = WG_NST, DONE = 2 * WG_NST;
+    const uint32_t sbase = tc::smem_u32(sm), bar0 = tc::smem_u32(bars);
+    auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    const int64_t units = (int64_t)a.batch * WG_UNITS;
+    const int64_t u_lo = units * blockIdx.x / WG_PARTS, u_hi = units * (blockIdx.x + 1) / WG_PARTS;
+    const int nstage = (int)((u_hi - u_lo + WG_SUB - 1) / WG_SUB);
+
+    if (warp == 1) tc::tmem_alloc(tslot, 256);
+    if (t == 0) {
+        for (int i = 0; i < WG_NST; i++) {
+            tc::mbar_init(bar(FULL + i), 1);
+            tc::mbar_init(bar(EMPTY + i), 1);
         }
-        __syncthreads();
-#pragma unroll 8
-        for (int qv = 0; qv < WG_CHUNK; qv++) acc = fmaf(As[qv][ci], Gs[qv][co], acc);
-        __syncthreads();
+        tc::mbar_init(bar(DONE), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    partial[(((int64_t)tap * WG_BLOCKS + blk) * C + co) * C + ci] = acc;
-}
-
-// dW[layer][tap][co][ci] = sum over blocks (in order); db[layer][co] = sum of grad over interior voxels.
-__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, float* __restrict__ dW) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= TAPS * C * C) return;
-    const int tap = e / (C * C), rc = e % (C * C);
-    float s = 0.f;
-    for (int b = 0; b < WG_BLOCKS; b++) s += partial[((int64_t)tap * WG_BLOCKS + b) * C * C + rc];
-    dW[e] = s;
-}
-
-__global__ void __launch_bounds__(256) bgrad_kernel(const __nv_bfloat16* __restrict__ grad, int n, float* __restrict__ db) {
-    __shared__ float sh[256];
-    const int c = blockIdx.x;                   // one block per channel, fixed-order tree
-    float acc = 0.f;
-    for (int64_t u = threadIdx.x; u < (int64_t)n * KV; u += blockDim.x) {
-        const int b = (int)(u / KV), v = (int)(u % KV);
-        const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
-        acc += __bfloat162float(grad[(int64_t)b * PATCH + ((c < 8 ? 0 : ROWS) + prow(i, j, k)) * 8 + (c & 7)]);
-    }
-    sh[threadIdx.x] = acc;
+    // A group 6 of every unit slot: ones (BF16 1.0 = 0x3F80); the copies never write it
+    constexpr int ONE_WORDS = WG_GROUP / 4;
+    for (int i = t; i < WG_NST * WG_SUB * ONE_WORDS; i += WG_THREADS)
+        reinterpret_cast<uint32_t*>(sm + (size_t)(i / ONE_WORDS) * WG_UNIT + WG_ONES)[i % ONE_WORDS] = 0x3F803F80u;
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
-        __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    int err = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {                                  // producer
+            bool alive = true;
+            int q = 0;
+            for (; q < nstage; q++) {
+                const uint32_t s = (uint32_t)q % WG_NST, use = (uint32_t)q / WG_NST;
+                if (use > 0 && !tc::mbar_wait(bar(EMPTY + (int)s), (use - 1) & 1u, a.wait_ns)) { alive = false; break; }
+                const int64_t u0 = u_lo + (int64_t)q * WG_SUB;
+                const int cnt = u_hi - u0 < WG_SUB ? (int)(u_hi - u0) : WG_SUB;
+                tc::mbar_arrive_expect_tx(bar(FULL + (int)s), (uint32_t)cnt * WG_TX);
+                for (int j = 0; j < cnt; j++) {
+                    const int64_t u = u0 + j;
+                    // buffer row of the unit's first row r (patch-major, half 0)
+                    const int64_t row = (u / WG_UNITS) * 2 * ROWS + GUARD + PLANE + (u % WG_UNITS) * WG_ROWS;
+                    const uint32_t dst = sbase + (s * WG_SUB + (uint32_t)j) * WG_UNIT;
+                    tc::tma_load_3d(dst, &tm_act, (int)((row - PLANE) * 8), 0, 0, bar(FULL + (int)s));
+                    tc::tma_load_4d(dst + WG_B, &tm_grad, (int)((row - PP - 1) * 8), 0, 0, 0, bar(FULL + (int)s));
+                }
+            }
+            for (int sl = 0; sl < WG_NST && sl < q; sl++) {   // the last copies into every used stage have landed
+                const uint32_t last = (uint32_t)(q - 1 - sl) / WG_NST;
+                if (!tc::mbar_wait(bar(FULL + sl), last & 1u, a.wait_ns)) err = 2;
+            }
+            if (!alive && err == 0) err = 1;
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {                                  // MMA issuer
+            // A and B MN-major (instruction descriptor bits 15 and 16); descriptors: K stride 128 B (8 rows),
+            // M / N stride 512 B (one group).  The start-address field counts 16-byte units.
+            constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, WG_N) | (1u << 15) | (1u << 16);
+            const uint64_t d0 = tc::smem_desc(sbase, 128, WG_GROUP);
+            bool alive = true, issued = false;
+            for (int q = 0; q < nstage; q++) {
+                const uint32_t s = (uint32_t)q % WG_NST;
+                if (!tc::mbar_wait(bar(FULL + (int)s), ((uint32_t)q / WG_NST) & 1u, a.wait_ns)) { alive = false; break; }
+                tc::fence_after_sync();
+                const int64_t u0 = u_lo + (int64_t)q * WG_SUB;
+                const int cnt = u_hi - u0 < WG_SUB ? (int)(u_hi - u0) : WG_SUB;
+                for (int j = 0; j < cnt; j++) {
+                    const uint32_t ub = (s * WG_SUB + (uint32_t)j) * WG_UNIT;
+#pragma unroll
+                    for (int k = 0; k < WG_ROWS / 16; k++)
+                        tc::mma_bf16(tmem, d0 + (uint64_t)((ub + k * 256) >> 4), d0 + (uint64_t)((ub + WG_B + k * 256) >> 4),
+                                     IDESC, (q > 0 || j > 0 || k > 0) ? 1u : 0u);
+                }
+                issued = true;
+                tc::mma_commit(bar(EMPTY + (int)s));
+            }
+            if (issued) tc::mma_commit(bar(DONE));        // arrives once every MMA issued has completed
+            else tc::mbar_arrive(bar(DONE));
+            if (!alive) err = 1;
+        }
+        __syncwarp();
     }
-    if (threadIdx.x == 0) db[c] = sh[0];
+    // epilogue: D row 8 gA + c (A group gA, channel c), column 8 gB + c' (B group gB, channel c')
+    const bool done = __all_sync(0xffffffffu, tc::mbar_wait(bar(DONE), 0, a.wait_ns) ? 1 : 0) != 0;
+    if (!done) {
+        if (lane == 0) err = 2;                           // MMAs may still be running
+    } else if (u_hi > u_lo) {
+        tc::fence_after_sync();
+        const int mrow = 32 * warp + lane, ga = mrow / 8, c8 = mrow % 8;
+        const bool ones = ga == WG_NA && c8 == 0;         // the bias row
+        float* part = a.partial + (int64_t)blockIdx.x * WG_SLOTS * C * C;
+        for (int jc = 0; jc < WG_N / 16; jc++) {
+            float v[16];
+            tc::tmem_ld16_wait(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * jc), v);
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int gb = 2 * jc + i / 8, co = 8 * (gb / 9) + i % 8, dyi = (gb / 3) % 3, dxi = gb % 3;
+                if (ga < WG_NA) {
+                    const int tap = (2 - dxi) + 3 * (2 - dyi) + 9 * (ga % 3), ci = 8 * (ga / 3) + c8;
+                    part[((int64_t)tap * C + co) * C + ci] = v[i];
+                } else if (ones && dyi == 1 && dxi == 1) {
+                    part[((int64_t)TAPS * C + co) * C] = v[i];
+                }
+            }
+        }
+    } else {                                              // no units: a zero partial
+        for (int i = t; i < WG_SLOTS * C * C; i += WG_THREADS) a.partial[(int64_t)blockIdx.x * WG_SLOTS * C * C + i] = 0.f;
+    }
+    if (err) atomicMax(a.err, err);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 256);
+}
+
+// dW[tap][co][ci] = sum over the WG_PARTS partials in order; db[co] = the same sum of the ones slot (ci 0).
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, float* __restrict__ dW, float* __restrict__ db) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= TAPS * C * C + C) return;
+    const int64_t idx = e < TAPS * C * C ? e : (int64_t)TAPS * C * C + (int64_t)(e - TAPS * C * C) * C;
+    float s = 0.f;
+    for (int p = 0; p < WG_PARTS; p++) s += partial[(int64_t)p * WG_SLOTS * C * C + idx];
+    if (e < TAPS * C * C) dW[e] = s;
+    else db[e - TAPS * C * C] = s;
 }
 
 // Canonical UMMA layouts of the BF16 weights for the N = 48 convolution: per (dy, dx) tap txy = (dx+1) +
@@ -556,6 +680,8 @@ struct fdirw_net {
     float* partial = nullptr;
     float* grads = nullptr;
     int* derr = nullptr;
+    CUtensorMap tm_act[NL];        // weight-gradient views of act[l] and gbuf[i] (encoded with the buffers)
+    CUtensorMap tm_grad[2];
     cudaEvent_t ev[2] = {};        // around the four convolutions of the last forward pass
     bool timed = false;
     uint64_t wait_ns = WAIT_NS;    // budget of each MMA wait (fdirw_net_test_wait)
@@ -579,6 +705,51 @@ int nfail(fdirw_net* net, int code, const std::string& msg) {
         if (e_ != cudaSuccess) return nfail((net), FDIRW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, fetched once through the runtime (no link against the driver library).
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor maps of the weight gradient for buffers of `cap` patches.  Activation view, innermost first: the
+// buffer's BF16 elements (box 256 = one unit's 32 rows x 8 channels), dz (one plane, 361 x 16 B), half
+// (ROWS x 16 B); box (256, 3, 2).  Gradient view: elements, dx (16 B), dy (one padded row of the plane,
+// 19 x 16 B), half; box (256, 3, 3, 2).  The views overlap themselves; each box is a unit's shifted groups.
+int encode_maps(fdirw_net* net, int cap) {
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return nfail(net, FDIRW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t elems = (cuuint64_t)cap * PATCH;
+    const cuuint64_t dim_a[3] = {elems, 3, 2};
+    const cuuint64_t str_a[2] = {PLANE * 16, (cuuint64_t)ROWS * 16};
+    const cuuint32_t box_a[3] = {256, 3, 2};
+    const cuuint64_t dim_g[4] = {elems, 3, 3, 2};
+    const cuuint64_t str_g[3] = {16, PP * 16, (cuuint64_t)ROWS * 16};
+    const cuuint32_t box_g[4] = {256, 3, 3, 2};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    for (int i = 0; i < NL + 2; i++) {
+        const bool act = i < NL;
+        const CUresult r = enc(act ? &net->tm_act[i] : &net->tm_grad[i - NL], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, act ? 3 : 4,
+                               act ? (void*)net->act[i] : (void*)net->gbuf[i - NL], act ? dim_a : dim_g, act ? str_a : str_g,
+                               act ? box_a : box_g, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return nfail(net, FDIRW_ERR_CUDA, std::string("encoding a weight-gradient tensor map failed (CUresult ") +
+                                                  std::to_string((int)r) + ")");
+    }
+    return FDIRW_OK;
+}
+
 int ensure_capacity(fdirw_net* net, int n) {
     if (n <= net->cap) return FDIRW_OK;
     const int cap = n;
@@ -599,6 +770,7 @@ int ensure_capacity(fdirw_net* net, int n) {
     NET_CUDA(net, cudaMalloc(&net->dmass, (size_t)cap * 8));
     NET_CUDA(net, cudaMalloc(&net->dacc, (size_t)cap * 4));
     NET_CUDA(net, cudaMalloc(&net->dloss, (size_t)cap * 8));
+    if (const int rc = encode_maps(net, cap); rc != FDIRW_OK) return rc;
     net->cap = cap;
     return FDIRW_OK;
 }
@@ -613,6 +785,18 @@ int launch_conv(fdirw_net* net, cudaStream_t st, int num_sms, const __nv_bfloat1
     const int units = n * NTILE;
     const int grid = units < num_sms ? units : num_sms;
     conv_kernel<<<grid, CONV_THREADS, CONV_SMEM, st>>>(a);
+    NET_CUDA(net, cudaGetLastError());
+    return FDIRW_OK;
+}
+
+// Weight and bias gradients of one layer: the tensor-core partial sums, then their fixed-order reduction.
+// Layer l's input is act[l]; the gradient of its output is gbuf[cur].
+int launch_wgrad(fdirw_net* net, cudaStream_t st, int l, int cur, int n, float* dW, float* db) {
+    WgradArgs a{net->partial, n, net->derr, net->wait_ns};
+    NET_CUDA(net, cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM));
+    wgrad_kernel<<<WG_PARTS, WG_THREADS, WG_SMEM, st>>>(net->tm_act[l], net->tm_grad[cur], a);
+    NET_CUDA(net, cudaGetLastError());
+    wgrad_reduce_kernel<<<(TAPS * C * C + C + 255) / 256, 256, 0, st>>>(net->partial, dW, db);
     NET_CUDA(net, cudaGetLastError());
     return FDIRW_OK;
 }
@@ -647,10 +831,10 @@ int check_err(fdirw_net* net, cudaStream_t st) {
         cudaMemsetAsync(net->derr, 0, 4, st);
         if (h >= 2) {
             net->failed = true;
-            return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core convolution gave up on MMAs that had not completed "
-                                                 "after two waits; the network refuses further calls");
+            return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core kernel (convolution or weight gradient) gave up on MMAs or copies that had not "
+                                                 "completed after two waits; the network refuses further calls");
         }
-        return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+        return nfail(net, FDIRW_ERR_TIMEOUT, "a tensor-core kernel (convolution or weight gradient) timed out waiting for its MMAs");
     }
     return FDIRW_OK;
 }
@@ -687,12 +871,8 @@ int backward(fdirw_ctx* c, fdirw_net* net, int n, const GradHook* hook = nullptr
             const int rc = (*hook)(l, net->gbuf[cur]);
             if (rc != FDIRW_OK) return rc;
         }
-        wgrad_partial_kernel<<<dim3(TAPS, WG_BLOCKS), 256, 0, st>>>(net->act[l], net->gbuf[cur], n, net->partial);
-        NET_CUDA(net, cudaGetLastError());
-        wgrad_reduce_kernel<<<(TAPS * C * C + 255) / 256, 256, 0, st>>>(net->partial, net->grads + (size_t)l * TAPS * C * C);
-        NET_CUDA(net, cudaGetLastError());
-        bgrad_kernel<<<C, 256, 0, st>>>(net->gbuf[cur], n, net->grads + NW + l * C);
-        NET_CUDA(net, cudaGetLastError());
+        const int rw = launch_wgrad(net, st, l, cur, n, net->grads + (size_t)l * TAPS * C * C, net->grads + NW + l * C);
+        if (rw != FDIRW_OK) return rw;
         if (l > 0) {
             const int rc = launch_conv(net, st, c->num_sms, net->gbuf[cur], net->gbuf[cur ^ 1], nullptr, net->act[l],
                                        net->wd + (size_t)l * WCAN, nullptr, n, DGRAD);
@@ -743,7 +923,7 @@ FDIRW_API int fdirw_net_create(const float* params, int32_t device, fdirw_net** 
     if (cudaMalloc(&net->params, NPARAM * 4) != cudaSuccess || cudaMalloc(&net->m, NPARAM * 4) != cudaSuccess ||
         cudaMalloc(&net->v, NPARAM * 4) != cudaSuccess || cudaMalloc(&net->grads, NPARAM * 4) != cudaSuccess ||
         cudaMalloc(&net->wf, (size_t)NL * WCAN * 2) != cudaSuccess || cudaMalloc(&net->wd, (size_t)NL * WCAN * 2) != cudaSuccess ||
-        cudaMalloc(&net->partial, (size_t)TAPS * WG_BLOCKS * C * C * 4) != cudaSuccess ||
+        cudaMalloc(&net->partial, (size_t)WG_PARTS * WG_SLOTS * C * C * 4) != cudaSuccess ||
         cudaMalloc(&net->derr, 4) != cudaSuccess || cudaEventCreate(&net->ev[0]) != cudaSuccess ||
         cudaEventCreate(&net->ev[1]) != cudaSuccess)
         return bail("allocating the network");

@@ -1,5 +1,5 @@
 // Thin inline-PTX wrappers for the sm_103a tensor-core path (tcgen05 MMA with TMEM accumulators,
-// mbarriers) used by the surrogate's convolution kernel.
+// mbarriers, bulk and tensor copies) used by the surrogate's convolution and weight-gradient kernels.
 #pragma once
 
 #include <cstdint>
@@ -81,6 +81,19 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar_saddr) {
 __device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void* src, uint32_t bytes, uint32_t mbar_saddr) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  :: "r"(dst_saddr), "l"(src), "r"(bytes), "r"(mbar_saddr) : "memory");
+}
+
+// Tiled tensor copies (TMA) of one box from global memory into this CTA's shared memory, described by a
+// tensor map in kernel-parameter space; completes the box's bytes on the mbarrier.  Coordinates count
+// elements, innermost first.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst_saddr, const void* tmap, int c0, int c1, int c2, uint32_t mbar_saddr) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(dst_saddr), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(mbar_saddr) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst_saddr, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar_saddr) {
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 :: "r"(dst_saddr), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar_saddr) : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -87,3 +87,42 @@ def train(net: fdirw.Net, data, epochs: int, batch: int = 256, lr: float = 2e-3,
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.4e} ({time.perf_counter() - t0:.1f} s)")
     return hist
+
+
+def train_rate(steps: int = 20, batch: int = 256, side: int = 64, seed: int = 20240827, device: int = 0) -> dict:
+    """Wall time of `steps` training steps (features, four convolutions, loss, input and weight gradients of
+    every layer, Adam; each step reads its loss back) on `batch` random sources of a seeded sphere packing,
+    with targets already on the device; three untimed steps first."""
+    import torch
+    shape = (side,) * 3
+    D = synth.diffusivity_per_sphere(synth.sphere_packing(shape, 0.4, seed))
+    dt = fdirw.fdirw_stable_dt(shape, D, device=device)
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, side ** 3, batch)
+    tg = torch.rand((batch, 17 ** 3), dtype=torch.float64, device=f"cuda:{device}",
+                    generator=torch.Generator(device=f"cuda:{device}").manual_seed(seed)) * 1e-3
+    with fdirw.FDiRW(shape, D, dt, 8, 1, "bf16", device=device) as f:
+        net = fdirw.Net(init_params(seed), device=device)
+        try:
+            for _ in range(3):
+                net.train_step(f.ctx, src, tg, 1e-4)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                net.train_step(f.ctx, src, tg, 1e-4)
+            torch.cuda.synchronize(device)
+            dt_step = (time.perf_counter() - t0) / steps
+        finally:
+            net.close()
+    return {"batch": batch, "steps": steps, "train_step_ms": dt_step * 1e3, "samples_per_s": batch / dt_step}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="Timing of the surrogate's training step")
+    ap.add_argument("--train-rate", action="store_true", help="time training steps of 256 sources on a 64^3 packing")
+    ap.add_argument("--steps", type=int, default=20)
+    a = ap.parse_args()
+    if a.train_rate:
+        print(json.dumps(train_rate(a.steps)))
