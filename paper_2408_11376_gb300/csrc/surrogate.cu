@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(256) head_store_kernel(const float* __restrict
 //   A (M = 128): groups g = 3 h + dz_i (g < 6) hold channels 8h.. of act rows r + 361 (dz_i - 1); group 6
 //     holds ones (its D rows are db); groups 7..15 are never read back;
 //   B (N = 144): groups 9 h + 3 dy_i + dx_i hold channels 8h.. of grad rows r + (dx_i - 1) + 19 (dy_i - 1);
-// so ONE MMA (K = 16 rows) yields every (tap, ci, co) pair: the MMA's cost does not depend on N, so one
-// N = 144 MMA replaces four N = 16 ones.  In the no-swizzle MN-major layout a core matrix is 8 rows x 16
+// so ONE MMA (K = 16 rows) yields every (tap, ci, co) pair (an N = 144 MMA takes 72 clocks at the tensor
+// rate, four N = 16 ones at least 4 x 45).  In the no-swizzle MN-major layout a core matrix is 8 rows x 16
 // bytes; a group of a unit is 512 contiguous bytes, core matrices of consecutive rows 128 B apart (the K
 // stride), groups 512 B apart (the M / N stride).
 //   Both operands arrive as one tiled tensor copy each: the activation buffer is described to the TMA unit
@@ -435,9 +435,13 @@ __global__ void __launch_bounds__(256) head_store_kernel(const float* __restrict
 //   gradient buffer as a 4-D one (elements, dx: 16 B, dy: 19 rows, half); each box lands in shared memory in
 //   the group order above.
 //   warp 0 (one thread): copies WG_SUB units per stage into a ring of WG_NST stages (full / empty mbarriers);
-//   warp 1 (one thread): 2 MMAs (M = 128, N = 144, K = 16) per unit, accumulating in TMEM over the CTA's
-//     contiguous range of units, then commits to the done barrier;
-//   warps 0..3: read the accumulator (warp w: TMEM lanes 32 w..) into partial[part][slot][co][ci].
+//   warp 1 (one thread): 2 MMAs (M = 128, N = 144, K = 16) per unit into one of two TMEM accumulators,
+//     switching accumulator every WG_GST stages (a group) and committing the finished one ("acc full");
+//   warps 2..5: add each finished group's accumulator (warp w: TMEM lanes 32 (w mod 4)..) into FP32 register
+//     sums, release it ("acc empty"), and at the end write the sums to partial[part][slot][co][ci].
+// The tensor core's FP32 accumulation is not round-to-nearest (a chain of ~160 MMAs per CTA showed errors
+// of one sign, 10x those of FP32 FMAs), and Adam integrates a one-sided error in a near-cancelling
+// gradient; short TMEM chains (16 MMAs) summed round-to-nearest in registers keep it at FP32-FMA level.
 // Fixed partition into WG_PARTS ranges and a fixed-order sum over them (wgrad_reduce_kernel): the result
 // depends on the batch only.  Waits are bounded like the convolution's (err 1, or 2 if MMAs or copies may
 // still be in flight).
@@ -453,9 +457,11 @@ constexpr int WG_N = WG_NB * 8;                                    // MMA N: 144
 constexpr int WG_SUB = 4;                                          // units per ring stage
 constexpr int WG_NST = 3;                                          // ring stages
 constexpr int WG_PARTS = 152;                                      // CTAs, each a contiguous range of units
-constexpr int WG_THREADS = 128;
+constexpr int WG_GST = 2;                                          // stages per accumulator group (8 units)
+constexpr int WG_THREADS = 192;                                    // producer, MMA, four drain warps
 constexpr uint32_t WG_TX = (WG_NA + WG_NB) * WG_GROUP;            // bytes copied per unit
-constexpr size_t WG_SMEM = (size_t)WG_NST * WG_SUB * WG_UNIT + (2 * WG_NST + 1) * 8 + 16;
+constexpr int WG_NBAR = 2 * WG_NST + 4;                            // ring full / empty, accumulator full / empty
+constexpr size_t WG_SMEM = (size_t)WG_NST * WG_SUB * WG_UNIT + WG_NBAR * 8 + 16;
 static_assert(WG_ROWS * 8 == 256, "one box row is 256 BF16 elements");
 static_assert(16 * WG_GROUP <= WG_UNIT, "A's 16 groups stay inside the unit's shared bytes");
 // The first unit's rows start at plane 1; the last unit ends 7 rows into plane 18.  A reaches one plane
@@ -477,22 +483,26 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(const __grid_constant
                                                            const __grid_constant__ CUtensorMap tm_grad, WgradArgs a) {
     extern __shared__ __align__(128) uint8_t sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)WG_NST * WG_SUB * WG_UNIT);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * WG_NST + 1);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + WG_NBAR);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    constexpr int FULL = 0, EMPTY = WG_NST, DONE = 2 * WG_NST;
+    constexpr int FULL = 0, EMPTY = WG_NST, AFULL = 2 * WG_NST, AEMPTY = 2 * WG_NST + 2;
     const uint32_t sbase = tc::smem_u32(sm), bar0 = tc::smem_u32(bars);
     auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
     const int64_t units = (int64_t)a.batch * WG_UNITS;
     const int64_t u_lo = units * blockIdx.x / WG_PARTS, u_hi = units * (blockIdx.x + 1) / WG_PARTS;
     const int nstage = (int)((u_hi - u_lo + WG_SUB - 1) / WG_SUB);
+    const int ngroup = (nstage + WG_GST - 1) / WG_GST;
 
-    if (warp == 1) tc::tmem_alloc(tslot, 256);
+    if (warp == 1) tc::tmem_alloc(tslot, 512);           // accumulators at columns 0 and 256
     if (t == 0) {
         for (int i = 0; i < WG_NST; i++) {
             tc::mbar_init(bar(FULL + i), 1);
             tc::mbar_init(bar(EMPTY + i), 1);
         }
-        tc::mbar_init(bar(DONE), 1);
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_init(bar(AFULL + i), 1);
+            tc::mbar_init(bar(AEMPTY + i), 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // A group 6 of every unit slot: ones (BF16 1.0 = 0x3F80); the copies never write it
@@ -538,9 +548,13 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(const __grid_constant
             // M / N stride 512 B (one group).  The start-address field counts 16-byte units.
             constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, WG_N) | (1u << 15) | (1u << 16);
             const uint64_t d0 = tc::smem_desc(sbase, 128, WG_GROUP);
-            bool alive = true, issued = false;
+            bool alive = true;
+            int g = 0, gs = 0;                            // accumulator group, stages issued into it
             for (int q = 0; q < nstage; q++) {
-                const uint32_t s = (uint32_t)q % WG_NST;
+                const uint32_t s = (uint32_t)q % WG_NST, acc = (uint32_t)(g & 1) * 256u;
+                // a group's accumulator is reused two groups later, once the drain warps have released it
+                if (gs == 0 && g >= 2 &&
+                    !tc::mbar_wait(bar(AEMPTY + (g & 1)), (uint32_t)((g >> 1) - 1) & 1u, a.wait_ns)) { alive = false; break; }
                 if (!tc::mbar_wait(bar(FULL + (int)s), ((uint32_t)q / WG_NST) & 1u, a.wait_ns)) { alive = false; break; }
                 tc::fence_after_sync();
                 const int64_t u0 = u_lo + (int64_t)q * WG_SUB;
@@ -549,49 +563,64 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(const __grid_constant
                     const uint32_t ub = (s * WG_SUB + (uint32_t)j) * WG_UNIT;
 #pragma unroll
                     for (int k = 0; k < WG_ROWS / 16; k++)
-                        tc::mma_bf16(tmem, d0 + (uint64_t)((ub + k * 256) >> 4), d0 + (uint64_t)((ub + WG_B + k * 256) >> 4),
-                                     IDESC, (q > 0 || j > 0 || k > 0) ? 1u : 0u);
+                        tc::mma_bf16(tmem + acc, d0 + (uint64_t)((ub + k * 256) >> 4), d0 + (uint64_t)((ub + WG_B + k * 256) >> 4),
+                                     IDESC, (gs > 0 || j > 0 || k > 0) ? 1u : 0u);
                 }
-                issued = true;
                 tc::mma_commit(bar(EMPTY + (int)s));
+                if (++gs == WG_GST || q == nstage - 1) {  // the group's accumulator is complete
+                    tc::mma_commit(bar(AFULL + (g & 1)));
+                    g++;
+                    gs = 0;
+                }
             }
-            if (issued) tc::mma_commit(bar(DONE));        // arrives once every MMA issued has completed
-            else tc::mbar_arrive(bar(DONE));
             if (!alive) err = 1;
         }
         __syncwarp();
-    }
-    // epilogue: D row 8 gA + c (A group gA, channel c), column 8 gB + c' (B group gB, channel c')
-    const bool done = __all_sync(0xffffffffu, tc::mbar_wait(bar(DONE), 0, a.wait_ns) ? 1 : 0) != 0;
-    if (!done) {
-        if (lane == 0) err = 2;                           // MMAs may still be running
-    } else if (u_hi > u_lo) {
-        tc::fence_after_sync();
-        const int mrow = 32 * warp + lane, ga = mrow / 8, c8 = mrow % 8;
-        const bool ones = ga == WG_NA && c8 == 0;         // the bias row
-        float* part = a.partial + (int64_t)blockIdx.x * WG_SLOTS * C * C;
-        for (int jc = 0; jc < WG_N / 16; jc++) {
-            float v[16];
-            tc::tmem_ld16_wait(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * jc), v);
+    } else {                                              // drain warps 2..5
+        // D row 8 gA + c (A group gA, channel c), column 8 gB + c' (B group gB, channel c')
+        const int quarter = warp & 3, mrow = 32 * quarter + lane, ga = mrow / 8, c8 = mrow % 8;
+        const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
+        float sum[WG_N];
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const int gb = 2 * jc + i / 8, co = 8 * (gb / 9) + i % 8, dyi = (gb / 3) % 3, dxi = gb % 3;
+        for (int i = 0; i < WG_N; i++) sum[i] = 0.f;
+        bool alive = true;
+        for (int g = 0; g < ngroup; g++) {
+            alive = __all_sync(0xffffffffu, tc::mbar_wait(bar(AFULL + (g & 1)), (uint32_t)(g >> 1) & 1u, a.wait_ns) ? 1 : 0) != 0;
+            if (!alive) break;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int jc = 0; jc < WG_N / 16; jc++) {
+                float v[16];
+                tc::tmem_ld16_wait(tmem + lanes + (uint32_t)(g & 1) * 256u + (uint32_t)(16 * jc), v);
+#pragma unroll
+                for (int i = 0; i < 16; i++) sum[16 * jc + i] += v[i];
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(bar(AEMPTY + (g & 1)));
+        }
+        if (!alive) {
+            if (lane == 0) err = 2;                       // MMAs may still be running
+        } else {
+            const bool ones = ga == WG_NA && c8 == 0;     // the bias row
+            float* part = a.partial + (int64_t)blockIdx.x * WG_SLOTS * C * C;
+#pragma unroll
+            for (int n = 0; n < WG_N; n++) {
+                const int gb = n / 8, co = 8 * (gb / 9) + n % 8, dyi = (gb / 3) % 3, dxi = gb % 3;
                 if (ga < WG_NA) {
                     const int tap = (2 - dxi) + 3 * (2 - dyi) + 9 * (ga % 3), ci = 8 * (ga / 3) + c8;
-                    part[((int64_t)tap * C + co) * C + ci] = v[i];
+                    part[((int64_t)tap * C + co) * C + ci] = sum[n];
                 } else if (ones && dyi == 1 && dxi == 1) {
-                    part[((int64_t)TAPS * C + co) * C] = v[i];
+                    part[((int64_t)TAPS * C + co) * C] = sum[n];
                 }
             }
         }
-    } else {                                              // no units: a zero partial
-        for (int i = t; i < WG_SLOTS * C * C; i += WG_THREADS) a.partial[(int64_t)blockIdx.x * WG_SLOTS * C * C + i] = 0.f;
     }
     if (err) atomicMax(a.err, err);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 1) tc::tmem_dealloc(tmem, 256);
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
 // dW[tap][co][ci] = sum over the WG_PARTS partials in order; db[co] = the same sum of the ones slot (ci 0).

@@ -156,10 +156,10 @@ def test_backward_layers_match_oracle_element_by_element():
             Sb[l] += np.abs(g[l]).sum(axis=(1, 2, 3))
     assert abs(loss - lo / n) <= 1e-12 * lo / n
     gW, gb = fdirw.unpack_params(pg)
-    # Weight and bias gradients: each of 152 CTAs accumulates a contiguous range of 32-row units (192 per
-    # patch) in one TMEM accumulator, and the 152 partials are summed in order: a chain of at most
-    # ceil(192 n / 152) x 32 rows + 152 additions.
-    per = -(-n * 192 // 152) * 32 + 152
+    # Weight and bias gradients: each of 152 CTAs takes a contiguous range of 32-row units (192 per patch);
+    # groups of 8 units (256 rows) accumulate in TMEM, the group sums are added in FP32 registers, and the
+    # 152 partials are summed in order: a chain of at most 256 + ceil(units / 8) + 152 additions.
+    per = 8 * 32 + -(-(-(-n * 192 // 152)) // 8) + 152
     for l in range(4):
         _layer_check(gW[l], dW[l], SW[l], per, False, ("weight gradient", l))
         _layer_check(gb[l], db[l], Sb[l], per, False, ("bias gradient", l))
