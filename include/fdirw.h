@@ -395,11 +395,11 @@ FDIRW_API int fdirw_net_trace(fdirw_ctx* ctx, fdirw_net* net, const int64_t* sou
  * (prediction, training step, gradients, trace or gated build batch), from CUDA events recorded on the
  * context stream around them; 0 before the first forward pass.  Errors: FDIRW_ERR_ARG, FDIRW_ERR_CUDA. */
 FDIRW_API int fdirw_net_timing(fdirw_net* net, float* conv_ms);
-/* Failure-injection hook for tests of the bounded wait.  Every convolution waits for its MMAs on an
- * mbarrier for at most wait_ns nanoseconds of the GPU's global timer (0 restores the default, 2 s).  With
- * withhold_mma != 0 the convolutions issue neither their MMAs nor the commit that completes the wait,
- * so the first wait runs out with nothing in flight: the call returns FDIRW_ERR_TIMEOUT, the kernel has
- * freed its tensor memory, and the network stays usable once the hook is cleared.  A wait that runs out
+/* Failure-injection hook for tests of the bounded wait.  Every convolution and weight-gradient kernel waits
+ * for its copies and MMAs on mbarriers for at most wait_ns nanoseconds of the GPU's global timer (0 restores
+ * the default, 2 s).  With withhold_mma != 0 those kernels issue neither their MMAs nor the commits that
+ * complete the waits, so the waits run out with nothing in flight: the call returns FDIRW_ERR_TIMEOUT, the
+ * kernels have freed their tensor memory, and the network stays usable once the hook is cleared.  A wait that runs out
  * while MMAs were issued is waited once more; if they still have not completed, the call returns
  * FDIRW_ERR_TIMEOUT and every later call on this network returns FDIRW_ERR_STATE (the tensor memory it
  * released may still be written).  Errors: FDIRW_ERR_ARG (NULL net). */

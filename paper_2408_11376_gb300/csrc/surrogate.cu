@@ -475,6 +475,7 @@ struct WgradArgs {
     int batch;
     int* err;
     uint64_t wait_ns;
+    int hold;                       // test hook: issue no MMA and no commit, so the drain warps' wait runs out
 };
 
 // tm_act: the layer's input [batch][PATCH] as the view (elements, dz, half), box (256, 3, 2); tm_grad: the
@@ -550,7 +551,7 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(const __grid_constant
             const uint64_t d0 = tc::smem_desc(sbase, 128, WG_GROUP);
             bool alive = true;
             int g = 0, gs = 0;                            // accumulator group, stages issued into it
-            for (int q = 0; q < nstage; q++) {
+            for (int q = 0; q < nstage && !a.hold; q++) {
                 const uint32_t s = (uint32_t)q % WG_NST, acc = (uint32_t)(g & 1) * 256u;
                 // a group's accumulator is reused two groups later, once the drain warps have released it
                 if (gs == 0 && g >= 2 &&
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(const __grid_constant
             if (lane == 0) tc::mbar_arrive(bar(AEMPTY + (g & 1)));
         }
         if (!alive) {
-            if (lane == 0) err = 2;                       // MMAs may still be running
+            if (lane == 0) err = a.hold ? 1 : 2;          // MMAs may still be running (none under the hook)
         } else {
             const bool ones = ga == WG_NA && c8 == 0;     // the bias row
             float* part = a.partial + (int64_t)blockIdx.x * WG_SLOTS * C * C;
@@ -714,7 +715,7 @@ struct fdirw_net {
     cudaEvent_t ev[2] = {};        // around the four convolutions of the last forward pass
     bool timed = false;
     uint64_t wait_ns = WAIT_NS;    // budget of each MMA wait (fdirw_net_test_wait)
-    int hold = 0;                  // test hook: convolutions withhold their MMAs (fdirw_net_test_wait)
+    int hold = 0;                  // test hook: convolutions and weight gradients withhold their MMAs
     bool failed = false;           // a wait gave up while MMAs may still have been running
     std::string err;
 };
@@ -821,7 +822,7 @@ int launch_conv(fdirw_net* net, cudaStream_t st, int num_sms, const __nv_bfloat1
 // Weight and bias gradients of one layer: the tensor-core partial sums, then their fixed-order reduction.
 // Layer l's input is act[l]; the gradient of its output is gbuf[cur].
 int launch_wgrad(fdirw_net* net, cudaStream_t st, int l, int cur, int n, float* dW, float* db) {
-    WgradArgs a{net->partial, n, net->derr, net->wait_ns};
+    WgradArgs a{net->partial, n, net->derr, net->wait_ns, net->hold};
     NET_CUDA(net, cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM));
     wgrad_kernel<<<WG_PARTS, WG_THREADS, WG_SMEM, st>>>(net->tm_act[l], net->tm_grad[cur], a);
     NET_CUDA(net, cudaGetLastError());

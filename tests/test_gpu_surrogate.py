@@ -186,6 +186,31 @@ def test_bounded_wait_runs_out_and_the_net_recovers():
     assert np.array_equal(k0, k1) and np.array_equal(m0, m1) and np.array_equal(a0, a1)
 
 
+def test_bounded_wait_in_training_runs_out_and_the_net_recovers():
+    """The same hook on a training pass: the convolutions and the weight-gradient kernel (whose drain warps
+    wait for accumulators that never fill, and whose producer waits for stages that are never released)
+    all run out of their 2 ms budget with nothing in flight, the call returns FDIRW_ERR_TIMEOUT, and the
+    next pass on the same network, hook cleared, returns the gradients and loss of a fresh network."""
+    shape = (24, 22, 20)
+    D = _domain(shape, 6)
+    Ws, bs = _random_params(2)
+    src = _edge_sources(shape, 64, 4)
+    tg = np.random.default_rng(7).random((len(src), 17, 17, 17)) * 1e-3
+    with FDiRW(shape, D, 0.1, 8, 1, "fp32") as f:
+        ref = Net(fdirw.pack_params(Ws, bs))
+        g0, l0 = ref.gradients(f.ctx, src, tg)
+        ref.close()
+        net = Net(fdirw.pack_params(Ws, bs))
+        net.test_wait(wait_ns=2_000_000, withhold_mma=True)
+        with pytest.raises(fdirw.FdirwError) as e:
+            net.gradients(f.ctx, src, tg)
+        assert e.value.code == fdirw.FDIRW_ERR_TIMEOUT
+        net.test_wait(0, False)
+        g1, l1 = net.gradients(f.ctx, src, tg)
+        net.close()
+    assert np.array_equal(g0, g1) and l0 == l1
+
+
 def _gate_params():
     """Hand-set weights: a source-marker path gives z = 0 at the source cell (y = 1) and z = -30
     elsewhere, and a log-D path adds 0.5 at pore sources (f0 = 1 -> relu(f0 - 0.5) = 0.5): solid sources
