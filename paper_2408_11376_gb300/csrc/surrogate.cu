@@ -97,8 +97,9 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 //   warp 0 (one thread): streams input planes 1..17 of the unit (the 168 rows the tile reaches, both
 //     8-channel halves) into a ring of NSLOT slots with cp.async.bulk ("full" mbarrier per slot), refilling
 //     a slot once its "empty" barrier says the 9 MMAs that read it have completed;
-//   warp 1 (one thread): per input plane, the 9 MMAs into accumulators q + 1, q, q - 1 (after the
-//     epilogue has released plane q + 1 of the previous unit), then commits to the slot's "empty" barrier
+//   warp 1 (one thread): per input plane, the 9 MMAs into accumulators q + 1, q, q - 1 (every fourth
+//     plane, after the epilogue has released the next four planes of the previous unit), then commits to
+//     the slot's "empty" barrier
 //     and, for the output plane now complete (q - 1; plane 17 too after plane 17), to its "acc full";
 //   warps 2..: EPI_SETS sets of 4 warps, set s taking the output planes z with z mod EPI_SETS = s: drain
 //     the plane's 16 columns with tcgen05.ld (warp w reads TMEM lanes 32 (w mod 4)..), arrive on its
@@ -186,11 +187,15 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
                 for (int zz = 1; zz <= SP; zz++, q++) {
                     const uint32_t slot = q % NSLOT;
                     alive = tc::mbar_wait(bar(FULL + (int)slot), (q / NSLOT) & 1u, a.wait_ns);
-                    // accumulators first written at this plane: zz + 1 (and plane 1 at zz = 1)
-                    if (alive && unit > 0 && zz + 1 <= SP)
-                        alive = tc::mbar_wait(bar(AEMPTY + zz), (unit - 1) & 1u, a.wait_ns);
-                    if (alive && unit > 0 && zz == 1)
-                        alive = tc::mbar_wait(bar(AEMPTY + 0), (unit - 1) & 1u, a.wait_ns);
+                    // accumulators first written at input planes zz .. zz + 3: planes zz + 1 .. zz + 4 (and plane
+                    // 1 at zz = 1).  Each epilogue set drains the planes of one parity in order, so the release
+                    // of the highest plane of each parity covers the lower ones: two waits per four planes.
+                    static_assert(EPI_SETS == 2, "one epilogue set per plane parity");
+                    if (alive && unit > 0 && (zz & 3) == 1 && zz + 1 <= SP) {
+                        const int hi = zz + 4 < SP ? zz + 4 : SP;
+                        alive = tc::mbar_wait(bar(AEMPTY + hi - 1), (unit - 1) & 1u, a.wait_ns);
+                        if (alive) alive = tc::mbar_wait(bar(AEMPTY + hi - 2), (unit - 1) & 1u, a.wait_ns);
+                    }
                     if (!alive) break;
                     tc::fence_after_sync();
                     if (!a.hold) {
