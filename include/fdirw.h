@@ -345,7 +345,9 @@ FDIRW_API const char* fdirw_last_error(const fdirw_ctx* ctx);
  * other weights and biases must be 0 and are kept at 0 by training).
  * Sources are host int64 arrays of cell indices of the context's grid; per call at most 1024 sources.
  * Kernel arrays are n * 17^3 float64 values, offset o = (i-8, j-8, k-8) at index i + 17 (j + 17 k), host or
- * device memory.  The calls run on the context's stream and synchronise it before returning. */
+ * device memory.  The calls run on the context's stream and synchronise it before returning.  The first
+ * surrogate call on a context stores feature channel 0 of every cell there (grid cells x 2 bytes, freed
+ * with the context); it returns FDIRW_ERR_NOMEM if that exceeds the context's mem_limit. */
 #define FDIRW_NET_NPARAM (4 * 27 * 16 * 16 + 4 * 16)
 typedef struct fdirw_net fdirw_net;
 

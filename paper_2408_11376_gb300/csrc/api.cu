@@ -131,6 +131,7 @@ void release(fdirw_ctx* c) {
     p = c->dfix; dfree(p); c->dfix = nullptr;
     p = c->obuf; dfree(p); c->obuf = nullptr;
     p = c->Dd; dfree(p); c->Dd = nullptr;
+    p = c->feat0; dfree(p); c->feat0 = nullptr;
     p = c->dsrc; dfree(p); c->dsrc = nullptr;
     p = c->dkout; dfree(p); c->dkout = nullptr;
     for (auto& e : c->ev) if (e) { cudaEventDestroy(e); e = nullptr; }

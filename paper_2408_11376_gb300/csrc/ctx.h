@@ -41,6 +41,7 @@ struct fdirw_ctx {
     double* obuf = nullptr;                         // streamed steps: output of the step being computed
     int accum = 0;                                  // fdirw_accum
     double* Dd = nullptr;                           // device copy of D (surrogate features)
+    uint16_t* feat0 = nullptr;                      // surrogate feature channel 0 per cell (BF16 bits), made on first use
     int64_t* dsrc = nullptr;
     double* dkout = nullptr;
     int64_t kcap = 0;

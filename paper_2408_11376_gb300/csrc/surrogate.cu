@@ -300,8 +300,20 @@ __device__ __forceinline__ bool in_domain(const PatchPos& q, int i, int j, int k
     return true;
 }
 
-// Feature patches (channels 0-2 of the first half; everything else stays zero from a prior memset).
-__global__ void features_kernel(const double* __restrict__ D, Grid g, const int64_t* __restrict__ src, int n,
+// Feature channel 0 per grid cell, once per context: log10 D / 8 + 1 clamped to [-0.5, 1.5] (FP64, -0.5
+// where D <= 0), rounded to BF16 (bits).
+__global__ void feat0_kernel(const double* __restrict__ D, int64_t n, uint16_t* __restrict__ f0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = D[i];
+        double f = d > 0.0 ? log10(d) / 8.0 + 1.0 : -0.5;
+        f = f < -0.5 ? -0.5 : (f > 1.5 ? 1.5 : f);
+        f0[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)f));
+    }
+}
+
+// Feature patches: channels 0-7 of every voxel in one 16-byte store (channels 7-15 are zero; the halo and
+// guard rows stay zero from a prior memset).
+__global__ void features_kernel(const uint16_t* __restrict__ f0, Grid g, const int64_t* __restrict__ src, int n,
                                 __nv_bfloat16* __restrict__ act) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * KV;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -309,20 +321,20 @@ __global__ void features_kernel(const double* __restrict__ D, Grid g, const int6
         const int i = v % SP, j = (v / SP) % SP, k = v / (SP * SP);
         const PatchPos q = pos_of(src[b], g);
         int64_t gi;
-        __nv_bfloat16* rowp = act + (int64_t)b * PATCH + (int64_t)prow(i, j, k) * 8;
+        float h[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint4 row;
         if (in_domain(q, i, j, k, g, &gi)) {
-            const double d = D[gi];
-            double f = d > 0.0 ? log10(d) / 8.0 + 1.0 : -0.5;
-            f = f < -0.5 ? -0.5 : (f > 1.5 ? 1.5 : f);
-            rowp[0] = __float2bfloat16_rn((float)f);
-            rowp[1] = __float2bfloat16_rn(1.f);
+            h[0] = __bfloat162float(__ushort_as_bfloat16(f0[gi]));    // exact: already BF16
+            h[1] = 1.f;
         }
-        if (i == SH && j == SH && k == SH) rowp[2] = __float2bfloat16_rn(1.f);
+        if (i == SH && j == SH && k == SH) h[2] = 1.f;
         const int ox = i - SH, oy = j - SH, oz = k - SH;     // offsets from the source: exact in BF16
-        rowp[3] = __float2bfloat16_rn((float)ox * 0.125f);
-        rowp[4] = __float2bfloat16_rn((float)oy * 0.125f);
-        rowp[5] = __float2bfloat16_rn((float)oz * 0.125f);
-        rowp[6] = __float2bfloat16_rn((float)(ox * ox + oy * oy + oz * oz) * (1.f / 256.f));
+        h[3] = (float)ox * 0.125f;
+        h[4] = (float)oy * 0.125f;
+        h[5] = (float)oz * 0.125f;
+        h[6] = (float)(ox * ox + oy * oy + oz * oz) * (1.f / 256.f);
+        row = pack8(h);
+        *reinterpret_cast<uint4*>(act + (int64_t)b * PATCH + (int64_t)prow(i, j, k) * 8) = row;
     }
 }
 
@@ -843,7 +855,13 @@ int forward(fdirw_ctx* c, fdirw_net* net, int n) {
     NET_CUDA(net, cudaMemsetAsync(net->act[0], 0, (size_t)n * PATCH * 2, st));
     const int64_t work = (int64_t)n * KV;
     const int fb = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
-    features_kernel<<<fb, 256, 0, st>>>(c->Dd, c->g, net->dsrc, n, net->act[0]);
+    if (!c->feat0) {                                      // channel 0 per cell, made once per context
+        if (fdirw::host::dalloc(c, reinterpret_cast<void**>(&c->feat0), (uint64_t)c->g.n * 2, "surrogate features") != FDIRW_OK)
+            return nfail(net, FDIRW_ERR_NOMEM, "allocating the surrogate's per-cell features");
+        feat0_kernel<<<152 * 8, 256, 0, st>>>(c->Dd, c->g.n, c->feat0);
+        NET_CUDA(net, cudaGetLastError());
+    }
+    features_kernel<<<fb, 256, 0, st>>>(c->feat0, c->g, net->dsrc, n, net->act[0]);
     NET_CUDA(net, cudaGetLastError());
     NET_CUDA(net, cudaEventRecord(net->ev[0], st));
     for (int l = 0; l < NL; l++) {
